@@ -1,0 +1,179 @@
+/*
+ * helm.h -- C ABI of the GB300 RS-CGC Helmholtz solver.
+ *
+ * Solves the finite-difference Helmholtz equation
+ *     -Lap p - k^2(x) (1 - i gamma(x)) p = q,   k = omega * kappa,
+ * on a regular 2D/3D node grid padded with an absorbing layer (Yovel & Treister,
+ * Sec. 1 Eq. acousitcHelm; 20-cell absorbing padding, Sec. 5), by flexible GMRES
+ * (Sec. 5) preconditioned with the 3-level real-shifted coarse grid correction
+ * cycle (RS-CGC, Sec. 3: Galerkin level 2, Eq. Galerkin; real-shifted Galerkin
+ * level 3, Eqs. realShift and CoarseRealShifted; exact coarsest solve and damped
+ * Jacobi smoothing, Sec. 2, Algorithm TwoGrid).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid.  An axis with n cells has n + 1 nodes, every node is an unknown and
+ *   values beyond the outermost nodes are zero.  Arrays are C-ordered with x
+ *   fastest: node (i, j, k) sits at i + (nx+1) * (j + (ny+1) * k).  Level 2 is
+ *   the grid of every second node (n/2 cells per axis), level 3 every fourth.
+ * Complex vectors.  Interleaved (re, im) pairs: "c128" = two doubles per node
+ *   (complex128), "c64" = two floats (complex64).  A batch of n_rhs vectors is
+ *   stored back to back: vector r starts at node offset r * nodes(level).
+ * Memory.  Unless stated otherwise, pointer arguments are caller-owned device
+ *   memory (e.g. torch tensors), contiguous, not retained after the call.  The
+ *   context owns only the buffers it allocates.  Work is issued on the stream
+ *   given in helm_opts.stream (NULL = legacy default stream); a call returns
+ *   after its work is queued, except where it says it synchronises.
+ * Errors.  Every call returns an int status (helm_status).  No exception or
+ *   abort crosses the ABI.  helm_last_error() describes the last failure of the
+ *   calling thread.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef enum {
+  HELM_OK = 0,
+  HELM_EINVAL = 1,          /* bad argument: sizes, enums, NaN/Inf input, null pointer */
+  HELM_ENOMEM = 2,          /* device allocation failed */
+  HELM_NOT_CONVERGED = 3,   /* solve stopped at maxit; the iterate is still written */
+  HELM_ECUDA = 4,           /* a CUDA runtime call or kernel launch failed */
+  HELM_ENUMERIC = 5         /* zero pivot in the coarsest factorisation, NaN in the iteration */
+} helm_status;
+
+typedef enum { HELM_STENCIL_2ND = 0, HELM_STENCIL_4TH = 1 } helm_stencil;
+typedef enum { HELM_INTERGRID_FW = 0, HELM_INTERGRID_CUBIC = 1, HELM_INTERGRID_LEVDEP = 2 } helm_intergrid;
+typedef enum { HELM_CYCLE_V = 0, HELM_CYCLE_W = 1 } helm_cycle_kind;
+typedef enum { HELM_SMOOTHER_JACOBI = 0, HELM_SMOOTHER_REDBLACK = 1 } helm_smoother;
+/* HELM_FP64: every step in complex FP64.  HELM_MIXED: the cycle on levels 1-2
+ * (smoothing, residuals, transfers) in complex FP32; FGMRES, the outer matvec,
+ * the true residual and the coarsest solve in complex FP64. */
+typedef enum { HELM_FP64 = 0, HELM_MIXED = 1 } helm_precision;
+typedef enum { HELM_C128 = 0, HELM_C64 = 1 } helm_dtype;
+
+/* Problem and method options; fill with helm_default_opts() first. */
+typedef struct {
+  int dim;                /* 2 or 3 */
+  int n[3];               /* cells per axis (x, y, z) incl. the absorbing layer; each a multiple of 4 */
+  double h;               /* grid spacing */
+  double omega;           /* angular frequency; k = omega * kappa */
+  int abc_width[6];       /* absorbing-layer width in cells per face: x-lo, x-hi, y-lo, y-hi, z-lo, z-hi */
+  double abc_gamma_max;   /* gamma = gamma_max * sum_axes (d/L)^2, d = depth into the layer */
+  double alpha2;          /* real shift of level 2 (1 = plain Galerkin, the paper's method) */
+  double alpha3;          /* real shift of the coarsest level (Eq. CoarseRealShifted) */
+  int stencil;            /* helm_stencil; HELM_STENCIL_2ND = 5-point (2D) / 7-point (3D) */
+  int intergrid;          /* helm_intergrid; HELM_INTERGRID_FW = full weighting + (bi/tri)linear */
+  int cycle;              /* helm_cycle_kind */
+  int nu1, nu2;           /* pre- / post-smoothing sweeps */
+  int smoother;           /* helm_smoother */
+  double jacobi_w[2];     /* Jacobi damping on levels 1 and 2 */
+  double rb_w;            /* relaxation weight of the red-black sweep */
+  int precision;          /* helm_precision used by helm_solve / helm_cycle */
+  int restart;            /* FGMRES restart length m (>= 1) */
+  int max_rhs;            /* largest n_rhs a solve will be given (sizes workspaces; grows on demand) */
+  void* stream;           /* cudaStream_t for all work of this context */
+} helm_opts;
+
+/* Per-solve statistics, one entry per right-hand side. */
+typedef struct {
+  int iterations;         /* preconditioner applications (FGMRES iterations) */
+  int converged;          /* 1 if the true relative residual is below tol */
+  double relres;          /* true relative residual ||q - H p|| / ||q|| in FP64 */
+  double est_relres;      /* last Givens estimate |g_{j+1}| / ||q|| */
+} helm_stats;
+
+typedef struct helm_ctx helm_ctx;
+
+/* Fills *o with defaults: 2D, h = 1, gamma_max = 1, alpha2 = alpha3 = 1,
+ * 2nd-order stencil, FW transfers, V(1,1), Jacobi w = (0.8, 0.8), rb_w = 1,
+ * FP64, restart 10, max_rhs 1, default stream.  The caller sets dim, n,
+ * omega, abc_width and the shifts. */
+int helm_default_opts(helm_opts* o);
+
+/* Builds the operator hierarchy for slowness squared kappa2 (real FP64, one
+ * value per fine node, device OR host pointer; copied, not retained):
+ * level-2 Galerkin stencils H_2h = R H_h P (Eq. Galerkin) and the real mass
+ * part R (omega^2 kappa^2 M) P, the real-shifted level-3 stencil
+ * H_4h^alpha = R (H_2h + (1 - alpha3^2) R omega^2 kappa^2 M P) P (Eqs. realShift,
+ * CoarseRealShifted, by the linearity of Eq. realShiftMeaning), and the
+ * direct factorisation of the level-3 operator (Sec. 3.1: the coarsest level is
+ * solved directly).  Synchronises the stream.  On success *out owns device
+ * memory until helm_destroy. */
+int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out);
+
+/* Releases every buffer of the context.  NULL is accepted. */
+int helm_destroy(helm_ctx* c);
+
+/* Solves H p_r = q_r for n_rhs right-hand sides by FGMRES(restart) with the
+ * RS-CGC cycle as right preconditioner, x0 = 0, until the relative residual is
+ * below tol (Sec. 5: 1e-6) or maxit preconditioner applications.  q, p: c128,
+ * n_rhs * nodes(1) each, device or host pointers (host buffers are staged
+ * through device memory inside the call).  stats: host array of n_rhs entries
+ * or NULL.  Synchronises the stream.  Returns HELM_NOT_CONVERGED if any right-
+ * hand side missed tol (p still holds the last iterate). */
+int helm_solve(helm_ctx* c, const void* q, void* p, int n_rhs, double tol, int maxit,
+               helm_stats* stats);
+
+/* Gradient of L = 1/2 sum_r ||P_rec p_r - d_r||^2 with respect to kappa^2, by
+ * the adjoint-state method: H is complex-symmetric, so mu_r = conj(lambda_r)
+ * solves H mu_r = conj(residual_r) with the same preconditioned solver, and
+ * dL/dkappa^2_j = omega^2 sum_r Re((1 - i gamma_j) mu_{r,j} p_{r,j}).
+ * p: c128 forward fields (n_rhs * nodes); resid: c128 receiver residuals
+ * P_rec^T (P_rec p - d) on the full grid (zero off receivers); grad: real FP64
+ * [nodes], ACCUMULATED into (caller zeroes it).  All device pointers.  stats as
+ * for helm_solve (adjoint solves).  Synchronises the stream. */
+int helm_adjoint_grad(helm_ctx* c, const void* p, const void* resid, int n_rhs, double tol,
+                      int maxit, double* grad, helm_stats* stats);
+
+/* ---- Component entry points (one step of the method each; device pointers) ---- */
+
+/* y = H_l x on level l (1, 2 or 3) for n_rhs vectors; dtype selects c128 or
+ * c64 arithmetic (level 3 is c128 only).  Level 1 is the fine operator of
+ * Sec. 3.1 with the absorbing layer; levels 2-3 the assembled stencils. */
+int helm_apply(helm_ctx* c, int level, int dtype, const void* x, void* y, int n_rhs);
+
+/* One smoothing sweep on level l (1 or 2) with the smoother of the options:
+ * damped Jacobi x <- x + w D^-1 (b - H x), or a red-black sweep (colour
+ * (i+j+k) even first, each colour updated simultaneously).  x in/out. */
+int helm_smooth(helm_ctx* c, int level, int dtype, const void* b, void* x, int n_rhs);
+
+/* r = b - H_l x on level l. */
+int helm_residual(helm_ctx* c, int level, int dtype, const void* b, const void* x, void* r,
+                  int n_rhs);
+
+/* rc = R_l rf: restriction from level l to l+1 (l = 1 or 2) with the
+ * transfer of the options (full weighting 1/4[1 2 1] per axis, or the cubic
+ * 1/16[1 4 6 4 1] of Eq. intergrid), out-of-grid fine nodes dropped. */
+int helm_restrict(helm_ctx* c, int level, int dtype, const void* rf, void* rc, int n_rhs);
+
+/* xf += P_l ec: prolongation from level l+1 to l, P = 2^d R^T (the paper prints
+ * 2^-d R^T; the coarse-grid correction is invariant to this scaling). */
+int helm_prolong_add(helm_ctx* c, int level, int dtype, const void* ec, void* xf, int n_rhs);
+
+/* Copies the assembled stencil of level l (2 or 3) to host memory `out`
+ * (real FP64 pairs, layout [ncoef][nodes(l)][2], ncoef = (2r+1)^d, offset
+ * index (dx+r) + (2r+1)((dy+r) + (2r+1)(dz+r))) and returns the radius r in
+ * *radius.  out may be NULL to query r only.  Synchronises the stream. */
+int helm_get_stencil(helm_ctx* c, int level, double* out, int* radius);
+
+/* e = (H_4h^alpha)^-1 b on level 3 by the direct factorisation (c128). */
+int helm_coarse_solve(helm_ctx* c, const void* b, void* e, int n_rhs);
+
+/* z = M^-1 v: one application of the 3-level cycle from a zero initial guess,
+ * v and z in c128 (the mixed precision mode computes levels 1-2 in c64). */
+int helm_cycle(helm_ctx* c, const void* v, void* z, int n_rhs);
+
+/* Number of kernel launches this context has issued so far (all entry points). */
+long long helm_launch_count(const helm_ctx* c);
+
+const char* helm_strerror(int status);
+const char* helm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HELM_H */

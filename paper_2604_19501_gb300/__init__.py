@@ -1,0 +1,200 @@
+"""GB300 RS-CGC Helmholtz solver: Python binding of the C ABI (include/helm.h).
+
+The binding only marshals arguments: every step of the method runs in the CUDA
+library ``lib/libhelm.so`` (built by :mod:`paper_2604_19501_gb300.build`).  Vectors are
+torch tensors on the GPU (complex128, or complex64 for the FP32 component calls) or
+host numpy arrays where an entry point accepts host memory.  Importing this package
+fails if the library has not been built.
+"""
+import ctypes
+
+from . import _ffi
+from ._ffi import HelmError, HelmOpts, HelmStats, check
+
+__all__ = ["Solver", "HelmError", "level_shape"]
+
+_lib = _ffi.load()
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+def level_shape(n, level):
+    """Array shape (z, y, x order) of the nodes of level ``level`` (1 = fine)."""
+    f = 2 ** (level - 1)
+    return tuple(v // f + 1 for v in reversed(tuple(n)))
+
+
+class Solver:
+    """A set-up RS-CGC context (helm_setup) for one medium and frequency.
+
+    ``kappa2``: slowness squared on the fine nodes (float64 torch CUDA tensor or
+    numpy array), ``n``: cells per axis (x, y[, z]), ``omega``: angular frequency,
+    ``abc_width``: absorbing-layer width (int for every face, or 6 per-face ints).
+    Remaining keywords mirror ``helm_opts``.
+    """
+
+    def __init__(self, kappa2, n, omega, h=1.0, abc_width=0, abc_gamma_max=1.0, alpha2=1.0,
+                 alpha3=1.0, stencil="2nd", intergrid="fw", cycle="V", nu=(1, 1),
+                 smoother="jacobi", jacobi_w=(0.8, 0.8), rb_w=1.0, precision="fp64", restart=10,
+                 max_rhs=1, stream=None):
+        self.n = tuple(int(v) for v in n)
+        self.dim = len(self.n)
+        o = HelmOpts()
+        check(_lib.helm_default_opts(ctypes.byref(o)), "helm_default_opts")
+        o.dim = self.dim
+        for a, v in enumerate(self.n):
+            o.n[a] = v
+        o.h, o.omega = float(h), float(omega)
+        widths = [int(abc_width)] * 6 if isinstance(abc_width, int) else [int(v) for v in abc_width]
+        for f in range(6):
+            o.abc_width[f] = widths[f] if f < 2 * self.dim else 0
+        o.abc_gamma_max = float(abc_gamma_max)
+        o.alpha2, o.alpha3 = float(alpha2), float(alpha3)
+        o.stencil = _ffi.STENCIL[stencil]
+        o.intergrid = _ffi.INTERGRID[intergrid]
+        o.cycle = _ffi.CYCLE[cycle]
+        o.nu1, o.nu2 = int(nu[0]), int(nu[1])
+        o.smoother = _ffi.SMOOTHER[smoother]
+        o.jacobi_w[0], o.jacobi_w[1] = float(jacobi_w[0]), float(jacobi_w[1])
+        o.rb_w = float(rb_w)
+        o.precision = _ffi.PRECISION[precision]
+        o.restart = int(restart)
+        o.max_rhs = int(max_rhs)
+        if stream is None:
+            import torch
+
+            stream = torch.cuda.current_stream().cuda_stream
+        o.stream = ctypes.c_void_p(int(stream))
+        self.opts = o
+        self.precision = precision
+        self._ctx = ctypes.c_void_p()
+        check(_lib.helm_setup(ctypes.byref(o), _ptr(kappa2), ctypes.byref(self._ctx)), "helm_setup")
+
+    # ------------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            _lib.helm_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shape(self, level=1):
+        return level_shape(self.n, level)
+
+    @property
+    def launches(self):
+        """Kernel launches issued by this context so far."""
+        return int(_lib.helm_launch_count(self._ctx))
+
+    # ------------------------------------------------------------------ solves
+    def _nrhs(self, x, level=1):
+        return x.numel() // _numel(self.shape(level)) if hasattr(x, "numel") else x.size // _numel(self.shape(level))
+
+    def solve(self, q, p=None, tol=1e-6, maxit=500, raise_on_nonconvergence=False):
+        """p = H^-1 q by FGMRES + RS-CGC (helm_solve).  q: complex128, shape
+        (n_rhs,) + grid or grid; device tensor or host array.  Returns (p, stats)."""
+        nrhs = self._nrhs(q)
+        if p is None:
+            p = _empty_like(q)
+        stats = (HelmStats * nrhs)()
+        st = _lib.helm_solve(self._ctx, _ptr(q), _ptr(p), nrhs, float(tol), int(maxit), stats)
+        if st not in (_ffi.HELM_OK, _ffi.HELM_NOT_CONVERGED) or (st and raise_on_nonconvergence):
+            check(st, "helm_solve")
+        return p, [dict(iterations=s.iterations, converged=bool(s.converged), relres=s.relres,
+                        est_relres=s.est_relres) for s in stats]
+
+    def adjoint_grad(self, p, resid, grad, tol=1e-6, maxit=500):
+        """Accumulates dL/dkappa^2 into ``grad`` (helm_adjoint_grad)."""
+        nrhs = self._nrhs(p)
+        stats = (HelmStats * nrhs)()
+        st = _lib.helm_adjoint_grad(self._ctx, _ptr(p), _ptr(resid), nrhs, float(tol), int(maxit),
+                                    _ptr(grad), stats)
+        if st not in (_ffi.HELM_OK, _ffi.HELM_NOT_CONVERGED):
+            check(st, "helm_adjoint_grad")
+        return [dict(iterations=s.iterations, converged=bool(s.converged), relres=s.relres) for s in stats]
+
+    # ------------------------------------------------------------------ components
+    @staticmethod
+    def _dt(x):
+        return _ffi.DTYPE["c64"] if str(x.dtype).endswith("complex64") else _ffi.DTYPE["c128"]
+
+    def apply(self, level, x, y=None):
+        y = _empty_like(x) if y is None else y
+        check(_lib.helm_apply(self._ctx, level, self._dt(x), _ptr(x), _ptr(y), self._nrhs(x, level)), "helm_apply")
+        return y
+
+    def residual(self, level, b, x, r=None):
+        r = _empty_like(x) if r is None else r
+        check(_lib.helm_residual(self._ctx, level, self._dt(x), _ptr(b), _ptr(x), _ptr(r),
+                                 self._nrhs(x, level)), "helm_residual")
+        return r
+
+    def smooth(self, level, b, x):
+        """One smoothing sweep in place on x."""
+        check(_lib.helm_smooth(self._ctx, level, self._dt(x), _ptr(b), _ptr(x), self._nrhs(x, level)),
+              "helm_smooth")
+        return x
+
+    def restrict(self, level, rf, rc=None):
+        import torch
+
+        nrhs = self._nrhs(rf, level)
+        if rc is None:
+            rc = torch.empty((nrhs,) + self.shape(level + 1), dtype=rf.dtype, device=rf.device)
+        check(_lib.helm_restrict(self._ctx, level, self._dt(rf), _ptr(rf), _ptr(rc), nrhs), "helm_restrict")
+        return rc
+
+    def prolong_add(self, level, ec, xf):
+        check(_lib.helm_prolong_add(self._ctx, level, self._dt(ec), _ptr(ec), _ptr(xf),
+                                    self._nrhs(xf, level)), "helm_prolong_add")
+        return xf
+
+    def stencil(self, level):
+        """Assembled stencil of level 2 or 3 as a numpy complex128 array
+        [ncoef, nodes] and its radius."""
+        import numpy as np
+
+        r = ctypes.c_int()
+        check(_lib.helm_get_stencil(self._ctx, level, None, ctypes.byref(r)), "helm_get_stencil")
+        ncoef = (2 * r.value + 1) ** self.dim
+        out = np.empty((ncoef, _numel(self.shape(level))), dtype=np.complex128)
+        check(_lib.helm_get_stencil(self._ctx, level, ctypes.c_void_p(out.ctypes.data), ctypes.byref(r)),
+              "helm_get_stencil")
+        return out, r.value
+
+    def coarse_solve(self, b, e=None):
+        e = _empty_like(b) if e is None else e
+        check(_lib.helm_coarse_solve(self._ctx, _ptr(b), _ptr(e), self._nrhs(b, 3)), "helm_coarse_solve")
+        return e
+
+    def cycle(self, v, z=None):
+        z = _empty_like(v) if z is None else z
+        check(_lib.helm_cycle(self._ctx, _ptr(v), _ptr(z), self._nrhs(v)), "helm_cycle")
+        return z
+
+
+def _numel(shape):
+    n = 1
+    for v in shape:
+        n *= v
+    return n
+
+
+def _empty_like(x):
+    if hasattr(x, "data_ptr"):
+        import torch
+
+        return torch.empty_like(x)
+    import numpy as np
+
+    return np.empty_like(x)

@@ -1,0 +1,606 @@
+// C ABI of the RS-CGC Helmholtz solver (declared in include/helm.h): context set-up,
+// the 3-level cycle (Algorithm TwoGrid applied recursively, Sec. 2) and the FGMRES
+// driver (Sec. 5).
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/helm.h"
+#include "coarse.cuh"
+#include "galerkin.cuh"
+#include "gridops.cuh"
+#include "krylov.cuh"
+
+namespace helm {
+
+thread_local long long* g_launch_counter = nullptr;
+static thread_local std::string t_last_error;
+std::string& last_error_ref() { return t_last_error; }
+void set_error(const std::string& s) { t_last_error = s; }
+
+}  // namespace helm
+
+using namespace helm;
+
+struct helm_ctx {
+  helm_opts o{};
+  cudaStream_t s = nullptr;
+  GridDims g[3];
+  FineOp fine{};
+  double* d_gam = nullptr;
+  double* kap64 = nullptr;
+  float* kap32 = nullptr;
+  double* h_gam = nullptr;                     // host copy of the per-axis profiles
+  int r2 = 1, r3 = 1, nc2 = 9, nc3 = 9;
+  double2* A2_64 = nullptr;
+  double2* A2_dinv64 = nullptr;
+  float2* A2_32 = nullptr;
+  float2* A2_dinv32 = nullptr;
+  double* Mk2 = nullptr;
+  double2* A3_64 = nullptr;
+  double2* A3_dinv64 = nullptr;
+  Transfer tR1{}, tP1{}, tR2{}, tP2{};
+  CoarseSolver cs;
+  // cycle workspaces (element size of c128 so either precision fits)
+  int rhs_cap = 0;
+  void *l1a = nullptr, *l1b = nullptr, *l1r = nullptr;
+  void *l2b = nullptr, *l2a = nullptr, *l2c = nullptr, *l2r = nullptr;
+  double2 *l3b = nullptr, *l3e = nullptr;
+  // Krylov workspaces (one right-hand side at a time)
+  double2 *V = nullptr, *w = nullptr, *r = nullptr;
+  void* Z = nullptr;
+  KrylovState ks;
+  double* h_scal = nullptr;                    // pinned copy of ks.scal
+  // staging for host buffers
+  double2* stage = nullptr;
+  long long stage_cap = 0;
+  long long launches = 0;
+  int* d_bad = nullptr;
+};
+
+namespace {
+
+struct LaunchScope {
+  long long* prev;
+  explicit LaunchScope(helm_ctx* c) : prev(g_launch_counter) { g_launch_counter = c ? &c->launches : nullptr; }
+  ~LaunchScope() { g_launch_counter = prev; }
+};
+
+int fail(int code, const std::string& msg) {
+  set_error(msg);
+  return code;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+Transfer make_transfer(int kind) {
+  Transfer t{};
+  if (kind == 0) {
+    t.radius = 1;
+    t.w[0] = 0.25; t.w[1] = 0.5; t.w[2] = 0.25;
+  } else {
+    t.radius = 2;
+    t.w[0] = 1.0 / 16; t.w[1] = 4.0 / 16; t.w[2] = 6.0 / 16; t.w[3] = 4.0 / 16; t.w[4] = 1.0 / 16;
+  }
+  return t;
+}
+
+GridDims dims_of(int dim, const int n[3], int level) {
+  GridDims g{};
+  g.dim = dim;
+  const int f = 1 << level;
+  for (int a = 0; a < 3; ++a) g.N[a] = a < dim ? n[a] / f + 1 : 1;
+  g.size = (long long)g.N[0] * g.N[1] * g.N[2];
+  return g;
+}
+
+size_t esize(Prec p) { return p == P64 ? sizeof(double2) : sizeof(float2); }
+
+template <typename T>
+int dmalloc(T** p, size_t bytes) {
+  if (cudaMalloc((void**)p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    return HELM_ENOMEM;
+  }
+  return 0;
+}
+
+void free_workspaces(helm_ctx* c) {
+  for (void* p : {c->l1a, c->l1b, c->l1r, c->l2b, c->l2a, c->l2c, c->l2r}) cudaFree(p);
+  cudaFree(c->l3b);
+  cudaFree(c->l3e);
+  c->l1a = c->l1b = c->l1r = c->l2b = c->l2a = c->l2c = c->l2r = nullptr;
+  c->l3b = c->l3e = nullptr;
+  c->rhs_cap = 0;
+}
+
+int ensure_workspaces(helm_ctx* c, int nrhs) {
+  if (nrhs <= c->rhs_cap) return 0;
+  free_workspaces(c);
+  const size_t e = sizeof(double2);
+  const size_t n1 = (size_t)c->g[0].size * nrhs, n2 = (size_t)c->g[1].size * nrhs, n3 = (size_t)c->g[2].size * nrhs;
+  if (int st = dmalloc(&c->l1a, n1 * e)) return st;
+  if (int st = dmalloc(&c->l1b, n1 * e)) return st;
+  if (int st = dmalloc(&c->l1r, n1 * e)) return st;
+  if (int st = dmalloc(&c->l2b, n2 * e)) return st;
+  if (int st = dmalloc(&c->l2a, n2 * e)) return st;
+  if (int st = dmalloc(&c->l2c, n2 * e)) return st;
+  if (int st = dmalloc(&c->l2r, n2 * e)) return st;
+  if (int st = dmalloc(&c->l3b, n3 * e)) return st;
+  if (int st = dmalloc(&c->l3e, n3 * e)) return st;
+  c->rhs_cap = nrhs;
+  return 0;
+}
+
+Prec cycle_prec(const helm_ctx* c) { return c->o.precision == HELM_MIXED ? P32 : P64; }
+
+// ---------------------------------------------------------------- row operations per level
+int row_op(helm_ctx* c, int level, Prec arith, int mode, Prec xs, Prec bs, Prec ys, const void* x,
+           const void* b, void* y, int nrhs, double w, int colour) {
+  if (level == 0)
+    return launch_fine_row(c->fine, mode, arith, xs, bs, ys, arith == P64 ? (const void*)c->kap64 : (const void*)c->kap32,
+                           x, b, y, nrhs, w, colour, c->s);
+  if (level == 1)
+    return launch_stencil_row(c->g[1], c->r2, arith, arith == P64 ? (const void*)c->A2_64 : (const void*)c->A2_32,
+                              arith == P64 ? (const void*)c->A2_dinv64 : (const void*)c->A2_dinv32, mode, xs,
+                              bs, ys, x, b, y, nrhs, w, colour, c->s);
+  if (arith != P64) return fail(HELM_EINVAL, "level 3 is c128 only");
+  return launch_stencil_row(c->g[2], c->r3, P64, c->A3_64, c->A3_dinv64, mode, xs, bs, ys, x, b, y, nrhs, w,
+                            colour, c->s);
+}
+
+// `nu` smoothing sweeps on level `level` (0-based) with right-hand side b (storage bs);
+// the iterate lives in *x, *t is the second buffer of the ping-pong pair.
+int smooth(helm_ctx* c, int level, Prec P, const void* b, Prec bs, void** x, void** t, int nu,
+           bool from_zero, int nrhs) {
+  const double wj = c->o.jacobi_w[level];
+  const long long n = c->g[level].size * nrhs;
+  if (nu == 0 && from_zero) HELM_CUDA_TRY(cudaMemsetAsync(*x, 0, n * esize(P), c->s));
+  for (int sweep = 0; sweep < nu; ++sweep) {
+    const bool zero = from_zero && sweep == 0;
+    if (c->o.smoother == HELM_SMOOTHER_JACOBI) {
+      const int mode = zero ? MODE_JACOBI0 : MODE_JACOBI;
+      if (int st = row_op(c, level, P, mode, P, bs, P, *x, b, *t, nrhs, wj, 0)) return st;
+      std::swap(*x, *t);
+    } else {
+      if (zero) HELM_CUDA_TRY(cudaMemsetAsync(*x, 0, n * esize(P), c->s));
+      for (int colour = 0; colour < 2; ++colour) {
+        if (int st = row_op(c, level, P, MODE_RB, P, bs, P, *x, b, *t, nrhs, c->o.rb_w, colour)) return st;
+        std::swap(*x, *t);
+      }
+    }
+  }
+  return 0;
+}
+
+// One visit of level 2 (index 1): smoothing, residual, restriction, exact coarsest solve,
+// prolongation and correction, smoothing.  x2 in/out through *x.
+int visit_level2(helm_ctx* c, Prec P, void** x, void** t, bool first, int nrhs) {
+  if (int st = smooth(c, 1, P, c->l2b, P, x, t, c->o.nu1, first, nrhs)) return st;
+  if (int st = row_op(c, 1, P, MODE_RESID, P, P, P, *x, c->l2b, c->l2r, nrhs, 0.0, 0)) return st;
+  const long long n3 = c->g[2].size * nrhs;
+  if (P == P64) {
+    if (int st = launch_restrict(c->g[1], c->g[2], c->tR2, P64, c->l2r, c->l3b, nrhs, c->s)) return st;
+    if (int st = coarse_solve(c->cs, c->l3b, c->l3e, nrhs, c->s)) return st;
+    if (int st = launch_prolong_add(c->g[1], c->g[2], c->tP2, P64, c->l3e, *x, nrhs, c->s)) return st;
+  } else {
+    // restrict in c64 into the upper half of l3e, widen to c128, solve, narrow back
+    float2* b32 = (float2*)c->l3e;
+    if (int st = launch_restrict(c->g[1], c->g[2], c->tR2, P32, c->l2r, b32, nrhs, c->s)) return st;
+    if (int st = launch_convert(P32, P64, b32, c->l3b, n3, c->s)) return st;
+    if (int st = coarse_solve(c->cs, c->l3b, c->l3e, nrhs, c->s)) return st;
+    float2* e32 = (float2*)c->l3b;
+    if (int st = launch_convert(P64, P32, c->l3e, e32, n3, c->s)) return st;
+    if (int st = launch_prolong_add(c->g[1], c->g[2], c->tP2, P32, e32, *x, nrhs, c->s)) return st;
+  }
+  return smooth(c, 1, P, c->l2b, P, x, t, c->o.nu2, false, nrhs);
+}
+
+// z = M^-1 v from a zero initial guess.  v has storage vs, z storage zs.
+int run_cycle(helm_ctx* c, const void* v, Prec vs, void* z, Prec zs, int nrhs) {
+  if (int st = ensure_workspaces(c, nrhs)) return st;
+  const Prec P = cycle_prec(c);
+  void* x = c->l1a;
+  void* t = c->l1b;
+  if (int st = smooth(c, 0, P, v, vs, &x, &t, c->o.nu1, true, nrhs)) return st;
+  if (int st = row_op(c, 0, P, MODE_RESID, P, vs, P, x, v, c->l1r, nrhs, 0.0, 0)) return st;
+  if (int st = launch_restrict(c->g[0], c->g[1], c->tR1, P, c->l1r, c->l2b, nrhs, c->s)) return st;
+  void* x2 = c->l2a;
+  void* t2 = c->l2c;
+  const int visits = c->o.cycle == HELM_CYCLE_W ? 2 : 1;
+  for (int v2 = 0; v2 < visits; ++v2)
+    if (int st = visit_level2(c, P, &x2, &t2, v2 == 0, nrhs)) return st;
+  if (int st = launch_prolong_add(c->g[0], c->g[1], c->tP1, P, x2, x, nrhs, c->s)) return st;
+  if (int st = smooth(c, 0, P, v, vs, &x, &t, c->o.nu2, false, nrhs)) return st;
+  const long long n1 = c->g[0].size * nrhs;
+  if (zs == P && x == z) return 0;
+  return launch_convert(P, zs, x, z, n1, c->s);
+}
+
+int sync_scal(helm_ctx* c) {
+  HELM_CUDA_TRY(cudaMemcpyAsync(c->h_scal, c->ks.scal, sizeof(double) * KS_COUNT, cudaMemcpyDeviceToHost, c->s));
+  HELM_CUDA_TRY(cudaStreamSynchronize(c->s));
+  return 0;
+}
+
+// FGMRES(m) for one right-hand side (device pointers).
+int fgmres_one(helm_ctx* c, const double2* q, double2* p, double tol, int maxit, helm_stats* out) {
+  const long long n = c->g[0].size;
+  const int m = c->o.restart;
+  const Prec zp = cycle_prec(c);
+  const size_t zes = esize(zp);
+  HELM_CUDA_TRY(cudaMemsetAsync(p, 0, n * sizeof(double2), c->s));
+  if (int st = k_norm(c->ks, n, q, c->r, c->s)) return st;
+  if (int st = sync_scal(c)) return st;
+  const double bnorm = c->h_scal[KS_BNORM];
+  helm_stats res{0, 1, 0.0, 0.0};
+  if (!std::isfinite(bnorm)) return fail(HELM_EINVAL, "right-hand side is not finite");
+  if (bnorm == 0.0) {
+    if (out) *out = res;
+    return 0;
+  }
+  double beta = c->h_scal[KS_BETA];
+  int its = 0;
+  double est = beta / bnorm;
+  while (true) {
+    if (beta / bnorm < tol || its >= maxit) break;
+    if (int st = k_start_cycle(c->ks, n, c->r, c->V, c->s)) return st;
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      void* zj = (char*)c->Z + (size_t)j * n * zes;
+      if (int st = run_cycle(c, c->V + (size_t)j * n, P64, zj, zp, 1)) return st;
+      if (int st = k_arnoldi(c->ks, c->fine, c->kap64, zj, zp, c->w, c->V, n, j, c->s)) return st;
+      if (int st = sync_scal(c)) return st;
+      ++its;
+      k = j + 1;
+      est = c->h_scal[KS_EST];
+      if (!std::isfinite(est)) return fail(HELM_ENUMERIC, "non-finite residual estimate");
+      if (est < tol || its >= maxit || c->h_scal[KS_HN] == 0.0) break;
+      if (int st = k_normalize(c->ks, n, c->w, c->V, n, j, c->V + (size_t)(j + 1) * n, c->s)) return st;
+    }
+    if (int st = k_update_solution(c->ks, n, p, c->Z, zp, n, k, c->s)) return st;
+    if (int st = k_true_residual(c->ks, c->fine, c->kap64, q, p, c->r, c->s)) return st;
+    if (int st = sync_scal(c)) return st;
+    beta = c->h_scal[KS_BETA];
+    if (!std::isfinite(beta)) return fail(HELM_ENUMERIC, "non-finite residual");
+  }
+  res.iterations = its;
+  res.relres = beta / bnorm;
+  res.converged = res.relres < tol ? 1 : 0;
+  res.est_relres = est;
+  if (out) *out = res;
+  return 0;
+}
+
+int check_level(const helm_ctx* c, int level, int lo, int hi) {
+  if (level < lo || level > hi) return fail(HELM_EINVAL, "level out of range");
+  return 0;
+}
+
+Prec dtype_prec(int dtype) { return dtype == HELM_C64 ? P32 : P64; }
+
+}  // namespace
+
+extern "C" {
+
+int helm_default_opts(helm_opts* o) {
+  if (!o) return fail(HELM_EINVAL, "null options");
+  std::memset(o, 0, sizeof(*o));
+  o->dim = 2;
+  o->h = 1.0;
+  o->abc_gamma_max = 1.0;
+  o->alpha2 = 1.0;
+  o->alpha3 = 1.0;
+  o->stencil = HELM_STENCIL_2ND;
+  o->intergrid = HELM_INTERGRID_FW;
+  o->cycle = HELM_CYCLE_V;
+  o->nu1 = 1;
+  o->nu2 = 1;
+  o->smoother = HELM_SMOOTHER_JACOBI;
+  o->jacobi_w[0] = 0.8;
+  o->jacobi_w[1] = 0.8;
+  o->rb_w = 1.0;
+  o->precision = HELM_FP64;
+  o->restart = 10;
+  o->max_rhs = 1;
+  o->stream = nullptr;
+  return HELM_OK;
+}
+
+int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
+  if (!o || !kappa2 || !out) return fail(HELM_EINVAL, "null argument");
+  *out = nullptr;
+  if (o->dim != 2 && o->dim != 3) return fail(HELM_EINVAL, "dim must be 2 or 3");
+  for (int a = 0; a < o->dim; ++a)
+    if (o->n[a] < 4 || o->n[a] % 4) return fail(HELM_EINVAL, "cells per axis must be a positive multiple of 4");
+  if (!(o->h > 0) || !std::isfinite(o->h) || !(o->omega >= 0) || !std::isfinite(o->omega))
+    return fail(HELM_EINVAL, "h must be > 0 and omega >= 0, both finite");
+  for (int f = 0; f < 2 * o->dim; ++f)
+    if (o->abc_width[f] < 0 || o->abc_width[f] > o->n[f / 2]) return fail(HELM_EINVAL, "bad absorbing-layer width");
+  if (!std::isfinite(o->alpha2) || !std::isfinite(o->alpha3) || !std::isfinite(o->abc_gamma_max))
+    return fail(HELM_EINVAL, "non-finite shift or layer amplitude");
+  if (o->stencil != HELM_STENCIL_2ND) return fail(HELM_EINVAL, "stencil not built");
+  if (o->intergrid != HELM_INTERGRID_FW) return fail(HELM_EINVAL, "intergrid transfer not built");
+  if (o->cycle != HELM_CYCLE_V && o->cycle != HELM_CYCLE_W) return fail(HELM_EINVAL, "bad cycle");
+  if (o->smoother != HELM_SMOOTHER_JACOBI && o->smoother != HELM_SMOOTHER_REDBLACK)
+    return fail(HELM_EINVAL, "bad smoother");
+  if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 > 16) return fail(HELM_EINVAL, "bad sweep counts");
+  if (o->precision != HELM_FP64 && o->precision != HELM_MIXED) return fail(HELM_EINVAL, "bad precision");
+  if (o->restart < 1 || o->restart > 40) return fail(HELM_EINVAL, "restart must be in [1, 40]");
+  if (o->max_rhs < 1) return fail(HELM_EINVAL, "max_rhs must be >= 1");
+
+  helm_ctx* c = new helm_ctx();
+  c->o = *o;
+  if (c->o.dim == 2) c->o.n[2] = 0;
+  c->s = (cudaStream_t)o->stream;
+  LaunchScope scope(c);
+  auto bail = [&](int st) { helm_destroy(c); return st; };
+  for (int l = 0; l < 3; ++l) c->g[l] = dims_of(o->dim, c->o.n, l);
+  const long long n1 = c->g[0].size;
+
+  // medium: validated on the host, stored as FP64 and FP32
+  std::vector<double> k64(n1);
+  cudaError_t ce = is_device_ptr(kappa2)
+                       ? cudaMemcpy(k64.data(), kappa2, n1 * sizeof(double), cudaMemcpyDeviceToHost)
+                       : cudaMemcpy(k64.data(), kappa2, n1 * sizeof(double), cudaMemcpyHostToHost);
+  if (ce != cudaSuccess) return bail(fail(HELM_ECUDA, std::string("reading kappa2: ") + cudaGetErrorString(ce)));
+  std::vector<float> k32(n1);
+  for (long long i = 0; i < n1; ++i) {
+    if (!std::isfinite(k64[i]) || k64[i] < 0) return bail(fail(HELM_EINVAL, "kappa2 must be finite and >= 0"));
+    k32[i] = (float)k64[i];
+  }
+  if (int st = dmalloc(&c->kap64, n1 * sizeof(double))) return bail(st);
+  if (int st = dmalloc(&c->kap32, n1 * sizeof(float))) return bail(st);
+  if (cudaMemcpy(c->kap64, k64.data(), n1 * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->kap32, k32.data(), n1 * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(fail(HELM_ECUDA, "uploading kappa2"));
+
+  // absorbing profile per axis: gamma_max * ((lo - i)/lo)^2 or ((i - (n - hi))/hi)^2
+  const int tot = c->g[0].N[0] + c->g[0].N[1] + c->g[0].N[2];
+  std::vector<double> gam(tot, 0.0);
+  int off = 0;
+  for (int a = 0; a < 3; ++a) {
+    const int nc = c->g[0].N[a] - 1;
+    if (a < o->dim) {
+      const int lo = o->abc_width[2 * a], hi = o->abc_width[2 * a + 1];
+      for (int i = 0; i <= nc; ++i) {
+        double t = 0.0;
+        if (lo > 0 && i < lo) t += ((double)(lo - i) / lo) * ((double)(lo - i) / lo);
+        if (hi > 0 && i > nc - hi) t += ((double)(i - (nc - hi)) / hi) * ((double)(i - (nc - hi)) / hi);
+        gam[off + i] = o->abc_gamma_max * t;
+      }
+    }
+    off += c->g[0].N[a];
+  }
+  if (int st = dmalloc(&c->d_gam, tot * sizeof(double))) return bail(st);
+  if (cudaMemcpy(c->d_gam, gam.data(), tot * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(fail(HELM_ECUDA, "uploading absorbing profile"));
+  c->h_gam = new double[tot];
+  std::memcpy(c->h_gam, gam.data(), tot * sizeof(double));
+  c->fine.g = c->g[0];
+  c->fine.order = 0;
+  c->fine.inv_h2 = 1.0 / (o->h * o->h);
+  c->fine.omega2 = o->omega * o->omega;
+  c->fine.gam[0] = c->d_gam;
+  c->fine.gam[1] = c->d_gam + c->g[0].N[0];
+  c->fine.gam[2] = c->d_gam + c->g[0].N[0] + c->g[0].N[1];
+
+  c->tR1 = c->tP1 = c->tR2 = c->tP2 = make_transfer(0);
+
+  // level 2: H_2h = R1 H_h P1 and the real mass part R1 omega^2 kappa^2 M P1
+  const long long n2 = c->g[1].size, n3 = c->g[2].size;
+  const int W = 3;
+  c->nc2 = o->dim == 3 ? W * W * W : W * W;
+  double2* H20 = nullptr;
+  if (int st = dmalloc(&H20, c->nc2 * n2 * sizeof(double2))) return bail(st);
+  if (int st = dmalloc(&c->Mk2, c->nc2 * n2 * sizeof(double))) { cudaFree(H20); return bail(st); }
+  int st = assemble_level2(c->fine, c->kap64, c->g[1], c->tR1.radius, c->tP1.radius, H20, c->Mk2, &c->r2, c->s);
+  if (st) { cudaFree(H20); return bail(HELM_ECUDA); }
+  // level-2 operator of the cycle: H_2h + (1 - alpha2^2) R1 K P1
+  if ((st = dmalloc(&c->A2_64, c->nc2 * n2 * sizeof(double2)))) { cudaFree(H20); return bail(st); }
+  if ((st = apply_shift(c->nc2 * n2, H20, c->Mk2, 1.0 - o->alpha2 * o->alpha2, c->A2_64, c->s))) {
+    cudaFree(H20); return bail(HELM_ECUDA);
+  }
+  // level 3: R2 (H_2h + (1 - alpha3^2) R1 K P1) P2 (Eq. CoarseRealShifted)
+  c->nc3 = c->nc2;
+  if ((st = dmalloc(&c->A3_64, c->nc3 * n3 * sizeof(double2)))) { cudaFree(H20); return bail(st); }
+  st = assemble_level3(c->g[1], c->r2, H20, c->Mk2, 1.0 - o->alpha3 * o->alpha3, c->g[2], c->tR2.radius,
+                       c->tP2.radius, c->A3_64, &c->r3, c->s);
+  cudaStreamSynchronize(c->s);
+  cudaFree(H20);
+  if (st) return bail(HELM_ECUDA);
+  if ((st = dmalloc(&c->A2_dinv64, n2 * sizeof(double2))) || (st = dmalloc(&c->A2_32, c->nc2 * n2 * sizeof(float2))) ||
+      (st = dmalloc(&c->A2_dinv32, n2 * sizeof(float2))) || (st = dmalloc(&c->A3_dinv64, n3 * sizeof(double2))) ||
+      (st = dmalloc(&c->d_bad, sizeof(int))))
+    return bail(st);
+  if (cudaMemsetAsync(c->d_bad, 0, sizeof(int), c->s) != cudaSuccess) return bail(fail(HELM_ECUDA, "memset"));
+  if (finalize_stencil(n2, c->nc2, c->nc2 / 2, c->A2_64, c->A2_dinv64, c->A2_32, c->A2_dinv32, c->d_bad, c->s) ||
+      finalize_stencil(n3, c->nc3, c->nc3 / 2, c->A3_64, c->A3_dinv64, nullptr, nullptr, c->d_bad, c->s))
+    return bail(HELM_ECUDA);
+  int bad = 0;
+  if (cudaMemcpy(&bad, c->d_bad, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return bail(fail(HELM_ECUDA, "reading diagonal check"));
+  if (bad) return bail(fail(HELM_ENUMERIC, "zero or non-finite coarse diagonal"));
+
+  // coarsest factorisation
+  if ((st = coarse_setup(c->cs, c->g[2], c->r3, c->A3_64, o->dim == 2 ? 64 : 64, c->s))) return bail(st);
+
+  // workspaces
+  const int m = o->restart;
+  if ((st = ensure_workspaces(c, o->max_rhs))) return bail(st);
+  if ((st = dmalloc(&c->V, (size_t)(m + 1) * n1 * sizeof(double2))) ||
+      (st = dmalloc(&c->Z, (size_t)m * n1 * esize(cycle_prec(c)))) ||
+      (st = dmalloc(&c->w, n1 * sizeof(double2))) || (st = dmalloc(&c->r, n1 * sizeof(double2))))
+    return bail(st);
+  if ((st = krylov_alloc(c->ks, m))) return bail(st);
+  if (cudaMallocHost(&c->h_scal, sizeof(double) * KS_COUNT) != cudaSuccess) return bail(fail(HELM_ENOMEM, "pinned alloc"));
+  if (cudaStreamSynchronize(c->s) != cudaSuccess) return bail(fail(HELM_ECUDA, cudaGetErrorString(cudaGetLastError())));
+  *out = c;
+  return HELM_OK;
+}
+
+int helm_destroy(helm_ctx* c) {
+  if (!c) return HELM_OK;
+  if (c->s) cudaStreamSynchronize(c->s);
+  else cudaDeviceSynchronize();
+  free_workspaces(c);
+  coarse_free(c->cs);
+  krylov_free(c->ks);
+  for (void* p : {(void*)c->d_gam, (void*)c->kap64, (void*)c->kap32, (void*)c->A2_64, (void*)c->A2_dinv64,
+                  (void*)c->A2_32, (void*)c->A2_dinv32, (void*)c->Mk2, (void*)c->A3_64, (void*)c->A3_dinv64,
+                  (void*)c->V, (void*)c->w, (void*)c->r, c->Z, (void*)c->stage, (void*)c->d_bad})
+    cudaFree(p);
+  if (c->h_scal) cudaFreeHost(c->h_scal);
+  delete[] c->h_gam;
+  delete c;
+  return HELM_OK;
+}
+
+int helm_solve(helm_ctx* c, const void* q, void* p, int n_rhs, double tol, int maxit, helm_stats* stats) {
+  if (!c || !q || !p) return fail(HELM_EINVAL, "null argument");
+  if (n_rhs < 1 || !(tol > 0) || maxit < 1) return fail(HELM_EINVAL, "bad n_rhs, tol or maxit");
+  LaunchScope scope(c);
+  const long long n = c->g[0].size;
+  const bool qd = is_device_ptr(q), pd = is_device_ptr(p);
+  const double2* dq = (const double2*)q;
+  double2* dp = (double2*)p;
+  const long long need = (long long)n_rhs * n * ((qd ? 0 : 1) + (pd ? 0 : 1));
+  if (need > c->stage_cap) {
+    cudaFree(c->stage);
+    c->stage = nullptr;
+    c->stage_cap = 0;
+    if (int st = dmalloc(&c->stage, need * sizeof(double2))) return st;
+    c->stage_cap = need;
+  }
+  double2* sp = c->stage;
+  if (!qd) {
+    HELM_CUDA_TRY(cudaMemcpyAsync(sp, q, n_rhs * n * sizeof(double2), cudaMemcpyHostToDevice, c->s));
+    dq = sp;
+    sp += n_rhs * n;
+  }
+  if (!pd) dp = sp;
+  int worst = HELM_OK;
+  for (int r = 0; r < n_rhs; ++r) {
+    helm_stats one{};
+    if (int st = fgmres_one(c, dq + (size_t)r * n, dp + (size_t)r * n, tol, maxit, &one)) return st;
+    if (stats) stats[r] = one;
+    if (!one.converged) worst = HELM_NOT_CONVERGED;
+  }
+  if (!pd) {
+    HELM_CUDA_TRY(cudaMemcpyAsync(p, dp, n_rhs * n * sizeof(double2), cudaMemcpyDeviceToHost, c->s));
+  }
+  HELM_CUDA_TRY(cudaStreamSynchronize(c->s));
+  if (worst != HELM_OK) set_error("not converged within maxit");
+  return worst;
+}
+
+int helm_adjoint_grad(helm_ctx* c, const void* p, const void* resid, int n_rhs, double tol, int maxit,
+                      double* grad, helm_stats* stats) {
+  (void)c; (void)p; (void)resid; (void)n_rhs; (void)tol; (void)maxit; (void)grad; (void)stats;
+  return fail(HELM_EINVAL, "adjoint gradient not built");
+}
+
+int helm_apply(helm_ctx* c, int level, int dtype, const void* x, void* y, int n_rhs) {
+  if (!c || !x || !y || n_rhs < 1) return fail(HELM_EINVAL, "bad argument");
+  if (int st = check_level(c, level, 1, 3)) return st;
+  LaunchScope scope(c);
+  const Prec P = dtype_prec(dtype);
+  if (int st = row_op(c, level - 1, P, MODE_APPLY, P, P, P, x, x, y, n_rhs, 0.0, 0)) return st;
+  return HELM_OK;
+}
+
+int helm_residual(helm_ctx* c, int level, int dtype, const void* b, const void* x, void* r, int n_rhs) {
+  if (!c || !b || !x || !r || n_rhs < 1) return fail(HELM_EINVAL, "bad argument");
+  if (int st = check_level(c, level, 1, 3)) return st;
+  LaunchScope scope(c);
+  const Prec P = dtype_prec(dtype);
+  if (int st = row_op(c, level - 1, P, MODE_RESID, P, P, P, x, b, r, n_rhs, 0.0, 0)) return st;
+  return HELM_OK;
+}
+
+int helm_smooth(helm_ctx* c, int level, int dtype, const void* b, void* x, int n_rhs) {
+  if (!c || !b || !x || n_rhs < 1) return fail(HELM_EINVAL, "bad argument");
+  if (int st = check_level(c, level, 1, 2)) return st;
+  LaunchScope scope(c);
+  if (int st = ensure_workspaces(c, n_rhs)) return st;
+  const Prec P = dtype_prec(dtype);
+  void* tmp = level == 1 ? c->l1r : c->l2r;
+  void* xx = x;
+  void* tt = tmp;
+  if (int st = smooth(c, level - 1, P, b, P, &xx, &tt, 1, false, n_rhs)) return st;
+  if (xx != x)
+    HELM_CUDA_TRY(cudaMemcpyAsync(x, xx, c->g[level - 1].size * n_rhs * esize(P), cudaMemcpyDeviceToDevice, c->s));
+  return HELM_OK;
+}
+
+int helm_restrict(helm_ctx* c, int level, int dtype, const void* rf, void* rc, int n_rhs) {
+  if (!c || !rf || !rc || n_rhs < 1) return fail(HELM_EINVAL, "bad argument");
+  if (int st = check_level(c, level, 1, 2)) return st;
+  LaunchScope scope(c);
+  const Transfer& t = level == 1 ? c->tR1 : c->tR2;
+  if (int st = launch_restrict(c->g[level - 1], c->g[level], t, dtype_prec(dtype), rf, rc, n_rhs, c->s)) return st;
+  return HELM_OK;
+}
+
+int helm_prolong_add(helm_ctx* c, int level, int dtype, const void* ec, void* xf, int n_rhs) {
+  if (!c || !ec || !xf || n_rhs < 1) return fail(HELM_EINVAL, "bad argument");
+  if (int st = check_level(c, level, 1, 2)) return st;
+  LaunchScope scope(c);
+  const Transfer& t = level == 1 ? c->tP1 : c->tP2;
+  if (int st = launch_prolong_add(c->g[level - 1], c->g[level], t, dtype_prec(dtype), ec, xf, n_rhs, c->s))
+    return st;
+  return HELM_OK;
+}
+
+int helm_get_stencil(helm_ctx* c, int level, double* out, int* radius) {
+  if (!c) return fail(HELM_EINVAL, "null context");
+  if (int st = check_level(c, level, 2, 3)) return st;
+  if (radius) *radius = level == 2 ? c->r2 : c->r3;
+  if (!out) return HELM_OK;
+  const long long n = c->g[level - 1].size * (level == 2 ? c->nc2 : c->nc3);
+  HELM_CUDA_TRY(cudaStreamSynchronize(c->s));
+  HELM_CUDA_TRY(cudaMemcpy(out, level == 2 ? c->A2_64 : c->A3_64, n * sizeof(double2), cudaMemcpyDeviceToHost));
+  return HELM_OK;
+}
+
+int helm_coarse_solve(helm_ctx* c, const void* b, void* e, int n_rhs) {
+  if (!c || !b || !e || n_rhs < 1) return fail(HELM_EINVAL, "bad argument");
+  LaunchScope scope(c);
+  if (int st = coarse_solve(c->cs, (const double2*)b, (double2*)e, n_rhs, c->s)) return st;
+  return HELM_OK;
+}
+
+int helm_cycle(helm_ctx* c, const void* v, void* z, int n_rhs) {
+  if (!c || !v || !z || n_rhs < 1) return fail(HELM_EINVAL, "bad argument");
+  LaunchScope scope(c);
+  if (int st = run_cycle(c, v, P64, z, P64, n_rhs)) return st;
+  return HELM_OK;
+}
+
+long long helm_launch_count(const helm_ctx* c) { return c ? c->launches : 0; }
+
+const char* helm_strerror(int status) {
+  switch (status) {
+    case HELM_OK: return "ok";
+    case HELM_EINVAL: return "invalid argument";
+    case HELM_ENOMEM: return "out of device memory";
+    case HELM_NOT_CONVERGED: return "not converged";
+    case HELM_ECUDA: return "CUDA error";
+    case HELM_ENUMERIC: return "numerical breakdown";
+    default: return "unknown status";
+  }
+}
+
+const char* helm_last_error(void) { return t_last_error.c_str(); }
+
+}  // extern "C"

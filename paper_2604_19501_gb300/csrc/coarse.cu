@@ -1,0 +1,553 @@
+// Exact solve on the coarsest level (Sec. 2: the coarse-grid correction uses an exact
+// solution on the coarsest grid; Sec. 3.1: three levels so that the coarsest is small
+// enough to solve directly).  The paper leaves the method open; this is a nested-
+// dissection multifrontal factorisation in complex FP64.
+//
+// Symbolic phase (host): the node box is bisected recursively along its longest axis by
+// separator slabs r nodes thick (r = stencil radius), which decouple the two halves.
+// Every tree node ("front") eliminates its separator S (a leaf: its whole box); its
+// boundary B is the ring of nodes within distance r around its box, all of which lie in
+// ancestor separators.
+//
+// Numeric phase (device, level by level from the leaves): the front matrix F over
+// S u B is assembled from the stencil entries of the S rows/columns and the children's
+// update matrices (extend-add), then Gauss-Jordan elimination with row pivoting inside S
+// on the augmented matrix [F | I_S] yields
+//   rows S: [ I | F_SS^-1 F_SB | F_SS^-1 ],   rows B: [ 0 | U | -F_BS F_SS^-1 ],
+// U = F_BB - F_BS F_SS^-1 F_SB being the update passed to the parent.
+//
+// Solve: forward, leaves to root, every front turns its assembled right-hand side r_F
+// into w_S = F_SS^-1 r_S and the update vector r_B - F_BS w_S for its parent; backward,
+// root to leaves, x_S = w_S - (F_SS^-1 F_SB) x_B.  Both are dense matrix-vector
+// products; no atomics, so results are reproducible bit for bit.
+#include <algorithm>
+#include <unordered_map>
+#include "coarse.cuh"
+
+namespace helm {
+
+namespace {
+
+struct HostFront {
+  int height = 0;
+  int parent = -1;
+  std::vector<int> S, B, kids;
+  int lo[3], hi[3];
+};
+
+struct Builder {
+  int dim, N[3], r, leaf_max;
+  std::vector<HostFront> fronts;
+
+  int gidx(int x, int y, int z) const { return x + N[0] * (y + N[1] * z); }
+
+  void box_nodes(const int lo[3], const int hi[3], std::vector<int>& out) const {
+    for (int z = lo[2]; z < hi[2]; ++z)
+      for (int y = lo[1]; y < hi[1]; ++y)
+        for (int x = lo[0]; x < hi[0]; ++x) out.push_back(gidx(x, y, z));
+  }
+
+  void ring_nodes(const int lo[3], const int hi[3], std::vector<int>& out) const {
+    int a[3], b[3];
+    for (int d = 0; d < 3; ++d) {
+      const int rr = d < dim ? r : 0;
+      a[d] = std::max(0, lo[d] - rr);
+      b[d] = std::min(N[d], hi[d] + rr);
+    }
+    for (int z = a[2]; z < b[2]; ++z)
+      for (int y = a[1]; y < b[1]; ++y)
+        for (int x = a[0]; x < b[0]; ++x) {
+          const bool inside = x >= lo[0] && x < hi[0] && y >= lo[1] && y < hi[1] && z >= lo[2] && z < hi[2];
+          if (!inside) out.push_back(gidx(x, y, z));
+        }
+  }
+
+  int build(const int lo[3], const int hi[3], int parent) {
+    const int id = (int)fronts.size();
+    fronts.emplace_back();
+    {
+      HostFront& f = fronts[id];
+      f.parent = parent;
+      for (int d = 0; d < 3; ++d) { f.lo[d] = lo[d]; f.hi[d] = hi[d]; }
+    }
+    long long vol = 1;
+    int axis = 0, ext = 0;
+    for (int d = 0; d < dim; ++d) {
+      vol *= (hi[d] - lo[d]);
+      if (hi[d] - lo[d] > ext) { ext = hi[d] - lo[d]; axis = d; }
+    }
+    std::vector<int> S, B;
+    ring_nodes(lo, hi, B);
+    if (vol <= leaf_max || ext < r + 2) {
+      box_nodes(lo, hi, S);
+    } else {
+      const int mid = lo[axis] + (ext - r) / 2;
+      int llo[3], lhi[3], slo[3], shi[3], rlo[3], rhi[3];
+      for (int d = 0; d < 3; ++d) {
+        llo[d] = slo[d] = rlo[d] = lo[d];
+        lhi[d] = shi[d] = rhi[d] = hi[d];
+      }
+      lhi[axis] = mid;
+      slo[axis] = mid;
+      shi[axis] = mid + r;
+      rlo[axis] = mid + r;
+      box_nodes(slo, shi, S);
+      std::vector<int> kids;
+      kids.push_back(build(llo, lhi, id));
+      if (rhi[axis] > rlo[axis]) kids.push_back(build(rlo, rhi, id));
+      int h = 0;
+      for (int k : kids) h = std::max(h, fronts[k].height + 1);
+      fronts[id].kids = kids;
+      fronts[id].height = h;
+    }
+    fronts[id].S = std::move(S);
+    fronts[id].B = std::move(B);
+    return id;
+  }
+};
+
+// ------------------------------------------------------------------ factorisation kernels
+__global__ void fact_assemble_kernel(const FrontDesc* __restrict__ desc, const int* __restrict__ list,
+                                     double2* __restrict__ aug, const int2* __restrict__ ents,
+                                     const double2* __restrict__ coef, const double2* __restrict__ upool,
+                                     const int* __restrict__ kids, const int* __restrict__ cmap) {
+  const FrontDesc d = desc[list[blockIdx.x]];
+  const int nF = d.nS + d.nB, ld = nF + d.nS;
+  double2* A = aug + d.aug_off;
+  const long long tot = (long long)nF * ld;
+  for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
+    const int row = (int)(t / ld), col = (int)(t % ld);
+    A[t] = make_double2((row < d.nS && col == nF + row) ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  // original entries: each destination appears once per front
+  for (int e = threadIdx.x; e < d.ent_cnt; e += blockDim.x) {
+    const int2 en = ents[d.ent_off + e];
+    const double2 v = coef[en.y];
+    A[en.x].x += v.x;
+    A[en.x].y += v.y;
+  }
+  __syncthreads();
+  // extend-add of the children's update matrices, one child at a time
+  for (int c = 0; c < d.nkids; ++c) {
+    const FrontDesc kd = desc[kids[d.kid_off + c]];
+    const int* map = cmap + kd.cmap_off;
+    const double2* U = upool + kd.U_off;
+    const long long n2 = (long long)kd.nB * kd.nB;
+    for (long long t = threadIdx.x; t < n2; t += blockDim.x) {
+      const int a = (int)(t / kd.nB), b = (int)(t % kd.nB);
+      const double2 v = U[t];
+      double2& dst = A[(long long)map[a] * ld + map[b]];
+      dst.x += v.x;
+      dst.y += v.y;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(512) fact_gj_kernel(const FrontDesc* __restrict__ desc,
+                                                      const int* __restrict__ list,
+                                                      double2* __restrict__ aug, int* __restrict__ err) {
+  const FrontDesc d = desc[list[blockIdx.x]];
+  const int nS = d.nS, nF = d.nS + d.nB, ld = nF + d.nS;
+  double2* A = aug + d.aug_off;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  __shared__ double s_val[32];
+  __shared__ int s_idx[32];
+  __shared__ int s_piv;
+  __shared__ double2 s_inv;
+  for (int k = 0; k < nS; ++k) {
+    // pivot: largest |a_ik| over the rows of S not yet eliminated (ties: lowest row)
+    double best = -1.0;
+    int bi = nS;
+    for (int i = k + tid; i < nS; i += blockDim.x) {
+      const double2 a = A[(long long)i * ld + k];
+      const double v = a.x * a.x + a.y * a.y;
+      if (v > best) { best = v; bi = i; }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const double ov = __shfl_down_sync(0xffffffffu, best, off);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { s_val[warp] = best; s_idx[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double bv = s_val[0];
+      int bidx = s_idx[0];
+      for (int w = 1; w < nwarp; ++w)
+        if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] < bidx)) { bv = s_val[w]; bidx = s_idx[w]; }
+      if (!(bv > 0.0) || !isfinite(bv) || bidx >= nS) { atomicExch(err, 1); bidx = k; }
+      s_piv = bidx;
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (p != k)
+      for (int c = k + tid; c < ld; c += blockDim.x) {
+        const double2 t = A[(long long)k * ld + c];
+        A[(long long)k * ld + c] = A[(long long)p * ld + c];
+        A[(long long)p * ld + c] = t;
+      }
+    __syncthreads();
+    if (tid == 0) {
+      const double2 a = A[(long long)k * ld + k];
+      const double m = a.x * a.x + a.y * a.y;
+      s_inv = make_double2(a.x / m, -a.y / m);
+    }
+    __syncthreads();
+    const double2 inv = s_inv;
+    for (int c = k + 1 + tid; c < ld; c += blockDim.x) {
+      const double2 a = A[(long long)k * ld + c];
+      A[(long long)k * ld + c] = make_double2(a.x * inv.x - a.y * inv.y, a.x * inv.y + a.y * inv.x);
+    }
+    __syncthreads();
+    if (tid == 0) A[(long long)k * ld + k] = make_double2(1.0, 0.0);
+    for (int i = warp; i < nF; i += nwarp) {
+      if (i == k) continue;
+      const double2 f = A[(long long)i * ld + k];
+      if (f.x == 0.0 && f.y == 0.0) continue;
+      double2* Ai = A + (long long)i * ld;
+      const double2* Ak = A + (long long)k * ld;
+      for (int c = k + 1 + lane; c < ld; c += 32) {
+        const double2 b = Ak[c];
+        double2 v = Ai[c];
+        v.x -= f.x * b.x - f.y * b.y;
+        v.y -= f.x * b.y + f.y * b.x;
+        Ai[c] = v;
+      }
+      __syncwarp();
+      if (lane == 0) Ai[k] = make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void fact_extract_kernel(const FrontDesc* __restrict__ desc, const int* __restrict__ list,
+                                    const double2* __restrict__ aug, double2* __restrict__ factors,
+                                    double2* __restrict__ upool) {
+  const FrontDesc d = desc[list[blockIdx.x]];
+  const int nS = d.nS, nB = d.nB, nF = nS + nB, ld = nF + nS;
+  const double2* A = aug + d.aug_off;
+  double2* X = factors + d.X_off;
+  double2* G = factors + d.G_off;
+  double2* U = upool + d.U_off;
+  for (long long t = threadIdx.x; t < (long long)nF * nS; t += blockDim.x) {
+    const int row = (int)(t / nS), col = (int)(t % nS);
+    X[t] = A[(long long)row * ld + nF + col];
+  }
+  for (long long t = threadIdx.x; t < (long long)nS * nB; t += blockDim.x) {
+    const int row = (int)(t / nB), col = (int)(t % nB);
+    G[t] = A[(long long)row * ld + nS + col];
+  }
+  for (long long t = threadIdx.x; t < (long long)nB * nB; t += blockDim.x) {
+    const int row = (int)(t / nB), col = (int)(t % nB);
+    U[t] = A[(long long)(nS + row) * ld + nS + col];
+  }
+}
+
+// ------------------------------------------------------------------ solve kernels
+__global__ void fwd_assemble_kernel(const FrontDesc* __restrict__ desc, const int* __restrict__ list,
+                                    const int* __restrict__ Sidx, const int* __restrict__ kids,
+                                    const int* __restrict__ cmap, const double2* __restrict__ b,
+                                    double2* __restrict__ rf, double2* __restrict__ uv, int nrhs,
+                                    long long nodes, long long rf_total, long long uv_total) {
+  const FrontDesc d = desc[list[blockIdx.x]];
+  const int nF = d.nS + d.nB;
+  for (int r = 0; r < nrhs; ++r) {
+    double2* R = rf + r * rf_total + d.rf_off;
+    const double2* br = b + r * nodes;
+    for (int t = threadIdx.x; t < nF; t += blockDim.x)
+      R[t] = t < d.nS ? br[Sidx[d.S_off + t]] : make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int c = 0; c < d.nkids; ++c) {
+      const FrontDesc kd = desc[kids[d.kid_off + c]];
+      const double2* V = uv + r * uv_total + kd.uv_off;
+      const int* map = cmap + kd.cmap_off;
+      for (int a = threadIdx.x; a < kd.nB; a += blockDim.x) {
+        const double2 v = V[a];
+        R[map[a]].x += v.x;
+        R[map[a]].y += v.y;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// one warp per row of X: out = X[row, :] . r_S
+__global__ void __launch_bounds__(256) fwd_matvec_kernel(const FrontDesc* __restrict__ desc,
+                                                         const int2* __restrict__ rows,
+                                                         const int* __restrict__ Sidx,
+                                                         const double2* __restrict__ factors,
+                                                         const double2* __restrict__ rf,
+                                                         double2* __restrict__ uv, double2* __restrict__ w,
+                                                         int nrhs, long long nodes, long long rf_total,
+                                                         long long uv_total) {
+  const int2 job = rows[blockIdx.x];
+  const FrontDesc d = desc[job.x];
+  const int row = job.y + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int nF = d.nS + d.nB;
+  if (row >= nF) return;
+  const double2* X = factors + d.X_off + (long long)row * d.nS;
+  for (int r = 0; r < nrhs; ++r) {
+    const double2* R = rf + r * rf_total + d.rf_off;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int c = lane; c < d.nS; c += 32) acc = cmac(acc, X[c], R[c]);
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
+    }
+    if (lane == 0) {
+      if (row < d.nS) {
+        w[r * nodes + Sidx[d.S_off + row]] = acc;
+      } else {
+        const double2 base = R[row];
+        uv[r * uv_total + d.uv_off + row - d.nS] = make_double2(base.x + acc.x, base.y + acc.y);
+      }
+    }
+  }
+}
+
+// one warp per row of G: x_S[row] = w_S[row] - G[row, :] . x_B
+__global__ void __launch_bounds__(256) bwd_matvec_kernel(const FrontDesc* __restrict__ desc,
+                                                         const int2* __restrict__ rows,
+                                                         const int* __restrict__ Sidx,
+                                                         const int* __restrict__ Bidx,
+                                                         const double2* __restrict__ factors,
+                                                         const double2* __restrict__ w,
+                                                         double2* __restrict__ x, int nrhs,
+                                                         long long nodes) {
+  const int2 job = rows[blockIdx.x];
+  const FrontDesc d = desc[job.x];
+  const int row = job.y + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= d.nS) return;
+  const double2* G = factors + d.G_off + (long long)row * d.nB;
+  const int* B = Bidx + d.B_off;
+  const int node = Sidx[d.S_off + row];
+  for (int r = 0; r < nrhs; ++r) {
+    const double2* xr = x + r * nodes;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int c = lane; c < d.nB; c += 32) acc = cmac(acc, G[c], xr[B[c]]);
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
+    }
+    if (lane == 0) {
+      const double2 wv = w[r * nodes + node];
+      x[r * nodes + node] = make_double2(wv.x - acc.x, wv.y - acc.y);
+    }
+  }
+}
+
+template <typename T>
+int upload(T** dst, const std::vector<T>& v) {
+  if (v.empty()) { *dst = nullptr; return 0; }
+  HELM_CUDA_TRY(cudaMalloc(dst, v.size() * sizeof(T)));
+  HELM_CUDA_TRY(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return 0;
+}
+
+constexpr int kRowsPerBlock = 8;   // warps per block in the solve kernels
+
+}  // namespace
+
+int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef, int leaf_max,
+                 cudaStream_t s) {
+  cs.g = g;
+  cs.r = r;
+  Builder bld;
+  bld.dim = g.dim;
+  for (int d = 0; d < 3; ++d) bld.N[d] = g.N[d];
+  bld.r = r;
+  bld.leaf_max = leaf_max;
+  int lo[3] = {0, 0, 0}, hi[3] = {g.N[0], g.N[1], g.N[2]};
+  bld.build(lo, hi, -1);
+  auto& F = bld.fronts;
+  cs.nfronts = (int)F.size();
+  int H = 0;
+  for (auto& f : F) H = std::max(H, f.height);
+  cs.nlevels = H + 1;
+  cs.level_fronts.assign(cs.nlevels, {});
+  for (int i = 0; i < cs.nfronts; ++i) cs.level_fronts[F[i].height].push_back(i);
+
+  const int W = 2 * r + 1;
+  std::vector<FrontDesc> desc(cs.nfronts);
+  std::vector<int> Sall, Ball, kids, cmap;
+  std::vector<int2> ents;
+  long long xg = 0, uoff = 0, rfo = 0, uvo = 0;
+  // positions of every node inside each front (for the child maps)
+  for (int i = 0; i < cs.nfronts; ++i) {
+    HostFront& f = F[i];
+    FrontDesc& d = desc[i];
+    d.nS = (int)f.S.size();
+    d.nB = (int)f.B.size();
+    d.S_off = (int)Sall.size();
+    d.B_off = (int)Ball.size();
+    Sall.insert(Sall.end(), f.S.begin(), f.S.end());
+    Ball.insert(Ball.end(), f.B.begin(), f.B.end());
+    const int nF = d.nS + d.nB;
+    d.X_off = xg;
+    xg += (long long)nF * d.nS;
+    d.G_off = xg;
+    xg += (long long)d.nS * d.nB;
+    d.U_off = uoff;
+    uoff += (long long)d.nB * d.nB;
+    d.rf_off = rfo;
+    rfo += nF;
+    d.uv_off = uvo;
+    uvo += d.nB;
+    d.kid_off = (int)kids.size();
+    d.nkids = (int)f.kids.size();
+    kids.insert(kids.end(), f.kids.begin(), f.kids.end());
+  }
+  // child maps and original entries need the position of a node inside a front
+  std::vector<int> cmap_off(cs.nfronts, 0);
+  for (int i = 0; i < cs.nfronts; ++i) {
+    HostFront& f = F[i];
+    FrontDesc& d = desc[i];
+    std::unordered_map<int, int> pos;
+    pos.reserve(2 * (f.S.size() + f.B.size()));
+    for (int t = 0; t < d.nS; ++t) pos[f.S[t]] = t;
+    for (int t = 0; t < d.nB; ++t) pos[f.B[t]] = d.nS + t;
+    for (int k : f.kids) {
+      desc[k].cmap_off = (int)cmap.size();
+      for (int node : F[k].B) {
+        auto it = pos.find(node);
+        if (it == pos.end()) { set_error("nested dissection: child boundary outside parent front"); return HELM_ECUDA; }
+        cmap.push_back(it->second);
+      }
+    }
+    const int ld = d.nS + d.nB + d.nS;
+    d.ent_off = (int)ents.size();
+    for (int t = 0; t < d.nS; ++t) {
+      const int node = f.S[t];
+      const int x = node % g.N[0], y = (node / g.N[0]) % g.N[1], z = node / (g.N[0] * g.N[1]);
+      for (int bz = (g.dim == 3 ? -r : 0); bz <= (g.dim == 3 ? r : 0); ++bz)
+        for (int by = -r; by <= r; ++by)
+          for (int bx = -r; bx <= r; ++bx) {
+            const int X = x + bx, Y = y + by, Z = z + bz;
+            if (X < 0 || X >= g.N[0] || Y < 0 || Y >= g.N[1] || Z < 0 || Z >= g.N[2]) continue;
+            const int nb = X + g.N[0] * (Y + g.N[1] * Z);
+            auto it = pos.find(nb);
+            if (it == pos.end()) continue;   // eliminated in a descendant front
+            const int o = (bx + r) + W * ((by + r) + W * (g.dim == 3 ? bz + r : 0));
+            const int oneg = (-bx + r) + W * ((-by + r) + W * (g.dim == 3 ? -bz + r : 0));
+            ents.push_back(make_int2(t * ld + it->second, (int)((long long)o * g.size + node)));
+            if (it->second >= d.nS)
+              ents.push_back(make_int2(it->second * ld + t, (int)((long long)oneg * g.size + nb)));
+          }
+    }
+    d.ent_cnt = (int)ents.size() - d.ent_off;
+  }
+  cs.factor_entries = xg;
+  cs.rf_total = rfo;
+  cs.uv_total = uvo;
+  // per-level augmented work offsets
+  long long aug_max = 0;
+  for (int h = 0; h < cs.nlevels; ++h) {
+    long long off = 0;
+    for (int f : cs.level_fronts[h]) {
+      desc[f].aug_off = off;
+      const long long nF = desc[f].nS + desc[f].nB;
+      off += nF * (nF + desc[f].nS);
+    }
+    aug_max = std::max(aug_max, off);
+  }
+  if (upload(&cs.d_desc, desc) || upload(&cs.d_S, Sall) || upload(&cs.d_B, Ball) ||
+      upload(&cs.d_kids, kids) || upload(&cs.d_cmap, cmap))
+    return HELM_ECUDA;
+  int2* d_ents = nullptr;
+  if (upload(&d_ents, ents)) return HELM_ECUDA;
+  cs.d_level_list.resize(cs.nlevels);
+  cs.d_fwd_rows.resize(cs.nlevels);
+  cs.d_bwd_rows.resize(cs.nlevels);
+  cs.n_fwd_rows.resize(cs.nlevels);
+  cs.n_bwd_rows.resize(cs.nlevels);
+  for (int h = 0; h < cs.nlevels; ++h) {
+    std::vector<int2> fr, br;
+    for (int f : cs.level_fronts[h]) {
+      const int nF = desc[f].nS + desc[f].nB;
+      for (int r0 = 0; r0 < nF; r0 += kRowsPerBlock) fr.push_back(make_int2(f, r0));
+      for (int r0 = 0; r0 < desc[f].nS; r0 += kRowsPerBlock) br.push_back(make_int2(f, r0));
+    }
+    cs.n_fwd_rows[h] = (int)fr.size();
+    cs.n_bwd_rows[h] = (int)br.size();
+    if (upload(&cs.d_level_list[h], cs.level_fronts[h]) || upload(&cs.d_fwd_rows[h], fr) ||
+        upload(&cs.d_bwd_rows[h], br))
+      return HELM_ECUDA;
+  }
+  HELM_CUDA_TRY(cudaMalloc(&cs.d_factors, std::max<long long>(1, xg) * sizeof(double2)));
+  HELM_CUDA_TRY(cudaMalloc(&cs.d_err, sizeof(int)));
+  HELM_CUDA_TRY(cudaMemsetAsync(cs.d_err, 0, sizeof(int), s));
+  double2 *d_aug = nullptr, *d_upool = nullptr;
+  HELM_CUDA_TRY(cudaMalloc(&d_aug, std::max<long long>(1, aug_max) * sizeof(double2)));
+  HELM_CUDA_TRY(cudaMalloc(&d_upool, std::max<long long>(1, uoff) * sizeof(double2)));
+  for (int h = 0; h < cs.nlevels; ++h) {
+    const int nf = (int)cs.level_fronts[h].size();
+    fact_assemble_kernel<<<nf, 256, 0, s>>>(cs.d_desc, cs.d_level_list[h], d_aug, d_ents, coef, d_upool,
+                                            cs.d_kids, cs.d_cmap);
+    HELM_LAUNCH_CHECK();
+    fact_gj_kernel<<<nf, 512, 0, s>>>(cs.d_desc, cs.d_level_list[h], d_aug, cs.d_err);
+    HELM_LAUNCH_CHECK();
+    fact_extract_kernel<<<nf, 256, 0, s>>>(cs.d_desc, cs.d_level_list[h], d_aug, cs.d_factors, d_upool);
+    HELM_LAUNCH_CHECK();
+  }
+  HELM_CUDA_TRY(cudaStreamSynchronize(s));
+  cudaFree(d_aug);
+  cudaFree(d_upool);
+  cudaFree(d_ents);
+  int herr = 0;
+  HELM_CUDA_TRY(cudaMemcpy(&herr, cs.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr) { set_error("coarsest factorisation: zero or non-finite pivot"); return HELM_ENUMERIC; }
+  return 0;
+}
+
+static int ensure_rhs(CoarseSolver& cs, int nrhs) {
+  if (nrhs <= cs.rhs_cap) return 0;
+  cudaFree(cs.d_rf);
+  cudaFree(cs.d_uv);
+  cudaFree(cs.d_w);
+  HELM_CUDA_TRY(cudaMalloc(&cs.d_rf, std::max<long long>(1, cs.rf_total) * nrhs * sizeof(double2)));
+  HELM_CUDA_TRY(cudaMalloc(&cs.d_uv, std::max<long long>(1, cs.uv_total) * nrhs * sizeof(double2)));
+  HELM_CUDA_TRY(cudaMalloc(&cs.d_w, cs.g.size * nrhs * sizeof(double2)));
+  cs.rhs_cap = nrhs;
+  return 0;
+}
+
+int coarse_solve(CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaStream_t s) {
+  if (int st = ensure_rhs(cs, nrhs)) return st;
+  for (int h = 0; h < cs.nlevels; ++h) {
+    const int nf = (int)cs.level_fronts[h].size();
+    fwd_assemble_kernel<<<nf, 256, 0, s>>>(cs.d_desc, cs.d_level_list[h], cs.d_S, cs.d_kids, cs.d_cmap, b,
+                                           cs.d_rf, cs.d_uv, nrhs, cs.g.size, cs.rf_total, cs.uv_total);
+    HELM_LAUNCH_CHECK();
+    fwd_matvec_kernel<<<cs.n_fwd_rows[h], 32 * kRowsPerBlock, 0, s>>>(
+        cs.d_desc, cs.d_fwd_rows[h], cs.d_S, cs.d_factors, cs.d_rf, cs.d_uv, cs.d_w, nrhs, cs.g.size,
+        cs.rf_total, cs.uv_total);
+    HELM_LAUNCH_CHECK();
+  }
+  for (int h = cs.nlevels - 1; h >= 0; --h) {
+    bwd_matvec_kernel<<<cs.n_bwd_rows[h], 32 * kRowsPerBlock, 0, s>>>(
+        cs.d_desc, cs.d_bwd_rows[h], cs.d_S, cs.d_B, cs.d_factors, cs.d_w, e, nrhs, cs.g.size);
+    HELM_LAUNCH_CHECK();
+  }
+  return 0;
+}
+
+void coarse_free(CoarseSolver& cs) {
+  cudaFree(cs.d_desc);
+  cudaFree(cs.d_S);
+  cudaFree(cs.d_B);
+  cudaFree(cs.d_kids);
+  cudaFree(cs.d_cmap);
+  cudaFree(cs.d_factors);
+  cudaFree(cs.d_err);
+  for (auto p : cs.d_level_list) cudaFree(p);
+  for (auto p : cs.d_fwd_rows) cudaFree(p);
+  for (auto p : cs.d_bwd_rows) cudaFree(p);
+  cudaFree(cs.d_rf);
+  cudaFree(cs.d_uv);
+  cudaFree(cs.d_w);
+  cs = CoarseSolver();
+}
+
+}  // namespace helm

@@ -1,0 +1,60 @@
+// Direct solver of the coarsest (level-3) operator: nested dissection with dense
+// frontal matrices (multifrontal), factorised and applied on the device in complex FP64.
+#pragma once
+#include <vector>
+#include "common.cuh"
+
+namespace helm {
+
+struct FrontDesc {
+  int nS, nB;             // eliminated (separator / leaf) nodes, boundary (ancestor) nodes
+  int S_off, B_off;       // offsets into the S / B node-index arrays
+  long long X_off;        // forward matrix  [nS+nB][nS]: rows S: F_SS^-1, rows B: -F_BS F_SS^-1
+  long long G_off;        // backward matrix [nS][nB]:    F_SS^-1 F_SB
+  long long aug_off;      // augmented front [nF][nF+nS] within the level work buffer
+  long long U_off;        // update matrix   [nB][nB] = F_BB - F_BS F_SS^-1 F_SB
+  int ent_off, ent_cnt;   // original matrix entries scattered into the front
+  int kid_off, nkids;     // children (front ids)
+  int cmap_off;           // this front's boundary positions inside its parent's front
+  long long rf_off;       // solve scratch: front vector (nF entries)
+  long long uv_off;       // solve scratch: update vector (nB entries)
+};
+
+struct CoarseSolver {
+  GridDims g;
+  int r = 1;                          // stencil radius of the coarsest operator
+  int nfronts = 0, nlevels = 0;
+  std::vector<std::vector<int>> level_fronts;      // fronts by height (0 = leaves)
+  // device arrays
+  FrontDesc* d_desc = nullptr;
+  int* d_S = nullptr;
+  int* d_B = nullptr;
+  int* d_kids = nullptr;
+  int* d_cmap = nullptr;
+  double2* d_factors = nullptr;       // X and G blocks of every front
+  long long factor_entries = 0;
+  std::vector<int*> d_level_list;     // per level: front ids
+  std::vector<int2*> d_fwd_rows;      // per level: (front, first row) blocks over nF rows
+  std::vector<int> n_fwd_rows;
+  std::vector<int2*> d_bwd_rows;      // per level: blocks over nS rows
+  std::vector<int> n_bwd_rows;
+  long long rf_total = 0, uv_total = 0;
+  double2* d_rf = nullptr;            // [nrhs][rf_total]
+  double2* d_uv = nullptr;            // [nrhs][uv_total]
+  double2* d_w = nullptr;             // [nrhs][nodes]
+  int rhs_cap = 0;
+  int* d_err = nullptr;
+  long long* launches = nullptr;
+};
+
+// Symbolic analysis and numeric factorisation of the coarsest operator given by its
+// assembled stencil coef (c128, [ncoef][nodes]) of radius r.  leaf_max: largest leaf box.
+int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef, int leaf_max,
+                 cudaStream_t s);
+
+// e = A^-1 b for nrhs vectors (c128, [nrhs][nodes]).
+int coarse_solve(CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaStream_t s);
+
+void coarse_free(CoarseSolver& cs);
+
+}  // namespace helm

@@ -1,0 +1,119 @@
+// Shared device helpers and internal types of the RS-CGC Helmholtz library.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <algorithm>
+
+#include "../../include/helm.h"
+
+namespace helm {
+
+// ---------------------------------------------------------------- complex types
+template <typename T> struct Cplx;
+template <> struct Cplx<double> { using type = double2; };
+template <> struct Cplx<float> { using type = float2; };
+template <typename T> using c2 = typename Cplx<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ c2<T> mk(T r, T i) {
+  c2<T> z; z.x = r; z.y = i; return z;
+}
+template <typename T, typename S> __host__ __device__ __forceinline__ c2<T> cvt(S a) {
+  return mk<T>(static_cast<T>(a.x), static_cast<T>(a.y));
+}
+// Arithmetic on the interleaved complex types (overloads for double2 and float2; the
+// template parameter of the call sites only selects the type).
+#define HELM_COMPLEX_OPS(C, R)                                                             \
+  __host__ __device__ __forceinline__ C operator+(C a, C b) { C z; z.x = a.x + b.x; z.y = a.y + b.y; return z; } \
+  __host__ __device__ __forceinline__ C operator-(C a, C b) { C z; z.x = a.x - b.x; z.y = a.y - b.y; return z; } \
+  __device__ __forceinline__ C cmul(C a, C b) {                                             \
+    C z; z.x = a.x * b.x - a.y * b.y; z.y = a.x * b.y + a.y * b.x; return z;                 \
+  }                                                                                          \
+  __device__ __forceinline__ C cmac(C acc, C a, C b) {                                      \
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);                             \
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);                              \
+    return acc;                                                                              \
+  }                                                                                          \
+  __device__ __forceinline__ C cmacc(C acc, C a, C b) {                                     \
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);                              \
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);                             \
+    return acc;                                                                              \
+  }                                                                                          \
+  __device__ __forceinline__ C cscale(C a, R s) { C z; z.x = a.x * s; z.y = a.y * s; return z; } \
+  __device__ __forceinline__ C crecip(C a) {                                                \
+    R d = a.x * a.x + a.y * a.y; C z; z.x = a.x / d; z.y = -a.y / d; return z;               \
+  }
+HELM_COMPLEX_OPS(double2, double)
+HELM_COMPLEX_OPS(float2, float)
+#undef HELM_COMPLEX_OPS
+
+
+// ---------------------------------------------------------------- grids
+struct GridDims {
+  int dim;
+  int N[3];          // nodes per axis (cells + 1); N[2] = 1 in 2D
+  long long size;    // total nodes
+};
+
+__host__ __device__ __forceinline__ void node_coords(const GridDims& g, long long idx, int& i, int& j,
+                                                     int& k) {
+  i = (int)(idx % g.N[0]);
+  long long t = idx / g.N[0];
+  j = (int)(t % g.N[1]);
+  k = (int)(t / g.N[1]);
+}
+
+// Fine (level-1) operator parameters: -Lap_h - omega^2 kappa^2 (1 - i gamma) with
+// gamma = sum over axes of a per-axis profile (already scaled by gamma_max).
+struct FineOp {
+  GridDims g;
+  int order;               // 0 = 2nd-order 5/7-point, 1 = compact 4th-order 9/19-point
+  double inv_h2;
+  double omega2;
+  const double* gam[3];    // per-axis gamma tables (device), length N[a]
+};
+
+// Assembled stencil on a coarse level: coef[o * size + node], o in [0, (2r+1)^d).
+template <typename T> struct StencilOp {
+  GridDims g;
+  int r;
+  int ncoef;
+  const c2<T>* coef;
+  const c2<T>* dinv;       // 1 / diagonal
+};
+
+// 1D transfer weights, radius 1 (full weighting) or 2 (cubic).
+struct Transfer {
+  int radius;
+  double w[5];             // w[o + radius]
+};
+
+// ---------------------------------------------------------------- launch accounting
+extern thread_local long long* g_launch_counter;
+inline void count_launch() { if (g_launch_counter) ++(*g_launch_counter); }
+
+std::string& last_error_ref();
+void set_error(const std::string& s);
+
+#define HELM_CUDA_TRY(call)                                                              \
+  do {                                                                                   \
+    cudaError_t _e = (call);                                                             \
+    if (_e != cudaSuccess) {                                                             \
+      ::helm::set_error(std::string(#call) + ": " + cudaGetErrorString(_e));            \
+      return HELM_ECUDA;                                                                 \
+    }                                                                                    \
+  } while (0)
+
+#define HELM_LAUNCH_CHECK()                                                              \
+  do {                                                                                   \
+    ::helm::count_launch();                                                              \
+    cudaError_t _e = cudaGetLastError();                                                 \
+    if (_e != cudaSuccess) {                                                             \
+      ::helm::set_error(std::string("kernel launch: ") + cudaGetErrorString(_e));       \
+      return HELM_ECUDA;                                                                 \
+    }                                                                                    \
+  } while (0)
+
+inline int blocks_for(long long n, int threads) { return (int)((n + threads - 1) / threads); }
+
+}  // namespace helm

@@ -1,0 +1,314 @@
+// Grid kernels of the RS-CGC cycle: the fine Helmholtz operator with the absorbing
+// layer (Sec. 3.1), assembled coarse stencils (Eqs. Galerkin, CoarseRealShifted),
+// damped-Jacobi and red-black point relaxation (Sec. 2), and the grid transfers
+// (full weighting / bilinear; cubic Eq. intergrid).
+//
+// Every row kernel maps one thread to one node and loops over the right-hand sides
+// of a batch inside the thread, so the coefficients of a node are read once per
+// batch.
+#include "gridops.cuh"
+#include "fineop.cuh"
+
+namespace helm {
+
+// 1D transfer weights by radius: full weighting 1/4 [1 2 1] (radius 1) and the cubic
+// 1/16 [1 4 6 4 1] of Eq. intergrid (radius 2).
+__constant__ double c_transfer_w[2][5] = {{0.25, 0.5, 0.25, 0.0, 0.0},
+                                          {1.0 / 16, 4.0 / 16, 6.0 / 16, 4.0 / 16, 1.0 / 16}};
+
+// --------------------------------------------------------------- fine operator
+template <typename T, typename TX, typename TB, typename TY, int MODE>
+__global__ void __launch_bounds__(256) fine_row_kernel(FineOp op, const T* __restrict__ kap,
+                                                       const c2<TX>* __restrict__ x,
+                                                       const c2<TB>* __restrict__ b,
+                                                       c2<TY>* __restrict__ y, int nrhs, T w,
+                                                       int colour) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= op.g.size) return;
+  int i, j, k;
+  node_coords(op.g, idx, i, j, k);
+  const c2<T> diag = fine_diag<T>(op, kap, idx, i, j, k);
+  const c2<T> dinv = crecip(diag);
+  const long long N = op.g.size;
+  const bool active = (MODE != MODE_RB) || (((i + j + k) & 1) == colour);
+  for (int r = 0; r < nrhs; ++r) {
+    const long long p = r * N + idx;
+    c2<T> out;
+    if (MODE == MODE_JACOBI0) {
+      out = cscale(cmul(dinv, cvt<T>(b[p])), w);
+    } else if (MODE == MODE_RB && !active) {
+      out = cvt<T>(x[p]);
+    } else {
+      const c2<T> Ax = fine_apply_at<T, TX>(op, diag, x, p, i, j, k);
+      if (MODE == MODE_APPLY) {
+        out = Ax;
+      } else {
+        const c2<T> res = cvt<T>(b[p]) - Ax;
+        if (MODE == MODE_RESID) out = res;
+        else out = cvt<T>(x[p]) + cscale(cmul(dinv, res), w);
+      }
+    }
+    y[p] = cvt<TY>(out);
+  }
+}
+
+template <typename T, typename TX, typename TB, typename TY>
+static int fine_dispatch(const FineOp& op, int mode, const void* kap, const void* x, const void* b,
+                         void* y, int nrhs, double w, int colour, cudaStream_t s) {
+  const int th = 256;
+  const int bl = blocks_for(op.g.size, th);
+  auto K = (const T*)kap;
+  auto X = (const c2<TX>*)x;
+  auto B = (const c2<TB>*)b;
+  auto Y = (c2<TY>*)y;
+  switch (mode) {
+    case MODE_APPLY: fine_row_kernel<T, TX, TB, TY, MODE_APPLY><<<bl, th, 0, s>>>(op, K, X, B, Y, nrhs, (T)w, colour); break;
+    case MODE_RESID: fine_row_kernel<T, TX, TB, TY, MODE_RESID><<<bl, th, 0, s>>>(op, K, X, B, Y, nrhs, (T)w, colour); break;
+    case MODE_JACOBI: fine_row_kernel<T, TX, TB, TY, MODE_JACOBI><<<bl, th, 0, s>>>(op, K, X, B, Y, nrhs, (T)w, colour); break;
+    case MODE_JACOBI0: fine_row_kernel<T, TX, TB, TY, MODE_JACOBI0><<<bl, th, 0, s>>>(op, K, X, B, Y, nrhs, (T)w, colour); break;
+    case MODE_RB: fine_row_kernel<T, TX, TB, TY, MODE_RB><<<bl, th, 0, s>>>(op, K, X, B, Y, nrhs, (T)w, colour); break;
+    default: set_error("bad row mode"); return 1;
+  }
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
+int launch_fine_row(const FineOp& op, int mode, Prec arith, Prec xs, Prec bs, Prec ys,
+                    const void* kappa2, const void* x, const void* b, void* y, int nrhs,
+                    double w, int colour, cudaStream_t s) {
+  if (op.order != 0) { set_error("fine stencil order not built"); return 1; }
+  if (arith == P64) {
+    if (xs != P64 || bs != P64 || ys != P64) { set_error("FP64 row kernel needs c128 storage"); return 1; }
+    return fine_dispatch<double, double, double, double>(op, mode, kappa2, x, b, y, nrhs, w, colour, s);
+  }
+  if (xs != P32 || ys != P32) { set_error("FP32 row kernel needs c64 x/y"); return 1; }
+  if (bs == P64)
+    return fine_dispatch<float, float, double, float>(op, mode, kappa2, x, b, y, nrhs, w, colour, s);
+  return fine_dispatch<float, float, float, float>(op, mode, kappa2, x, b, y, nrhs, w, colour, s);
+}
+
+// --------------------------------------------------------------- assembled stencils
+template <typename T, typename TX, typename TB, typename TY, int MODE, int DIM, int R>
+__global__ void __launch_bounds__(256) stencil_row_kernel(GridDims g, const c2<T>* __restrict__ coef,
+                                                          const c2<T>* __restrict__ dinvp,
+                                                          const c2<TX>* __restrict__ x,
+                                                          const c2<TB>* __restrict__ b,
+                                                          c2<TY>* __restrict__ y, int nrhs, T w,
+                                                          int colour) {
+  constexpr int W = 2 * R + 1;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= g.size) return;
+  int i, j, k;
+  node_coords(g, idx, i, j, k);
+  const long long N = g.size;
+  const long long sy = g.N[0];
+  const long long sz = (long long)g.N[0] * g.N[1];
+  const c2<T> dinv = dinvp[idx];
+  const bool active = (MODE != MODE_RB) || (((i + j + k) & 1) == colour);
+  for (int r = 0; r < nrhs; ++r) {
+    const long long p = r * N + idx;
+    c2<T> out;
+    if (MODE == MODE_JACOBI0) {
+      out = cscale(cmul(dinv, cvt<T>(b[p])), w);
+    } else if (MODE == MODE_RB && !active) {
+      out = cvt<T>(x[p]);
+    } else {
+      c2<T> Ax = mk<T>(0, 0);
+#pragma unroll
+      for (int dz = (DIM == 3 ? -R : 0); dz <= (DIM == 3 ? R : 0); ++dz) {
+        if (k + dz < 0 || k + dz >= g.N[2]) continue;
+#pragma unroll
+        for (int dy = -R; dy <= R; ++dy) {
+          if (j + dy < 0 || j + dy >= g.N[1]) continue;
+#pragma unroll
+          for (int dx = -R; dx <= R; ++dx) {
+            if (i + dx < 0 || i + dx >= g.N[0]) continue;
+            const int o = (dx + R) + W * ((dy + R) + W * (DIM == 3 ? dz + R : 0));
+            Ax = cmac(Ax, coef[o * N + idx], cvt<T>(x[p + dx + dy * sy + dz * sz]));
+          }
+        }
+      }
+      if (MODE == MODE_APPLY) {
+        out = Ax;
+      } else {
+        const c2<T> res = cvt<T>(b[p]) - Ax;
+        if (MODE == MODE_RESID) out = res;
+        else out = cvt<T>(x[p]) + cscale(cmul(dinv, res), w);
+      }
+    }
+    y[p] = cvt<TY>(out);
+  }
+}
+
+template <typename T, typename TX, typename TB, typename TY, int DIM, int R>
+static int stencil_dispatch_mode(const GridDims& g, const void* coef, const void* dinv, int mode,
+                                 const void* x, const void* b, void* y, int nrhs, double w,
+                                 int colour, cudaStream_t s) {
+  const int th = 256;
+  const int bl = blocks_for(g.size, th);
+  auto C = (const c2<T>*)coef;
+  auto D = (const c2<T>*)dinv;
+  auto X = (const c2<TX>*)x;
+  auto B = (const c2<TB>*)b;
+  auto Y = (c2<TY>*)y;
+  switch (mode) {
+    case MODE_APPLY: stencil_row_kernel<T, TX, TB, TY, MODE_APPLY, DIM, R><<<bl, th, 0, s>>>(g, C, D, X, B, Y, nrhs, (T)w, colour); break;
+    case MODE_RESID: stencil_row_kernel<T, TX, TB, TY, MODE_RESID, DIM, R><<<bl, th, 0, s>>>(g, C, D, X, B, Y, nrhs, (T)w, colour); break;
+    case MODE_JACOBI: stencil_row_kernel<T, TX, TB, TY, MODE_JACOBI, DIM, R><<<bl, th, 0, s>>>(g, C, D, X, B, Y, nrhs, (T)w, colour); break;
+    case MODE_JACOBI0: stencil_row_kernel<T, TX, TB, TY, MODE_JACOBI0, DIM, R><<<bl, th, 0, s>>>(g, C, D, X, B, Y, nrhs, (T)w, colour); break;
+    case MODE_RB: stencil_row_kernel<T, TX, TB, TY, MODE_RB, DIM, R><<<bl, th, 0, s>>>(g, C, D, X, B, Y, nrhs, (T)w, colour); break;
+    default: set_error("bad row mode"); return 1;
+  }
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
+template <typename T, typename TX, typename TB, typename TY>
+static int stencil_dispatch(const GridDims& g, int r, const void* coef, const void* dinv, int mode,
+                            const void* x, const void* b, void* y, int nrhs, double w, int colour,
+                            cudaStream_t s) {
+  if (g.dim == 2 && r == 1)
+    return stencil_dispatch_mode<T, TX, TB, TY, 2, 1>(g, coef, dinv, mode, x, b, y, nrhs, w, colour, s);
+  if (g.dim == 3 && r == 1)
+    return stencil_dispatch_mode<T, TX, TB, TY, 3, 1>(g, coef, dinv, mode, x, b, y, nrhs, w, colour, s);
+  set_error("stencil radius not built for this dimension");
+  return 1;
+}
+
+int launch_stencil_row(const GridDims& g, int r, Prec arith, const void* coef, const void* dinv,
+                       int mode, Prec xs, Prec bs, Prec ys, const void* x, const void* b, void* y,
+                       int nrhs, double w, int colour, cudaStream_t s) {
+  if (arith == P64) {
+    if (xs != P64 || bs != P64 || ys != P64) { set_error("FP64 row kernel needs c128 storage"); return 1; }
+    return stencil_dispatch<double, double, double, double>(g, r, coef, dinv, mode, x, b, y, nrhs, w, colour, s);
+  }
+  if (xs != P32 || ys != P32) { set_error("FP32 row kernel needs c64 x/y"); return 1; }
+  if (bs == P64)
+    return stencil_dispatch<float, float, double, float>(g, r, coef, dinv, mode, x, b, y, nrhs, w, colour, s);
+  return stencil_dispatch<float, float, float, float>(g, r, coef, dinv, mode, x, b, y, nrhs, w, colour, s);
+}
+
+// --------------------------------------------------------------- transfers
+template <typename T, int RW>
+__global__ void __launch_bounds__(256) restrict_kernel(GridDims gf, GridDims gc,
+                                                       const c2<T>* __restrict__ rf,
+                                                       c2<T>* __restrict__ rc, int nrhs) {
+  const long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (I >= gc.size) return;
+  int ci, cj, ck;
+  node_coords(gc, I, ci, cj, ck);
+  const double* wt = c_transfer_w[RW - 1];
+  const long long sy = gf.N[0];
+  const long long sz = (long long)gf.N[0] * gf.N[1];
+  for (int r = 0; r < nrhs; ++r) {
+    c2<T> acc = mk<T>(0, 0);
+    const long long base = r * gf.size;
+    for (int az = (gf.dim == 3 ? -RW : 0); az <= (gf.dim == 3 ? RW : 0); ++az) {
+      const int fk = 2 * ck + az;
+      if (fk < 0 || fk >= gf.N[2]) continue;
+      const T wz = gf.dim == 3 ? (T)wt[az + RW] : T(1);
+#pragma unroll
+      for (int ay = -RW; ay <= RW; ++ay) {
+        const int fj = 2 * cj + ay;
+        if (fj < 0 || fj >= gf.N[1]) continue;
+        const T wyz = wz * (T)wt[ay + RW];
+#pragma unroll
+        for (int ax = -RW; ax <= RW; ++ax) {
+          const int fi = 2 * ci + ax;
+          if (fi < 0 || fi >= gf.N[0]) continue;
+          const c2<T> v = rf[base + fi + fj * sy + fk * sz];
+          const T wgt = wyz * (T)wt[ax + RW];
+          acc.x = fma(wgt, v.x, acc.x);
+          acc.y = fma(wgt, v.y, acc.y);
+        }
+      }
+    }
+    rc[r * gc.size + I] = acc;
+  }
+}
+
+template <typename T, int RW>
+__global__ void __launch_bounds__(256) prolong_add_kernel(GridDims gf, GridDims gc,
+                                                          const c2<T>* __restrict__ ec,
+                                                          c2<T>* __restrict__ xf, int nrhs) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= gf.size) return;
+  int fi, fj, fk;
+  node_coords(gf, idx, fi, fj, fk);
+  const double* wt = c_transfer_w[RW - 1];
+  const long long sy = gc.N[0];
+  const long long sz = (long long)gc.N[0] * gc.N[1];
+  // coarse J with |f - 2J| <= RW along each axis; weight 2 * w(f - 2J) per axis
+  const int i0 = max(0, (fi - RW + 1) >> 1), i1 = min(gc.N[0] - 1, (fi + RW) >> 1);
+  const int j0 = max(0, (fj - RW + 1) >> 1), j1 = min(gc.N[1] - 1, (fj + RW) >> 1);
+  int k0 = 0, k1 = 0;
+  if (gf.dim == 3) { k0 = max(0, (fk - RW + 1) >> 1); k1 = min(gc.N[2] - 1, (fk + RW) >> 1); }
+  for (int r = 0; r < nrhs; ++r) {
+    c2<T> acc = mk<T>(0, 0);
+    const long long base = r * gc.size;
+    for (int K = k0; K <= k1; ++K) {
+      const T wz = gf.dim == 3 ? T(2) * (T)wt[fk - 2 * K + RW] : T(1);
+      for (int J = j0; J <= j1; ++J) {
+        const T wyz = wz * T(2) * (T)wt[fj - 2 * J + RW];
+        for (int I = i0; I <= i1; ++I) {
+          const T wgt = wyz * T(2) * (T)wt[fi - 2 * I + RW];
+          const c2<T> v = ec[base + I + J * sy + K * sz];
+          acc.x = fma(wgt, v.x, acc.x);
+          acc.y = fma(wgt, v.y, acc.y);
+        }
+      }
+    }
+    const long long p = r * gf.size + idx;
+    c2<T> o = xf[p];
+    xf[p] = o + acc;
+  }
+}
+
+int launch_restrict(const GridDims& gf, const GridDims& gc, const Transfer& t, Prec p,
+                    const void* rf, void* rc, int nrhs, cudaStream_t s) {
+  const int th = 256, bl = blocks_for(gc.size, th);
+  if (p == P64) {
+    if (t.radius == 1) restrict_kernel<double, 1><<<bl, th, 0, s>>>(gf, gc, (const double2*)rf, (double2*)rc, nrhs);
+    else restrict_kernel<double, 2><<<bl, th, 0, s>>>(gf, gc, (const double2*)rf, (double2*)rc, nrhs);
+  } else {
+    if (t.radius == 1) restrict_kernel<float, 1><<<bl, th, 0, s>>>(gf, gc, (const float2*)rf, (float2*)rc, nrhs);
+    else restrict_kernel<float, 2><<<bl, th, 0, s>>>(gf, gc, (const float2*)rf, (float2*)rc, nrhs);
+  }
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
+int launch_prolong_add(const GridDims& gf, const GridDims& gc, const Transfer& t, Prec p,
+                       const void* ec, void* xf, int nrhs, cudaStream_t s) {
+  const int th = 256, bl = blocks_for(gf.size, th);
+  if (p == P64) {
+    if (t.radius == 1) prolong_add_kernel<double, 1><<<bl, th, 0, s>>>(gf, gc, (const double2*)ec, (double2*)xf, nrhs);
+    else prolong_add_kernel<double, 2><<<bl, th, 0, s>>>(gf, gc, (const double2*)ec, (double2*)xf, nrhs);
+  } else {
+    if (t.radius == 1) prolong_add_kernel<float, 1><<<bl, th, 0, s>>>(gf, gc, (const float2*)ec, (float2*)xf, nrhs);
+    else prolong_add_kernel<float, 2><<<bl, th, 0, s>>>(gf, gc, (const float2*)ec, (float2*)xf, nrhs);
+  }
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
+// --------------------------------------------------------------- conversions
+template <typename S, typename D>
+__global__ void convert_kernel(const c2<S>* __restrict__ x, c2<D>* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = cvt<D>(x[i]);
+}
+
+int launch_convert(Prec from, Prec to, const void* x, void* y, long long n, cudaStream_t s) {
+  const int th = 256;
+  const int bl = (int)std::min<long long>(blocks_for(n, th), 152LL * 16);
+  if (from == P64 && to == P32) convert_kernel<double, float><<<bl, th, 0, s>>>((const double2*)x, (float2*)y, n);
+  else if (from == P32 && to == P64) convert_kernel<float, double><<<bl, th, 0, s>>>((const float2*)x, (double2*)y, n);
+  else if (from == P64) convert_kernel<double, double><<<bl, th, 0, s>>>((const double2*)x, (double2*)y, n);
+  else convert_kernel<float, float><<<bl, th, 0, s>>>((const float2*)x, (float2*)y, n);
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
+}  // namespace helm

@@ -1,0 +1,388 @@
+// Flexible GMRES machinery on the device (Sec. 5: FGMRES with the RS-CGC cycle as
+// preconditioner, stopping at a relative residual of 1e-6), in complex FP64.
+//
+// One Arnoldi step j, after z_j = M^-1 v_j:
+//   arnoldi_matvec   w = H z_j and the first classical Gram-Schmidt pass h1 = V^H w
+//   arnoldi_update   w <- w - V h1 and the second pass h2 = V^H w, ||w||^2
+//   arnoldi_small    H(:, j) = h1 + h2, ||w - V h2||, Givens rotations, residual estimate
+//   arnoldi_normalize v_{j+1} = (w - V h2) / ||w - V h2||
+// (classical Gram-Schmidt with one re-orthogonalisation, CGS2).  Every reduction keeps
+// per-thread partial sums in shared memory over a fixed grid, reduces each block once and
+// lets the last block sum the block partials in block order, so the result does not
+// depend on scheduling.
+#include "krylov.cuh"
+#include "fineop.cuh"
+
+namespace helm {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double2 warp_sum2(double2 v) {
+  for (int off = 16; off > 0; off >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, off);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+  }
+  return v;
+}
+
+// sacc[i * blockDim + tid] holds per-thread partials of nval sums.  Reduces the block,
+// then the last block to finish reduces all blocks into out[0..nval).
+__device__ void reduce_finish(double2* sacc, int nval, double2* __restrict__ part,
+                              unsigned* __restrict__ counter, double2* __restrict__ out) {
+  __shared__ bool s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  __syncthreads();
+  for (int i = warp; i < nval; i += nwarp) {
+    double2 v = make_double2(0.0, 0.0);
+    for (int t = lane; t < (int)blockDim.x; t += 32) {
+      const double2 a = sacc[i * blockDim.x + t];
+      v.x += a.x;
+      v.y += a.y;
+    }
+    v = warp_sum2(v);
+    if (lane == 0) part[(long long)blockIdx.x * nval + i] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int i = warp; i < nval; i += nwarp) {
+    double2 v = make_double2(0.0, 0.0);
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
+      const double2 a = __ldcg(part + (long long)b * nval + i);
+      v.x += a.x;
+      v.y += a.y;
+    }
+    v = warp_sum2(v);
+    if (lane == 0) out[i] = v;
+  }
+  if (tid == 0) *counter = 0u;
+}
+
+// w = H z (FP64 arithmetic; z stored as c128 or c64), h1_i = v_i^H w (i < nv), ||w||^2.
+template <typename TZ>
+__global__ void __launch_bounds__(kThreads) arnoldi_matvec_kernel(
+    FineOp op, const double* __restrict__ kap, const c2<TZ>* __restrict__ z, double2* __restrict__ w,
+    const double2* __restrict__ V, long long vstride, int nv, double2* __restrict__ part,
+    unsigned* __restrict__ counter, double2* __restrict__ out) {
+  extern __shared__ double2 sacc[];
+  const int tid = threadIdx.x;
+  for (int i = 0; i <= nv; ++i) sacc[i * blockDim.x + tid] = make_double2(0.0, 0.0);
+  const long long n = op.g.size;
+  for (long long p = blockIdx.x * (long long)blockDim.x + tid; p < n; p += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    node_coords(op.g, p, i, j, k);
+    const double2 d = fine_diag<double>(op, kap, p, i, j, k);
+    const double2 wv = fine_apply_at<double, TZ>(op, d, z, p, i, j, k);
+    w[p] = wv;
+    for (int q = 0; q < nv; ++q) {
+      double2& a = sacc[q * blockDim.x + tid];
+      a = cmacc(a, V[q * vstride + p], wv);
+    }
+    sacc[nv * blockDim.x + tid].x += wv.x * wv.x + wv.y * wv.y;
+  }
+  reduce_finish(sacc, nv + 1, part, counter, out);
+}
+
+// w <- w - sum_i h1_i v_i; h2_i = v_i^H w; ||w||^2.
+__global__ void __launch_bounds__(kThreads) arnoldi_update_kernel(
+    long long n, double2* __restrict__ w, const double2* __restrict__ V, long long vstride, int nv,
+    const double2* __restrict__ h1, double2* __restrict__ part, unsigned* __restrict__ counter,
+    double2* __restrict__ out) {
+  extern __shared__ double2 sacc[];
+  __shared__ double2 sh[64];
+  const int tid = threadIdx.x;
+  for (int i = 0; i <= nv; ++i) sacc[i * blockDim.x + tid] = make_double2(0.0, 0.0);
+  for (int i = tid; i < nv; i += blockDim.x) sh[i] = h1[i];
+  __syncthreads();
+  for (long long p = blockIdx.x * (long long)blockDim.x + tid; p < n; p += (long long)gridDim.x * blockDim.x) {
+    double2 wv = w[p];
+    for (int q = 0; q < nv; ++q) {
+      const double2 v = V[q * vstride + p];
+      const double2 h = sh[q];
+      wv.x -= h.x * v.x - h.y * v.y;
+      wv.y -= h.x * v.y + h.y * v.x;
+    }
+    w[p] = wv;
+    for (int q = 0; q < nv; ++q) {
+      double2& a = sacc[q * blockDim.x + tid];
+      a = cmacc(a, V[q * vstride + p], wv);
+    }
+    sacc[nv * blockDim.x + tid].x += wv.x * wv.x + wv.y * wv.y;
+  }
+  reduce_finish(sacc, nv + 1, part, counter, out);
+}
+
+// v_out = (w - sum_i h2_i v_i) * st->inv_hn
+__global__ void __launch_bounds__(kThreads) arnoldi_normalize_kernel(
+    long long n, const double2* __restrict__ w, const double2* __restrict__ V, long long vstride, int nv,
+    const double2* __restrict__ h2, const double* __restrict__ inv_hn, double2* __restrict__ vout) {
+  __shared__ double2 sh[64];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) sh[i] = h2[i];
+  __syncthreads();
+  const double s = *inv_hn;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    double2 wv = w[p];
+    for (int q = 0; q < nv; ++q) {
+      const double2 v = V[q * vstride + p];
+      const double2 h = sh[q];
+      wv.x -= h.x * v.x - h.y * v.y;
+      wv.y -= h.x * v.y + h.y * v.x;
+    }
+    vout[p] = make_double2(wv.x * s, wv.y * s);
+  }
+}
+
+// Hessenberg column j, Givens rotations and the residual estimate (one thread).
+__global__ void arnoldi_small_kernel(KrylovState st, int j, int m) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double2* H = st.H;   // [(m+1) x m], column j at H[i * m + j]
+  double hs2 = 0.0;
+  for (int i = 0; i <= j; ++i) {
+    const double2 a = st.h1[i], b = st.h2[i];
+    H[i * m + j] = make_double2(a.x + b.x, a.y + b.y);
+    hs2 += b.x * b.x + b.y * b.y;
+  }
+  const double hn = sqrt(fmax(st.h2[j + 1].x - hs2, 0.0));
+  for (int i = 0; i < j; ++i) {
+    const double c = st.cs[i];
+    const double2 s = st.sn[i];
+    const double2 a = H[i * m + j], b = H[(i + 1) * m + j];
+    // [a; b] <- [c a + s b; -conj(s) a + c b]
+    H[i * m + j] = make_double2(c * a.x + s.x * b.x - s.y * b.y, c * a.y + s.x * b.y + s.y * b.x);
+    H[(i + 1) * m + j] = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y);
+  }
+  const double2 a = H[j * m + j];
+  const double aa = hypot(a.x, a.y);
+  double c;
+  double2 s, rr;
+  if (aa == 0.0) {
+    c = 0.0;
+    s = make_double2(1.0, 0.0);
+    rr = make_double2(hn, 0.0);
+  } else {
+    const double t = hypot(aa, hn);
+    const double2 ph = make_double2(a.x / aa, a.y / aa);
+    c = aa / t;
+    s = make_double2(ph.x * hn / t, ph.y * hn / t);   // ph * conj(hn) / t, hn real
+    rr = make_double2(ph.x * t, ph.y * t);
+  }
+  H[j * m + j] = rr;
+  st.cs[j] = c;
+  st.sn[j] = s;
+  const double2 gj = st.g[j];
+  // g_{j+1} = -conj(s) g_j ; g_j = c g_j
+  st.g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
+  st.g[j] = make_double2(c * gj.x, c * gj.y);
+  st.scal[KS_HN] = hn;
+  st.scal[KS_INV_HN] = hn > 0.0 ? 1.0 / hn : 0.0;
+  st.scal[KS_EST] = hypot(st.g[j + 1].x, st.g[j + 1].y) / st.scal[KS_BNORM];
+}
+
+// y = R^-1 g on the k x k leading block of the rotated Hessenberg matrix (one thread).
+__global__ void lsq_kernel(KrylovState st, int k, int m) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; --i) {
+    double2 acc = st.g[i];
+    for (int l = i + 1; l < k; ++l) {
+      const double2 h = st.H[i * m + l], y = st.y[l];
+      acc.x -= h.x * y.x - h.y * y.y;
+      acc.y -= h.x * y.y + h.y * y.x;
+    }
+    const double2 d = st.H[i * m + i];
+    const double dd = d.x * d.x + d.y * d.y;
+    st.y[i] = make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd);
+  }
+}
+
+// x += sum_i y_i z_i
+template <typename TZ>
+__global__ void __launch_bounds__(kThreads) solution_update_kernel(long long n, double2* __restrict__ x,
+                                                                   const c2<TZ>* __restrict__ Z,
+                                                                   long long zstride, int k,
+                                                                   const double2* __restrict__ y) {
+  __shared__ double2 sy[64];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sy[i] = y[i];
+  __syncthreads();
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    double2 acc = x[p];
+    for (int q = 0; q < k; ++q) acc = cmac(acc, sy[q], cvt<double>(Z[q * zstride + p]));
+    x[p] = acc;
+  }
+}
+
+// r = b - H x (FP64) and ||r||^2 (in out[0].x)
+__global__ void __launch_bounds__(kThreads) true_residual_kernel(FineOp op, const double* __restrict__ kap,
+                                                                 const double2* __restrict__ b,
+                                                                 const double2* __restrict__ x,
+                                                                 double2* __restrict__ r,
+                                                                 double2* __restrict__ part,
+                                                                 unsigned* __restrict__ counter,
+                                                                 double2* __restrict__ out) {
+  extern __shared__ double2 sacc[];
+  const int tid = threadIdx.x;
+  sacc[tid] = make_double2(0.0, 0.0);
+  for (long long p = blockIdx.x * (long long)blockDim.x + tid; p < op.g.size;
+       p += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    node_coords(op.g, p, i, j, k);
+    const double2 d = fine_diag<double>(op, kap, p, i, j, k);
+    const double2 ax = fine_apply_at<double, double>(op, d, x, p, i, j, k);
+    const double2 rv = make_double2(b[p].x - ax.x, b[p].y - ax.y);
+    r[p] = rv;
+    sacc[tid].x += rv.x * rv.x + rv.y * rv.y;
+  }
+  reduce_finish(sacc, 1, part, counter, out);
+}
+
+// ||b||^2 (out[0].x) and, if vout, vout = b (a copy used as the first residual)
+__global__ void __launch_bounds__(kThreads) norm2_kernel(long long n, const double2* __restrict__ b,
+                                                         double2* __restrict__ vout,
+                                                         double2* __restrict__ part,
+                                                         unsigned* __restrict__ counter,
+                                                         double2* __restrict__ out) {
+  extern __shared__ double2 sacc[];
+  const int tid = threadIdx.x;
+  sacc[tid] = make_double2(0.0, 0.0);
+  for (long long p = blockIdx.x * (long long)blockDim.x + tid; p < n; p += (long long)gridDim.x * blockDim.x) {
+    const double2 v = b[p];
+    if (vout) vout[p] = v;
+    sacc[tid].x += v.x * v.x + v.y * v.y;
+  }
+  reduce_finish(sacc, 1, part, counter, out);
+}
+
+// v = r * (1 / beta); resets g = (beta, 0, ...)
+__global__ void __launch_bounds__(kThreads) start_cycle_kernel(long long n, const double2* __restrict__ r,
+                                                               double2* __restrict__ v, KrylovState st,
+                                                               int m) {
+  const double beta = st.scal[KS_BETA];
+  const double s = 1.0 / beta;
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) st.g[i] = make_double2(i == 0 ? beta : 0.0, 0.0);
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const double2 a = r[p];
+    v[p] = make_double2(a.x * s, a.y * s);
+  }
+}
+
+__global__ void set_scalar_kernel(double* dst, const double2* src_x, int do_sqrt) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *dst = do_sqrt ? sqrt(src_x->x) : src_x->x;
+}
+
+int grid_blocks(long long n) {
+  const long long want = (n + kThreads - 1) / kThreads;
+  return (int)std::max<long long>(1, std::min<long long>(want, 152LL * 4));
+}
+
+}  // namespace
+
+int krylov_alloc(KrylovState& st, int m) {
+  st.m = m;
+  HELM_CUDA_TRY(cudaMalloc(&st.H, sizeof(double2) * (m + 1) * m));
+  HELM_CUDA_TRY(cudaMalloc(&st.g, sizeof(double2) * (m + 1)));
+  HELM_CUDA_TRY(cudaMalloc(&st.sn, sizeof(double2) * m));
+  HELM_CUDA_TRY(cudaMalloc(&st.cs, sizeof(double) * m));
+  HELM_CUDA_TRY(cudaMalloc(&st.y, sizeof(double2) * m));
+  HELM_CUDA_TRY(cudaMalloc(&st.h1, sizeof(double2) * (m + 2)));
+  HELM_CUDA_TRY(cudaMalloc(&st.h2, sizeof(double2) * (m + 2)));
+  HELM_CUDA_TRY(cudaMalloc(&st.red, sizeof(double2) * 4));
+  HELM_CUDA_TRY(cudaMalloc(&st.scal, sizeof(double) * KS_COUNT));
+  HELM_CUDA_TRY(cudaMalloc(&st.part, sizeof(double2) * 152 * 4 * (m + 2)));
+  HELM_CUDA_TRY(cudaMalloc(&st.counter, sizeof(unsigned)));
+  HELM_CUDA_TRY(cudaMemset(st.counter, 0, sizeof(unsigned)));
+  HELM_CUDA_TRY(cudaMemset(st.H, 0, sizeof(double2) * (m + 1) * m));
+  return 0;
+}
+
+void krylov_free(KrylovState& st) {
+  cudaFree(st.H); cudaFree(st.g); cudaFree(st.sn); cudaFree(st.cs); cudaFree(st.y);
+  cudaFree(st.h1); cudaFree(st.h2); cudaFree(st.red); cudaFree(st.scal); cudaFree(st.part);
+  cudaFree(st.counter);
+  st = KrylovState();
+}
+
+int k_norm(const KrylovState& st, long long n, const double2* b, double2* copy_to, cudaStream_t s) {
+  const int bl = grid_blocks(n);
+  norm2_kernel<<<bl, kThreads, kThreads * sizeof(double2), s>>>(n, b, copy_to, st.part, st.counter, st.red);
+  HELM_LAUNCH_CHECK();
+  set_scalar_kernel<<<1, 32, 0, s>>>(st.scal + KS_BNORM, st.red, 1);
+  HELM_LAUNCH_CHECK();
+  set_scalar_kernel<<<1, 32, 0, s>>>(st.scal + KS_BETA, st.red, 1);
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
+int k_start_cycle(const KrylovState& st, long long n, const double2* r, double2* v0, cudaStream_t s) {
+  start_cycle_kernel<<<grid_blocks(n), kThreads, 0, s>>>(n, r, v0, st, st.m);
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
+int k_arnoldi(const KrylovState& st, const FineOp& op, const double* kap64, const void* z, Prec zp,
+              double2* w, const double2* V, long long vstride, int j, cudaStream_t s) {
+  const long long n = op.g.size;
+  const int bl = grid_blocks(n);
+  const int nv = j + 1;
+  const size_t sm = (size_t)(nv + 1) * kThreads * sizeof(double2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    const int lim = 200 * 1024;
+    cudaFuncSetAttribute(arnoldi_matvec_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(arnoldi_matvec_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(arnoldi_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    attr_set = true;
+  }
+  if (zp == P64)
+    arnoldi_matvec_kernel<double><<<bl, kThreads, sm, s>>>(op, kap64, (const double2*)z, w, V, vstride, nv,
+                                                          st.part, st.counter, st.h1);
+  else
+    arnoldi_matvec_kernel<float><<<bl, kThreads, sm, s>>>(op, kap64, (const float2*)z, w, V, vstride, nv,
+                                                         st.part, st.counter, st.h1);
+  HELM_LAUNCH_CHECK();
+  arnoldi_update_kernel<<<bl, kThreads, sm, s>>>(n, w, V, vstride, nv, st.h1, st.part, st.counter, st.h2);
+  HELM_LAUNCH_CHECK();
+  arnoldi_small_kernel<<<1, 32, 0, s>>>(st, j, st.m);
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
+int k_normalize(const KrylovState& st, long long n, const double2* w, const double2* V, long long vstride,
+                int j, double2* vout, cudaStream_t s) {
+  arnoldi_normalize_kernel<<<grid_blocks(n), kThreads, 0, s>>>(n, w, V, vstride, j + 1, st.h2,
+                                                               st.scal + KS_INV_HN, vout);
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
+int k_update_solution(const KrylovState& st, long long n, double2* x, const void* Z, Prec zp,
+                      long long zstride, int k, cudaStream_t s) {
+  lsq_kernel<<<1, 32, 0, s>>>(st, k, st.m);
+  HELM_LAUNCH_CHECK();
+  if (zp == P64)
+    solution_update_kernel<double><<<grid_blocks(n), kThreads, 0, s>>>(n, x, (const double2*)Z, zstride, k, st.y);
+  else
+    solution_update_kernel<float><<<grid_blocks(n), kThreads, 0, s>>>(n, x, (const float2*)Z, zstride, k, st.y);
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
+int k_true_residual(const KrylovState& st, const FineOp& op, const double* kap64, const double2* b,
+                    const double2* x, double2* r, cudaStream_t s) {
+  const int bl = grid_blocks(op.g.size);
+  true_residual_kernel<<<bl, kThreads, kThreads * sizeof(double2), s>>>(op, kap64, b, x, r, st.part,
+                                                                       st.counter, st.red);
+  HELM_LAUNCH_CHECK();
+  set_scalar_kernel<<<1, 32, 0, s>>>(st.scal + KS_BETA, st.red, 1);
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
+}  // namespace helm

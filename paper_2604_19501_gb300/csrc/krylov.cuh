@@ -1,0 +1,46 @@
+// Host-side launchers of the FGMRES kernels.
+#pragma once
+#include "common.cuh"
+#include "gridops.cuh"
+
+namespace helm {
+
+enum { KS_BNORM = 0, KS_BETA = 1, KS_HN = 2, KS_INV_HN = 3, KS_EST = 4, KS_COUNT = 8 };
+
+// Device-resident state of one FGMRES(m) solve (FP64).
+struct KrylovState {
+  int m = 0;
+  double2* H = nullptr;      // (m+1) x m Hessenberg, rotated in place
+  double2* g = nullptr;      // m+1 right-hand side of the least-squares problem
+  double2* sn = nullptr;     // m Givens sines
+  double* cs = nullptr;      // m Givens cosines
+  double2* y = nullptr;      // m least-squares solution
+  double2* h1 = nullptr;     // first Gram-Schmidt pass (+ ||w||^2)
+  double2* h2 = nullptr;     // second pass (+ ||w||^2)
+  double2* red = nullptr;    // reduction outputs
+  double* scal = nullptr;    // KS_* scalars
+  double2* part = nullptr;   // per-block partial sums
+  unsigned* counter = nullptr;
+};
+
+int krylov_alloc(KrylovState& st, int m);
+void krylov_free(KrylovState& st);
+
+// scal[KS_BNORM] = scal[KS_BETA] = ||b||; if copy_to, copy_to = b.
+int k_norm(const KrylovState& st, long long n, const double2* b, double2* copy_to, cudaStream_t s);
+// v0 = r / beta (beta = scal[KS_BETA]); g = (beta, 0, ...).
+int k_start_cycle(const KrylovState& st, long long n, const double2* r, double2* v0, cudaStream_t s);
+// Arnoldi step j from z_j (c128 or c64): w, H(:, j), rotations, estimate scal[KS_EST].
+int k_arnoldi(const KrylovState& st, const FineOp& op, const double* kap64, const void* z, Prec zp,
+              double2* w, const double2* V, long long vstride, int j, cudaStream_t s);
+// v_{j+1} = (w - V h2) / hn.
+int k_normalize(const KrylovState& st, long long n, const double2* w, const double2* V, long long vstride,
+                int j, double2* vout, cudaStream_t s);
+// y = R^-1 g (k x k) and x += Z y.
+int k_update_solution(const KrylovState& st, long long n, double2* x, const void* Z, Prec zp,
+                      long long zstride, int k, cudaStream_t s);
+// r = b - H x in FP64, scal[KS_BETA] = ||r||.
+int k_true_residual(const KrylovState& st, const FineOp& op, const double* kap64, const double2* b,
+                    const double2* x, double2* r, cudaStream_t s);
+
+}  // namespace helm

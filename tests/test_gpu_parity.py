@@ -1,0 +1,247 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle, element by element.
+
+Tolerances: the FP64 path within 1e-12 relative for single kernels and 1e-10 for
+solutions; the c64 kernels within 2e-5 relative (FP32 rounding of a few terms); the
+mixed-precision solve within 1e-5 relative of the FP64 oracle solution at a 1e-6
+relative residual, with the same iteration count +-1.
+"""
+import numpy as np
+import pytest
+
+from oracle import cycle as OC
+from oracle import krylov as OK
+from oracle import smoothers as OS
+from tests._cases import Case, rand_complex, rel, stencil_to_dense
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES_2D = [(16, 16), (12, 20), (32, 24), (4, 4), (40, 8)]
+CASES_3D = [(8, 8, 8), (8, 12, 16), (4, 4, 4)]
+
+
+def _t(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return t if dtype is None else t.to(dtype)
+
+
+def _n(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def cases():
+    out = {}
+    for n in CASES_2D + CASES_3D:
+        c = Case(n, abc=1 if min(n) <= 4 else 3, alpha2=1.02, alpha3=1.08, seed=sum(n))
+        out[n] = (c, c.solver())
+    yield out
+    for _, s in out.values():
+        s.close()
+
+
+@pytest.mark.parametrize("n", CASES_2D + CASES_3D)
+@pytest.mark.parametrize("level", [1, 2, 3])
+def test_apply_c128(cases, n, level):
+    c, s = cases[n]
+    x = rand_complex((2,) + c.hier.grids[level - 1].shape, seed=level)
+    y = _n(s.apply(level, _t(x)))
+    A = c.hier.A[level - 1]
+    ref = np.stack([(A @ xi.ravel()).reshape(xi.shape) for xi in x])
+    assert rel(y, ref) < 1e-12
+
+
+@pytest.mark.parametrize("n", [(32, 24), (8, 12, 16)])
+@pytest.mark.parametrize("level", [1, 2])
+def test_apply_c64(cases, n, level):
+    c, s = cases[n]
+    x = rand_complex(c.hier.grids[level - 1].shape, seed=3, dtype=np.complex64)
+    y = _n(s.apply(level, _t(x)))
+    ref = (c.hier.A[level - 1] @ x.astype(np.complex128).ravel()).reshape(x.shape)
+    assert rel(y, ref) < 2e-5
+
+
+@pytest.mark.parametrize("n", CASES_2D + CASES_3D)
+@pytest.mark.parametrize("level", [2, 3])
+def test_assembled_stencils(cases, n, level):
+    """Galerkin level 2 with the alpha2 shift and the real-shifted level 3 against the
+    oracle's sparse products (Eqs. Galerkin, realShift, CoarseRealShifted)."""
+    c, s = cases[n]
+    coef, r = s.stencil(level)
+    assert r == 1
+    A = stencil_to_dense(coef, r, c.hier.grids[level - 1])
+    ref = c.hier.A[level - 1].toarray()
+    assert rel(A, ref) < 1e-12
+
+
+@pytest.mark.parametrize("n", CASES_2D + CASES_3D)
+def test_residual(cases, n):
+    c, s = cases[n]
+    b = rand_complex(c.grid.shape, 1)
+    x = rand_complex(c.grid.shape, 2)
+    r = _n(s.residual(1, _t(b), _t(x)))
+    ref = b - (c.hier.A[0] @ x.ravel()).reshape(x.shape)
+    assert rel(r, ref) < 1e-12
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "rb"])
+@pytest.mark.parametrize("level", [1, 2])
+@pytest.mark.parametrize("n", [(12, 20), (8, 12, 16)])
+def test_smoother_sweep(n, level, smoother):
+    c = Case(n, alpha2=1.02, alpha3=1.08, seed=5)
+    s = c.solver(smoother=smoother, jacobi_w=(0.8, 0.7), rb_w=0.9)
+    g = c.hier.grids[level - 1]
+    b = rand_complex(g.shape, 7)
+    x = rand_complex(g.shape, 8)
+    got = _n(s.smooth(level, _t(b), _t(x)))
+    A, d = c.hier.A[level - 1], c.hier.diag[level - 1]
+    if smoother == "jacobi":
+        ref = OS.jacobi(A, d, x.ravel(), b.ravel(), (0.8, 0.7)[level - 1])
+    else:
+        ref = OS.red_black(A, d, x.ravel(), b.ravel(), OS.colours(g), 0.9)
+    assert rel(got.ravel(), ref) < 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("n", CASES_2D + CASES_3D)
+@pytest.mark.parametrize("level", [1, 2])
+def test_transfers(cases, n, level):
+    c, s = cases[n]
+    gf, gc = c.hier.grids[level - 1], c.hier.grids[level]
+    rf = rand_complex(gf.shape, 11)
+    rc = _n(s.restrict(level, _t(rf)))
+    assert rel(rc.ravel(), c.hier.R[level - 1] @ rf.ravel()) < 1e-13
+    ec = rand_complex(gc.shape, 12)
+    xf = rand_complex(gf.shape, 13)
+    out = _n(s.prolong_add(level, _t(ec), _t(xf)))
+    assert rel(out.ravel(), xf.ravel() + c.hier.P[level - 1] @ ec.ravel()) < 1e-13
+    rc32 = _n(s.restrict(level, _t(rf.astype(np.complex64))))
+    assert rel(rc32.ravel(), c.hier.R[level - 1] @ rf.astype(np.complex64).ravel()) < 1e-6
+
+
+@pytest.mark.parametrize("n", CASES_2D + CASES_3D)
+def test_coarse_solve(cases, n):
+    """Nested-dissection direct solve of the real-shifted coarsest operator."""
+    c, s = cases[n]
+    b = rand_complex((2,) + c.hier.grids[2].shape, 21)
+    e = _n(s.coarse_solve(_t(b)))
+    ref = np.stack([c.hier.coarse_solve(bi.ravel()).reshape(bi.shape) for bi in b])
+    assert rel(e, ref) < 1e-10
+    res = np.stack([(c.hier.A[2] @ ei.ravel()).reshape(ei.shape) for ei in e]) - b
+    assert np.max(np.abs(res)) < 1e-10 * np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("cyc", ["V", "W"])
+@pytest.mark.parametrize("smoother", ["jacobi", "rb"])
+@pytest.mark.parametrize("n", [(32, 24), (8, 12, 16), (4, 4)])
+def test_cycle_fp64(n, cyc, smoother):
+    c = Case(n, abc=1 if min(n) <= 4 else 3, alpha2=1.0, alpha3=1.1, seed=9)
+    s = c.solver(cycle=cyc, smoother=smoother, jacobi_w=(0.8, 0.75), rb_w=0.95, nu=(1, 2))
+    cy = OC.Cycle(c.hier, cycle=cyc, nu1=1, nu2=2, smoother=smoother, weights=(0.8, 0.75), rb_weight=0.95)
+    v = rand_complex((2,) + c.grid.shape, 31)
+    z = _n(s.cycle(_t(v)))
+    ref = np.stack([cy(vi.ravel()).reshape(vi.shape) for vi in v])
+    assert rel(z, ref) < 1e-10
+    s.close()
+
+
+@pytest.mark.parametrize("n", [(32, 24), (8, 12, 16)])
+def test_cycle_mixed(n):
+    c = Case(n, alpha3=1.1, seed=10)
+    s = c.solver(precision="mixed")
+    v = rand_complex(c.grid.shape, 32)
+    z = _n(s.cycle(_t(v)))
+    ref = OC.Cycle(c.hier)(v.ravel()).reshape(v.shape)
+    assert rel(z, ref) < 1e-5
+    s.close()
+
+
+def _oracle_solve(c, q, restart=10, cyc="V", tol=1e-6, maxit=400):
+    cy = OC.Cycle(c.hier, cycle=cyc)
+    return OK.fgmres(lambda v: c.hier.A[0] @ v, q.ravel(), cy, tol=tol, maxit=maxit, restart=restart)
+
+
+def _point_source(c):
+    import workloads
+
+    return workloads.point_source(c.n)
+
+
+@pytest.mark.parametrize("n,cyc", [((128, 128), "V"), ((64, 96), "W"), ((16, 16, 24), "V")])
+def test_solve_fp64_matches_oracle(n, cyc):
+    """Config-1-like solves: identical iteration counts and solutions within 1e-10."""
+    import workloads
+
+    kappa2 = workloads.constant_medium(n) if len(n) == 2 and n[0] == 128 else None
+    c = Case(n, abc=16 if n[0] == 128 else 4, alpha3=1.117, kappa2=kappa2, G_ppw=12, seed=3)
+    s = c.solver(cycle=cyc)
+    q = _point_source(c)
+    p, st = s.solve(_t(q), tol=1e-6, maxit=400)
+    xo, info = _oracle_solve(c, q, cyc=cyc)
+    assert st[0]["converged"] and info["converged"]
+    assert st[0]["iterations"] == info["iterations"]
+    assert rel(_n(p).ravel(), xo) < 1e-10
+    s.close()
+
+
+def test_solve_mixed_matches_oracle():
+    import workloads
+
+    n = (128, 128)
+    c = Case(n, abc=16, alpha3=1.117, kappa2=workloads.constant_medium(n), G_ppw=12)
+    s = c.solver(precision="mixed")
+    q = _point_source(c)
+    p, st = s.solve(_t(q), tol=1e-6, maxit=400)
+    xo, info = _oracle_solve(c, q)
+    assert st[0]["converged"]
+    assert abs(st[0]["iterations"] - info["iterations"]) <= 1
+    assert rel(_n(p).ravel(), xo) < 1e-5
+    s.close()
+
+
+def test_solve_host_pointers_and_batch():
+    """Host numpy buffers are staged through the device; a batch of right-hand sides
+    gives the same answers as separate solves."""
+    c = Case((32, 32), alpha3=1.1, seed=4)
+    s = c.solver()
+    q = rand_complex((3,) + c.grid.shape, 41)
+    p_host, st_host = s.solve(q.copy(), tol=1e-8, maxit=200)
+    p_dev, st_dev = s.solve(_t(q), tol=1e-8, maxit=200)
+    assert np.array_equal(p_host, _n(p_dev))
+    for i in range(3):
+        pi, sti = s.solve(_t(q[i]), tol=1e-8, maxit=200)
+        assert np.array_equal(_n(pi), p_host[i])
+        assert sti[0]["iterations"] == st_host[i]["iterations"]
+        xo, info = _oracle_solve(c, q[i], tol=1e-8, maxit=200)
+        assert info["iterations"] == sti[0]["iterations"]
+    s.close()
+
+
+def test_restart_and_maxit():
+    c = Case((32, 32), alpha3=1.1, seed=6)
+    s = c.solver(restart=3)
+    q = _point_source(c)
+    p, st = s.solve(_t(q), tol=1e-8, maxit=300)
+    xo, info = _oracle_solve(c, q, restart=3, tol=1e-8, maxit=300)
+    assert st[0]["iterations"] == info["iterations"]
+    assert rel(_n(p).ravel(), xo) < 1e-10
+    p2, st2 = s.solve(_t(q), tol=1e-12, maxit=2)
+    assert st2[0]["iterations"] == 2 and not st2[0]["converged"]
+    s.close()
+
+
+def test_zero_rhs_and_errors():
+    from paper_2604_19501_gb300 import HelmError
+
+    c = Case((16, 16), seed=7)
+    s = c.solver()
+    p, st = s.solve(_t(np.zeros(c.grid.shape, np.complex128)))
+    assert st[0]["iterations"] == 0 and np.all(_n(p) == 0)
+    bad = c.kappa2.copy()
+    bad[3, 3] = np.nan
+    with pytest.raises(HelmError):
+        Case((16, 16), kappa2=bad).solver()
+    with pytest.raises(HelmError):
+        Case((18, 16)).solver()
+    s.close()
