@@ -65,8 +65,10 @@ typedef struct {
   double abc_gamma_max;   /* gamma = gamma_max * sum_axes (d/L)^2, d = depth into the layer */
   double alpha2;          /* real shift of level 2 (1 = plain Galerkin, the paper's method) */
   double alpha3;          /* real shift of the coarsest level (Eq. CoarseRealShifted) */
-  int stencil;            /* helm_stencil; HELM_STENCIL_2ND = 5-point (2D) / 7-point (3D) */
-  int intergrid;          /* helm_intergrid; HELM_INTERGRID_FW = full weighting + (bi/tri)linear */
+  int stencil;            /* helm_stencil; HELM_STENCIL_2ND = 5-point (2D) / 7-point (3D);
+                             HELM_STENCIL_4TH = compact 9-point / 19-point (Eqs. disc4thCompact(3D)) */
+  int intergrid;          /* helm_intergrid; HELM_INTERGRID_FW = full weighting + (bi/tri)linear;
+                             CUBIC = Eq. intergrid on both levels (2D only); LEVDEP = Eq. levdep */
   int cycle;              /* helm_cycle_kind */
   int nu1, nu2;           /* pre- / post-smoothing sweeps */
   int smoother;           /* helm_smoother */
@@ -169,6 +171,31 @@ int helm_cycle(helm_ctx* c, const void* v, void* z, int n_rhs);
 
 /* Number of kernel launches this context has issued so far (all entry points). */
 long long helm_launch_count(const helm_ctx* c);
+
+/* ---- Launch timer (tracing) ---- */
+
+/* Kernel classes of the launch timer. */
+typedef enum {
+  HELM_K_FINE = 0,          /* level-1 cycle kernels: smoothing / residual on the fine grid */
+  HELM_K_STENCIL = 1,       /* level-2/3 assembled-stencil smoothing / residual */
+  HELM_K_TRANSFER = 2,      /* restriction, prolongation, precision conversion */
+  HELM_K_COARSE = 3,        /* coarsest-level direct solve (forward + backward sweeps) */
+  HELM_K_ARNOLDI_MATVEC = 4,/* w = H z fused with the first Gram-Schmidt pass */
+  HELM_K_ARNOLDI_UPDATE = 5,/* w <- w - V h fused with the re-orthogonalisation pass */
+  HELM_K_ARNOLDI_NORM = 6,  /* v_{j+1} = (w - V h) / ||.|| */
+  HELM_K_KRYLOV_OTHER = 7,  /* solution update, true residual, norms, Givens */
+  HELM_K_SETUP = 8,         /* Galerkin assembly and coarsest factorisation */
+  HELM_K_COUNT = 9
+} helm_kernel_class;
+
+/* Starts timing (CUDA event pairs on the context stream) every launch of the
+ * classes whose bit (1 << class) is set in mask, after clearing the totals;
+ * mask = 0 stops timing.  Timing adds two event records per timed launch. */
+int helm_timer_enable(helm_ctx* c, unsigned mask);
+
+/* Waits for the timed launches and returns the summed device time (ms) and the
+ * number of timed launches of class cls.  Synchronises the stream. */
+int helm_timer_read(helm_ctx* c, int cls, double* total_ms, long long* launches);
 
 const char* helm_strerror(int status);
 const char* helm_last_error(void);

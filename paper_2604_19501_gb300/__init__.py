@@ -96,6 +96,23 @@ class Solver:
         """Kernel launches issued by this context so far."""
         return int(_lib.helm_launch_count(self._ctx))
 
+    def timer_enable(self, classes=None):
+        """Time every launch of the named kernel classes (all when None)."""
+        names = _ffi.KERNEL_CLASSES if classes is None else classes
+        mask = 0
+        for nme in names:
+            mask |= 1 << _ffi.KERNEL_CLASSES.index(nme)
+        check(_lib.helm_timer_enable(self._ctx, mask), "helm_timer_enable")
+
+    def timer_read(self):
+        """{class: (total device ms, launches)} of the timed launches."""
+        out = {}
+        for i, nme in enumerate(_ffi.KERNEL_CLASSES):
+            ms, cnt = ctypes.c_double(), ctypes.c_longlong()
+            check(_lib.helm_timer_read(self._ctx, i, ctypes.byref(ms), ctypes.byref(cnt)), "helm_timer_read")
+            out[nme] = (ms.value, cnt.value)
+        return out
+
     # ------------------------------------------------------------------ solves
     def _nrhs(self, x, level=1):
         return x.numel() // _numel(self.shape(level)) if hasattr(x, "numel") else x.size // _numel(self.shape(level))

@@ -12,6 +12,7 @@
 #include "galerkin.cuh"
 #include "gridops.cuh"
 #include "krylov.cuh"
+#include "timer.cuh"
 
 namespace helm {
 
@@ -58,14 +59,22 @@ struct helm_ctx {
   long long stage_cap = 0;
   long long launches = 0;
   int* d_bad = nullptr;
+  LaunchTimer timer;
 };
 
 namespace {
 
 struct LaunchScope {
   long long* prev;
-  explicit LaunchScope(helm_ctx* c) : prev(g_launch_counter) { g_launch_counter = c ? &c->launches : nullptr; }
-  ~LaunchScope() { g_launch_counter = prev; }
+  LaunchTimer* prev_timer;
+  explicit LaunchScope(helm_ctx* c) : prev(g_launch_counter), prev_timer(g_timer) {
+    g_launch_counter = c ? &c->launches : nullptr;
+    g_timer = c ? &c->timer : nullptr;
+  }
+  ~LaunchScope() {
+    g_launch_counter = prev;
+    g_timer = prev_timer;
+  }
 };
 
 int fail(int code, const std::string& msg) {
@@ -329,8 +338,11 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
     if (o->abc_width[f] < 0 || o->abc_width[f] > o->n[f / 2]) return fail(HELM_EINVAL, "bad absorbing-layer width");
   if (!std::isfinite(o->alpha2) || !std::isfinite(o->alpha3) || !std::isfinite(o->abc_gamma_max))
     return fail(HELM_EINVAL, "non-finite shift or layer amplitude");
-  if (o->stencil != HELM_STENCIL_2ND) return fail(HELM_EINVAL, "stencil not built");
-  if (o->intergrid != HELM_INTERGRID_FW) return fail(HELM_EINVAL, "intergrid transfer not built");
+  if (o->stencil != HELM_STENCIL_2ND && o->stencil != HELM_STENCIL_4TH) return fail(HELM_EINVAL, "bad stencil");
+  if (o->intergrid < HELM_INTERGRID_FW || o->intergrid > HELM_INTERGRID_LEVDEP)
+    return fail(HELM_EINVAL, "bad intergrid transfer");
+  if (o->dim == 3 && o->intergrid == HELM_INTERGRID_CUBIC)
+    return fail(HELM_EINVAL, "3D cubic transfers (343-point coarsest stencil) are not built; use lev-dep");
   if (o->cycle != HELM_CYCLE_V && o->cycle != HELM_CYCLE_W) return fail(HELM_EINVAL, "bad cycle");
   if (o->smoother != HELM_SMOOTHER_JACOBI && o->smoother != HELM_SMOOTHER_REDBLACK)
     return fail(HELM_EINVAL, "bad smoother");
@@ -388,19 +400,26 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
   c->h_gam = new double[tot];
   std::memcpy(c->h_gam, gam.data(), tot * sizeof(double));
   c->fine.g = c->g[0];
-  c->fine.order = 0;
+  c->fine.order = o->stencil == HELM_STENCIL_4TH ? 1 : 0;
   c->fine.inv_h2 = 1.0 / (o->h * o->h);
   c->fine.omega2 = o->omega * o->omega;
   c->fine.gam[0] = c->d_gam;
   c->fine.gam[1] = c->d_gam + c->g[0].N[0];
   c->fine.gam[2] = c->d_gam + c->g[0].N[0] + c->g[0].N[1];
 
-  c->tR1 = c->tP1 = c->tR2 = c->tP2 = make_transfer(0);
+  // transfers: full weighting / linear everywhere (FW); the cubic stencil of Eq.
+  // intergrid everywhere (cubic); cubic except the restriction to level 3 (Eq. levdep)
+  const int cubic1 = o->intergrid != HELM_INTERGRID_FW;
+  c->tR1 = c->tP1 = make_transfer(cubic1);
+  c->tR2 = make_transfer(o->intergrid == HELM_INTERGRID_CUBIC);
+  c->tP2 = make_transfer(cubic1);
+  const int r2 = (c->tR1.radius + 1 + c->tP1.radius) / 2;
+  const int r3 = (c->tR2.radius + r2 + c->tP2.radius) / 2;
+  auto ncoef = [&](int r) { const int w = 2 * r + 1; return o->dim == 3 ? w * w * w : w * w; };
 
   // level 2: H_2h = R1 H_h P1 and the real mass part R1 omega^2 kappa^2 M P1
   const long long n2 = c->g[1].size, n3 = c->g[2].size;
-  const int W = 3;
-  c->nc2 = o->dim == 3 ? W * W * W : W * W;
+  c->nc2 = ncoef(r2);
   double2* H20 = nullptr;
   if (int st = dmalloc(&H20, c->nc2 * n2 * sizeof(double2))) return bail(st);
   if (int st = dmalloc(&c->Mk2, c->nc2 * n2 * sizeof(double))) { cudaFree(H20); return bail(st); }
@@ -412,7 +431,7 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
     cudaFree(H20); return bail(HELM_ECUDA);
   }
   // level 3: R2 (H_2h + (1 - alpha3^2) R1 K P1) P2 (Eq. CoarseRealShifted)
-  c->nc3 = c->nc2;
+  c->nc3 = ncoef(r3);
   if ((st = dmalloc(&c->A3_64, c->nc3 * n3 * sizeof(double2)))) { cudaFree(H20); return bail(st); }
   st = assemble_level3(c->g[1], c->r2, H20, c->Mk2, 1.0 - o->alpha3 * o->alpha3, c->g[2], c->tR2.radius,
                        c->tP2.radius, c->A3_64, &c->r3, c->s);
@@ -588,6 +607,21 @@ int helm_cycle(helm_ctx* c, const void* v, void* z, int n_rhs) {
 }
 
 long long helm_launch_count(const helm_ctx* c) { return c ? c->launches : 0; }
+
+int helm_timer_enable(helm_ctx* c, unsigned mask) {
+  if (!c) return fail(HELM_EINVAL, "null context");
+  c->timer.reset();
+  c->timer.mask = mask;
+  return HELM_OK;
+}
+
+int helm_timer_read(helm_ctx* c, int cls, double* total_ms, long long* launches) {
+  if (!c || cls < 0 || cls >= HELM_K_COUNT) return fail(HELM_EINVAL, "bad timer class");
+  c->timer.resolve();
+  if (total_ms) *total_ms = c->timer.total_ms[cls];
+  if (launches) *launches = c->timer.count[cls];
+  return HELM_OK;
+}
 
 const char* helm_strerror(int status) {
   switch (status) {

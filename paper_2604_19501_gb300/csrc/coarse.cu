@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <unordered_map>
 #include "coarse.cuh"
+#include "timer.cuh"
 
 namespace helm {
 
@@ -481,6 +482,7 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
   double2 *d_aug = nullptr, *d_upool = nullptr;
   HELM_CUDA_TRY(cudaMalloc(&d_aug, std::max<long long>(1, aug_max) * sizeof(double2)));
   HELM_CUDA_TRY(cudaMalloc(&d_upool, std::max<long long>(1, uoff) * sizeof(double2)));
+  KernelTimer kt(HELM_K_SETUP, s);
   for (int h = 0; h < cs.nlevels; ++h) {
     const int nf = (int)cs.level_fronts[h].size();
     fact_assemble_kernel<<<nf, 256, 0, s>>>(cs.d_desc, cs.d_level_list[h], d_aug, d_ents, coef, d_upool,
@@ -515,6 +517,7 @@ static int ensure_rhs(CoarseSolver& cs, int nrhs) {
 
 int coarse_solve(CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaStream_t s) {
   if (int st = ensure_rhs(cs, nrhs)) return st;
+  KernelTimer kt(HELM_K_COARSE, s);
   for (int h = 0; h < cs.nlevels; ++h) {
     const int nf = (int)cs.level_fronts[h].size();
     fwd_assemble_kernel<<<nf, 256, 0, s>>>(cs.d_desc, cs.d_level_list[h], cs.d_S, cs.d_kids, cs.d_cmap, b,

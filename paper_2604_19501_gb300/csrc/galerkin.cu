@@ -8,31 +8,56 @@
 // that the coarsest shift can be applied by linearity:
 //   H_4h^alpha = R2 (H_2h + (1 - alpha^2) R1 omega^2 kappa^2 M P1) P2   (Eq. realShiftMeaning).
 #include "galerkin.cuh"
+#include "timer.cuh"
 
 namespace helm {
 
 __constant__ double c_rap_w[2][5] = {{0.25, 0.5, 0.25, 0.0, 0.0},
                                      {1.0 / 16, 4.0 / 16, 6.0 / 16, 4.0 / 16, 1.0 / 16}};
 
-// Rows of the fine operator, computed from kappa^2 and the absorbing profile.
+// Rows of the fine operator, computed from kappa^2 and the absorbing profile: the
+// 2nd-order 5/7-point stencil, or the compact 4th-order 9/19-point stencils of Eqs.
+// disc4thCompact / disc4thCompact3D with the coefficient mean (c_i + c_j) / 2 on every
+// mass coupling.  a: the operator entry; m: its real mass part omega^2 kappa^2 M.
 struct FineRows {
   FineOp op;
   const double* kap;
+  __device__ __forceinline__ double gam_at(int ii, int jj, int kk) const {
+    return op.gam[0][ii] + op.gam[1][jj] + (op.g.dim == 3 ? op.gam[2][kk] : 0.0);
+  }
   __device__ __forceinline__ void get(long long i, int ii, int jj, int kk, int bx, int by, int bz,
                                       double2& a, double& m) const {
     const int nz = abs(bx) + abs(by) + abs(bz);
-    if (nz == 0) {
-      const double gam = op.gam[0][ii] + op.gam[1][jj] + (op.g.dim == 3 ? op.gam[2][kk] : 0.0);
-      const double cre = op.omega2 * kap[i];
-      a = make_double2(2.0 * op.g.dim * op.inv_h2 - cre, cre * gam);
-      m = cre;
+    const bool is3 = op.g.dim == 3;
+    double lap, mw;
+    if (op.order == 0) {
+      lap = nz == 0 ? 2.0 * op.g.dim * op.inv_h2 : (nz == 1 ? -op.inv_h2 : 0.0);
+      mw = nz == 0 ? 1.0 : 0.0;
+    } else if (nz == 0) {
+      lap = (is3 ? 4.0 : 20.0 / 6.0) * op.inv_h2;
+      mw = is3 ? 6.0 / 12.0 : 8.0 / 12.0;
     } else if (nz == 1) {
-      a = make_double2(-op.inv_h2, 0.0);
-      m = 0.0;
+      lap = (is3 ? -2.0 / 6.0 : -4.0 / 6.0) * op.inv_h2;
+      mw = 1.0 / 12.0;
+    } else if (nz == 2) {
+      lap = -op.inv_h2 / 6.0;
+      mw = 0.0;
     } else {
-      a = make_double2(0.0, 0.0);
-      m = 0.0;
+      lap = 0.0;
+      mw = 0.0;
     }
+    if (mw == 0.0) {
+      a = make_double2(lap, 0.0);
+      m = 0.0;
+      return;
+    }
+    const long long j = i + bx + (long long)by * op.g.N[0] + (long long)bz * op.g.N[0] * op.g.N[1];
+    const double ki = op.omega2 * kap[i], kj = op.omega2 * kap[j];
+    const double gi = gam_at(ii, jj, kk), gj = gam_at(ii + bx, jj + by, kk + bz);
+    // c = k^2 (1 - i gamma); mean of the two coupled nodes
+    const double cre = 0.5 * (ki + kj), cim = -0.5 * (ki * gi + kj * gj);
+    a = make_double2(lap - mw * cre, -mw * cim);
+    m = mw * cre;
   }
 };
 
@@ -146,6 +171,7 @@ template <class Rows, int DIM, int RR, int RP, int RA, int RC>
 static int rap_launch(const Rows& rows, const GridDims& gf, const GridDims& gc, double2* h, double* m,
                       cudaStream_t s) {
   const int th = 128;
+  KernelTimer kt(HELM_K_SETUP, s);
   rap_kernel<Rows, DIM, RR, RP, RA, RC><<<blocks_for(gc.size, th), th, 0, s>>>(rows, gf, gc, h, m);
   HELM_LAUNCH_CHECK();
   return 0;
@@ -154,14 +180,15 @@ static int rap_launch(const Rows& rows, const GridDims& gf, const GridDims& gc, 
 int assemble_level2(const FineOp& op, const double* kappa2, const GridDims& gc, int rR, int rP,
                     double2* h, double* mk, int* rc_out, cudaStream_t s) {
   FineRows rows{op, kappa2};
-  const int ra = 1;
-  const int rc = (rR + ra + rP) / 2;
+  const int rc = (rR + 1 + rP) / 2;
   *rc_out = rc;
-  if (op.order != 0) { set_error("fine stencil order not built"); return 1; }
-  if (rR == 1 && rP == 1) {
-    if (op.g.dim == 2) return rap_launch<FineRows, 2, 1, 1, 1, 1>(rows, op.g, gc, h, mk, s);
-    return rap_launch<FineRows, 3, 1, 1, 1, 1>(rows, op.g, gc, h, mk, s);
-  }
+  const bool d2 = op.g.dim == 2;
+  if (rR == 1 && rP == 1)
+    return d2 ? rap_launch<FineRows, 2, 1, 1, 1, 1>(rows, op.g, gc, h, mk, s)
+              : rap_launch<FineRows, 3, 1, 1, 1, 1>(rows, op.g, gc, h, mk, s);
+  if (rR == 2 && rP == 2)
+    return d2 ? rap_launch<FineRows, 2, 2, 2, 1, 2>(rows, op.g, gc, h, mk, s)
+              : rap_launch<FineRows, 3, 2, 2, 1, 2>(rows, op.g, gc, h, mk, s);
   set_error("transfer combination not built");
   return 1;
 }
@@ -171,10 +198,15 @@ int assemble_level3(const GridDims& g2, int r2, const double2* h2, const double*
   StoredRows rows{g2, r2, h2, mk2, shift};
   const int rc = (rR + r2 + rP) / 2;
   *rc_out = rc;
-  if (rR == 1 && rP == 1 && r2 == 1) {
-    if (g2.dim == 2) return rap_launch<StoredRows, 2, 1, 1, 1, 1>(rows, g2, g3, h3, nullptr, s);
-    return rap_launch<StoredRows, 3, 1, 1, 1, 1>(rows, g2, g3, h3, nullptr, s);
-  }
+  const bool d2 = g2.dim == 2;
+  if (rR == 1 && rP == 1 && r2 == 1)
+    return d2 ? rap_launch<StoredRows, 2, 1, 1, 1, 1>(rows, g2, g3, h3, nullptr, s)
+              : rap_launch<StoredRows, 3, 1, 1, 1, 1>(rows, g2, g3, h3, nullptr, s);
+  if (rR == 2 && rP == 2 && r2 == 2 && d2)
+    return rap_launch<StoredRows, 2, 2, 2, 2, 3>(rows, g2, g3, h3, nullptr, s);
+  if (rR == 1 && rP == 2 && r2 == 2)
+    return d2 ? rap_launch<StoredRows, 2, 1, 2, 2, 2>(rows, g2, g3, h3, nullptr, s)
+              : rap_launch<StoredRows, 3, 1, 2, 2, 2>(rows, g2, g3, h3, nullptr, s);
   set_error("transfer combination not built");
   return 1;
 }

@@ -8,6 +8,7 @@
 // batch.
 #include "gridops.cuh"
 #include "fineop.cuh"
+#include "timer.cuh"
 
 namespace helm {
 
@@ -39,7 +40,7 @@ __global__ void __launch_bounds__(256) fine_row_kernel(FineOp op, const T* __res
     } else if (MODE == MODE_RB && !active) {
       out = cvt<T>(x[p]);
     } else {
-      const c2<T> Ax = fine_apply_at<T, TX>(op, diag, x, p, i, j, k);
+      const c2<T> Ax = fine_apply_at<T, TX>(op, diag, x, p, idx, i, j, k, kap);
       if (MODE == MODE_APPLY) {
         out = Ax;
       } else {
@@ -61,6 +62,7 @@ static int fine_dispatch(const FineOp& op, int mode, const void* kap, const void
   auto X = (const c2<TX>*)x;
   auto B = (const c2<TB>*)b;
   auto Y = (c2<TY>*)y;
+  KernelTimer kt(HELM_K_FINE, s);
   switch (mode) {
     case MODE_APPLY: fine_row_kernel<T, TX, TB, TY, MODE_APPLY><<<bl, th, 0, s>>>(op, K, X, B, Y, nrhs, (T)w, colour); break;
     case MODE_RESID: fine_row_kernel<T, TX, TB, TY, MODE_RESID><<<bl, th, 0, s>>>(op, K, X, B, Y, nrhs, (T)w, colour); break;
@@ -76,7 +78,6 @@ static int fine_dispatch(const FineOp& op, int mode, const void* kap, const void
 int launch_fine_row(const FineOp& op, int mode, Prec arith, Prec xs, Prec bs, Prec ys,
                     const void* kappa2, const void* x, const void* b, void* y, int nrhs,
                     double w, int colour, cudaStream_t s) {
-  if (op.order != 0) { set_error("fine stencil order not built"); return 1; }
   if (arith == P64) {
     if (xs != P64 || bs != P64 || ys != P64) { set_error("FP64 row kernel needs c128 storage"); return 1; }
     return fine_dispatch<double, double, double, double>(op, mode, kappa2, x, b, y, nrhs, w, colour, s);
@@ -88,104 +89,29 @@ int launch_fine_row(const FineOp& op, int mode, Prec arith, Prec xs, Prec bs, Pr
 }
 
 // --------------------------------------------------------------- assembled stencils
-template <typename T, typename TX, typename TB, typename TY, int MODE, int DIM, int R>
-__global__ void __launch_bounds__(256) stencil_row_kernel(GridDims g, const c2<T>* __restrict__ coef,
-                                                          const c2<T>* __restrict__ dinvp,
-                                                          const c2<TX>* __restrict__ x,
-                                                          const c2<TB>* __restrict__ b,
-                                                          c2<TY>* __restrict__ y, int nrhs, T w,
-                                                          int colour) {
-  constexpr int W = 2 * R + 1;
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= g.size) return;
-  int i, j, k;
-  node_coords(g, idx, i, j, k);
-  const long long N = g.size;
-  const long long sy = g.N[0];
-  const long long sz = (long long)g.N[0] * g.N[1];
-  const c2<T> dinv = dinvp[idx];
-  const bool active = (MODE != MODE_RB) || (((i + j + k) & 1) == colour);
-  for (int r = 0; r < nrhs; ++r) {
-    const long long p = r * N + idx;
-    c2<T> out;
-    if (MODE == MODE_JACOBI0) {
-      out = cscale(cmul(dinv, cvt<T>(b[p])), w);
-    } else if (MODE == MODE_RB && !active) {
-      out = cvt<T>(x[p]);
-    } else {
-      c2<T> Ax = mk<T>(0, 0);
-#pragma unroll
-      for (int dz = (DIM == 3 ? -R : 0); dz <= (DIM == 3 ? R : 0); ++dz) {
-        if (k + dz < 0 || k + dz >= g.N[2]) continue;
-#pragma unroll
-        for (int dy = -R; dy <= R; ++dy) {
-          if (j + dy < 0 || j + dy >= g.N[1]) continue;
-#pragma unroll
-          for (int dx = -R; dx <= R; ++dx) {
-            if (i + dx < 0 || i + dx >= g.N[0]) continue;
-            const int o = (dx + R) + W * ((dy + R) + W * (DIM == 3 ? dz + R : 0));
-            Ax = cmac(Ax, coef[o * N + idx], cvt<T>(x[p + dx + dy * sy + dz * sz]));
-          }
-        }
-      }
-      if (MODE == MODE_APPLY) {
-        out = Ax;
-      } else {
-        const c2<T> res = cvt<T>(b[p]) - Ax;
-        if (MODE == MODE_RESID) out = res;
-        else out = cvt<T>(x[p]) + cscale(cmul(dinv, res), w);
-      }
-    }
-    y[p] = cvt<TY>(out);
-  }
-}
-
-template <typename T, typename TX, typename TB, typename TY, int DIM, int R>
-static int stencil_dispatch_mode(const GridDims& g, const void* coef, const void* dinv, int mode,
-                                 const void* x, const void* b, void* y, int nrhs, double w,
-                                 int colour, cudaStream_t s) {
-  const int th = 256;
-  const int bl = blocks_for(g.size, th);
-  auto C = (const c2<T>*)coef;
-  auto D = (const c2<T>*)dinv;
-  auto X = (const c2<TX>*)x;
-  auto B = (const c2<TB>*)b;
-  auto Y = (c2<TY>*)y;
-  switch (mode) {
-    case MODE_APPLY: stencil_row_kernel<T, TX, TB, TY, MODE_APPLY, DIM, R><<<bl, th, 0, s>>>(g, C, D, X, B, Y, nrhs, (T)w, colour); break;
-    case MODE_RESID: stencil_row_kernel<T, TX, TB, TY, MODE_RESID, DIM, R><<<bl, th, 0, s>>>(g, C, D, X, B, Y, nrhs, (T)w, colour); break;
-    case MODE_JACOBI: stencil_row_kernel<T, TX, TB, TY, MODE_JACOBI, DIM, R><<<bl, th, 0, s>>>(g, C, D, X, B, Y, nrhs, (T)w, colour); break;
-    case MODE_JACOBI0: stencil_row_kernel<T, TX, TB, TY, MODE_JACOBI0, DIM, R><<<bl, th, 0, s>>>(g, C, D, X, B, Y, nrhs, (T)w, colour); break;
-    case MODE_RB: stencil_row_kernel<T, TX, TB, TY, MODE_RB, DIM, R><<<bl, th, 0, s>>>(g, C, D, X, B, Y, nrhs, (T)w, colour); break;
-    default: set_error("bad row mode"); return 1;
-  }
-  HELM_LAUNCH_CHECK();
-  return 0;
-}
-
-template <typename T, typename TX, typename TB, typename TY>
-static int stencil_dispatch(const GridDims& g, int r, const void* coef, const void* dinv, int mode,
-                            const void* x, const void* b, void* y, int nrhs, double w, int colour,
-                            cudaStream_t s) {
-  if (g.dim == 2 && r == 1)
-    return stencil_dispatch_mode<T, TX, TB, TY, 2, 1>(g, coef, dinv, mode, x, b, y, nrhs, w, colour, s);
-  if (g.dim == 3 && r == 1)
-    return stencil_dispatch_mode<T, TX, TB, TY, 3, 1>(g, coef, dinv, mode, x, b, y, nrhs, w, colour, s);
-  set_error("stencil radius not built for this dimension");
-  return 1;
-}
+template <int DIM, int R>
+int stencil_rows(Prec arith, const GridDims& g, const void* coef, const void* dinv, int mode, Prec bs,
+                 const void* x, const void* b, void* y, int nrhs, double w, int colour, cudaStream_t s);
 
 int launch_stencil_row(const GridDims& g, int r, Prec arith, const void* coef, const void* dinv,
                        int mode, Prec xs, Prec bs, Prec ys, const void* x, const void* b, void* y,
                        int nrhs, double w, int colour, cudaStream_t s) {
   if (arith == P64) {
     if (xs != P64 || bs != P64 || ys != P64) { set_error("FP64 row kernel needs c128 storage"); return 1; }
-    return stencil_dispatch<double, double, double, double>(g, r, coef, dinv, mode, x, b, y, nrhs, w, colour, s);
+  } else if (xs != P32 || ys != P32) {
+    set_error("FP32 row kernel needs c64 x/y");
+    return 1;
   }
-  if (xs != P32 || ys != P32) { set_error("FP32 row kernel needs c64 x/y"); return 1; }
-  if (bs == P64)
-    return stencil_dispatch<float, float, double, float>(g, r, coef, dinv, mode, x, b, y, nrhs, w, colour, s);
-  return stencil_dispatch<float, float, float, float>(g, r, coef, dinv, mode, x, b, y, nrhs, w, colour, s);
+#define HELM_STENCIL_CASE(D, RR) \
+  if (g.dim == D && r == RR) return stencil_rows<D, RR>(arith, g, coef, dinv, mode, bs, x, b, y, nrhs, w, colour, s);
+  HELM_STENCIL_CASE(2, 1)
+  HELM_STENCIL_CASE(2, 2)
+  HELM_STENCIL_CASE(2, 3)
+  HELM_STENCIL_CASE(3, 1)
+  HELM_STENCIL_CASE(3, 2)
+#undef HELM_STENCIL_CASE
+  set_error("stencil radius not built for this dimension");
+  return 1;
 }
 
 // --------------------------------------------------------------- transfers
@@ -267,6 +193,7 @@ __global__ void __launch_bounds__(256) prolong_add_kernel(GridDims gf, GridDims 
 int launch_restrict(const GridDims& gf, const GridDims& gc, const Transfer& t, Prec p,
                     const void* rf, void* rc, int nrhs, cudaStream_t s) {
   const int th = 256, bl = blocks_for(gc.size, th);
+  KernelTimer kt(HELM_K_TRANSFER, s);
   if (p == P64) {
     if (t.radius == 1) restrict_kernel<double, 1><<<bl, th, 0, s>>>(gf, gc, (const double2*)rf, (double2*)rc, nrhs);
     else restrict_kernel<double, 2><<<bl, th, 0, s>>>(gf, gc, (const double2*)rf, (double2*)rc, nrhs);
@@ -281,6 +208,7 @@ int launch_restrict(const GridDims& gf, const GridDims& gc, const Transfer& t, P
 int launch_prolong_add(const GridDims& gf, const GridDims& gc, const Transfer& t, Prec p,
                        const void* ec, void* xf, int nrhs, cudaStream_t s) {
   const int th = 256, bl = blocks_for(gf.size, th);
+  KernelTimer kt(HELM_K_TRANSFER, s);
   if (p == P64) {
     if (t.radius == 1) prolong_add_kernel<double, 1><<<bl, th, 0, s>>>(gf, gc, (const double2*)ec, (double2*)xf, nrhs);
     else prolong_add_kernel<double, 2><<<bl, th, 0, s>>>(gf, gc, (const double2*)ec, (double2*)xf, nrhs);
@@ -303,6 +231,7 @@ __global__ void convert_kernel(const c2<S>* __restrict__ x, c2<D>* __restrict__ 
 int launch_convert(Prec from, Prec to, const void* x, void* y, long long n, cudaStream_t s) {
   const int th = 256;
   const int bl = (int)std::min<long long>(blocks_for(n, th), 152LL * 16);
+  KernelTimer kt(HELM_K_TRANSFER, s);
   if (from == P64 && to == P32) convert_kernel<double, float><<<bl, th, 0, s>>>((const double2*)x, (float2*)y, n);
   else if (from == P32 && to == P64) convert_kernel<float, double><<<bl, th, 0, s>>>((const float2*)x, (double2*)y, n);
   else if (from == P64) convert_kernel<double, double><<<bl, th, 0, s>>>((const double2*)x, (double2*)y, n);

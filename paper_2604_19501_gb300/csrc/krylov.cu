@@ -12,6 +12,7 @@
 // depend on scheduling.
 #include "krylov.cuh"
 #include "fineop.cuh"
+#include "timer.cuh"
 
 namespace helm {
 
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(kThreads) arnoldi_matvec_kernel(
     int i, j, k;
     node_coords(op.g, p, i, j, k);
     const double2 d = fine_diag<double>(op, kap, p, i, j, k);
-    const double2 wv = fine_apply_at<double, TZ>(op, d, z, p, i, j, k);
+    const double2 wv = fine_apply_at<double, TZ>(op, d, z, p, p, i, j, k, kap);
     w[p] = wv;
     for (int q = 0; q < nv; ++q) {
       double2& a = sacc[q * blockDim.x + tid];
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(kThreads) true_residual_kernel(FineOp op, cons
     int i, j, k;
     node_coords(op.g, p, i, j, k);
     const double2 d = fine_diag<double>(op, kap, p, i, j, k);
-    const double2 ax = fine_apply_at<double, double>(op, d, x, p, i, j, k);
+    const double2 ax = fine_apply_at<double, double>(op, d, x, p, p, i, j, k, kap);
     const double2 rv = make_double2(b[p].x - ax.x, b[p].y - ax.y);
     r[p] = rv;
     sacc[tid].x += rv.x * rv.x + rv.y * rv.y;
@@ -311,6 +312,7 @@ void krylov_free(KrylovState& st) {
 
 int k_norm(const KrylovState& st, long long n, const double2* b, double2* copy_to, cudaStream_t s) {
   const int bl = grid_blocks(n);
+  KernelTimer kt(HELM_K_KRYLOV_OTHER, s);
   norm2_kernel<<<bl, kThreads, kThreads * sizeof(double2), s>>>(n, b, copy_to, st.part, st.counter, st.red);
   HELM_LAUNCH_CHECK();
   set_scalar_kernel<<<1, 32, 0, s>>>(st.scal + KS_BNORM, st.red, 1);
@@ -321,6 +323,7 @@ int k_norm(const KrylovState& st, long long n, const double2* b, double2* copy_t
 }
 
 int k_start_cycle(const KrylovState& st, long long n, const double2* r, double2* v0, cudaStream_t s) {
+  KernelTimer kt(HELM_K_KRYLOV_OTHER, s);
   start_cycle_kernel<<<grid_blocks(n), kThreads, 0, s>>>(n, r, v0, st, st.m);
   HELM_LAUNCH_CHECK();
   return 0;
@@ -340,6 +343,8 @@ int k_arnoldi(const KrylovState& st, const FineOp& op, const double* kap64, cons
     cudaFuncSetAttribute(arnoldi_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     attr_set = true;
   }
+  {
+  KernelTimer kt(HELM_K_ARNOLDI_MATVEC, s);
   if (zp == P64)
     arnoldi_matvec_kernel<double><<<bl, kThreads, sm, s>>>(op, kap64, (const double2*)z, w, V, vstride, nv,
                                                           st.part, st.counter, st.h1);
@@ -347,8 +352,13 @@ int k_arnoldi(const KrylovState& st, const FineOp& op, const double* kap64, cons
     arnoldi_matvec_kernel<float><<<bl, kThreads, sm, s>>>(op, kap64, (const float2*)z, w, V, vstride, nv,
                                                          st.part, st.counter, st.h1);
   HELM_LAUNCH_CHECK();
+  }
+  {
+  KernelTimer kt(HELM_K_ARNOLDI_UPDATE, s);
   arnoldi_update_kernel<<<bl, kThreads, sm, s>>>(n, w, V, vstride, nv, st.h1, st.part, st.counter, st.h2);
   HELM_LAUNCH_CHECK();
+  }
+  KernelTimer kt(HELM_K_KRYLOV_OTHER, s);
   arnoldi_small_kernel<<<1, 32, 0, s>>>(st, j, st.m);
   HELM_LAUNCH_CHECK();
   return 0;
@@ -356,6 +366,7 @@ int k_arnoldi(const KrylovState& st, const FineOp& op, const double* kap64, cons
 
 int k_normalize(const KrylovState& st, long long n, const double2* w, const double2* V, long long vstride,
                 int j, double2* vout, cudaStream_t s) {
+  KernelTimer kt(HELM_K_ARNOLDI_NORM, s);
   arnoldi_normalize_kernel<<<grid_blocks(n), kThreads, 0, s>>>(n, w, V, vstride, j + 1, st.h2,
                                                                st.scal + KS_INV_HN, vout);
   HELM_LAUNCH_CHECK();
@@ -364,6 +375,7 @@ int k_normalize(const KrylovState& st, long long n, const double2* w, const doub
 
 int k_update_solution(const KrylovState& st, long long n, double2* x, const void* Z, Prec zp,
                       long long zstride, int k, cudaStream_t s) {
+  KernelTimer kt(HELM_K_KRYLOV_OTHER, s);
   lsq_kernel<<<1, 32, 0, s>>>(st, k, st.m);
   HELM_LAUNCH_CHECK();
   if (zp == P64)
@@ -377,6 +389,7 @@ int k_update_solution(const KrylovState& st, long long n, double2* x, const void
 int k_true_residual(const KrylovState& st, const FineOp& op, const double* kap64, const double2* b,
                     const double2* x, double2* r, cudaStream_t s) {
   const int bl = grid_blocks(op.g.size);
+  KernelTimer kt(HELM_K_KRYLOV_OTHER, s);
   true_residual_kernel<<<bl, kThreads, kThreads * sizeof(double2), s>>>(op, kap64, b, x, r, st.part,
                                                                        st.counter, st.red);
   HELM_LAUNCH_CHECK();

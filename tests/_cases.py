@@ -17,7 +17,8 @@ def medium(n, seed=0, lo=0.3, hi=1.0):
 
 class Case:
     def __init__(self, n, omega=None, abc=3, gamma_max=1.0, alpha2=1.0, alpha3=1.0, seed=0, kappa2=None,
-                 G_ppw=10.0):
+                 G_ppw=10.0, order="2nd", intergrid="fw"):
+        self.order, self.intergrid = order, intergrid
         self.n = tuple(n)
         self.dim = len(n)
         self.grid = G.Grid(self.n)
@@ -34,8 +35,8 @@ class Case:
     @property
     def hier(self):
         if self._hier is None:
-            self._hier = Hy.Hierarchy(self.grid, self.kappa2, self.omega, self.gamma, "2nd", "fw",
-                                      alpha2=self.alpha2, alpha3=self.alpha3)
+            self._hier = Hy.Hierarchy(self.grid, self.kappa2, self.omega, self.gamma, self.order,
+                                      self.intergrid, alpha2=self.alpha2, alpha3=self.alpha3)
         return self._hier
 
     def solver(self, **kw):
@@ -44,7 +45,7 @@ class Case:
 
         k = torch.from_numpy(self.kappa2).cuda()
         return Solver(k, self.n, self.omega, abc_width=self.abc, abc_gamma_max=self.gamma_max,
-                      alpha2=self.alpha2, alpha3=self.alpha3, **kw)
+                      alpha2=self.alpha2, alpha3=self.alpha3, stencil=self.order, intergrid=self.intergrid, **kw)
 
 
 def rand_complex(shape, seed, dtype=np.complex128):
