@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 RS-CGC Helmholtz solver.
+
+Metric: fine-grid Mdof.solves/s to a 1e-6 relative residual (Sec. 5 tolerance), i.e.
+(fine nodes x solves) / solve time, on the 2D heterogeneous workload of 2048^2 cells
+plus a 32-cell absorbing layer on every side (2113^2 = 4,464,769 unknowns), 12 grid
+points per wavelength at the slowest velocity, a unit point source at the centre.
+A step is one complete solve (FGMRES + RS-CGC preconditioner) of that right-hand side
+with the context already set up; set-up time is reported separately.
+
+One JSON line on stdout (rank 0).  Diagnostics go to stderr.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+The reference arm (--impl reference) times the CPU oracle on the host cores: every
+step is a bounded sample of FGMRES iterations of the same workload, scaled by the
+oracle's own iteration count to the metric's unit.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mdof*solves/s to 1e-6 rel-res"
+UNIT = "Mdof*solves/s"
+FP64_PEAK_TFLOPS = 1.26   # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=2048, help="interior cells per axis")
+    ap.add_argument("--pad", type=int, default=32, help="absorbing-layer cells per side")
+    ap.add_argument("--ppw", type=int, default=12)
+    ap.add_argument("--method", default="paper", choices=["paper", "baseline"],
+                    help="paper: 4th-order 9-point + cubic transfers (Sec. 3); baseline: 5-point + FW/bilinear")
+    ap.add_argument("--cycle", default="V")
+    ap.add_argument("--jacobi", type=float, default=None)
+    ap.add_argument("--restart", type=int, default=10)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--maxit", type=int, default=400)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=3, help="oracle FGMRES iterations per CPU sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ workload
+def workload(args):
+    import numpy as np
+
+    import workloads
+
+    N = args.n + 2 * args.pad
+    n = (N, N)
+    kappa2 = workloads.layered_faulted_2d(args.n, args.pad, seed=0)
+    vmin = 1.0 / float(np.sqrt(kappa2.max()))
+    omega = workloads.omega_for_ppw(args.ppw, vmin)
+    with open(os.path.join(ROOT, "workloads", "shifts.json")) as f:
+        shifts = json.load(f)["2d"]
+    if args.method == "paper":
+        order, ig = "4th", "cubic"
+        alpha3 = shifts["4th"]["cubic"][str(args.ppw)]
+        jw = 0.89 if args.jacobi is None else args.jacobi
+    else:
+        order, ig = "2nd", "fw"
+        alpha3 = shifts["2nd"]["fw"][str(args.ppw)]["alpha3"]
+        jw = 0.8 if args.jacobi is None else args.jacobi
+    q = workloads.point_source(n)
+    return dict(n=n, kappa2=kappa2, omega=omega, q=q, order=order, intergrid=ig, alpha3=alpha3,
+                jacobi=jw, pad=args.pad, vmin=vmin)
+
+
+def describe(args, wl):
+    return {
+        "workload": (f"2D heterogeneous layered/faulted medium (1.5-4.5 km/s, seeded) {args.n}^2 cells "
+                     f"+ {args.pad}-cell absorbing layer per side = {wl['n'][0]}^2 cells "
+                     f"({(wl['n'][0] + 1) ** 2} nodes), {args.ppw} points per wavelength, centre point source"),
+        "method": (f"RS-CGC {args.cycle}(1,1) damped Jacobi w={wl['jacobi']}, "
+                   f"{'4th-order 9-point + cubic transfers' if wl['order'] == '4th' else '5-point + FW/bilinear'}, "
+                   f"alpha3={wl['alpha3']}, FGMRES({args.restart}), tol {args.tol}"),
+        "precision": ("FP32 cycle on levels 1-2, FP64 FGMRES / outer matvec / true residual / coarsest solve"
+                      if args.precision == "mixed" else "FP64 throughout"),
+        "l2": "inputs larger than L2 (Krylov basis and operators: several GB per solve)",
+        "setup": "excluded from the timed region, reported as setup_ms",
+    }
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ distributed
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group(backend="nccl" if args.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, value, device=None):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ oracle timing
+def oracle_sample(args, wl, iters, log):
+    """Oracle set-up, one full solve for its iteration count, then timed samples of
+    `iters` FGMRES iterations.  Returns (seconds per iteration list, full iteration count)."""
+    import numpy as np
+
+    from oracle import cycle as OC
+    from oracle import grid as OG
+    from oracle import hierarchy as OH
+    from oracle import krylov as OK
+
+    grid = OG.Grid(wl["n"])
+    gamma = OG.abc_profile(grid, OG.uniform_widths(2, wl["pad"]), 1.0)
+    t0 = time.perf_counter()
+    h = OH.Hierarchy(grid, wl["kappa2"], wl["omega"], gamma, wl["order"], wl["intergrid"], alpha3=wl["alpha3"])
+    h.coarsest_lu
+    cy = OC.Cycle(h, cycle=args.cycle, weights=(wl["jacobi"], wl["jacobi"]))
+    log(f"oracle set-up {time.perf_counter() - t0:.1f} s")
+    A = h.A[0]
+    q = wl["q"].ravel()
+    return h, cy, A, q
+
+
+def run_oracle_iters(A, q, cy, iters, restart, tol):
+    from oracle import krylov as OK
+
+    t = time.perf_counter()
+    _, info = OK.fgmres(lambda v: A @ v, q, cy, tol=tol, maxit=iters, restart=restart)
+    return (time.perf_counter() - t), info
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+
+        return max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
+    except Exception:
+        return int(os.environ.get("OMP_NUM_THREADS", "0")) or None
+
+
+# ------------------------------------------------------------------ reference arm
+def reference_arm(args):
+    world, rank, _ = dist_init(args)
+    if rank != 0:
+        return 0
+    log = lambda m: print(m, file=sys.stderr, flush=True)
+    wl = workload(args)
+    nodes = (wl["n"][0] + 1) * (wl["n"][1] + 1)
+    h, cy, A, q = oracle_sample(args, wl, args.cpu_iters, log)
+    t_full, info = run_oracle_iters(A, q, cy, args.maxit, args.restart, args.tol)
+    its = info["iterations"]
+    log(f"oracle full solve: {its} iterations, relres {info['relres']:.2e}, {t_full:.1f} s")
+    for _ in range(args.warmup):
+        run_oracle_iters(A, q, cy, args.cpu_iters, args.restart, args.tol)
+    times = [run_oracle_iters(A, q, cy, args.cpu_iters, args.restart, args.tol)[0] for _ in range(args.steps)]
+    per_iter = sum(times) / (args.steps * args.cpu_iters)
+    solve_s = per_iter * its
+    value = nodes / 1e6 / solve_s
+    cores = blas_threads() or cpu_cores()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": describe(args, wl),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.cpu_iters} FGMRES iterations per step, scaled by the oracle's own "
+                                   f"{its}-iteration full solve"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "iterations": its,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def kernel_model(info, its, restart, n1):
+    """Algorithmic bytes and flops per launch of the timed kernel classes."""
+    nv_sum = sum((i % restart) + 1 for i in range(its))
+    return {
+        "coarse": {"flops": 8.0 * info["coarse_entries"], "bytes": 16.0 * info["coarse_entries"]},
+        "arnoldi_update": {"flops": 8.0 * 2 * nv_sum / its * n1, "bytes": (32.0 + 16.0 * nv_sum / its) * n1},
+        "arnoldi_norm": {"flops": 8.0 * nv_sum / its * n1, "bytes": (32.0 + 16.0 * nv_sum / its) * n1},
+        "arnoldi_matvec": {"flops": (8.0 * nv_sum / its + 40.0) * n1, "bytes": (40.0 + 16.0 * nv_sum / its) * n1},
+    }
+
+
+def our_arm(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_init(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    log = (lambda m: print(m, file=sys.stderr, flush=True)) if rank == 0 else (lambda m: None)
+    from paper_2604_19501_gb300 import Solver
+
+    wl = workload(args)
+    nodes = (wl["n"][0] + 1) * (wl["n"][1] + 1)
+    stream = torch.cuda.current_stream(dev)
+    kap = torch.from_numpy(wl["kappa2"]).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = Solver(kap, wl["n"], wl["omega"], abc_width=wl["pad"], alpha3=wl["alpha3"], stencil=wl["order"],
+               intergrid=wl["intergrid"], cycle=args.cycle, jacobi_w=(wl["jacobi"], wl["jacobi"]),
+               precision=args.precision, restart=args.restart, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    info = s.info()
+    log(f"set-up {setup_ms:.0f} ms, {info}")
+    q = torch.from_numpy(wl["q"]).to(dev)
+    p = torch.empty_like(q)
+    stats = None
+    for _ in range(args.warmup):
+        p, stats = s.solve(q, p, tol=args.tol, maxit=args.maxit)
+    its = stats[0]["iterations"] if stats else None
+    log(f"warm-up: {stats}")
+
+    # ---- device-resident timed region
+    s.timer_enable(["coarse", "arnoldi_update", "arnoldi_matvec", "arnoldi_norm", "fine", "stencil",
+                    "transfer", "krylov_other"])
+    sampler = ClockSampler(local).start()
+    l0 = s.launches
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    all_stats = []
+    for _ in range(args.steps):
+        p, st = s.solve(q, p, tol=args.tol, maxit=args.maxit)
+        all_stats.append(st[0])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    launches = s.launches - l0
+    t_dev = e0.elapsed_time(e1) / 1e3
+    prof = s.timer_read()
+    s.timer_enable([])
+    t_max = max_over_ranks(world, t_dev, dev)
+    value = world * args.steps * nodes / 1e6 / t_max
+    its = all_stats[-1]["iterations"]
+    converged = all(x["converged"] for x in all_stats)
+
+    # ---- end to end through the C ABI with pinned host buffers
+    qh = torch.from_numpy(wl["q"]).pin_memory()
+    ph = torch.empty_like(qh).pin_memory()
+    s.solve(qh, ph, tol=args.tol, maxit=args.maxit)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.solve(qh, ph, tol=args.tol, maxit=args.maxit)
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(world, time.perf_counter() - t0, dev)
+    e2e_value = world * args.steps * nodes / 1e6 / t_e2e
+    qbytes = qh.numel() * qh.element_size()
+
+    # ---- roofline of the dominant kernel class
+    total_ms = t_dev * 1e3
+    kernels = {k: {"ms_per_solve": v[0] / args.steps, "launches_per_solve": v[1] / args.steps,
+                   "share": v[0] / total_ms} for k, v in prof.items() if v[1]}
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_solve"])
+    model = kernel_model(info, its, args.restart, nodes)
+    roof = None
+    if dom in model:
+        ms, cnt = prof[dom]
+        per_launch_s = ms / 1e3 / cnt
+        fl = model[dom]["flops"] / per_launch_s / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": fl / FP64_PEAK_TFLOPS, "traffic": None,
+                "algorithmic_bytes_per_launch": model[dom]["bytes"],
+                "achieved_gbs": model[dom]["bytes"] / per_launch_s / 1e9,
+                "peak_note": "FP64 ALU peak derived from unit counts and clock; HBM peak in MEASURED_PEAKS.json"}
+
+    # ---- CPU oracle on a bounded sample
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        h, cy, A, qo = oracle_sample(args, wl, args.cpu_iters, log)
+        dt, _ = run_oracle_iters(A, qo, cy, args.cpu_iters, args.restart, args.tol)
+        per_iter = dt / args.cpu_iters
+        cpu_solve = per_iter * its
+        cpu = {"value": nodes / 1e6 / cpu_solve, "unit": UNIT, "cores": blas_threads() or cpu_cores(),
+               "kind": "oracle",
+               "sample": f"{args.cpu_iters} oracle FGMRES iterations on the full workload ({per_iter:.2f} s each), "
+                         f"scaled to the {its}-iteration solve"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": describe(args, wl),
+        "iterations": its, "converged": converged, "relres": all_stats[-1]["relres"],
+        "setup_ms": setup_ms,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": qbytes, "d2h_bytes_per_step": qbytes},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "kernels": kernels,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return our_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -172,6 +172,21 @@ int helm_cycle(helm_ctx* c, const void* v, void* z, int n_rhs);
 /* Number of kernel launches this context has issued so far (all entry points). */
 long long helm_launch_count(const helm_ctx* c);
 
+/* Facts about a set-up context (for byte / flop accounting). */
+typedef enum {
+  HELM_INFO_NODES1 = 0,              /* nodes of level 1 (fine) */
+  HELM_INFO_NODES2 = 1,              /* nodes of level 2 */
+  HELM_INFO_NODES3 = 2,              /* nodes of level 3 (coarsest) */
+  HELM_INFO_RADIUS2 = 3,             /* stencil radius of the level-2 operator */
+  HELM_INFO_RADIUS3 = 4,             /* stencil radius of the level-3 operator */
+  HELM_INFO_COARSE_ENTRIES = 5,      /* complex entries of the coarsest factors read per solve */
+  HELM_INFO_COARSE_FRONTS = 6,       /* fronts of the nested-dissection tree */
+  HELM_INFO_COARSE_LEVELS = 7        /* levels of the nested-dissection tree */
+} helm_info_key;
+
+/* *value = the quantity selected by key. */
+int helm_info(const helm_ctx* c, int key, long long* value);
+
 /* ---- Launch timer (tracing) ---- */
 
 /* Kernel classes of the launch timer. */

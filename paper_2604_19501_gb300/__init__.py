@@ -96,6 +96,15 @@ class Solver:
         """Kernel launches issued by this context so far."""
         return int(_lib.helm_launch_count(self._ctx))
 
+    def info(self):
+        """Context facts (node counts, stencil radii, coarsest-factor size)."""
+        out = {}
+        for i, key in enumerate(_ffi.INFO_KEYS):
+            v = ctypes.c_longlong()
+            check(_lib.helm_info(self._ctx, i, ctypes.byref(v)), "helm_info")
+            out[key] = v.value
+        return out
+
     def timer_enable(self, classes=None):
         """Time every launch of the named kernel classes (all when None)."""
         names = _ffi.KERNEL_CLASSES if classes is None else classes

@@ -12,6 +12,8 @@ CYCLE = {"V": 0, "W": 1}
 SMOOTHER = {"jacobi": 0, "redblack": 1, "rb": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 DTYPE = {"c128": 0, "c64": 1}
+INFO_KEYS = ["nodes1", "nodes2", "nodes3", "radius2", "radius3", "coarse_entries", "coarse_fronts",
+             "coarse_levels"]
 KERNEL_CLASSES = ["fine", "stencil", "transfer", "coarse", "arnoldi_matvec", "arnoldi_update",
                   "arnoldi_norm", "krylov_other", "setup"]
 
@@ -70,6 +72,7 @@ SIGNATURES = {
     "helm_coarse_solve": (_I, [_P, _P, _P, _I]),
     "helm_cycle": (_I, [_P, _P, _P, _I]),
     "helm_launch_count": (ctypes.c_longlong, [_P]),
+    "helm_info": (_I, [_P, _I, ctypes.POINTER(ctypes.c_longlong)]),
     "helm_timer_enable": (_I, [_P, ctypes.c_uint]),
     "helm_timer_read": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)]),
     "helm_strerror": (ctypes.c_char_p, [_I]),

@@ -608,6 +608,22 @@ int helm_cycle(helm_ctx* c, const void* v, void* z, int n_rhs) {
 
 long long helm_launch_count(const helm_ctx* c) { return c ? c->launches : 0; }
 
+int helm_info(const helm_ctx* c, int key, long long* value) {
+  if (!c || !value) return fail(HELM_EINVAL, "null argument");
+  switch (key) {
+    case HELM_INFO_NODES1: *value = c->g[0].size; break;
+    case HELM_INFO_NODES2: *value = c->g[1].size; break;
+    case HELM_INFO_NODES3: *value = c->g[2].size; break;
+    case HELM_INFO_RADIUS2: *value = c->r2; break;
+    case HELM_INFO_RADIUS3: *value = c->r3; break;
+    case HELM_INFO_COARSE_ENTRIES: *value = c->cs.factor_entries; break;
+    case HELM_INFO_COARSE_FRONTS: *value = c->cs.nfronts; break;
+    case HELM_INFO_COARSE_LEVELS: *value = c->cs.nlevels; break;
+    default: return fail(HELM_EINVAL, "unknown info key");
+  }
+  return HELM_OK;
+}
+
 int helm_timer_enable(helm_ctx* c, unsigned mask) {
   if (!c) return fail(HELM_EINVAL, "null context");
   c->timer.reset();
