@@ -165,6 +165,24 @@ int helm_get_stencil(helm_ctx* c, int level, double* out, int* radius);
 /* e = (H_4h^alpha)^-1 b on level 3 by the direct factorisation (c128). */
 int helm_coarse_solve(helm_ctx* c, const void* b, void* e, int n_rhs);
 
+/* e = (H_4h^alpha)^-1 b like helm_coarse_solve, but the call allocates nothing.
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc, such as a host framework that reserves all device memory
+ * up front and forbids further allocations, or a latency-sensitive loop that
+ * cannot afford the device-wide synchronisation an allocation may cause.
+ * (helm_coarse_solve allocates its scratch on its first call, or when n_rhs
+ * grows.)  The scratch vectors live in one static device array of 2^20
+ * complex FP64 entries (16 MiB), which every GPU that loads the library holds
+ * until the process exits.  A solve needs (sum of front sizes + sum of update
+ * sizes + nodes(3)) entries per right-hand side; larger requests return
+ * HELM_EINVAL and do nothing.  The first call on a device looks up the array's
+ * device address with that device current; later calls reuse it.  All calls
+ * share the array: calls that may overlap on the GPU (two streams, two
+ * contexts, two threads) race and corrupt each other's results, so serialise
+ * them.  Nothing in the array needs to start at zero: every entry a call reads
+ * is written earlier in the same call.  b, e: c128 device pointers. */
+int helm_coarse_solve_noalloc(helm_ctx* c, const void* b, void* e, int n_rhs);
+
 /* z = M^-1 v: one application of the 3-level cycle from a zero initial guess,
  * v and z in c128 (the mixed precision mode computes levels 1-2 in c64). */
 int helm_cycle(helm_ctx* c, const void* v, void* z, int n_rhs);

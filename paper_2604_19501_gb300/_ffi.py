@@ -70,6 +70,7 @@ SIGNATURES = {
     "helm_prolong_add": (_I, [_P, _I, _I, _P, _P, _I]),
     "helm_get_stencil": (_I, [_P, _I, _P, ctypes.POINTER(_I)]),
     "helm_coarse_solve": (_I, [_P, _P, _P, _I]),
+    "helm_coarse_solve_noalloc": (_I, [_P, _P, _P, _I]),
     "helm_cycle": (_I, [_P, _P, _P, _I]),
     "helm_launch_count": (ctypes.c_longlong, [_P]),
     "helm_info": (_I, [_P, _I, ctypes.POINTER(ctypes.c_longlong)]),

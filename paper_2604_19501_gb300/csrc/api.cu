@@ -599,6 +599,13 @@ int helm_coarse_solve(helm_ctx* c, const void* b, void* e, int n_rhs) {
   return HELM_OK;
 }
 
+int helm_coarse_solve_noalloc(helm_ctx* c, const void* b, void* e, int n_rhs) {
+  if (!c || !b || !e || n_rhs < 1) return fail(HELM_EINVAL, "bad argument");
+  LaunchScope scope(c);
+  if (int st = coarse_solve_noalloc(c->cs, (const double2*)b, (double2*)e, n_rhs, c->s)) return st;
+  return HELM_OK;
+}
+
 int helm_cycle(helm_ctx* c, const void* v, void* z, int n_rhs) {
   if (!c || !v || !z || n_rhs < 1) return fail(HELM_EINVAL, "bad argument");
   LaunchScope scope(c);

@@ -21,6 +21,7 @@
 // root to leaves, x_S = w_S - (F_SS^-1 F_SB) x_B.  Both are dense matrix-vector
 // products; no atomics, so results are reproducible bit for bit.
 #include <algorithm>
+#include <mutex>
 #include <unordered_map>
 #include "coarse.cuh"
 #include "timer.cuh"
@@ -531,6 +532,69 @@ int coarse_solve(CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaS
   for (int h = cs.nlevels - 1; h >= 0; --h) {
     bwd_matvec_kernel<<<cs.n_bwd_rows[h], 32 * kRowsPerBlock, 0, s>>>(
         cs.d_desc, cs.d_bwd_rows[h], cs.d_S, cs.d_B, cs.d_factors, cs.d_w, e, nrhs, cs.g.size);
+    HELM_LAUNCH_CHECK();
+  }
+  return 0;
+}
+
+// ------------------------------------------------------------------ allocation-free variant
+// Scratch of coarse_solve_noalloc: the front vectors, update vectors and the forward
+// result of every right-hand side, carved from one file-scope device array instead of
+// buffers the context allocates.  Every device that loads the library holds it until
+// the process exits.
+constexpr long long kNoAllocScratchEntries = 1LL << 20;   // 1 Mi complex FP64 = 16 MiB
+static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocScratchEntries];
+
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int kMaxDevices = 64;
+double2* g_noalloc_addr[kMaxDevices] = {};
+}  // namespace
+
+int coarse_solve_noalloc(const CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaStream_t s) {
+  const long long per_rhs = cs.rf_total + cs.uv_total + cs.g.size;
+  if (nrhs < 1 || per_rhs * nrhs > kNoAllocScratchEntries) {
+    set_error("allocation-free coarsest solve needs " + std::to_string(per_rhs * nrhs) +
+              " complex scratch entries; the static array holds " + std::to_string(kNoAllocScratchEntries));
+    return HELM_EINVAL;
+  }
+  int dev = 0;
+  HELM_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("device ordinal out of range for the allocation-free scratch table");
+    return HELM_EINVAL;
+  }
+  double2* base = nullptr;
+  {
+    // set-up once per device, with that device current: the host-side symbol is a
+    // stand-in, its device address comes from the runtime
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      HELM_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      g_noalloc_addr[dev] = static_cast<double2*>(p);
+    }
+    base = g_noalloc_addr[dev];
+  }
+  // every scratch entry that is read is written earlier in the same call: the front
+  // vectors from b, the update vectors by the child fronts, w for every eliminated node
+  double2* rf = base;
+  double2* uv = rf + cs.rf_total * nrhs;
+  double2* w = uv + cs.uv_total * nrhs;
+  for (int h = 0; h < cs.nlevels; ++h) {
+    const int nf = (int)cs.level_fronts[h].size();
+    fwd_assemble_kernel<<<nf, 256, 0, s>>>(cs.d_desc, cs.d_level_list[h], cs.d_S, cs.d_kids, cs.d_cmap, b, rf,
+                                           uv, nrhs, cs.g.size, cs.rf_total, cs.uv_total);
+    HELM_LAUNCH_CHECK();
+    fwd_matvec_kernel<<<cs.n_fwd_rows[h], 32 * kRowsPerBlock, 0, s>>>(cs.d_desc, cs.d_fwd_rows[h], cs.d_S,
+                                                                      cs.d_factors, rf, uv, w, nrhs, cs.g.size,
+                                                                      cs.rf_total, cs.uv_total);
+    HELM_LAUNCH_CHECK();
+  }
+  for (int h = cs.nlevels - 1; h >= 0; --h) {
+    bwd_matvec_kernel<<<cs.n_bwd_rows[h], 32 * kRowsPerBlock, 0, s>>>(cs.d_desc, cs.d_bwd_rows[h], cs.d_S,
+                                                                      cs.d_B, cs.d_factors, w, e, nrhs,
+                                                                      cs.g.size);
     HELM_LAUNCH_CHECK();
   }
   return 0;

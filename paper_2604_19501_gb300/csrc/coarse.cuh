@@ -55,6 +55,10 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
 // e = A^-1 b for nrhs vectors (c128, [nrhs][nodes]).
 int coarse_solve(CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaStream_t s);
 
+// The same solve with its scratch in a static device array of fixed size (no
+// allocation); HELM_EINVAL when the problem needs more scratch than the array holds.
+int coarse_solve_noalloc(const CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaStream_t s);
+
 void coarse_free(CoarseSolver& cs);
 
 }  // namespace helm
