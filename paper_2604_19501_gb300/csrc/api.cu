@@ -452,7 +452,9 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
   if (bad) return bail(fail(HELM_ENUMERIC, "zero or non-finite coarse diagonal"));
 
   // coarsest factorisation
-  if ((st = coarse_setup(c->cs, c->g[2], c->r3, c->A3_64, o->dim == 2 ? 64 : 64, c->s))) return bail(st);
+  // the coarsest operator is complex-symmetric when R and P / 2^d are transposes on both levels
+  const bool symmetric = o->intergrid != HELM_INTERGRID_LEVDEP;
+  if ((st = coarse_setup(c->cs, c->g[2], c->r3, c->A3_64, 64, symmetric, c->s))) return bail(st);
 
   // workspaces
   const int m = o->restart;

@@ -16,10 +16,18 @@
 //   rows S: [ I | F_SS^-1 F_SB | F_SS^-1 ],   rows B: [ 0 | U | -F_BS F_SS^-1 ],
 // U = F_BB - F_BS F_SS^-1 F_SB being the update passed to the parent.
 //
+// Stored per front: M = [F_SS^-1 | F_SS^-1 F_SB] (|S| x |F|) when the coarsest operator is
+// complex-symmetric (full-weighting or cubic transfers on both levels), since then
+// F_BS F_SS^-1 = (F_SS^-1 F_SB)^T; otherwise M = [F_SS^-1 | -F_BS F_SS^-1]^T plus
+// G = F_SS^-1 F_SB.  Small fronts are eliminated by one thread block each; large fronts by
+// a pair of grid-wide kernels per pivot (pivot search + row swap/scale, elimination).
+//
 // Solve: forward, leaves to root, every front turns its assembled right-hand side r_F
-// into w_S = F_SS^-1 r_S and the update vector r_B - F_BS w_S for its parent; backward,
-// root to leaves, x_S = w_S - (F_SS^-1 F_SB) x_B.  Both are dense matrix-vector
-// products; no atomics, so results are reproducible bit for bit.
+// into w_S = F_SS^-1 r_S and the update vector r_B - F_BS F_SS^-1 r_S for its parent:
+// column sums over M, split into row chunks whose partial sums the last block of a column
+// tile adds in chunk order.  Backward, root to leaves, x_S = w_S - (F_SS^-1 F_SB) x_B
+// (row dot products).  The summation order is fixed, so results are reproducible bit
+// for bit.
 #include <algorithm>
 #include <mutex>
 #include <unordered_map>
@@ -224,22 +232,126 @@ __global__ void __launch_bounds__(512) fact_gj_kernel(const FrontDesc* __restric
   }
 }
 
+
+// ------------------------------------------------------------------ large-front elimination
+// One pivot step k of Gauss-Jordan elimination on the augmented fronts of a level, split
+// over many blocks.  Kernel 1: every block finds the same pivot row p (largest |a_ik|,
+// rows k..nS-1, lowest index on ties), block 0 records p and the old a_kk, and every
+// block swaps rows k and p and scales the new row k over its slice of columns k+1..ld-1
+// (column k is left alone so that all blocks read the same pivot value).  Kernel 2: every
+// other row i subtracts f_i times row k (f_p = old a_kk) and its column-k entry becomes 0.
+__global__ void __launch_bounds__(256) gj_pivot_kernel(const FrontDesc* __restrict__ desc,
+                                                       const int* __restrict__ list, double2* __restrict__ aug,
+                                                       int k, int* __restrict__ piv, double2* __restrict__ akk,
+                                                       int* __restrict__ err) {
+  const int fi = blockIdx.y;
+  const FrontDesc d = desc[list[fi]];
+  const int nS = d.nS, nF = d.nS + d.nB, ld = nF + d.nS;
+  if (k >= nS) return;
+  double2* A = aug + d.aug_off;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  __shared__ double s_val[32];
+  __shared__ int s_idx[32];
+  __shared__ int s_p;
+  double best = -1.0;
+  int bi = nS;
+  for (int i = k + tid; i < nS; i += blockDim.x) {
+    const double2 a = A[(long long)i * ld + k];
+    const double v = a.x * a.x + a.y * a.y;
+    if (v > best) { best = v; bi = i; }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, best, off);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+  }
+  if (lane == 0) { s_val[warp] = best; s_idx[warp] = bi; }
+  __syncthreads();
+  if (tid == 0) {
+    double bv = s_val[0];
+    int bidx = s_idx[0];
+    for (int w = 1; w < nwarp; ++w)
+      if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] < bidx)) { bv = s_val[w]; bidx = s_idx[w]; }
+    if (!(bv > 0.0) || !isfinite(bv) || bidx >= nS) {
+      if (blockIdx.x == 0) atomicExch(err, 1);
+      bidx = k;
+    }
+    s_p = bidx;
+    if (blockIdx.x == 0) {
+      piv[fi] = bidx;
+      akk[fi] = A[(long long)k * ld + k];
+    }
+  }
+  __syncthreads();
+  const int p = s_p;
+  const double2 a = A[(long long)p * ld + k];
+  const double m = a.x * a.x + a.y * a.y;
+  const double2 inv = make_double2(a.x / m, -a.y / m);
+  const int span = (ld - k - 1 + gridDim.x - 1) / gridDim.x;
+  const int c0 = k + 1 + blockIdx.x * span, c1 = min(ld, c0 + span);
+  for (int c = c0 + tid; c < c1; c += blockDim.x) {
+    const double2 vk = A[(long long)k * ld + c];
+    const double2 vp = A[(long long)p * ld + c];
+    A[(long long)k * ld + c] = make_double2(vp.x * inv.x - vp.y * inv.y, vp.x * inv.y + vp.y * inv.x);
+    if (p != k) A[(long long)p * ld + c] = vk;
+  }
+}
+
+__global__ void __launch_bounds__(256) gj_elim_kernel(const FrontDesc* __restrict__ desc,
+                                                      const int* __restrict__ list, double2* __restrict__ aug,
+                                                      int k, const int* __restrict__ piv,
+                                                      const double2* __restrict__ akk) {
+  const int fi = blockIdx.y;
+  const FrontDesc d = desc[list[fi]];
+  const int nS = d.nS, nF = d.nS + d.nB, ld = nF + d.nS;
+  if (k >= nS) return;
+  double2* A = aug + d.aug_off;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int p = piv[fi];
+  const double2* Ak = A + (long long)k * ld;
+  for (int i = blockIdx.x * nwarp + warp; i < nF; i += gridDim.x * nwarp) {
+    double2* Ai = A + (long long)i * ld;
+    if (i == k) {
+      if (lane == 0) Ai[k] = make_double2(1.0, 0.0);
+      continue;
+    }
+    const double2 f = (i == p) ? akk[fi] : Ai[k];
+    if (f.x != 0.0 || f.y != 0.0) {
+      for (int c = k + 1 + lane; c < ld; c += 32) {
+        const double2 b = Ak[c];
+        double2 v = Ai[c];
+        v.x -= f.x * b.x - f.y * b.y;
+        v.y -= f.x * b.y + f.y * b.x;
+        Ai[c] = v;
+      }
+    }
+    if (lane == 0) Ai[k] = make_double2(0.0, 0.0);
+  }
+}
+
+// Copies the factors out of the eliminated augmented fronts.
 __global__ void fact_extract_kernel(const FrontDesc* __restrict__ desc, const int* __restrict__ list,
                                     const double2* __restrict__ aug, double2* __restrict__ factors,
                                     double2* __restrict__ upool) {
   const FrontDesc d = desc[list[blockIdx.x]];
   const int nS = d.nS, nB = d.nB, nF = nS + nB, ld = nF + nS;
   const double2* A = aug + d.aug_off;
-  double2* X = factors + d.X_off;
-  double2* G = factors + d.G_off;
+  double2* M = factors + d.M_off;
   double2* U = upool + d.U_off;
-  for (long long t = threadIdx.x; t < (long long)nF * nS; t += blockDim.x) {
-    const int row = (int)(t / nS), col = (int)(t % nS);
-    X[t] = A[(long long)row * ld + nF + col];
+  const long long nm = (long long)nS * nF;
+  for (long long t = threadIdx.x; t < nm; t += blockDim.x) {
+    const int row = (int)(t / nF), col = (int)(t % nF);
+    if (d.bsign < 0)   // [F_SS^-1 | G]
+      M[t] = A[(long long)row * ld + (col < nS ? nF + col : col)];
+    else               // X^T, X = [F_SS^-1 ; -F_BS F_SS^-1]
+      M[t] = A[(long long)col * ld + nF + row];
   }
-  for (long long t = threadIdx.x; t < (long long)nS * nB; t += blockDim.x) {
-    const int row = (int)(t / nB), col = (int)(t % nB);
-    G[t] = A[(long long)row * ld + nS + col];
+  if (d.bsign > 0) {
+    double2* G = factors + d.G_off;
+    for (long long t = threadIdx.x; t < (long long)nS * nB; t += blockDim.x) {
+      const int row = (int)(t / nB), col = (int)(t % nB);
+      G[t] = A[(long long)row * ld + nS + col];
+    }
   }
   for (long long t = threadIdx.x; t < (long long)nB * nB; t += blockDim.x) {
     const int row = (int)(t / nB), col = (int)(t % nB);
@@ -275,38 +387,67 @@ __global__ void fwd_assemble_kernel(const FrontDesc* __restrict__ desc, const in
   }
 }
 
-// one warp per row of X: out = X[row, :] . r_S
-__global__ void __launch_bounds__(256) fwd_matvec_kernel(const FrontDesc* __restrict__ desc,
-                                                         const int2* __restrict__ rows,
-                                                         const int* __restrict__ Sidx,
-                                                         const double2* __restrict__ factors,
-                                                         const double2* __restrict__ rf,
-                                                         double2* __restrict__ uv, double2* __restrict__ w,
-                                                         int nrhs, long long nodes, long long rf_total,
-                                                         long long uv_total) {
-  const int2 job = rows[blockIdx.x];
-  const FrontDesc d = desc[job.x];
-  const int row = job.y + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  const int nF = d.nS + d.nB;
-  if (row >= nF) return;
-  const double2* X = factors + d.X_off + (long long)row * d.nS;
-  for (int r = 0; r < nrhs; ++r) {
-    const double2* R = rf + r * rf_total + d.rf_off;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int c = lane; c < d.nS; c += 32) acc = cmac(acc, X[c], R[c]);
-    for (int off = 16; off > 0; off >>= 1) {
-      acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
-      acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
-    }
-    if (lane == 0) {
-      if (row < d.nS) {
-        w[r * nodes + Sidx[d.S_off + row]] = acc;
-      } else {
-        const double2 base = R[row];
-        uv[r * uv_total + d.uv_off + row - d.nS] = make_double2(base.x + acc.x, base.y + acc.y);
-      }
-    }
+// Forward sweep of one level: out_t = sum_s M[s][t] r_S[s] over a column tile and a chunk
+// of rows; t < nS gives w at node S[t], t >= nS the update vector r_B + bsign * out.
+__device__ __forceinline__ void fwd_write(const FrontDesc& d, const int* __restrict__ Sidx, int t, int r,
+                                          double2 v, const double2* __restrict__ rf, double2* __restrict__ uv,
+                                          double2* __restrict__ w, long long nodes, long long rf_total,
+                                          long long uv_total) {
+  if (t < d.nS) {
+    w[r * nodes + Sidx[d.S_off + t]] = v;
+  } else {
+    const double2 rb = rf[r * rf_total + d.rf_off + t];
+    uv[r * uv_total + d.uv_off + t - d.nS] = make_double2(rb.x + d.bsign * v.x, rb.y + d.bsign * v.y);
   }
+}
+
+__global__ void __launch_bounds__(kFwdCols) fwd_colsum_kernel(
+    const FrontDesc* __restrict__ desc, const FwdJob* __restrict__ jobs, const int* __restrict__ Sidx,
+    const double2* __restrict__ factors, const double2* __restrict__ rf, double2* __restrict__ uv,
+    double2* __restrict__ w, double2* __restrict__ part, unsigned* __restrict__ counters, int nrhs,
+    long long nodes, long long rf_total, long long uv_total) {
+  const FwdJob job = jobs[blockIdx.x];
+  const FrontDesc d = desc[job.front];
+  const int nF = d.nS + d.nB;
+  const int tid = threadIdx.x;
+  const int t = job.tile * kFwdCols + tid;
+  const int s0 = job.chunk * kFwdChunk, s1 = min(d.nS, s0 + kFwdChunk);
+  const double2* M = factors + d.M_off;
+  __shared__ double2 rs[kFwdChunk];
+  __shared__ bool s_last;
+  for (int r = 0; r < nrhs; ++r) {
+    for (int q = tid; q < s1 - s0; q += blockDim.x) rs[q] = rf[r * rf_total + d.rf_off + s0 + q];
+    __syncthreads();
+    double2 acc = make_double2(0.0, 0.0);
+    if (t < nF) {
+      const double2* col = M + (long long)s0 * nF + t;
+#pragma unroll 4
+      for (int s = 0; s < s1 - s0; ++s) acc = cmac(acc, col[(long long)s * nF], rs[s]);
+    }
+    if (job.nchunks == 1) {
+      if (t < nF) fwd_write(d, Sidx, t, r, acc, rf, uv, w, nodes, rf_total, uv_total);
+    } else {
+      part[((long long)(job.pbase + job.chunk) * nrhs + r) * kFwdCols + tid] = acc;
+    }
+    __syncthreads();
+  }
+  if (job.nchunks == 1) return;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = (atomicAdd(&counters[job.slot], 1u) == (unsigned)job.nchunks - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int r = 0; r < nrhs; ++r) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int q = 0; q < job.nchunks; ++q) {
+      const double2 v = __ldcg(part + ((long long)(job.pbase + q) * nrhs + r) * kFwdCols + tid);
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    if (t < nF) fwd_write(d, Sidx, t, r, acc, rf, uv, w, nodes, rf_total, uv_total);
+  }
+  if (tid == 0) counters[job.slot] = 0u;
 }
 
 // one warp per row of G: x_S[row] = w_S[row] - G[row, :] . x_B
@@ -322,7 +463,7 @@ __global__ void __launch_bounds__(256) bwd_matvec_kernel(const FrontDesc* __rest
   const FrontDesc d = desc[job.x];
   const int row = job.y + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (row >= d.nS) return;
-  const double2* G = factors + d.G_off + (long long)row * d.nB;
+  const double2* G = factors + d.G_off + (long long)row * d.g_ld;
   const int* B = Bidx + d.B_off;
   const int node = Sidx[d.S_off + row];
   for (int r = 0; r < nrhs; ++r) {
@@ -348,12 +489,13 @@ int upload(T** dst, const std::vector<T>& v) {
   return 0;
 }
 
-constexpr int kRowsPerBlock = 8;   // warps per block in the solve kernels
+constexpr int kRowsPerBlock = 8;   // warps per block in the backward sweep
+constexpr int kBigFront = 96;      // fronts with at least this many eliminated nodes use the grid-wide elimination
 
 }  // namespace
 
 int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef, int leaf_max,
-                 cudaStream_t s) {
+                 bool symmetric, cudaStream_t s) {
   cs.g = g;
   cs.r = r;
   Builder bld;
@@ -376,7 +518,6 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
   std::vector<int> Sall, Ball, kids, cmap;
   std::vector<int2> ents;
   long long xg = 0, uoff = 0, rfo = 0, uvo = 0;
-  // positions of every node inside each front (for the child maps)
   for (int i = 0; i < cs.nfronts; ++i) {
     HostFront& f = F[i];
     FrontDesc& d = desc[i];
@@ -387,10 +528,17 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
     Sall.insert(Sall.end(), f.S.begin(), f.S.end());
     Ball.insert(Ball.end(), f.B.begin(), f.B.end());
     const int nF = d.nS + d.nB;
-    d.X_off = xg;
+    d.bsign = symmetric ? -1 : 1;
+    d.M_off = xg;
     xg += (long long)nF * d.nS;
-    d.G_off = xg;
-    xg += (long long)d.nS * d.nB;
+    if (symmetric) {
+      d.G_off = d.M_off + d.nS;
+      d.g_ld = nF;
+    } else {
+      d.G_off = xg;
+      d.g_ld = d.nB;
+      xg += (long long)d.nS * d.nB;
+    }
     d.U_off = uoff;
     uoff += (long long)d.nB * d.nB;
     d.rf_off = rfo;
@@ -402,7 +550,6 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
     kids.insert(kids.end(), f.kids.begin(), f.kids.end());
   }
   // child maps and original entries need the position of a node inside a front
-  std::vector<int> cmap_off(cs.nfronts, 0);
   for (int i = 0; i < cs.nfronts; ++i) {
     HostFront& f = F[i];
     FrontDesc& d = desc[i];
@@ -443,61 +590,104 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
   cs.factor_entries = xg;
   cs.rf_total = rfo;
   cs.uv_total = uvo;
-  // per-level augmented work offsets
+  // per-level augmented work offsets and solve job lists
   long long aug_max = 0;
+  cs.d_level_list.resize(cs.nlevels);
+  cs.d_fwd_jobs.resize(cs.nlevels);
+  cs.d_bwd_rows.resize(cs.nlevels);
+  cs.n_fwd_jobs.resize(cs.nlevels);
+  cs.n_bwd_rows.resize(cs.nlevels);
+  cs.big_list.resize(cs.nlevels);
+  cs.small_list.resize(cs.nlevels);
+  cs.part_entries = 1;
+  cs.n_slots = 1;
+  std::vector<std::vector<int>> bigs(cs.nlevels), smalls(cs.nlevels);
+  std::vector<std::vector<FwdJob>> fjobs(cs.nlevels);
+  std::vector<std::vector<int2>> brows(cs.nlevels);
   for (int h = 0; h < cs.nlevels; ++h) {
     long long off = 0;
+    int slot = 0, pbase = 0;
     for (int f : cs.level_fronts[h]) {
       desc[f].aug_off = off;
-      const long long nF = desc[f].nS + desc[f].nB;
-      off += nF * (nF + desc[f].nS);
+      const int nS = desc[f].nS, nF = nS + desc[f].nB;
+      off += (long long)nF * (nF + nS);
+      (nS >= kBigFront ? bigs[h] : smalls[h]).push_back(f);
+      const int tiles = (nF + kFwdCols - 1) / kFwdCols;
+      const int chunks = (nS + kFwdChunk - 1) / kFwdChunk;
+      for (int tl = 0; tl < tiles; ++tl) {
+        for (int ch = 0; ch < chunks; ++ch) fjobs[h].push_back(FwdJob{f, tl, ch, chunks, slot, pbase});
+        if (chunks > 1) {
+          pbase += chunks;
+          ++slot;
+        }
+      }
+      for (int r0 = 0; r0 < nS; r0 += kRowsPerBlock) brows[h].push_back(make_int2(f, r0));
     }
     aug_max = std::max(aug_max, off);
+    cs.part_entries = std::max<long long>(cs.part_entries, (long long)pbase * kFwdCols);
+    cs.n_slots = std::max(cs.n_slots, slot);
+    cs.n_fwd_jobs[h] = (int)fjobs[h].size();
+    cs.n_bwd_rows[h] = (int)brows[h].size();
   }
   if (upload(&cs.d_desc, desc) || upload(&cs.d_S, Sall) || upload(&cs.d_B, Ball) ||
       upload(&cs.d_kids, kids) || upload(&cs.d_cmap, cmap))
     return HELM_ECUDA;
   int2* d_ents = nullptr;
   if (upload(&d_ents, ents)) return HELM_ECUDA;
-  cs.d_level_list.resize(cs.nlevels);
-  cs.d_fwd_rows.resize(cs.nlevels);
-  cs.d_bwd_rows.resize(cs.nlevels);
-  cs.n_fwd_rows.resize(cs.nlevels);
-  cs.n_bwd_rows.resize(cs.nlevels);
   for (int h = 0; h < cs.nlevels; ++h) {
-    std::vector<int2> fr, br;
-    for (int f : cs.level_fronts[h]) {
-      const int nF = desc[f].nS + desc[f].nB;
-      for (int r0 = 0; r0 < nF; r0 += kRowsPerBlock) fr.push_back(make_int2(f, r0));
-      for (int r0 = 0; r0 < desc[f].nS; r0 += kRowsPerBlock) br.push_back(make_int2(f, r0));
-    }
-    cs.n_fwd_rows[h] = (int)fr.size();
-    cs.n_bwd_rows[h] = (int)br.size();
-    if (upload(&cs.d_level_list[h], cs.level_fronts[h]) || upload(&cs.d_fwd_rows[h], fr) ||
-        upload(&cs.d_bwd_rows[h], br))
+    if (upload(&cs.d_level_list[h], cs.level_fronts[h]) || upload(&cs.d_fwd_jobs[h], fjobs[h]) ||
+        upload(&cs.d_bwd_rows[h], brows[h]) || upload(&cs.big_list[h], bigs[h]) ||
+        upload(&cs.small_list[h], smalls[h]))
       return HELM_ECUDA;
   }
   HELM_CUDA_TRY(cudaMalloc(&cs.d_factors, std::max<long long>(1, xg) * sizeof(double2)));
   HELM_CUDA_TRY(cudaMalloc(&cs.d_err, sizeof(int)));
   HELM_CUDA_TRY(cudaMemsetAsync(cs.d_err, 0, sizeof(int), s));
-  double2 *d_aug = nullptr, *d_upool = nullptr;
+  double2 *d_aug = nullptr, *d_upool = nullptr, *d_akk = nullptr;
+  int* d_piv = nullptr;
+  size_t maxbig = 1;
+  for (auto& v : bigs) maxbig = std::max(maxbig, v.size());
   HELM_CUDA_TRY(cudaMalloc(&d_aug, std::max<long long>(1, aug_max) * sizeof(double2)));
   HELM_CUDA_TRY(cudaMalloc(&d_upool, std::max<long long>(1, uoff) * sizeof(double2)));
-  KernelTimer kt(HELM_K_SETUP, s);
-  for (int h = 0; h < cs.nlevels; ++h) {
-    const int nf = (int)cs.level_fronts[h].size();
-    fact_assemble_kernel<<<nf, 256, 0, s>>>(cs.d_desc, cs.d_level_list[h], d_aug, d_ents, coef, d_upool,
-                                            cs.d_kids, cs.d_cmap);
-    HELM_LAUNCH_CHECK();
-    fact_gj_kernel<<<nf, 512, 0, s>>>(cs.d_desc, cs.d_level_list[h], d_aug, cs.d_err);
-    HELM_LAUNCH_CHECK();
-    fact_extract_kernel<<<nf, 256, 0, s>>>(cs.d_desc, cs.d_level_list[h], d_aug, cs.d_factors, d_upool);
-    HELM_LAUNCH_CHECK();
+  HELM_CUDA_TRY(cudaMalloc(&d_piv, maxbig * sizeof(int)));
+  HELM_CUDA_TRY(cudaMalloc(&d_akk, maxbig * sizeof(double2)));
+  {
+    KernelTimer kt(HELM_K_SETUP, s);
+    for (int h = 0; h < cs.nlevels; ++h) {
+      const int nf = (int)cs.level_fronts[h].size();
+      fact_assemble_kernel<<<nf, 256, 0, s>>>(cs.d_desc, cs.d_level_list[h], d_aug, d_ents, coef, d_upool,
+                                              cs.d_kids, cs.d_cmap);
+      HELM_LAUNCH_CHECK();
+      if (!smalls[h].empty()) {
+        fact_gj_kernel<<<(int)smalls[h].size(), 512, 0, s>>>(cs.d_desc, cs.small_list[h], d_aug, cs.d_err);
+        HELM_LAUNCH_CHECK();
+      }
+      if (!bigs[h].empty()) {
+        int maxS = 0, maxF = 0, maxLd = 0;
+        for (int f : bigs[h]) {
+          maxS = std::max(maxS, desc[f].nS);
+          maxF = std::max(maxF, desc[f].nS + desc[f].nB);
+          maxLd = std::max(maxLd, 2 * desc[f].nS + desc[f].nB);
+        }
+        const dim3 gp((maxLd + 2047) / 2048, (unsigned)bigs[h].size());
+        const dim3 ge((maxF + 7) / 8, (unsigned)bigs[h].size());
+        for (int k = 0; k < maxS; ++k) {
+          gj_pivot_kernel<<<gp, 256, 0, s>>>(cs.d_desc, cs.big_list[h], d_aug, k, d_piv, d_akk, cs.d_err);
+          HELM_LAUNCH_CHECK();
+          gj_elim_kernel<<<ge, 256, 0, s>>>(cs.d_desc, cs.big_list[h], d_aug, k, d_piv, d_akk);
+          HELM_LAUNCH_CHECK();
+        }
+      }
+      fact_extract_kernel<<<nf, 256, 0, s>>>(cs.d_desc, cs.d_level_list[h], d_aug, cs.d_factors, d_upool);
+      HELM_LAUNCH_CHECK();
+    }
   }
   HELM_CUDA_TRY(cudaStreamSynchronize(s));
   cudaFree(d_aug);
   cudaFree(d_upool);
   cudaFree(d_ents);
+  cudaFree(d_piv);
+  cudaFree(d_akk);
   int herr = 0;
   HELM_CUDA_TRY(cudaMemcpy(&herr, cs.d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (herr) { set_error("coarsest factorisation: zero or non-finite pivot"); return HELM_ENUMERIC; }
@@ -509,32 +699,43 @@ static int ensure_rhs(CoarseSolver& cs, int nrhs) {
   cudaFree(cs.d_rf);
   cudaFree(cs.d_uv);
   cudaFree(cs.d_w);
+  cudaFree(cs.d_part);
+  cudaFree(cs.d_counters);
   HELM_CUDA_TRY(cudaMalloc(&cs.d_rf, std::max<long long>(1, cs.rf_total) * nrhs * sizeof(double2)));
   HELM_CUDA_TRY(cudaMalloc(&cs.d_uv, std::max<long long>(1, cs.uv_total) * nrhs * sizeof(double2)));
   HELM_CUDA_TRY(cudaMalloc(&cs.d_w, cs.g.size * nrhs * sizeof(double2)));
+  HELM_CUDA_TRY(cudaMalloc(&cs.d_part, cs.part_entries * nrhs * sizeof(double2)));
+  HELM_CUDA_TRY(cudaMalloc(&cs.d_counters, cs.n_slots * sizeof(unsigned)));
+  HELM_CUDA_TRY(cudaMemset(cs.d_counters, 0, cs.n_slots * sizeof(unsigned)));
   cs.rhs_cap = nrhs;
+  return 0;
+}
+
+static int solve_sweeps(const CoarseSolver& cs, const double2* b, double2* e, int nrhs, double2* rf,
+                        double2* uv, double2* w, double2* part, unsigned* counters, cudaStream_t s) {
+  for (int h = 0; h < cs.nlevels; ++h) {
+    const int nf = (int)cs.level_fronts[h].size();
+    fwd_assemble_kernel<<<nf, 256, 0, s>>>(cs.d_desc, cs.d_level_list[h], cs.d_S, cs.d_kids, cs.d_cmap, b, rf,
+                                           uv, nrhs, cs.g.size, cs.rf_total, cs.uv_total);
+    HELM_LAUNCH_CHECK();
+    fwd_colsum_kernel<<<cs.n_fwd_jobs[h], kFwdCols, 0, s>>>(cs.d_desc, cs.d_fwd_jobs[h], cs.d_S, cs.d_factors,
+                                                            rf, uv, w, part, counters, nrhs, cs.g.size,
+                                                            cs.rf_total, cs.uv_total);
+    HELM_LAUNCH_CHECK();
+  }
+  for (int h = cs.nlevels - 1; h >= 0; --h) {
+    bwd_matvec_kernel<<<cs.n_bwd_rows[h], 32 * kRowsPerBlock, 0, s>>>(cs.d_desc, cs.d_bwd_rows[h], cs.d_S,
+                                                                      cs.d_B, cs.d_factors, w, e, nrhs,
+                                                                      cs.g.size);
+    HELM_LAUNCH_CHECK();
+  }
   return 0;
 }
 
 int coarse_solve(CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaStream_t s) {
   if (int st = ensure_rhs(cs, nrhs)) return st;
   KernelTimer kt(HELM_K_COARSE, s);
-  for (int h = 0; h < cs.nlevels; ++h) {
-    const int nf = (int)cs.level_fronts[h].size();
-    fwd_assemble_kernel<<<nf, 256, 0, s>>>(cs.d_desc, cs.d_level_list[h], cs.d_S, cs.d_kids, cs.d_cmap, b,
-                                           cs.d_rf, cs.d_uv, nrhs, cs.g.size, cs.rf_total, cs.uv_total);
-    HELM_LAUNCH_CHECK();
-    fwd_matvec_kernel<<<cs.n_fwd_rows[h], 32 * kRowsPerBlock, 0, s>>>(
-        cs.d_desc, cs.d_fwd_rows[h], cs.d_S, cs.d_factors, cs.d_rf, cs.d_uv, cs.d_w, nrhs, cs.g.size,
-        cs.rf_total, cs.uv_total);
-    HELM_LAUNCH_CHECK();
-  }
-  for (int h = cs.nlevels - 1; h >= 0; --h) {
-    bwd_matvec_kernel<<<cs.n_bwd_rows[h], 32 * kRowsPerBlock, 0, s>>>(
-        cs.d_desc, cs.d_bwd_rows[h], cs.d_S, cs.d_B, cs.d_factors, cs.d_w, e, nrhs, cs.g.size);
-    HELM_LAUNCH_CHECK();
-  }
-  return 0;
+  return solve_sweeps(cs, b, e, nrhs, cs.d_rf, cs.d_uv, cs.d_w, cs.d_part, cs.d_counters, s);
 }
 
 // ------------------------------------------------------------------ allocation-free variant
@@ -552,9 +753,10 @@ double2* g_noalloc_addr[kMaxDevices] = {};
 }  // namespace
 
 int coarse_solve_noalloc(const CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaStream_t s) {
-  const long long per_rhs = cs.rf_total + cs.uv_total + cs.g.size;
-  if (nrhs < 1 || per_rhs * nrhs > kNoAllocScratchEntries) {
-    set_error("allocation-free coarsest solve needs " + std::to_string(per_rhs * nrhs) +
+  const long long per_rhs = cs.rf_total + cs.uv_total + cs.g.size + cs.part_entries;
+  const long long counter_entries = (cs.n_slots * (long long)sizeof(unsigned) + sizeof(double2) - 1) / sizeof(double2);
+  if (nrhs < 1 || per_rhs * nrhs + counter_entries > kNoAllocScratchEntries) {
+    set_error("allocation-free coarsest solve needs " + std::to_string(per_rhs * nrhs + counter_entries) +
               " complex scratch entries; the static array holds " + std::to_string(kNoAllocScratchEntries));
     return HELM_EINVAL;
   }
@@ -576,28 +778,17 @@ int coarse_solve_noalloc(const CoarseSolver& cs, const double2* b, double2* e, i
     }
     base = g_noalloc_addr[dev];
   }
-  // every scratch entry that is read is written earlier in the same call: the front
-  // vectors from b, the update vectors by the child fronts, w for every eliminated node
-  double2* rf = base;
+  // The column-tile counters must start at zero and are cleared here; every other
+  // scratch entry that is read is written earlier in the same call (front vectors from
+  // b, update vectors and partial sums by the kernels that produce them, w for every
+  // eliminated node).
+  unsigned* counters = reinterpret_cast<unsigned*>(base);
+  HELM_CUDA_TRY(cudaMemsetAsync(counters, 0, cs.n_slots * sizeof(unsigned), s));
+  double2* rf = base + counter_entries;
   double2* uv = rf + cs.rf_total * nrhs;
   double2* w = uv + cs.uv_total * nrhs;
-  for (int h = 0; h < cs.nlevels; ++h) {
-    const int nf = (int)cs.level_fronts[h].size();
-    fwd_assemble_kernel<<<nf, 256, 0, s>>>(cs.d_desc, cs.d_level_list[h], cs.d_S, cs.d_kids, cs.d_cmap, b, rf,
-                                           uv, nrhs, cs.g.size, cs.rf_total, cs.uv_total);
-    HELM_LAUNCH_CHECK();
-    fwd_matvec_kernel<<<cs.n_fwd_rows[h], 32 * kRowsPerBlock, 0, s>>>(cs.d_desc, cs.d_fwd_rows[h], cs.d_S,
-                                                                      cs.d_factors, rf, uv, w, nrhs, cs.g.size,
-                                                                      cs.rf_total, cs.uv_total);
-    HELM_LAUNCH_CHECK();
-  }
-  for (int h = cs.nlevels - 1; h >= 0; --h) {
-    bwd_matvec_kernel<<<cs.n_bwd_rows[h], 32 * kRowsPerBlock, 0, s>>>(cs.d_desc, cs.d_bwd_rows[h], cs.d_S,
-                                                                      cs.d_B, cs.d_factors, w, e, nrhs,
-                                                                      cs.g.size);
-    HELM_LAUNCH_CHECK();
-  }
-  return 0;
+  double2* part = w + cs.g.size * nrhs;
+  return solve_sweeps(cs, b, e, nrhs, rf, uv, w, part, counters, s);
 }
 
 void coarse_free(CoarseSolver& cs) {
@@ -609,8 +800,12 @@ void coarse_free(CoarseSolver& cs) {
   cudaFree(cs.d_factors);
   cudaFree(cs.d_err);
   for (auto p : cs.d_level_list) cudaFree(p);
-  for (auto p : cs.d_fwd_rows) cudaFree(p);
+  for (auto p : cs.d_fwd_jobs) cudaFree(p);
   for (auto p : cs.d_bwd_rows) cudaFree(p);
+  for (auto p : cs.big_list) cudaFree(p);
+  for (auto p : cs.small_list) cudaFree(p);
+  cudaFree(cs.d_part);
+  cudaFree(cs.d_counters);
   cudaFree(cs.d_rf);
   cudaFree(cs.d_uv);
   cudaFree(cs.d_w);

@@ -6,11 +6,16 @@
 
 namespace helm {
 
+constexpr int kFwdCols = 256;    // columns per block of the forward sweep
+constexpr int kFwdChunk = 64;    // rows per partial sum of the forward sweep
+
 struct FrontDesc {
   int nS, nB;             // eliminated (separator / leaf) nodes, boundary (ancestor) nodes
   int S_off, B_off;       // offsets into the S / B node-index arrays
-  long long X_off;        // forward matrix  [nS+nB][nS]: rows S: F_SS^-1, rows B: -F_BS F_SS^-1
-  long long G_off;        // backward matrix [nS][nB]:    F_SS^-1 F_SB
+  long long M_off;        // forward matrix [nS][nS+nB], read as column sums (see coarse.cu)
+  long long G_off;        // backward matrix F_SS^-1 F_SB, rows of stride g_ld
+  int g_ld;
+  int bsign;              // -1: M = [F_SS^-1 | G] (symmetric operator); +1: M = X^T
   long long aug_off;      // augmented front [nF][nF+nS] within the level work buffer
   long long U_off;        // update matrix   [nB][nB] = F_BB - F_BS F_SS^-1 F_SB
   int ent_off, ent_cnt;   // original matrix entries scattered into the front
@@ -18,6 +23,11 @@ struct FrontDesc {
   int cmap_off;           // this front's boundary positions inside its parent's front
   long long rf_off;       // solve scratch: front vector (nF entries)
   long long uv_off;       // solve scratch: update vector (nB entries)
+};
+
+struct FwdJob {
+  int front, tile, chunk, nchunks;   // column tile and row chunk of one front
+  int slot, pbase;                   // counter of the tile; first partial-sum slot of the tile
 };
 
 struct CoarseSolver {
@@ -31,11 +41,16 @@ struct CoarseSolver {
   int* d_B = nullptr;
   int* d_kids = nullptr;
   int* d_cmap = nullptr;
-  double2* d_factors = nullptr;       // X and G blocks of every front
+  double2* d_factors = nullptr;       // M (and G) blocks of every front
   long long factor_entries = 0;
   std::vector<int*> d_level_list;     // per level: front ids
-  std::vector<int2*> d_fwd_rows;      // per level: (front, first row) blocks over nF rows
-  std::vector<int> n_fwd_rows;
+  std::vector<FwdJob*> d_fwd_jobs;    // per level: forward-sweep blocks
+  std::vector<int> n_fwd_jobs;
+  std::vector<int*> big_list, small_list;   // per level: fronts by elimination path
+  long long part_entries = 1;         // partial sums of the forward sweep (per right-hand side)
+  int n_slots = 1;                    // column-tile counters
+  double2* d_part = nullptr;
+  unsigned* d_counters = nullptr;
   std::vector<int2*> d_bwd_rows;      // per level: blocks over nS rows
   std::vector<int> n_bwd_rows;
   long long rf_total = 0, uv_total = 0;
@@ -49,8 +64,9 @@ struct CoarseSolver {
 
 // Symbolic analysis and numeric factorisation of the coarsest operator given by its
 // assembled stencil coef (c128, [ncoef][nodes]) of radius r.  leaf_max: largest leaf box.
+// symmetric: the operator is complex-symmetric (A = A^T), which halves the stored coupling.
 int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef, int leaf_max,
-                 cudaStream_t s);
+                 bool symmetric, cudaStream_t s);
 
 // e = A^-1 b for nrhs vectors (c128, [nrhs][nodes]).
 int coarse_solve(CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaStream_t s);
