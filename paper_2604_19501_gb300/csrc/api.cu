@@ -454,7 +454,10 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
   // coarsest factorisation
   // the coarsest operator is complex-symmetric when R and P / 2^d are transposes on both levels
   const bool symmetric = o->intergrid != HELM_INTERGRID_LEVDEP;
-  if ((st = coarse_setup(c->cs, c->g[2], c->r3, c->A3_64, 64, symmetric, c->s))) return bail(st);
+  // mixed precision: the coarsest factors in double-float arithmetic (FP32 pipes);
+  // FP64 mode: native FP64
+  const bool df = o->precision == HELM_MIXED;
+  if ((st = coarse_setup(c->cs, c->g[2], c->r3, c->A3_64, 64, symmetric, df, c->s))) return bail(st);
 
   // workspaces
   const int m = o->restart;

@@ -32,6 +32,7 @@
 #include <mutex>
 #include <unordered_map>
 #include "coarse.cuh"
+#include "df64.cuh"
 #include "timer.cuh"
 
 namespace helm {
@@ -330,9 +331,16 @@ __global__ void __launch_bounds__(256) gj_elim_kernel(const FrontDesc* __restric
 }
 
 // Copies the factors out of the eliminated augmented fronts.
+// Factors are stored as complex FP64 (double2) or, with `df`, as double-float float4 of the
+// same size.
+__device__ __forceinline__ void store_factor(double2* base, long long i, double2 v, bool df) {
+  if (df) reinterpret_cast<float4*>(base)[i] = to_df(v);
+  else base[i] = v;
+}
+
 __global__ void fact_extract_kernel(const FrontDesc* __restrict__ desc, const int* __restrict__ list,
                                     const double2* __restrict__ aug, double2* __restrict__ factors,
-                                    double2* __restrict__ upool) {
+                                    double2* __restrict__ upool, bool df) {
   const FrontDesc d = desc[list[blockIdx.x]];
   const int nS = d.nS, nB = d.nB, nF = nS + nB, ld = nF + nS;
   const double2* A = aug + d.aug_off;
@@ -342,15 +350,15 @@ __global__ void fact_extract_kernel(const FrontDesc* __restrict__ desc, const in
   for (long long t = threadIdx.x; t < nm; t += blockDim.x) {
     const int row = (int)(t / nF), col = (int)(t % nF);
     if (d.bsign < 0)   // [F_SS^-1 | G]
-      M[t] = A[(long long)row * ld + (col < nS ? nF + col : col)];
+      store_factor(M, t, A[(long long)row * ld + (col < nS ? nF + col : col)], df);
     else               // X^T, X = [F_SS^-1 ; -F_BS F_SS^-1]
-      M[t] = A[(long long)col * ld + nF + row];
+      store_factor(M, t, A[(long long)col * ld + nF + row], df);
   }
   if (d.bsign > 0) {
     double2* G = factors + d.G_off;
     for (long long t = threadIdx.x; t < (long long)nS * nB; t += blockDim.x) {
       const int row = (int)(t / nB), col = (int)(t % nB);
-      G[t] = A[(long long)row * ld + nS + col];
+      store_factor(G, t, A[(long long)row * ld + nS + col], df);
     }
   }
   for (long long t = threadIdx.x; t < (long long)nB * nB; t += blockDim.x) {
@@ -401,6 +409,7 @@ __device__ __forceinline__ void fwd_write(const FrontDesc& d, const int* __restr
   }
 }
 
+template <bool DF>
 __global__ void __launch_bounds__(kFwdCols) fwd_colsum_kernel(
     const FrontDesc* __restrict__ desc, const FwdJob* __restrict__ jobs, const int* __restrict__ Sidx,
     const double2* __restrict__ factors, const double2* __restrict__ rf, double2* __restrict__ uv,
@@ -412,17 +421,29 @@ __global__ void __launch_bounds__(kFwdCols) fwd_colsum_kernel(
   const int tid = threadIdx.x;
   const int t = job.tile * kFwdCols + tid;
   const int s0 = job.chunk * kFwdChunk, s1 = min(d.nS, s0 + kFwdChunk);
-  const double2* M = factors + d.M_off;
   __shared__ double2 rs[kFwdChunk];
+  __shared__ float4 rsd[kFwdChunk];
   __shared__ bool s_last;
   for (int r = 0; r < nrhs; ++r) {
-    for (int q = tid; q < s1 - s0; q += blockDim.x) rs[q] = rf[r * rf_total + d.rf_off + s0 + q];
+    for (int q = tid; q < s1 - s0; q += blockDim.x) {
+      const double2 v = rf[r * rf_total + d.rf_off + s0 + q];
+      if (DF) rsd[q] = to_df(v);
+      else rs[q] = v;
+    }
     __syncthreads();
     double2 acc = make_double2(0.0, 0.0);
     if (t < nF) {
-      const double2* col = M + (long long)s0 * nF + t;
+      if (DF) {
+        const float4* col = reinterpret_cast<const float4*>(factors + d.M_off) + (long long)s0 * nF + t;
+        float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 4
-      for (int s = 0; s < s1 - s0; ++s) acc = cmac(acc, col[(long long)s * nF], rs[s]);
+        for (int s = 0; s < s1 - s0; ++s) df_cmac(a4, col[(long long)s * nF], rsd[s]);
+        acc = from_df(a4);
+      } else {
+        const double2* col = factors + d.M_off + (long long)s0 * nF + t;
+#pragma unroll 4
+        for (int s = 0; s < s1 - s0; ++s) acc = cmac(acc, col[(long long)s * nF], rs[s]);
+      }
     }
     if (job.nchunks == 1) {
       if (t < nF) fwd_write(d, Sidx, t, r, acc, rf, uv, w, nodes, rf_total, uv_total);
@@ -450,33 +471,46 @@ __global__ void __launch_bounds__(kFwdCols) fwd_colsum_kernel(
   if (tid == 0) counters[job.slot] = 0u;
 }
 
-// one warp per row of G: x_S[row] = w_S[row] - G[row, :] . x_B
+// one warp per row of G: x_S[row] = w_S[row] - G[row, :] . x_B.  With DF the factors are
+// double-float and x_B is read from the double-float copy xd of x, which this sweep
+// also writes.
+template <bool DF>
 __global__ void __launch_bounds__(256) bwd_matvec_kernel(const FrontDesc* __restrict__ desc,
                                                          const int2* __restrict__ rows,
                                                          const int* __restrict__ Sidx,
                                                          const int* __restrict__ Bidx,
                                                          const double2* __restrict__ factors,
                                                          const double2* __restrict__ w,
-                                                         double2* __restrict__ x, int nrhs,
-                                                         long long nodes) {
+                                                         double2* __restrict__ x, float4* __restrict__ xd,
+                                                         int nrhs, long long nodes) {
   const int2 job = rows[blockIdx.x];
   const FrontDesc d = desc[job.x];
   const int row = job.y + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (row >= d.nS) return;
-  const double2* G = factors + d.G_off + (long long)row * d.g_ld;
   const int* B = Bidx + d.B_off;
   const int node = Sidx[d.S_off + row];
   for (int r = 0; r < nrhs; ++r) {
-    const double2* xr = x + r * nodes;
     double2 acc = make_double2(0.0, 0.0);
-    for (int c = lane; c < d.nB; c += 32) acc = cmac(acc, G[c], xr[B[c]]);
+    if (DF) {
+      const float4* G = reinterpret_cast<const float4*>(factors + d.G_off) + (long long)row * d.g_ld;
+      const float4* xr = xd + r * nodes;
+      float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int c = lane; c < d.nB; c += 32) df_cmac(a4, G[c], xr[B[c]]);
+      acc = from_df(a4);
+    } else {
+      const double2* G = factors + d.G_off + (long long)row * d.g_ld;
+      const double2* xr = x + r * nodes;
+      for (int c = lane; c < d.nB; c += 32) acc = cmac(acc, G[c], xr[B[c]]);
+    }
     for (int off = 16; off > 0; off >>= 1) {
       acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
       acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
     }
     if (lane == 0) {
       const double2 wv = w[r * nodes + node];
-      x[r * nodes + node] = make_double2(wv.x - acc.x, wv.y - acc.y);
+      const double2 xv = make_double2(wv.x - acc.x, wv.y - acc.y);
+      x[r * nodes + node] = xv;
+      if (DF) xd[r * nodes + node] = to_df(xv);
     }
   }
 }
@@ -495,9 +529,10 @@ constexpr int kBigFront = 96;      // fronts with at least this many eliminated 
 }  // namespace
 
 int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef, int leaf_max,
-                 bool symmetric, cudaStream_t s) {
+                 bool symmetric, bool df, cudaStream_t s) {
   cs.g = g;
   cs.r = r;
+  cs.df = df;
   Builder bld;
   bld.dim = g.dim;
   for (int d = 0; d < 3; ++d) bld.N[d] = g.N[d];
@@ -678,7 +713,7 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
           HELM_LAUNCH_CHECK();
         }
       }
-      fact_extract_kernel<<<nf, 256, 0, s>>>(cs.d_desc, cs.d_level_list[h], d_aug, cs.d_factors, d_upool);
+      fact_extract_kernel<<<nf, 256, 0, s>>>(cs.d_desc, cs.d_level_list[h], d_aug, cs.d_factors, d_upool, df);
       HELM_LAUNCH_CHECK();
     }
   }
@@ -701,6 +736,8 @@ static int ensure_rhs(CoarseSolver& cs, int nrhs) {
   cudaFree(cs.d_w);
   cudaFree(cs.d_part);
   cudaFree(cs.d_counters);
+  cudaFree(cs.d_xd);
+  HELM_CUDA_TRY(cudaMalloc(&cs.d_xd, cs.g.size * nrhs * sizeof(float4)));
   HELM_CUDA_TRY(cudaMalloc(&cs.d_rf, std::max<long long>(1, cs.rf_total) * nrhs * sizeof(double2)));
   HELM_CUDA_TRY(cudaMalloc(&cs.d_uv, std::max<long long>(1, cs.uv_total) * nrhs * sizeof(double2)));
   HELM_CUDA_TRY(cudaMalloc(&cs.d_w, cs.g.size * nrhs * sizeof(double2)));
@@ -712,21 +749,30 @@ static int ensure_rhs(CoarseSolver& cs, int nrhs) {
 }
 
 static int solve_sweeps(const CoarseSolver& cs, const double2* b, double2* e, int nrhs, double2* rf,
-                        double2* uv, double2* w, double2* part, unsigned* counters, cudaStream_t s) {
+                        double2* uv, double2* w, double2* part, unsigned* counters, float4* xd,
+                        cudaStream_t s) {
   for (int h = 0; h < cs.nlevels; ++h) {
     const int nf = (int)cs.level_fronts[h].size();
     fwd_assemble_kernel<<<nf, 256, 0, s>>>(cs.d_desc, cs.d_level_list[h], cs.d_S, cs.d_kids, cs.d_cmap, b, rf,
                                            uv, nrhs, cs.g.size, cs.rf_total, cs.uv_total);
     HELM_LAUNCH_CHECK();
-    fwd_colsum_kernel<<<cs.n_fwd_jobs[h], kFwdCols, 0, s>>>(cs.d_desc, cs.d_fwd_jobs[h], cs.d_S, cs.d_factors,
-                                                            rf, uv, w, part, counters, nrhs, cs.g.size,
-                                                            cs.rf_total, cs.uv_total);
+    if (cs.df)
+      fwd_colsum_kernel<true><<<cs.n_fwd_jobs[h], kFwdCols, 0, s>>>(cs.d_desc, cs.d_fwd_jobs[h], cs.d_S,
+                                                                    cs.d_factors, rf, uv, w, part, counters, nrhs,
+                                                                    cs.g.size, cs.rf_total, cs.uv_total);
+    else
+      fwd_colsum_kernel<false><<<cs.n_fwd_jobs[h], kFwdCols, 0, s>>>(cs.d_desc, cs.d_fwd_jobs[h], cs.d_S,
+                                                                     cs.d_factors, rf, uv, w, part, counters, nrhs,
+                                                                     cs.g.size, cs.rf_total, cs.uv_total);
     HELM_LAUNCH_CHECK();
   }
   for (int h = cs.nlevels - 1; h >= 0; --h) {
-    bwd_matvec_kernel<<<cs.n_bwd_rows[h], 32 * kRowsPerBlock, 0, s>>>(cs.d_desc, cs.d_bwd_rows[h], cs.d_S,
-                                                                      cs.d_B, cs.d_factors, w, e, nrhs,
-                                                                      cs.g.size);
+    if (cs.df)
+      bwd_matvec_kernel<true><<<cs.n_bwd_rows[h], 32 * kRowsPerBlock, 0, s>>>(
+          cs.d_desc, cs.d_bwd_rows[h], cs.d_S, cs.d_B, cs.d_factors, w, e, xd, nrhs, cs.g.size);
+    else
+      bwd_matvec_kernel<false><<<cs.n_bwd_rows[h], 32 * kRowsPerBlock, 0, s>>>(
+          cs.d_desc, cs.d_bwd_rows[h], cs.d_S, cs.d_B, cs.d_factors, w, e, xd, nrhs, cs.g.size);
     HELM_LAUNCH_CHECK();
   }
   return 0;
@@ -735,7 +781,7 @@ static int solve_sweeps(const CoarseSolver& cs, const double2* b, double2* e, in
 int coarse_solve(CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaStream_t s) {
   if (int st = ensure_rhs(cs, nrhs)) return st;
   KernelTimer kt(HELM_K_COARSE, s);
-  return solve_sweeps(cs, b, e, nrhs, cs.d_rf, cs.d_uv, cs.d_w, cs.d_part, cs.d_counters, s);
+  return solve_sweeps(cs, b, e, nrhs, cs.d_rf, cs.d_uv, cs.d_w, cs.d_part, cs.d_counters, cs.d_xd, s);
 }
 
 // ------------------------------------------------------------------ allocation-free variant
@@ -753,7 +799,7 @@ double2* g_noalloc_addr[kMaxDevices] = {};
 }  // namespace
 
 int coarse_solve_noalloc(const CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaStream_t s) {
-  const long long per_rhs = cs.rf_total + cs.uv_total + cs.g.size + cs.part_entries;
+  const long long per_rhs = cs.rf_total + cs.uv_total + cs.g.size + cs.part_entries + cs.g.size;
   const long long counter_entries = (cs.n_slots * (long long)sizeof(unsigned) + sizeof(double2) - 1) / sizeof(double2);
   if (nrhs < 1 || per_rhs * nrhs + counter_entries > kNoAllocScratchEntries) {
     set_error("allocation-free coarsest solve needs " + std::to_string(per_rhs * nrhs + counter_entries) +
@@ -788,7 +834,8 @@ int coarse_solve_noalloc(const CoarseSolver& cs, const double2* b, double2* e, i
   double2* uv = rf + cs.rf_total * nrhs;
   double2* w = uv + cs.uv_total * nrhs;
   double2* part = w + cs.g.size * nrhs;
-  return solve_sweeps(cs, b, e, nrhs, rf, uv, w, part, counters, s);
+  float4* xd = reinterpret_cast<float4*>(part + cs.part_entries * nrhs);   // float4 and double2 are both 16 bytes
+  return solve_sweeps(cs, b, e, nrhs, rf, uv, w, part, counters, xd, s);
 }
 
 void coarse_free(CoarseSolver& cs) {
@@ -809,6 +856,7 @@ void coarse_free(CoarseSolver& cs) {
   cudaFree(cs.d_rf);
   cudaFree(cs.d_uv);
   cudaFree(cs.d_w);
+  cudaFree(cs.d_xd);
   cs = CoarseSolver();
 }
 

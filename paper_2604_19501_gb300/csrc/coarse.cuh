@@ -51,6 +51,8 @@ struct CoarseSolver {
   int n_slots = 1;                    // column-tile counters
   double2* d_part = nullptr;
   unsigned* d_counters = nullptr;
+  bool df = false;                    // factors stored and applied in double-float arithmetic
+  float4* d_xd = nullptr;             // double-float copy of the backward-sweep result
   std::vector<int2*> d_bwd_rows;      // per level: blocks over nS rows
   std::vector<int> n_bwd_rows;
   long long rf_total = 0, uv_total = 0;
@@ -65,8 +67,9 @@ struct CoarseSolver {
 // Symbolic analysis and numeric factorisation of the coarsest operator given by its
 // assembled stencil coef (c128, [ncoef][nodes]) of radius r.  leaf_max: largest leaf box.
 // symmetric: the operator is complex-symmetric (A = A^T), which halves the stored coupling.
+// df: store the factors as double-float and apply them on the FP32 pipes.
 int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef, int leaf_max,
-                 bool symmetric, cudaStream_t s);
+                 bool symmetric, bool df, cudaStream_t s);
 
 // e = A^-1 b for nrhs vectors (c128, [nrhs][nodes]).
 int coarse_solve(CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaStream_t s);

@@ -132,6 +132,20 @@ def test_coarse_solve(cases, n):
     assert np.max(np.abs(res)) < 1e-10 * np.max(np.abs(b))
 
 
+@pytest.mark.parametrize("n,order,ig", [((32, 24), "2nd", "fw"), ((48, 40), "4th", "cubic"),
+                                        ((8, 12, 16), "2nd", "fw"), ((8, 8, 8), "4th", "levdep")])
+def test_coarse_solve_double_float(n, order, ig):
+    """Mixed-precision contexts apply the coarsest factors in double-float arithmetic;
+    the result stays within 1e-10 of the FP64 direct solve."""
+    c = Case(n, abc=2, alpha3=1.05, seed=12, order=order, intergrid=ig)
+    s = c.solver(precision="mixed")
+    b = rand_complex((2,) + c.hier.grids[2].shape, 22)
+    e = _n(s.coarse_solve(_t(b)))
+    ref = np.stack([c.hier.coarse_solve(bi.ravel()).reshape(bi.shape) for bi in b])
+    assert rel(e, ref) < 1e-10
+    s.close()
+
+
 @pytest.mark.parametrize("cyc", ["V", "W"])
 @pytest.mark.parametrize("smoother", ["jacobi", "rb"])
 @pytest.mark.parametrize("n", [(32, 24), (8, 12, 16), (4, 4)])
