@@ -60,6 +60,7 @@ struct helm_ctx {
   long long launches = 0;
   int* d_bad = nullptr;
   LaunchTimer timer;
+  float4* cdf = nullptr;                       // mixed precision: fine coefficients as double-float
 };
 
 namespace {
@@ -112,7 +113,7 @@ GridDims dims_of(int dim, const int n[3], int level) {
   return g;
 }
 
-size_t esize(Prec p) { return p == P64 ? sizeof(double2) : sizeof(float2); }
+size_t esize(Prec p) { return p == P32 ? sizeof(float2) : sizeof(double2); }
 
 template <typename T>
 int dmalloc(T** p, size_t bytes) {
@@ -248,6 +249,10 @@ int fgmres_one(helm_ctx* c, const double2* q, double2* p, double tol, int maxit,
   const int m = c->o.restart;
   const Prec zp = cycle_prec(c);
   const size_t zes = esize(zp);
+  // mixed precision: the basis V and w are double-float (float4), arithmetic on FP32 pipes
+  const bool df = zp == P32;
+  float4* Vd = reinterpret_cast<float4*>(c->V);
+  float4* wd = reinterpret_cast<float4*>(c->w);
   HELM_CUDA_TRY(cudaMemsetAsync(p, 0, n * sizeof(double2), c->s));
   if (int st = k_norm(c->ks, n, q, c->r, c->s)) return st;
   if (int st = sync_scal(c)) return st;
@@ -263,19 +268,32 @@ int fgmres_one(helm_ctx* c, const double2* q, double2* p, double tol, int maxit,
   double est = beta / bnorm;
   while (true) {
     if (beta / bnorm < tol || its >= maxit) break;
-    if (int st = k_start_cycle(c->ks, n, c->r, c->V, c->s)) return st;
+    if (df) {
+      if (int st = k_start_cycle_df(c->ks, n, c->r, Vd, c->s)) return st;
+    } else if (int st = k_start_cycle(c->ks, n, c->r, c->V, c->s)) {
+      return st;
+    }
     int k = 0;
     for (int j = 0; j < m; ++j) {
       void* zj = (char*)c->Z + (size_t)j * n * zes;
-      if (int st = run_cycle(c, c->V + (size_t)j * n, P64, zj, zp, 1)) return st;
-      if (int st = k_arnoldi(c->ks, c->fine, c->kap64, zj, zp, c->w, c->V, n, j, c->s)) return st;
+      if (df) {
+        if (int st = run_cycle(c, Vd + (size_t)j * n, P_DF, zj, zp, 1)) return st;
+        if (int st = k_arnoldi_df(c->ks, c->fine, c->cdf, (const float2*)zj, wd, Vd, n, j, c->s)) return st;
+      } else {
+        if (int st = run_cycle(c, c->V + (size_t)j * n, P64, zj, zp, 1)) return st;
+        if (int st = k_arnoldi(c->ks, c->fine, c->kap64, zj, zp, c->w, c->V, n, j, c->s)) return st;
+      }
       if (int st = sync_scal(c)) return st;
       ++its;
       k = j + 1;
       est = c->h_scal[KS_EST];
       if (!std::isfinite(est)) return fail(HELM_ENUMERIC, "non-finite residual estimate");
       if (est < tol || its >= maxit || c->h_scal[KS_HN] == 0.0) break;
-      if (int st = k_normalize(c->ks, n, c->w, c->V, n, j, c->V + (size_t)(j + 1) * n, c->s)) return st;
+      if (df) {
+        if (int st = k_normalize_df(c->ks, n, wd, Vd, n, j, Vd + (size_t)(j + 1) * n, c->s)) return st;
+      } else if (int st = k_normalize(c->ks, n, c->w, c->V, n, j, c->V + (size_t)(j + 1) * n, c->s)) {
+        return st;
+      }
     }
     if (int st = k_update_solution(c->ks, n, p, c->Z, zp, n, k, c->s)) return st;
     if (int st = k_true_residual(c->ks, c->fine, c->kap64, q, p, c->r, c->s)) return st;
@@ -467,6 +485,10 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
       (st = dmalloc(&c->w, n1 * sizeof(double2))) || (st = dmalloc(&c->r, n1 * sizeof(double2))))
     return bail(st);
   if ((st = krylov_alloc(c->ks, m))) return bail(st);
+  if (o->precision == HELM_MIXED) {
+    if ((st = dmalloc(&c->cdf, n1 * sizeof(float4)))) return bail(st);
+    if ((st = k_coef_df(c->fine, c->kap64, c->cdf, c->s))) return bail(HELM_ECUDA);
+  }
   if (cudaMallocHost(&c->h_scal, sizeof(double) * KS_COUNT) != cudaSuccess) return bail(fail(HELM_ENOMEM, "pinned alloc"));
   if (cudaStreamSynchronize(c->s) != cudaSuccess) return bail(fail(HELM_ECUDA, cudaGetErrorString(cudaGetLastError())));
   *out = c;
@@ -482,7 +504,8 @@ int helm_destroy(helm_ctx* c) {
   krylov_free(c->ks);
   for (void* p : {(void*)c->d_gam, (void*)c->kap64, (void*)c->kap32, (void*)c->A2_64, (void*)c->A2_dinv64,
                   (void*)c->A2_32, (void*)c->A2_dinv32, (void*)c->Mk2, (void*)c->A3_64, (void*)c->A3_dinv64,
-                  (void*)c->V, (void*)c->w, (void*)c->r, c->Z, (void*)c->stage, (void*)c->d_bad})
+                  (void*)c->V, (void*)c->w, (void*)c->r, c->Z, (void*)c->stage, (void*)c->d_bad,
+                  (void*)c->cdf})
     cudaFree(p);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   delete[] c->h_gam;

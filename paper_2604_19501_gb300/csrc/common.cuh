@@ -21,6 +21,18 @@ template <typename T> __host__ __device__ __forceinline__ c2<T> mk(T r, T i) {
 template <typename T, typename S> __host__ __device__ __forceinline__ c2<T> cvt(S a) {
   return mk<T>(static_cast<T>(a.x), static_cast<T>(a.y));
 }
+// double-float storage (re_hi, im_hi, re_lo, im_lo): FP32 arithmetic takes the high parts
+// (the value rounded to float), FP64 arithmetic the sum.
+template <typename T> struct DfLoad;
+template <> struct DfLoad<float> {
+  __host__ __device__ static c2<float> get(float4 a) { return mk<float>(a.x, a.y); }
+};
+template <> struct DfLoad<double> {
+  __host__ __device__ static c2<double> get(float4 a) {
+    return mk<double>((double)a.x + (double)a.z, (double)a.y + (double)a.w);
+  }
+};
+template <typename T> __host__ __device__ __forceinline__ c2<T> cvt(float4 a) { return DfLoad<T>::get(a); }
 // Arithmetic on the interleaved complex types (overloads for double2 and float2; the
 // template parameter of the call sites only selects the type).
 #define HELM_COMPLEX_OPS(C, R)                                                             \

@@ -46,4 +46,83 @@ __device__ __forceinline__ void df_cmac(float4& acc, float4 x, float4 r) {
   acc.w += t + e + fmaf(x.y, r.z, x.w * r.x);
 }
 
+// acc += conj(v) * w (same accumulator convention as df_cmac)
+__device__ __forceinline__ void df_cmacc(float4& acc, float4 v, float4 w) {
+  float p, e, s, t;
+  // re += v.re * w.re
+  p = v.x * w.x; e = fmaf(v.x, w.x, -p);
+  two_sum(acc.x, p, s, t); acc.x = s;
+  acc.z += t + e + fmaf(v.x, w.z, v.z * w.x);
+  // re += v.im * w.im
+  p = v.y * w.y; e = fmaf(v.y, w.y, -p);
+  two_sum(acc.x, p, s, t); acc.x = s;
+  acc.z += t + e + fmaf(v.y, w.w, v.w * w.y);
+  // im += v.re * w.im
+  p = v.x * w.y; e = fmaf(v.x, w.y, -p);
+  two_sum(acc.y, p, s, t); acc.y = s;
+  acc.w += t + e + fmaf(v.x, w.w, v.z * w.y);
+  // im -= v.im * w.re
+  p = v.y * w.x; e = fmaf(v.y, w.x, -p);
+  two_sum(acc.y, -p, s, t); acc.y = s;
+  acc.w += t - e - fmaf(v.y, w.z, v.w * w.x);
+}
+
+// ---- normalised double-float reals (hi, lo with |lo| <= ulp(hi) / 2) and complex values
+struct dd {
+  float hi, lo;
+};
+struct cdd {
+  dd re, im;
+};
+
+__device__ __forceinline__ dd dd_norm(float s, float t) {
+  const float hi = s + t;
+  return dd{hi, t - (hi - s)};
+}
+__device__ __forceinline__ dd dd_make(double v) {
+  const float hi = __double2float_rn(v);
+  return dd{hi, __double2float_rn(v - (double)hi)};
+}
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  float s, t;
+  two_sum(a.hi, b.hi, s, t);
+  return dd_norm(s, t + a.lo + b.lo);
+}
+__device__ __forceinline__ dd dd_neg(dd a) { return dd{-a.hi, -a.lo}; }
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+  const float p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.hi, -p) + fmaf(a.hi, b.lo, a.lo * b.hi);
+  return dd_norm(p, e);
+}
+// a * b with b an exact float
+__device__ __forceinline__ dd dd_mulf(dd a, float b) {
+  const float p = a.hi * b;
+  return dd_norm(p, fmaf(a.hi, b, -p) + a.lo * b);
+}
+__device__ __forceinline__ dd dd_prodf(float a, float b) {
+  const float p = a * b;
+  return dd_norm(p, fmaf(a, b, -p));
+}
+
+__device__ __forceinline__ cdd cdd_load(float4 v) { return cdd{dd{v.x, v.z}, dd{v.y, v.w}}; }
+__device__ __forceinline__ float4 cdd_store(cdd a) { return make_float4(a.re.hi, a.im.hi, a.re.lo, a.im.lo); }
+__device__ __forceinline__ cdd cdd_make(double2 v) { return cdd{dd_make(v.x), dd_make(v.y)}; }
+__device__ __forceinline__ cdd cdd_add(cdd a, cdd b) { return cdd{dd_add(a.re, b.re), dd_add(a.im, b.im)}; }
+__device__ __forceinline__ cdd cdd_sub(cdd a, cdd b) {
+  return cdd{dd_add(a.re, dd_neg(b.re)), dd_add(a.im, dd_neg(b.im))};
+}
+__device__ __forceinline__ cdd cdd_mul(cdd a, cdd b) {
+  return cdd{dd_add(dd_mul(a.re, b.re), dd_neg(dd_mul(a.im, b.im))),
+             dd_add(dd_mul(a.re, b.im), dd_mul(a.im, b.re))};
+}
+// a * z with z a complex of exact floats
+__device__ __forceinline__ cdd cdd_mulf(cdd a, float2 z) {
+  return cdd{dd_add(dd_mulf(a.re, z.x), dd_neg(dd_mulf(a.im, z.y))),
+             dd_add(dd_mulf(a.re, z.y), dd_mulf(a.im, z.x))};
+}
+__device__ __forceinline__ cdd cdd_scale(cdd a, dd s) { return cdd{dd_mul(a.re, s), dd_mul(a.im, s)}; }
+// w * z with w a small exact float weight and z a complex of exact floats
+__device__ __forceinline__ cdd cdd_wz(float w, float2 z) { return cdd{dd_prodf(w, z.x), dd_prodf(w, z.y)}; }
+__device__ __forceinline__ cdd cdd_zero() { return cdd{dd{0.f, 0.f}, dd{0.f, 0.f}}; }
+
 }  // namespace helm

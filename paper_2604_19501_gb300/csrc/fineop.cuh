@@ -2,6 +2,7 @@
 // (Sec. 1 Eq. acousitcHelm; Sec. 3.1), shared by the cycle and the Krylov kernels.
 #pragma once
 #include "common.cuh"
+#include "df64.cuh"
 
 namespace helm {
 
@@ -80,6 +81,67 @@ __device__ __forceinline__ c2<T> fine_apply_at(const FineOp& op, c2<T> diag, con
     }
   }
   return acc;
+}
+
+// (H z) at node p in double-float arithmetic for a vector z of exact floats (c64), with
+// the coefficients c as double-float per node (cdf).  The operator is regrouped with
+// small integer weights so that every weighted sum of z is formed exactly:
+//   2nd order:  H z = ih2 (2d z_c - sum_f z_f) - c_c z_c
+//   4th order:  H z = (ih2 / 6) L - (1/24) (c_c Mz + Mcz),
+//     L   = wc z_c - wf sum_f z_f - sum_e z_e       (wc, wf = 20, 4 in 2D; 24, 2 in 3D)
+//     Mz  = mc z_c + sum_f z_f,  Mcz = mc c_c z_c + sum_f c_f z_f   (mc = 8 in 2D, 6 in 3D)
+// (f: face neighbours, e: the other non-zero offsets, i.e. 2D corners and 3D edges).
+__device__ __forceinline__ cdd fine_apply_df(const FineOp& op, const float4* __restrict__ cdf,
+                                             const float2* __restrict__ z, long long p, int i, int j, int k,
+                                             dd ih2, dd ih2_6, dd inv24) {
+  const long long sy = op.g.N[0];
+  const long long sz = (long long)op.g.N[0] * op.g.N[1];
+  const cdd cc = cdd_load(cdf[p]);
+  const float2 zc = z[p];
+  const bool is3 = op.g.dim == 3;
+  if (op.order == 0) {
+    cdd L = cdd_wz(2.0f * op.g.dim, zc);
+    if (i > 0) L = cdd_sub(L, cdd_wz(1.f, z[p - 1]));
+    if (i < op.g.N[0] - 1) L = cdd_sub(L, cdd_wz(1.f, z[p + 1]));
+    if (j > 0) L = cdd_sub(L, cdd_wz(1.f, z[p - sy]));
+    if (j < op.g.N[1] - 1) L = cdd_sub(L, cdd_wz(1.f, z[p + sy]));
+    if (is3) {
+      if (k > 0) L = cdd_sub(L, cdd_wz(1.f, z[p - sz]));
+      if (k < op.g.N[2] - 1) L = cdd_sub(L, cdd_wz(1.f, z[p + sz]));
+    }
+    return cdd_sub(cdd_scale(L, ih2), cdd_mulf(cc, zc));
+  }
+  const float wc = is3 ? 24.f : 20.f, wf = is3 ? 2.f : 4.f, mc = is3 ? 6.f : 8.f;
+  cdd L = cdd_wz(wc, zc);
+  cdd Mz = cdd_wz(mc, zc);
+  const cdd czc = cdd_mulf(cc, zc);
+  cdd Mcz = cdd{dd_mulf(czc.re, mc), dd_mulf(czc.im, mc)};
+  const int zlo = is3 ? -1 : 0, zhi = is3 ? 1 : 0;
+  for (int dz = zlo; dz <= zhi; ++dz) {
+    const int kk = k + dz;
+    if (kk < 0 || kk >= op.g.N[2]) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int jj = j + dy;
+      if (jj < 0 || jj >= op.g.N[1]) continue;
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int ii = i + dx;
+        if (ii < 0 || ii >= op.g.N[0]) continue;
+        const int nz = (dx != 0) + (dy != 0) + (dz != 0);
+        if (nz == 0 || nz == 3) continue;
+        const long long q = p + dx + dy * sy + dz * sz;
+        const float2 zq = z[q];
+        if (nz == 1) {
+          L = cdd_sub(L, cdd_wz(wf, zq));
+          Mz = cdd_add(Mz, cdd_wz(1.f, zq));
+          Mcz = cdd_add(Mcz, cdd_mulf(cdd_load(cdf[q]), zq));
+        } else {
+          L = cdd_sub(L, cdd_wz(1.f, zq));
+        }
+      }
+    }
+  }
+  const cdd mass = cdd_add(cdd_mul(cc, Mz), Mcz);
+  return cdd_sub(cdd_scale(L, ih2_6), cdd_scale(mass, inv24));
 }
 
 }  // namespace helm

@@ -18,10 +18,10 @@ __constant__ double c_transfer_w[2][5] = {{0.25, 0.5, 0.25, 0.0, 0.0},
                                           {1.0 / 16, 4.0 / 16, 6.0 / 16, 4.0 / 16, 1.0 / 16}};
 
 // --------------------------------------------------------------- fine operator
-template <typename T, typename TX, typename TB, typename TY, int MODE>
+template <typename T, typename TX, typename SB, typename TY, int MODE>
 __global__ void __launch_bounds__(256) fine_row_kernel(FineOp op, const T* __restrict__ kap,
                                                        const c2<TX>* __restrict__ x,
-                                                       const c2<TB>* __restrict__ b,
+                                                       const SB* __restrict__ b,
                                                        c2<TY>* __restrict__ y, int nrhs, T w,
                                                        int colour) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -53,22 +53,22 @@ __global__ void __launch_bounds__(256) fine_row_kernel(FineOp op, const T* __res
   }
 }
 
-template <typename T, typename TX, typename TB, typename TY>
+template <typename T, typename TX, typename SB, typename TY>
 static int fine_dispatch(const FineOp& op, int mode, const void* kap, const void* x, const void* b,
                          void* y, int nrhs, double w, int colour, cudaStream_t s) {
   const int th = 256;
   const int bl = blocks_for(op.g.size, th);
   auto K = (const T*)kap;
   auto X = (const c2<TX>*)x;
-  auto B = (const c2<TB>*)b;
+  auto B = (const SB*)b;
   auto Y = (c2<TY>*)y;
   KernelTimer kt(HELM_K_FINE, s);
   switch (mode) {
-    case MODE_APPLY: fine_row_kernel<T, TX, TB, TY, MODE_APPLY><<<bl, th, 0, s>>>(op, K, X, B, Y, nrhs, (T)w, colour); break;
-    case MODE_RESID: fine_row_kernel<T, TX, TB, TY, MODE_RESID><<<bl, th, 0, s>>>(op, K, X, B, Y, nrhs, (T)w, colour); break;
-    case MODE_JACOBI: fine_row_kernel<T, TX, TB, TY, MODE_JACOBI><<<bl, th, 0, s>>>(op, K, X, B, Y, nrhs, (T)w, colour); break;
-    case MODE_JACOBI0: fine_row_kernel<T, TX, TB, TY, MODE_JACOBI0><<<bl, th, 0, s>>>(op, K, X, B, Y, nrhs, (T)w, colour); break;
-    case MODE_RB: fine_row_kernel<T, TX, TB, TY, MODE_RB><<<bl, th, 0, s>>>(op, K, X, B, Y, nrhs, (T)w, colour); break;
+    case MODE_APPLY: fine_row_kernel<T, TX, SB, TY, MODE_APPLY><<<bl, th, 0, s>>>(op, K, X, B, Y, nrhs, (T)w, colour); break;
+    case MODE_RESID: fine_row_kernel<T, TX, SB, TY, MODE_RESID><<<bl, th, 0, s>>>(op, K, X, B, Y, nrhs, (T)w, colour); break;
+    case MODE_JACOBI: fine_row_kernel<T, TX, SB, TY, MODE_JACOBI><<<bl, th, 0, s>>>(op, K, X, B, Y, nrhs, (T)w, colour); break;
+    case MODE_JACOBI0: fine_row_kernel<T, TX, SB, TY, MODE_JACOBI0><<<bl, th, 0, s>>>(op, K, X, B, Y, nrhs, (T)w, colour); break;
+    case MODE_RB: fine_row_kernel<T, TX, SB, TY, MODE_RB><<<bl, th, 0, s>>>(op, K, X, B, Y, nrhs, (T)w, colour); break;
     default: set_error("bad row mode"); return 1;
   }
   HELM_LAUNCH_CHECK();
@@ -80,12 +80,14 @@ int launch_fine_row(const FineOp& op, int mode, Prec arith, Prec xs, Prec bs, Pr
                     double w, int colour, cudaStream_t s) {
   if (arith == P64) {
     if (xs != P64 || bs != P64 || ys != P64) { set_error("FP64 row kernel needs c128 storage"); return 1; }
-    return fine_dispatch<double, double, double, double>(op, mode, kappa2, x, b, y, nrhs, w, colour, s);
+    return fine_dispatch<double, double, double2, double>(op, mode, kappa2, x, b, y, nrhs, w, colour, s);
   }
   if (xs != P32 || ys != P32) { set_error("FP32 row kernel needs c64 x/y"); return 1; }
   if (bs == P64)
-    return fine_dispatch<float, float, double, float>(op, mode, kappa2, x, b, y, nrhs, w, colour, s);
-  return fine_dispatch<float, float, float, float>(op, mode, kappa2, x, b, y, nrhs, w, colour, s);
+    return fine_dispatch<float, float, double2, float>(op, mode, kappa2, x, b, y, nrhs, w, colour, s);
+  if (bs == P_DF)
+    return fine_dispatch<float, float, float4, float>(op, mode, kappa2, x, b, y, nrhs, w, colour, s);
+  return fine_dispatch<float, float, float2, float>(op, mode, kappa2, x, b, y, nrhs, w, colour, s);
 }
 
 // --------------------------------------------------------------- assembled stencils

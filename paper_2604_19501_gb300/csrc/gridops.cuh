@@ -14,7 +14,8 @@ enum RowMode {
 };
 
 // Element types of a row kernel: arithmetic T, and the storage type of x, b, y.
-enum Prec { P64 = 0, P32 = 1 };
+// P_DF: double-float storage (float4 per complex entry), read-only input of the fine kernels.
+enum Prec { P64 = 0, P32 = 1, P_DF = 2 };
 
 // Fine-grid (level 1) row kernel.  kappa2 has the arithmetic type (double for P64).
 int launch_fine_row(const FineOp& op, int mode, Prec arith, Prec xs, Prec bs, Prec ys,

@@ -278,6 +278,108 @@ __global__ void set_scalar_kernel(double* dst, const double2* src_x, int do_sqrt
   if (threadIdx.x == 0 && blockIdx.x == 0) *dst = do_sqrt ? sqrt(src_x->x) : src_x->x;
 }
 
+
+// ------------------------------------------------------------------ double-float variants
+// Mixed-precision contexts keep the Krylov basis V and w as double-float (float4 per
+// complex entry, the size of complex FP64) and run the Arnoldi streams on the FP32 pipes.
+struct DfConsts {
+  dd ih2, ih2_6, inv24;
+};
+
+// c = omega^2 kappa^2 (1 - i gamma) per node as double-float.
+__global__ void coef_df_kernel(FineOp op, const double* __restrict__ kap, float4* __restrict__ cdf) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < op.g.size;
+       p += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    node_coords(op.g, p, i, j, k);
+    cdf[p] = cdd_store(cdd_make(fine_coef<double>(op, kap, p, i, j, k)));
+  }
+}
+
+// Per-thread double-float accumulators live in shared memory as float4 [value][thread];
+// each is turned into complex FP64 in place before the block reduction.
+__device__ __forceinline__ void df_to_double_inplace(double2* sacc, int nval) {
+  float4* sdf = reinterpret_cast<float4*>(sacc);
+  for (int i = 0; i < nval; ++i) {
+    const int s = i * blockDim.x + threadIdx.x;
+    sacc[s] = from_df(sdf[s]);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) arnoldi_matvec_df_kernel(
+    FineOp op, DfConsts K, const float4* __restrict__ cdf, const float2* __restrict__ z, float4* __restrict__ w,
+    const float4* __restrict__ V, long long vstride, int nv, double2* __restrict__ part,
+    unsigned* __restrict__ counter, double2* __restrict__ out) {
+  extern __shared__ double2 sacc[];
+  float4* sdf = reinterpret_cast<float4*>(sacc);
+  const int tid = threadIdx.x;
+  for (int i = 0; i <= nv; ++i) sdf[i * blockDim.x + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (long long p = blockIdx.x * (long long)blockDim.x + tid; p < op.g.size; p += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    node_coords(op.g, p, i, j, k);
+    const float4 wv = cdd_store(fine_apply_df(op, cdf, z, p, i, j, k, K.ih2, K.ih2_6, K.inv24));
+    w[p] = wv;
+    for (int q = 0; q < nv; ++q) df_cmacc(sdf[q * blockDim.x + tid], V[q * vstride + p], wv);
+    df_cmacc(sdf[nv * blockDim.x + tid], wv, wv);
+  }
+  df_to_double_inplace(sacc, nv + 1);
+  reduce_finish(sacc, nv + 1, part, counter, out);
+}
+
+__global__ void __launch_bounds__(kThreads) arnoldi_update_df_kernel(
+    long long n, float4* __restrict__ w, const float4* __restrict__ V, long long vstride, int nv,
+    const double2* __restrict__ h1, double2* __restrict__ part, unsigned* __restrict__ counter,
+    double2* __restrict__ out) {
+  extern __shared__ double2 sacc[];
+  float4* sdf = reinterpret_cast<float4*>(sacc);
+  __shared__ float4 sh[64];
+  const int tid = threadIdx.x;
+  for (int i = 0; i <= nv; ++i) sdf[i * blockDim.x + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = tid; i < nv; i += blockDim.x) sh[i] = cdd_store(cdd_make(h1[i]));
+  __syncthreads();
+  for (long long p = blockIdx.x * (long long)blockDim.x + tid; p < n; p += (long long)gridDim.x * blockDim.x) {
+    cdd wv = cdd_load(w[p]);
+    for (int q = 0; q < nv; ++q) wv = cdd_sub(wv, cdd_mul(cdd_load(sh[q]), cdd_load(V[q * vstride + p])));
+    const float4 w4 = cdd_store(wv);
+    w[p] = w4;
+    for (int q = 0; q < nv; ++q) df_cmacc(sdf[q * blockDim.x + tid], V[q * vstride + p], w4);
+    df_cmacc(sdf[nv * blockDim.x + tid], w4, w4);
+  }
+  df_to_double_inplace(sacc, nv + 1);
+  reduce_finish(sacc, nv + 1, part, counter, out);
+}
+
+__global__ void __launch_bounds__(kThreads) arnoldi_normalize_df_kernel(
+    long long n, const float4* __restrict__ w, const float4* __restrict__ V, long long vstride, int nv,
+    const double2* __restrict__ h2, const double* __restrict__ inv_hn, float4* __restrict__ vout) {
+  __shared__ float4 sh[64];
+  __shared__ dd s_inv;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) sh[i] = cdd_store(cdd_make(h2[i]));
+  if (threadIdx.x == 0) s_inv = dd_make(*inv_hn);
+  __syncthreads();
+  const dd sc = s_inv;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    cdd wv = cdd_load(w[p]);
+    for (int q = 0; q < nv; ++q) wv = cdd_sub(wv, cdd_mul(cdd_load(sh[q]), cdd_load(V[q * vstride + p])));
+    vout[p] = cdd_store(cdd_scale(wv, sc));
+  }
+}
+
+// v = r / beta into double-float storage; resets g = (beta, 0, ...)
+__global__ void __launch_bounds__(kThreads) start_cycle_df_kernel(long long n, const double2* __restrict__ r,
+                                                                  float4* __restrict__ v, KrylovState st, int m) {
+  const double beta = st.scal[KS_BETA];
+  const double s = 1.0 / beta;
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) st.g[i] = make_double2(i == 0 ? beta : 0.0, 0.0);
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const double2 a = r[p];
+    v[p] = cdd_store(cdd_make(make_double2(a.x * s, a.y * s)));
+  }
+}
+
 int grid_blocks(long long n) {
   const long long want = (n + kThreads - 1) / kThreads;
   return (int)std::max<long long>(1, std::min<long long>(want, 152LL * 4));
@@ -360,6 +462,72 @@ int k_arnoldi(const KrylovState& st, const FineOp& op, const double* kap64, cons
   }
   KernelTimer kt(HELM_K_KRYLOV_OTHER, s);
   arnoldi_small_kernel<<<1, 32, 0, s>>>(st, j, st.m);
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
+DfConsts df_consts(const FineOp& op) {
+  DfConsts K;
+  const double ih2 = op.inv_h2;
+  auto mk_dd = [](double v) {
+    const float hi = (float)v;
+    return dd{hi, (float)(v - (double)hi)};
+  };
+  K.ih2 = mk_dd(ih2);
+  K.ih2_6 = mk_dd(ih2 / 6.0);
+  K.inv24 = mk_dd(1.0 / 24.0);
+  return K;
+}
+
+int k_coef_df(const FineOp& op, const double* kap64, float4* cdf, cudaStream_t s) {
+  KernelTimer kt(HELM_K_SETUP, s);
+  coef_df_kernel<<<grid_blocks(op.g.size), kThreads, 0, s>>>(op, kap64, cdf);
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
+int k_start_cycle_df(const KrylovState& st, long long n, const double2* r, float4* v0, cudaStream_t s) {
+  KernelTimer kt(HELM_K_KRYLOV_OTHER, s);
+  start_cycle_df_kernel<<<grid_blocks(n), kThreads, 0, s>>>(n, r, v0, st, st.m);
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
+int k_arnoldi_df(const KrylovState& st, const FineOp& op, const float4* cdf, const float2* z, float4* w,
+                 const float4* V, long long vstride, int j, cudaStream_t s) {
+  const long long n = op.g.size;
+  const int bl = grid_blocks(n);
+  const int nv = j + 1;
+  const size_t sm = (size_t)(nv + 1) * kThreads * sizeof(double2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    const int lim = 200 * 1024;
+    cudaFuncSetAttribute(arnoldi_matvec_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(arnoldi_update_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    attr_set = true;
+  }
+  const DfConsts K = df_consts(op);
+  {
+    KernelTimer kt(HELM_K_ARNOLDI_MATVEC, s);
+    arnoldi_matvec_df_kernel<<<bl, kThreads, sm, s>>>(op, K, cdf, z, w, V, vstride, nv, st.part, st.counter, st.h1);
+    HELM_LAUNCH_CHECK();
+  }
+  {
+    KernelTimer kt(HELM_K_ARNOLDI_UPDATE, s);
+    arnoldi_update_df_kernel<<<bl, kThreads, sm, s>>>(n, w, V, vstride, nv, st.h1, st.part, st.counter, st.h2);
+    HELM_LAUNCH_CHECK();
+  }
+  KernelTimer kt(HELM_K_KRYLOV_OTHER, s);
+  arnoldi_small_kernel<<<1, 32, 0, s>>>(st, j, st.m);
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
+int k_normalize_df(const KrylovState& st, long long n, const float4* w, const float4* V, long long vstride, int j,
+                   float4* vout, cudaStream_t s) {
+  KernelTimer kt(HELM_K_ARNOLDI_NORM, s);
+  arnoldi_normalize_df_kernel<<<grid_blocks(n), kThreads, 0, s>>>(n, w, V, vstride, j + 1, st.h2,
+                                                                  st.scal + KS_INV_HN, vout);
   HELM_LAUNCH_CHECK();
   return 0;
 }

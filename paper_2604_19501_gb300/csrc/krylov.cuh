@@ -36,6 +36,13 @@ int k_arnoldi(const KrylovState& st, const FineOp& op, const double* kap64, cons
 // v_{j+1} = (w - V h2) / hn.
 int k_normalize(const KrylovState& st, long long n, const double2* w, const double2* V, long long vstride,
                 int j, double2* vout, cudaStream_t s);
+// Double-float variants (mixed precision): V and w stored as float4 (hi, lo) pairs.
+int k_coef_df(const FineOp& op, const double* kap64, float4* cdf, cudaStream_t s);
+int k_start_cycle_df(const KrylovState& st, long long n, const double2* r, float4* v0, cudaStream_t s);
+int k_arnoldi_df(const KrylovState& st, const FineOp& op, const float4* cdf, const float2* z, float4* w,
+                 const float4* V, long long vstride, int j, cudaStream_t s);
+int k_normalize_df(const KrylovState& st, long long n, const float4* w, const float4* V, long long vstride, int j,
+                   float4* vout, cudaStream_t s);
 // y = R^-1 g (k x k) and x += Z y.
 int k_update_solution(const KrylovState& st, long long n, double2* x, const void* Z, Prec zp,
                       long long zstride, int k, cudaStream_t s);
