@@ -173,9 +173,10 @@ int helm_coarse_solve(helm_ctx* c, const void* b, void* e, int n_rhs);
  * (helm_coarse_solve allocates its scratch on its first call, or when n_rhs
  * grows.)  The scratch vectors live in one static device array of 2^20
  * complex FP64 entries (16 MiB), which every GPU that loads the library holds
- * until the process exits.  A solve needs (sum of front sizes + sum of update
- * sizes + nodes(3)) entries per right-hand side; larger requests return
- * HELM_EINVAL and do nothing.  The first call on a device looks up the array's
+ * until the process exits.  A solve needs, per right-hand side, the update
+ * vectors of all nested-dissection fronts, two vectors over the coarsest nodes
+ * and the forward sweep's partial sums, plus one counter per split column
+ * tile; larger requests return HELM_EINVAL and do nothing.  The first call on a device looks up the array's
  * device address with that device current; later calls reuse it.  All calls
  * share the array: calls that may overlap on the GPU (two streams, two
  * contexts, two threads) race and corrupt each other's results, so serialise

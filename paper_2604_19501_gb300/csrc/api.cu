@@ -110,6 +110,7 @@ GridDims dims_of(int dim, const int n[3], int level) {
   const int f = 1 << level;
   for (int a = 0; a < 3; ++a) g.N[a] = a < dim ? n[a] / f + 1 : 1;
   g.size = (long long)g.N[0] * g.N[1] * g.N[2];
+  finish_dims(g);
   return g;
 }
 
@@ -368,6 +369,11 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
   if (o->precision != HELM_FP64 && o->precision != HELM_MIXED) return fail(HELM_EINVAL, "bad precision");
   if (o->restart < 1 || o->restart > 40) return fail(HELM_EINVAL, "restart must be in [1, 40]");
   if (o->max_rhs < 1) return fail(HELM_EINVAL, "max_rhs must be >= 1");
+  {
+    long long nodes = 1;
+    for (int a = 0; a < o->dim; ++a) nodes *= (o->n[a] + 1);
+    if (nodes >= (1LL << 31)) return fail(HELM_EINVAL, "more than 2^31 - 1 nodes per right-hand side");
+  }
 
   helm_ctx* c = new helm_ctx();
   c->o = *o;

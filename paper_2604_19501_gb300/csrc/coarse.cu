@@ -368,65 +368,62 @@ __global__ void fact_extract_kernel(const FrontDesc* __restrict__ desc, const in
 }
 
 // ------------------------------------------------------------------ solve kernels
-__global__ void fwd_assemble_kernel(const FrontDesc* __restrict__ desc, const int* __restrict__ list,
-                                    const int* __restrict__ Sidx, const int* __restrict__ kids,
-                                    const int* __restrict__ cmap, const double2* __restrict__ b,
-                                    double2* __restrict__ rf, double2* __restrict__ uv, int nrhs,
-                                    long long nodes, long long rf_total, long long uv_total) {
-  const FrontDesc d = desc[list[blockIdx.x]];
-  const int nF = d.nS + d.nB;
-  for (int r = 0; r < nrhs; ++r) {
-    double2* R = rf + r * rf_total + d.rf_off;
-    const double2* br = b + r * nodes;
-    for (int t = threadIdx.x; t < nF; t += blockDim.x)
-      R[t] = t < d.nS ? br[Sidx[d.S_off + t]] : make_double2(0.0, 0.0);
-    __syncthreads();
-    for (int c = 0; c < d.nkids; ++c) {
-      const FrontDesc kd = desc[kids[d.kid_off + c]];
-      const double2* V = uv + r * uv_total + kd.uv_off;
-      const int* map = cmap + kd.cmap_off;
-      for (int a = threadIdx.x; a < kd.nB; a += blockDim.x) {
-        const double2 v = V[a];
-        R[map[a]].x += v.x;
-        R[map[a]].y += v.y;
-      }
-      __syncthreads();
-    }
+// Right-hand side of front position t: b at the eliminated nodes plus the entries of the
+// children's update vectors that map to t (at most one per child), added in child order.
+__device__ __forceinline__ double2 front_rhs(const FrontDesc& d, const int* __restrict__ Sidx,
+                                             const int2* __restrict__ ctb, const double2* __restrict__ b,
+                                             const double2* __restrict__ uv, int t, int r, long long nodes,
+                                             long long uv_total) {
+  double2 v = t < d.nS ? b[r * nodes + Sidx[d.S_off + t]] : make_double2(0.0, 0.0);
+  const int2 c = ctb[d.ctb_off + t];
+  if (c.x >= 0) {
+    const double2 u = uv[r * uv_total + c.x];
+    v.x += u.x;
+    v.y += u.y;
   }
+  if (c.y >= 0) {
+    const double2 u = uv[r * uv_total + c.y];
+    v.x += u.x;
+    v.y += u.y;
+  }
+  return v;
 }
 
-// Forward sweep of one level: out_t = sum_s M[s][t] r_S[s] over a column tile and a chunk
-// of rows; t < nS gives w at node S[t], t >= nS the update vector r_B + bsign * out.
-__device__ __forceinline__ void fwd_write(const FrontDesc& d, const int* __restrict__ Sidx, int t, int r,
-                                          double2 v, const double2* __restrict__ rf, double2* __restrict__ uv,
-                                          double2* __restrict__ w, long long nodes, long long rf_total,
-                                          long long uv_total) {
+// out_t < nS: w at node S[t]; t >= nS: the update vector r_B + bsign * out.
+__device__ __forceinline__ void fwd_write(const FrontDesc& d, const int* __restrict__ Sidx,
+                                          const int2* __restrict__ ctb, const double2* __restrict__ b, int t,
+                                          int r, double2 v, double2* __restrict__ uv, double2* __restrict__ w,
+                                          long long nodes, long long uv_total) {
   if (t < d.nS) {
     w[r * nodes + Sidx[d.S_off + t]] = v;
   } else {
-    const double2 rb = rf[r * rf_total + d.rf_off + t];
+    const double2 rb = front_rhs(d, Sidx, ctb, b, uv, t, r, nodes, uv_total);
     uv[r * uv_total + d.uv_off + t - d.nS] = make_double2(rb.x + d.bsign * v.x, rb.y + d.bsign * v.y);
   }
 }
 
+// Forward sweep of one level: out_t = sum_{s in [s0, s1)} M[s][t] r_S[s] for one column tile;
+// r_S is assembled on the fly from b and the children's update vectors.  Fronts split
+// into several row chunks leave partial sums that the last block of the tile adds in
+// chunk order.
 template <bool DF>
 __global__ void __launch_bounds__(kFwdCols) fwd_colsum_kernel(
     const FrontDesc* __restrict__ desc, const FwdJob* __restrict__ jobs, const int* __restrict__ Sidx,
-    const double2* __restrict__ factors, const double2* __restrict__ rf, double2* __restrict__ uv,
-    double2* __restrict__ w, double2* __restrict__ part, unsigned* __restrict__ counters, int nrhs,
-    long long nodes, long long rf_total, long long uv_total) {
+    const int2* __restrict__ ctb, const double2* __restrict__ factors, const double2* __restrict__ b,
+    double2* __restrict__ uv, double2* __restrict__ w, double2* __restrict__ part,
+    unsigned* __restrict__ counters, int nrhs, long long nodes, long long uv_total) {
   const FwdJob job = jobs[blockIdx.x];
   const FrontDesc d = desc[job.front];
   const int nF = d.nS + d.nB;
   const int tid = threadIdx.x;
   const int t = job.tile * kFwdCols + tid;
-  const int s0 = job.chunk * kFwdChunk, s1 = min(d.nS, s0 + kFwdChunk);
-  __shared__ double2 rs[kFwdChunk];
-  __shared__ float4 rsd[kFwdChunk];
+  const int s0 = job.s0, s1 = job.s1;
+  __shared__ double2 rs[kFwdMaxChunk];
+  __shared__ float4 rsd[kFwdMaxChunk];
   __shared__ bool s_last;
   for (int r = 0; r < nrhs; ++r) {
     for (int q = tid; q < s1 - s0; q += blockDim.x) {
-      const double2 v = rf[r * rf_total + d.rf_off + s0 + q];
+      const double2 v = front_rhs(d, Sidx, ctb, b, uv, s0 + q, r, nodes, uv_total);
       if (DF) rsd[q] = to_df(v);
       else rs[q] = v;
     }
@@ -436,17 +433,17 @@ __global__ void __launch_bounds__(kFwdCols) fwd_colsum_kernel(
       if (DF) {
         const float4* col = reinterpret_cast<const float4*>(factors + d.M_off) + (long long)s0 * nF + t;
         float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
+#pragma unroll 8
         for (int s = 0; s < s1 - s0; ++s) df_cmac(a4, col[(long long)s * nF], rsd[s]);
         acc = from_df(a4);
       } else {
         const double2* col = factors + d.M_off + (long long)s0 * nF + t;
-#pragma unroll 4
+#pragma unroll 8
         for (int s = 0; s < s1 - s0; ++s) acc = cmac(acc, col[(long long)s * nF], rs[s]);
       }
     }
     if (job.nchunks == 1) {
-      if (t < nF) fwd_write(d, Sidx, t, r, acc, rf, uv, w, nodes, rf_total, uv_total);
+      if (t < nF) fwd_write(d, Sidx, ctb, b, t, r, acc, uv, w, nodes, uv_total);
     } else {
       part[((long long)(job.pbase + job.chunk) * nrhs + r) * kFwdCols + tid] = acc;
     }
@@ -466,52 +463,75 @@ __global__ void __launch_bounds__(kFwdCols) fwd_colsum_kernel(
       acc.x += v.x;
       acc.y += v.y;
     }
-    if (t < nF) fwd_write(d, Sidx, t, r, acc, rf, uv, w, nodes, rf_total, uv_total);
+    if (t < nF) fwd_write(d, Sidx, ctb, b, t, r, acc, uv, w, nodes, uv_total);
   }
   if (tid == 0) counters[job.slot] = 0u;
 }
 
-// one warp per row of G: x_S[row] = w_S[row] - G[row, :] . x_B.  With DF the factors are
-// double-float and x_B is read from the double-float copy xd of x, which this sweep
-// also writes.
+// One warp per row of G: x_S[row] = w_S[row] - G[row, :] . x_B; a block handles a range
+// of rows of one front and first stages x_B in shared memory (as double-float with DF),
+// so the row loops stream G and read x_B without dependent gathers.  With DF
+// the factors are double-float and the sweep also writes the double-float copy xd of x.
 template <bool DF>
-__global__ void __launch_bounds__(256) bwd_matvec_kernel(const FrontDesc* __restrict__ desc,
-                                                         const int2* __restrict__ rows,
+__global__ void __launch_bounds__(512) bwd_matvec_kernel(const FrontDesc* __restrict__ desc,
+                                                         const int4* __restrict__ rows,
                                                          const int* __restrict__ Sidx,
                                                          const int* __restrict__ Bidx,
                                                          const double2* __restrict__ factors,
                                                          const double2* __restrict__ w,
                                                          double2* __restrict__ x, float4* __restrict__ xd,
-                                                         int nrhs, long long nodes) {
-  const int2 job = rows[blockIdx.x];
+                                                         int nrhs, long long nodes, int smem_cap) {
+  extern __shared__ float4 xs[];
+  const int4 job = rows[blockIdx.x];
   const FrontDesc d = desc[job.x];
-  const int row = job.y + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (row >= d.nS) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int* B = Bidx + d.B_off;
-  const int node = Sidx[d.S_off + row];
+  const bool staged = d.nB <= smem_cap;
   for (int r = 0; r < nrhs; ++r) {
-    double2 acc = make_double2(0.0, 0.0);
-    if (DF) {
-      const float4* G = reinterpret_cast<const float4*>(factors + d.G_off) + (long long)row * d.g_ld;
-      const float4* xr = xd + r * nodes;
-      float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int c = lane; c < d.nB; c += 32) df_cmac(a4, G[c], xr[B[c]]);
-      acc = from_df(a4);
-    } else {
-      const double2* G = factors + d.G_off + (long long)row * d.g_ld;
-      const double2* xr = x + r * nodes;
-      for (int c = lane; c < d.nB; c += 32) acc = cmac(acc, G[c], xr[B[c]]);
+    if (staged) {
+      for (int c = threadIdx.x; c < d.nB; c += blockDim.x) {
+        if (DF) xs[c] = xd[r * nodes + B[c]];
+        else reinterpret_cast<double2*>(xs)[c] = x[r * nodes + B[c]];
+      }
+      __syncthreads();
     }
-    for (int off = 16; off > 0; off >>= 1) {
-      acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
-      acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
+    for (int row = job.y + warp; row < job.z; row += nwarp) {
+      const int node = Sidx[d.S_off + row];
+      double2 acc = make_double2(0.0, 0.0);
+      if (DF) {
+        const float4* G = reinterpret_cast<const float4*>(factors + d.G_off) + (long long)row * d.g_ld;
+        float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (staged) {
+#pragma unroll 4
+          for (int c = lane; c < d.nB; c += 32) df_cmac(a4, G[c], xs[c]);
+        } else {
+          const float4* xr = xd + r * nodes;
+          for (int c = lane; c < d.nB; c += 32) df_cmac(a4, G[c], xr[B[c]]);
+        }
+        acc = from_df(a4);
+      } else {
+        const double2* G = factors + d.G_off + (long long)row * d.g_ld;
+        if (staged) {
+          const double2* xs2 = reinterpret_cast<const double2*>(xs);
+#pragma unroll 4
+          for (int c = lane; c < d.nB; c += 32) acc = cmac(acc, G[c], xs2[c]);
+        } else {
+          const double2* xr = x + r * nodes;
+          for (int c = lane; c < d.nB; c += 32) acc = cmac(acc, G[c], xr[B[c]]);
+        }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
+        acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
+      }
+      if (lane == 0) {
+        const double2 wv = w[r * nodes + node];
+        const double2 xv = make_double2(wv.x - acc.x, wv.y - acc.y);
+        x[r * nodes + node] = xv;
+        if (DF) xd[r * nodes + node] = to_df(xv);
+      }
     }
-    if (lane == 0) {
-      const double2 wv = w[r * nodes + node];
-      const double2 xv = make_double2(wv.x - acc.x, wv.y - acc.y);
-      x[r * nodes + node] = xv;
-      if (DF) xd[r * nodes + node] = to_df(xv);
-    }
+    if (staged) __syncthreads();
   }
 }
 
@@ -523,7 +543,9 @@ int upload(T** dst, const std::vector<T>& v) {
   return 0;
 }
 
-constexpr int kRowsPerBlock = 8;   // warps per block in the backward sweep
+constexpr int kRowsPerBlock = 16;  // warps per block in the backward sweep (minimum rows per block)
+constexpr int kTargetBlocks = 1024;   // blocks per tree level the sweeps aim for
+constexpr int kBwdSmemEntries = 3072;   // x_B entries staged in shared memory (48 KiB)
 constexpr int kBigFront = 96;      // fronts with at least this many eliminated nodes use the grid-wide elimination
 
 }  // namespace
@@ -576,7 +598,7 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
     }
     d.U_off = uoff;
     uoff += (long long)d.nB * d.nB;
-    d.rf_off = rfo;
+    d.ctb_off = rfo;
     rfo += nF;
     d.uv_off = uvo;
     uvo += d.nB;
@@ -623,8 +645,24 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
     d.ent_cnt = (int)ents.size() - d.ent_off;
   }
   cs.factor_entries = xg;
-  cs.rf_total = rfo;
+  cs.max_nB = 0;
+  for (auto& d : desc) cs.max_nB = std::max(cs.max_nB, d.nB);
   cs.uv_total = uvo;
+  // for every front position, the update-vector entries of the children that map to it
+  std::vector<int2> ctb(rfo, make_int2(-1, -1));
+  for (int i = 0; i < cs.nfronts; ++i) {
+    const FrontDesc& d = desc[i];
+    for (int c = 0; c < d.nkids; ++c) {
+      const FrontDesc& kd = desc[kids[d.kid_off + c]];
+      for (int a = 0; a < kd.nB; ++a) {
+        int2& slot = ctb[d.ctb_off + cmap[kd.cmap_off + a]];
+        const int src = (int)(kd.uv_off + a);
+        if (c == 0) slot.x = src;
+        else if (c == 1) slot.y = src;
+        else { set_error("nested dissection: more than two children"); return HELM_ECUDA; }
+      }
+    }
+  }
   // per-level augmented work offsets and solve job lists
   long long aug_max = 0;
   cs.d_level_list.resize(cs.nlevels);
@@ -638,25 +676,37 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
   cs.n_slots = 1;
   std::vector<std::vector<int>> bigs(cs.nlevels), smalls(cs.nlevels);
   std::vector<std::vector<FwdJob>> fjobs(cs.nlevels);
-  std::vector<std::vector<int2>> brows(cs.nlevels);
+  std::vector<std::vector<int4>> brows(cs.nlevels);
   for (int h = 0; h < cs.nlevels; ++h) {
     long long off = 0;
     int slot = 0, pbase = 0;
+    // row chunks and backward rows per block sized so that a level has about
+    // kTargetBlocks blocks: small fronts are not split, large fronts are
+    long long work = 0, rows_total = 0;
+    for (int f : cs.level_fronts[h]) {
+      work += (long long)((desc[f].nS + desc[f].nB + kFwdCols - 1) / kFwdCols) * desc[f].nS;
+      rows_total += desc[f].nS;
+    }
+    int chunk_rows = (int)std::max<long long>(kFwdMinChunk, (work + kTargetBlocks - 1) / kTargetBlocks);
+    chunk_rows = std::min(kFwdMaxChunk, (chunk_rows + kFwdMinChunk - 1) / kFwdMinChunk * kFwdMinChunk);
+    const int bwd_rows = (int)std::max<long long>(kRowsPerBlock, (rows_total + kTargetBlocks - 1) / kTargetBlocks);
     for (int f : cs.level_fronts[h]) {
       desc[f].aug_off = off;
       const int nS = desc[f].nS, nF = nS + desc[f].nB;
       off += (long long)nF * (nF + nS);
       (nS >= kBigFront ? bigs[h] : smalls[h]).push_back(f);
       const int tiles = (nF + kFwdCols - 1) / kFwdCols;
-      const int chunks = (nS + kFwdChunk - 1) / kFwdChunk;
+      const int chunks = (nS + chunk_rows - 1) / chunk_rows;
       for (int tl = 0; tl < tiles; ++tl) {
-        for (int ch = 0; ch < chunks; ++ch) fjobs[h].push_back(FwdJob{f, tl, ch, chunks, slot, pbase});
+        for (int ch = 0; ch < chunks; ++ch)
+          fjobs[h].push_back(FwdJob{f, tl, ch * chunk_rows, std::min(nS, (ch + 1) * chunk_rows), chunks, ch,
+                                    slot, pbase});
         if (chunks > 1) {
           pbase += chunks;
           ++slot;
         }
       }
-      for (int r0 = 0; r0 < nS; r0 += kRowsPerBlock) brows[h].push_back(make_int2(f, r0));
+      for (int r0 = 0; r0 < nS; r0 += bwd_rows) brows[h].push_back(make_int4(f, r0, std::min(nS, r0 + bwd_rows), 0));
     }
     aug_max = std::max(aug_max, off);
     cs.part_entries = std::max<long long>(cs.part_entries, (long long)pbase * kFwdCols);
@@ -665,7 +715,7 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
     cs.n_bwd_rows[h] = (int)brows[h].size();
   }
   if (upload(&cs.d_desc, desc) || upload(&cs.d_S, Sall) || upload(&cs.d_B, Ball) ||
-      upload(&cs.d_kids, kids) || upload(&cs.d_cmap, cmap))
+      upload(&cs.d_kids, kids) || upload(&cs.d_cmap, cmap) || upload(&cs.d_ctb, ctb))
     return HELM_ECUDA;
   int2* d_ents = nullptr;
   if (upload(&d_ents, ents)) return HELM_ECUDA;
@@ -731,14 +781,12 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
 
 static int ensure_rhs(CoarseSolver& cs, int nrhs) {
   if (nrhs <= cs.rhs_cap) return 0;
-  cudaFree(cs.d_rf);
   cudaFree(cs.d_uv);
   cudaFree(cs.d_w);
   cudaFree(cs.d_part);
   cudaFree(cs.d_counters);
   cudaFree(cs.d_xd);
   HELM_CUDA_TRY(cudaMalloc(&cs.d_xd, cs.g.size * nrhs * sizeof(float4)));
-  HELM_CUDA_TRY(cudaMalloc(&cs.d_rf, std::max<long long>(1, cs.rf_total) * nrhs * sizeof(double2)));
   HELM_CUDA_TRY(cudaMalloc(&cs.d_uv, std::max<long long>(1, cs.uv_total) * nrhs * sizeof(double2)));
   HELM_CUDA_TRY(cudaMalloc(&cs.d_w, cs.g.size * nrhs * sizeof(double2)));
   HELM_CUDA_TRY(cudaMalloc(&cs.d_part, cs.part_entries * nrhs * sizeof(double2)));
@@ -748,31 +796,29 @@ static int ensure_rhs(CoarseSolver& cs, int nrhs) {
   return 0;
 }
 
-static int solve_sweeps(const CoarseSolver& cs, const double2* b, double2* e, int nrhs, double2* rf,
-                        double2* uv, double2* w, double2* part, unsigned* counters, float4* xd,
-                        cudaStream_t s) {
+static int solve_sweeps(const CoarseSolver& cs, const double2* b, double2* e, int nrhs, double2* uv,
+                        double2* w, double2* part, unsigned* counters, float4* xd, cudaStream_t s) {
   for (int h = 0; h < cs.nlevels; ++h) {
-    const int nf = (int)cs.level_fronts[h].size();
-    fwd_assemble_kernel<<<nf, 256, 0, s>>>(cs.d_desc, cs.d_level_list[h], cs.d_S, cs.d_kids, cs.d_cmap, b, rf,
-                                           uv, nrhs, cs.g.size, cs.rf_total, cs.uv_total);
-    HELM_LAUNCH_CHECK();
     if (cs.df)
-      fwd_colsum_kernel<true><<<cs.n_fwd_jobs[h], kFwdCols, 0, s>>>(cs.d_desc, cs.d_fwd_jobs[h], cs.d_S,
-                                                                    cs.d_factors, rf, uv, w, part, counters, nrhs,
-                                                                    cs.g.size, cs.rf_total, cs.uv_total);
+      fwd_colsum_kernel<true><<<cs.n_fwd_jobs[h], kFwdCols, 0, s>>>(cs.d_desc, cs.d_fwd_jobs[h], cs.d_S, cs.d_ctb,
+                                                                    cs.d_factors, b, uv, w, part, counters, nrhs,
+                                                                    cs.g.size, cs.uv_total);
     else
-      fwd_colsum_kernel<false><<<cs.n_fwd_jobs[h], kFwdCols, 0, s>>>(cs.d_desc, cs.d_fwd_jobs[h], cs.d_S,
-                                                                     cs.d_factors, rf, uv, w, part, counters, nrhs,
-                                                                     cs.g.size, cs.rf_total, cs.uv_total);
+      fwd_colsum_kernel<false><<<cs.n_fwd_jobs[h], kFwdCols, 0, s>>>(cs.d_desc, cs.d_fwd_jobs[h], cs.d_S, cs.d_ctb,
+                                                                     cs.d_factors, b, uv, w, part, counters, nrhs,
+                                                                     cs.g.size, cs.uv_total);
     HELM_LAUNCH_CHECK();
   }
   for (int h = cs.nlevels - 1; h >= 0; --h) {
+    const size_t sm = (size_t)std::min(cs.max_nB, kBwdSmemEntries) * sizeof(float4);
     if (cs.df)
-      bwd_matvec_kernel<true><<<cs.n_bwd_rows[h], 32 * kRowsPerBlock, 0, s>>>(
-          cs.d_desc, cs.d_bwd_rows[h], cs.d_S, cs.d_B, cs.d_factors, w, e, xd, nrhs, cs.g.size);
+      bwd_matvec_kernel<true><<<cs.n_bwd_rows[h], 32 * kRowsPerBlock, sm, s>>>(
+          cs.d_desc, cs.d_bwd_rows[h], cs.d_S, cs.d_B, cs.d_factors, w, e, xd, nrhs, cs.g.size,
+          kBwdSmemEntries);
     else
-      bwd_matvec_kernel<false><<<cs.n_bwd_rows[h], 32 * kRowsPerBlock, 0, s>>>(
-          cs.d_desc, cs.d_bwd_rows[h], cs.d_S, cs.d_B, cs.d_factors, w, e, xd, nrhs, cs.g.size);
+      bwd_matvec_kernel<false><<<cs.n_bwd_rows[h], 32 * kRowsPerBlock, sm, s>>>(
+          cs.d_desc, cs.d_bwd_rows[h], cs.d_S, cs.d_B, cs.d_factors, w, e, xd, nrhs, cs.g.size,
+          kBwdSmemEntries);
     HELM_LAUNCH_CHECK();
   }
   return 0;
@@ -781,7 +827,7 @@ static int solve_sweeps(const CoarseSolver& cs, const double2* b, double2* e, in
 int coarse_solve(CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaStream_t s) {
   if (int st = ensure_rhs(cs, nrhs)) return st;
   KernelTimer kt(HELM_K_COARSE, s);
-  return solve_sweeps(cs, b, e, nrhs, cs.d_rf, cs.d_uv, cs.d_w, cs.d_part, cs.d_counters, cs.d_xd, s);
+  return solve_sweeps(cs, b, e, nrhs, cs.d_uv, cs.d_w, cs.d_part, cs.d_counters, cs.d_xd, s);
 }
 
 // ------------------------------------------------------------------ allocation-free variant
@@ -799,7 +845,7 @@ double2* g_noalloc_addr[kMaxDevices] = {};
 }  // namespace
 
 int coarse_solve_noalloc(const CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaStream_t s) {
-  const long long per_rhs = cs.rf_total + cs.uv_total + cs.g.size + cs.part_entries + cs.g.size;
+  const long long per_rhs = cs.uv_total + cs.g.size + cs.part_entries + cs.g.size;
   const long long counter_entries = (cs.n_slots * (long long)sizeof(unsigned) + sizeof(double2) - 1) / sizeof(double2);
   if (nrhs < 1 || per_rhs * nrhs + counter_entries > kNoAllocScratchEntries) {
     set_error("allocation-free coarsest solve needs " + std::to_string(per_rhs * nrhs + counter_entries) +
@@ -825,17 +871,16 @@ int coarse_solve_noalloc(const CoarseSolver& cs, const double2* b, double2* e, i
     base = g_noalloc_addr[dev];
   }
   // The column-tile counters must start at zero and are cleared here; every other
-  // scratch entry that is read is written earlier in the same call (front vectors from
-  // b, update vectors and partial sums by the kernels that produce them, w for every
-  // eliminated node).
+  // scratch entry that is read is written earlier in the same call (update vectors and
+  // partial sums by the kernels that produce them, w and its double-float copy for
+  // every eliminated node).
   unsigned* counters = reinterpret_cast<unsigned*>(base);
   HELM_CUDA_TRY(cudaMemsetAsync(counters, 0, cs.n_slots * sizeof(unsigned), s));
-  double2* rf = base + counter_entries;
-  double2* uv = rf + cs.rf_total * nrhs;
+  double2* uv = base + counter_entries;
   double2* w = uv + cs.uv_total * nrhs;
   double2* part = w + cs.g.size * nrhs;
   float4* xd = reinterpret_cast<float4*>(part + cs.part_entries * nrhs);   // float4 and double2 are both 16 bytes
-  return solve_sweeps(cs, b, e, nrhs, rf, uv, w, part, counters, xd, s);
+  return solve_sweeps(cs, b, e, nrhs, uv, w, part, counters, xd, s);
 }
 
 void coarse_free(CoarseSolver& cs) {
@@ -853,7 +898,7 @@ void coarse_free(CoarseSolver& cs) {
   for (auto p : cs.small_list) cudaFree(p);
   cudaFree(cs.d_part);
   cudaFree(cs.d_counters);
-  cudaFree(cs.d_rf);
+  cudaFree(cs.d_ctb);
   cudaFree(cs.d_uv);
   cudaFree(cs.d_w);
   cudaFree(cs.d_xd);

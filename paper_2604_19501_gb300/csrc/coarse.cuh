@@ -7,7 +7,8 @@
 namespace helm {
 
 constexpr int kFwdCols = 256;    // columns per block of the forward sweep
-constexpr int kFwdChunk = 64;    // rows per partial sum of the forward sweep
+constexpr int kFwdMinChunk = 16;   // rows per partial sum of the forward sweep: at least ...
+constexpr int kFwdMaxChunk = 256;  // ... and at most
 
 struct FrontDesc {
   int nS, nB;             // eliminated (separator / leaf) nodes, boundary (ancestor) nodes
@@ -21,12 +22,13 @@ struct FrontDesc {
   int ent_off, ent_cnt;   // original matrix entries scattered into the front
   int kid_off, nkids;     // children (front ids)
   int cmap_off;           // this front's boundary positions inside its parent's front
-  long long rf_off;       // solve scratch: front vector (nF entries)
+  long long ctb_off;      // per front position: the children's update-vector entries added to it
   long long uv_off;       // solve scratch: update vector (nB entries)
 };
 
 struct FwdJob {
-  int front, tile, chunk, nchunks;   // column tile and row chunk of one front
+  int front, tile, s0, s1;           // column tile and rows [s0, s1) of one front
+  int nchunks, chunk;                // row chunks of the tile and the index of this one
   int slot, pbase;                   // counter of the tile; first partial-sum slot of the tile
 };
 
@@ -53,13 +55,14 @@ struct CoarseSolver {
   unsigned* d_counters = nullptr;
   bool df = false;                    // factors stored and applied in double-float arithmetic
   float4* d_xd = nullptr;             // double-float copy of the backward-sweep result
-  std::vector<int2*> d_bwd_rows;      // per level: blocks over nS rows
+  std::vector<int4*> d_bwd_rows;      // per level: (front, first row, end row) blocks
   std::vector<int> n_bwd_rows;
-  long long rf_total = 0, uv_total = 0;
-  double2* d_rf = nullptr;            // [nrhs][rf_total]
+  long long uv_total = 0;
+  int2* d_ctb = nullptr;              // children's contributions per front position
   double2* d_uv = nullptr;            // [nrhs][uv_total]
   double2* d_w = nullptr;             // [nrhs][nodes]
   int rhs_cap = 0;
+  int max_nB = 0;                     // largest boundary of a front
   int* d_err = nullptr;
   long long* launches = nullptr;
 };

@@ -65,14 +65,37 @@ struct GridDims {
   int dim;
   int N[3];          // nodes per axis (cells + 1); N[2] = 1 in 2D
   long long size;    // total nodes
+  // division by N[0] and N[1] as a multiply and shift: n / d = (n * m) >> (32 + s) with
+  // s = ceil(log2 d), m = ceil(2^(32+s) / d), exact for every n < 2^31
+  unsigned long long m0, m1;
+  int s0, s1;
 };
 
+// Fills the division constants of a GridDims whose N[] is set.
+inline void finish_dims(GridDims& g) {
+  auto magic = [](unsigned d, unsigned long long& m, int& s) {
+    s = 0;
+    while ((1ull << s) < d) ++s;
+    const unsigned long long num = 1ull << (32 + s);
+    m = (num + d - 1) / d;
+  };
+  magic((unsigned)g.N[0], g.m0, g.s0);
+  magic((unsigned)g.N[1], g.m1, g.s1);
+}
+
+__host__ __device__ __forceinline__ unsigned fast_div(unsigned n, unsigned long long m, int s) {
+  return (unsigned)((n * m) >> (32 + s));
+}
+
+// (i, j, k) of node idx < 2^31.
 __host__ __device__ __forceinline__ void node_coords(const GridDims& g, long long idx, int& i, int& j,
                                                      int& k) {
-  i = (int)(idx % g.N[0]);
-  long long t = idx / g.N[0];
-  j = (int)(t % g.N[1]);
-  k = (int)(t / g.N[1]);
+  const unsigned n = (unsigned)idx;
+  const unsigned t = fast_div(n, g.m0, g.s0);
+  i = (int)(n - t * (unsigned)g.N[0]);
+  const unsigned kk = fast_div(t, g.m1, g.s1);
+  j = (int)(t - kk * (unsigned)g.N[1]);
+  k = (int)kk;
 }
 
 // Fine (level-1) operator parameters: -Lap_h - omega^2 kappa^2 (1 - i gamma) with
