@@ -89,8 +89,9 @@ def describe(args, wl):
         "method": (f"RS-CGC {args.cycle}(1,1) damped Jacobi w={wl['jacobi']}, "
                    f"{'4th-order 9-point + cubic transfers' if wl['order'] == '4th' else '5-point + FW/bilinear'}, "
                    f"alpha3={wl['alpha3']}, FGMRES({args.restart}), tol {args.tol}"),
-        "precision": ("FP32 cycle on levels 1-2, FP64 FGMRES / outer matvec / true residual / coarsest solve"
-                      if args.precision == "mixed" else "FP64 throughout"),
+        "precision": ("FP32 cycle on levels 1-2; FGMRES basis, Arnoldi streams and coarsest solve in "
+                      "double-FP32 arithmetic (about 48 significant bits); Givens, solution update and true "
+                      "residual in FP64" if args.precision == "mixed" else "FP64 throughout"),
         "l2": "inputs larger than L2 (Krylov basis and operators: several GB per solve)",
         "setup": "excluded from the timed region, reported as setup_ms",
     }
@@ -209,6 +210,15 @@ def run_oracle_iters(A, q, cy, iters, restart, tol):
     return (time.perf_counter() - t), info
 
 
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of the GB300s; the recipe's fallback otherwise."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -260,14 +270,20 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------------ our arm
-def kernel_model(info, its, restart, n1):
-    """Algorithmic bytes and flops per launch of the timed kernel classes."""
-    nv_sum = sum((i % restart) + 1 for i in range(its))
+def kernel_model(info, its, restart, n1, n3):
+    """Algorithmic bytes and flops per launch of the timed kernel classes.
+
+    coarse: the forward sweep reads every factor entry, the backward sweep the G blocks
+    again (16 B per complex entry, FP64 or double-float), plus the vectors (b, w, x and
+    the update vectors, about 6 x 16 B per coarsest node).  Arnoldi kernels: one complex
+    value of 16 B per basis vector and node, plus w, z and the coefficient."""
+    nv_avg = sum((i % restart) + 1 for i in range(its)) / its
+    cb = 16.0 * (info["coarse_entries"] + info["coarse_bwd_entries"]) + 6 * 16.0 * n3
     return {
-        "coarse": {"flops": 8.0 * info["coarse_entries"], "bytes": 16.0 * info["coarse_entries"]},
-        "arnoldi_update": {"flops": 8.0 * 2 * nv_sum / its * n1, "bytes": (32.0 + 16.0 * nv_sum / its) * n1},
-        "arnoldi_norm": {"flops": 8.0 * nv_sum / its * n1, "bytes": (32.0 + 16.0 * nv_sum / its) * n1},
-        "arnoldi_matvec": {"flops": (8.0 * nv_sum / its + 40.0) * n1, "bytes": (40.0 + 16.0 * nv_sum / its) * n1},
+        "coarse": {"flops": 8.0 * (info["coarse_entries"] + info["coarse_bwd_entries"]), "bytes": cb},
+        "arnoldi_update": {"flops": 8.0 * 2 * nv_avg * n1, "bytes": (32.0 + 16.0 * nv_avg) * n1},
+        "arnoldi_norm": {"flops": 8.0 * nv_avg * n1, "bytes": (32.0 + 16.0 * nv_avg) * n1},
+        "arnoldi_matvec": {"flops": (8.0 * nv_avg + 40.0) * n1, "bytes": (40.0 + 16.0 * nv_avg) * n1},
     }
 
 
@@ -347,17 +363,24 @@ def our_arm(args):
     kernels = {k: {"ms_per_solve": v[0] / args.steps, "launches_per_solve": v[1] / args.steps,
                    "share": v[0] / total_ms} for k, v in prof.items() if v[1]}
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_solve"])
-    model = kernel_model(info, its, args.restart, nodes)
+    model = kernel_model(info, its, args.restart, nodes, info["nodes3"])
     roof = None
     if dom in model:
         ms, cnt = prof[dom]
         per_launch_s = ms / 1e3 / cnt
-        fl = model[dom]["flops"] / per_launch_s / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": fl / FP64_PEAK_TFLOPS, "traffic": None,
-                "algorithmic_bytes_per_launch": model[dom]["bytes"],
-                "achieved_gbs": model[dom]["bytes"] / per_launch_s / 1e9,
-                "peak_note": "FP64 ALU peak derived from unit counts and clock; HBM peak in MEASURED_PEAKS.json"}
+        if info.get("double_float"):
+            # double-float arithmetic on the FP32 pipes: the stream is bound by HBM
+            gbs = model[dom]["bytes"] / per_launch_s / 1e9
+            peak = hbm_peak_gbs()
+            roof = {"kernel": dom, "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                    "frac": gbs / peak, "traffic": None, "algorithmic_bytes_per_launch": model[dom]["bytes"],
+                    "launches_timed": cnt, "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json)"}
+        else:
+            fl = model[dom]["flops"] / per_launch_s / 1e12
+            roof = {"kernel": dom, "bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": fl / FP64_PEAK_TFLOPS, "traffic": None,
+                    "algorithmic_bytes_per_launch": model[dom]["bytes"], "launches_timed": cnt,
+                    "peak_note": "FP64 ALU peak derived from unit counts and clock (DESIGN.md)"}
 
     # ---- CPU oracle on a bounded sample
     cpu = None

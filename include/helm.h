@@ -200,7 +200,9 @@ typedef enum {
   HELM_INFO_RADIUS3 = 4,             /* stencil radius of the level-3 operator */
   HELM_INFO_COARSE_ENTRIES = 5,      /* complex entries of the coarsest factors read per solve */
   HELM_INFO_COARSE_FRONTS = 6,       /* fronts of the nested-dissection tree */
-  HELM_INFO_COARSE_LEVELS = 7        /* levels of the nested-dissection tree */
+  HELM_INFO_COARSE_LEVELS = 7,       /* levels of the nested-dissection tree */
+  HELM_INFO_COARSE_BWD_ENTRIES = 8,  /* complex entries the backward sweep reads per solve */
+  HELM_INFO_DOUBLE_FLOAT = 9         /* 1 if the coarsest factors and Krylov basis are double-float */
 } helm_info_key;
 
 /* *value = the quantity selected by key. */

@@ -31,6 +31,7 @@ struct helm_ctx {
   GridDims g[3];
   FineOp fine{};
   double* d_gam = nullptr;
+  float* d_gam32 = nullptr;
   double* kap64 = nullptr;
   float* kap32 = nullptr;
   double* h_gam = nullptr;                     // host copy of the per-axis profiles
@@ -430,6 +431,15 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
   c->fine.gam[0] = c->d_gam;
   c->fine.gam[1] = c->d_gam + c->g[0].N[0];
   c->fine.gam[2] = c->d_gam + c->g[0].N[0] + c->g[0].N[1];
+  {
+    std::vector<float> g32(gam.begin(), gam.end());
+    if (int st = dmalloc(&c->d_gam32, tot * sizeof(float))) return bail(st);
+    if (cudaMemcpy(c->d_gam32, g32.data(), tot * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(fail(HELM_ECUDA, "uploading absorbing profile"));
+    c->fine.gam32[0] = c->d_gam32;
+    c->fine.gam32[1] = c->d_gam32 + c->g[0].N[0];
+    c->fine.gam32[2] = c->d_gam32 + c->g[0].N[0] + c->g[0].N[1];
+  }
 
   // transfers: full weighting / linear everywhere (FW); the cubic stencil of Eq.
   // intergrid everywhere (cubic); cubic except the restriction to level 3 (Eq. levdep)
@@ -508,7 +518,7 @@ int helm_destroy(helm_ctx* c) {
   free_workspaces(c);
   coarse_free(c->cs);
   krylov_free(c->ks);
-  for (void* p : {(void*)c->d_gam, (void*)c->kap64, (void*)c->kap32, (void*)c->A2_64, (void*)c->A2_dinv64,
+  for (void* p : {(void*)c->d_gam, (void*)c->d_gam32, (void*)c->kap64, (void*)c->kap32, (void*)c->A2_64, (void*)c->A2_dinv64,
                   (void*)c->A2_32, (void*)c->A2_dinv32, (void*)c->Mk2, (void*)c->A3_64, (void*)c->A3_dinv64,
                   (void*)c->V, (void*)c->w, (void*)c->r, c->Z, (void*)c->stage, (void*)c->d_bad,
                   (void*)c->cdf})
@@ -660,6 +670,8 @@ int helm_info(const helm_ctx* c, int key, long long* value) {
     case HELM_INFO_COARSE_ENTRIES: *value = c->cs.factor_entries; break;
     case HELM_INFO_COARSE_FRONTS: *value = c->cs.nfronts; break;
     case HELM_INFO_COARSE_LEVELS: *value = c->cs.nlevels; break;
+    case HELM_INFO_COARSE_BWD_ENTRIES: *value = c->cs.bwd_entries; break;
+    case HELM_INFO_DOUBLE_FLOAT: *value = c->cs.df ? 1 : 0; break;
     default: return fail(HELM_EINVAL, "unknown info key");
   }
   return HELM_OK;

@@ -429,13 +429,12 @@ __global__ void __launch_bounds__(kFwdCols) fwd_colsum_kernel(
     }
     __syncthreads();
     double2 acc = make_double2(0.0, 0.0);
+    float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (t < nF) {
       if (DF) {
         const float4* col = reinterpret_cast<const float4*>(factors + d.M_off) + (long long)s0 * nF + t;
-        float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 8
         for (int s = 0; s < s1 - s0; ++s) df_cmac(a4, col[(long long)s * nF], rsd[s]);
-        acc = from_df(a4);
       } else {
         const double2* col = factors + d.M_off + (long long)s0 * nF + t;
 #pragma unroll 8
@@ -443,9 +442,11 @@ __global__ void __launch_bounds__(kFwdCols) fwd_colsum_kernel(
       }
     }
     if (job.nchunks == 1) {
-      if (t < nF) fwd_write(d, Sidx, ctb, b, t, r, acc, uv, w, nodes, uv_total);
+      if (t < nF) fwd_write(d, Sidx, ctb, b, t, r, DF ? from_df(a4) : acc, uv, w, nodes, uv_total);
     } else {
-      part[((long long)(job.pbase + job.chunk) * nrhs + r) * kFwdCols + tid] = acc;
+      const long long pi = ((long long)(job.pbase + job.chunk) * nrhs + r) * kFwdCols + tid;
+      if (DF) reinterpret_cast<float4*>(part)[pi] = a4;
+      else part[pi] = acc;
     }
     __syncthreads();
   }
@@ -458,12 +459,18 @@ __global__ void __launch_bounds__(kFwdCols) fwd_colsum_kernel(
   __threadfence();
   for (int r = 0; r < nrhs; ++r) {
     double2 acc = make_double2(0.0, 0.0);
+    float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int q = 0; q < job.nchunks; ++q) {
-      const double2 v = __ldcg(part + ((long long)(job.pbase + q) * nrhs + r) * kFwdCols + tid);
-      acc.x += v.x;
-      acc.y += v.y;
+      const long long pi = ((long long)(job.pbase + q) * nrhs + r) * kFwdCols + tid;
+      if (DF) {
+        df_acc_add(a4, __ldcg(reinterpret_cast<const float4*>(part) + pi));
+      } else {
+        const double2 v = __ldcg(part + pi);
+        acc.x += v.x;
+        acc.y += v.y;
+      }
     }
-    if (t < nF) fwd_write(d, Sidx, ctb, b, t, r, acc, uv, w, nodes, uv_total);
+    if (t < nF) fwd_write(d, Sidx, ctb, b, t, r, DF ? from_df(a4) : acc, uv, w, nodes, uv_total);
   }
   if (tid == 0) counters[job.slot] = 0u;
 }
@@ -508,7 +515,8 @@ __global__ void __launch_bounds__(512) bwd_matvec_kernel(const FrontDesc* __rest
           const float4* xr = xd + r * nodes;
           for (int c = lane; c < d.nB; c += 32) df_cmac(a4, G[c], xr[B[c]]);
         }
-        acc = from_df(a4);
+        a4 = df_warp_sum(a4);
+        if (lane == 0) acc = from_df(a4);
       } else {
         const double2* G = factors + d.G_off + (long long)row * d.g_ld;
         if (staged) {
@@ -520,10 +528,11 @@ __global__ void __launch_bounds__(512) bwd_matvec_kernel(const FrontDesc* __rest
           for (int c = lane; c < d.nB; c += 32) acc = cmac(acc, G[c], xr[B[c]]);
         }
       }
-      for (int off = 16; off > 0; off >>= 1) {
-        acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
-        acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
-      }
+      if (!DF)
+        for (int off = 16; off > 0; off >>= 1) {
+          acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
+          acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
+        }
       if (lane == 0) {
         const double2 wv = w[r * nodes + node];
         const double2 xv = make_double2(wv.x - acc.x, wv.y - acc.y);
@@ -645,6 +654,8 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
     d.ent_cnt = (int)ents.size() - d.ent_off;
   }
   cs.factor_entries = xg;
+  cs.bwd_entries = 0;
+  for (auto& d : desc) cs.bwd_entries += (long long)d.nS * d.nB;
   cs.max_nB = 0;
   for (auto& d : desc) cs.max_nB = std::max(cs.max_nB, d.nB);
   cs.uv_total = uvo;

@@ -45,6 +45,7 @@ struct CoarseSolver {
   int* d_cmap = nullptr;
   double2* d_factors = nullptr;       // M (and G) blocks of every front
   long long factor_entries = 0;
+  long long bwd_entries = 0;          // entries of the G blocks (read again by the backward sweep)
   std::vector<int*> d_level_list;     // per level: front ids
   std::vector<FwdJob*> d_fwd_jobs;    // per level: forward-sweep blocks
   std::vector<int> n_fwd_jobs;

@@ -106,6 +106,16 @@ struct FineOp {
   double inv_h2;
   double omega2;
   const double* gam[3];    // per-axis gamma tables (device), length N[a]
+  const float* gam32[3];   // the same tables in FP32 (FP32 kernels read these)
+};
+
+// The per-axis absorbing profile in the arithmetic type of a kernel.
+template <typename T> struct GamTab;
+template <> struct GamTab<double> {
+  __device__ static double at(const FineOp& op, int a, int i) { return op.gam[a][i]; }
+};
+template <> struct GamTab<float> {
+  __device__ static float at(const FineOp& op, int a, int i) { return op.gam32[a][i]; }
 };
 
 // Assembled stencil on a coarse level: coef[o * size + node], o in [0, (2r+1)^d).

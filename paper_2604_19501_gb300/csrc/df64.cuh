@@ -67,6 +67,30 @@ __device__ __forceinline__ void df_cmacc(float4& acc, float4 v, float4 w) {
   acc.w += t - e - fmaf(v.y, w.z, v.w * w.x);
 }
 
+// a += b for two accumulators in the convention above (FP32 operations only)
+__device__ __forceinline__ void df_acc_add(float4& a, float4 b) {
+  float s, t;
+  two_sum(a.x, b.x, s, t);
+  a.x = s;
+  a.z += t + b.z;
+  two_sum(a.y, b.y, s, t);
+  a.y = s;
+  a.w += t + b.w;
+}
+
+// Sum of an accumulator over the 32 lanes of a warp, in lane 0.
+__device__ __forceinline__ float4 df_warp_sum(float4 v) {
+  for (int off = 16; off > 0; off >>= 1) {
+    float4 o;
+    o.x = __shfl_down_sync(0xffffffffu, v.x, off);
+    o.y = __shfl_down_sync(0xffffffffu, v.y, off);
+    o.z = __shfl_down_sync(0xffffffffu, v.z, off);
+    o.w = __shfl_down_sync(0xffffffffu, v.w, off);
+    df_acc_add(v, o);
+  }
+  return v;
+}
+
 // ---- normalised double-float reals (hi, lo with |lo| <= ulp(hi) / 2) and complex values
 struct dd {
   float hi, lo;

@@ -10,7 +10,7 @@ namespace helm {
 template <typename T>
 __device__ __forceinline__ c2<T> fine_coef(const FineOp& op, const T* __restrict__ kap, long long idx, int i,
                                            int j, int k) {
-  const T gam = (T)op.gam[0][i] + (T)op.gam[1][j] + (op.g.dim == 3 ? (T)op.gam[2][k] : T(0));
+  const T gam = GamTab<T>::at(op, 0, i) + GamTab<T>::at(op, 1, j) + (op.g.dim == 3 ? GamTab<T>::at(op, 2, k) : T(0));
   const T cre = (T)op.omega2 * kap[idx];
   return mk<T>(cre, -cre * gam);
 }

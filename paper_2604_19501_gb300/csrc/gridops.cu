@@ -16,6 +16,17 @@ namespace helm {
 // 1/16 [1 4 6 4 1] of Eq. intergrid (radius 2).
 __constant__ double c_transfer_w[2][5] = {{0.25, 0.5, 0.25, 0.0, 0.0},
                                           {1.0 / 16, 4.0 / 16, 6.0 / 16, 4.0 / 16, 1.0 / 16}};
+// The same weights in FP32 (exact: all are dyadic), read by the FP32 kernels.
+__constant__ float c_transfer_wf[2][5] = {{0.25f, 0.5f, 0.25f, 0.0f, 0.0f},
+                                          {1.0f / 16, 4.0f / 16, 6.0f / 16, 4.0f / 16, 1.0f / 16}};
+
+template <typename T> struct TransferW;
+template <> struct TransferW<double> {
+  __device__ static const double* get(int rw) { return c_transfer_w[rw - 1]; }
+};
+template <> struct TransferW<float> {
+  __device__ static const float* get(int rw) { return c_transfer_wf[rw - 1]; }
+};
 
 // --------------------------------------------------------------- fine operator
 template <typename T, typename TX, typename SB, typename TY, int MODE>
@@ -125,7 +136,7 @@ __global__ void __launch_bounds__(256) restrict_kernel(GridDims gf, GridDims gc,
   if (I >= gc.size) return;
   int ci, cj, ck;
   node_coords(gc, I, ci, cj, ck);
-  const double* wt = c_transfer_w[RW - 1];
+  const T* wt = TransferW<T>::get(RW);
   const long long sy = gf.N[0];
   const long long sz = (long long)gf.N[0] * gf.N[1];
   for (int r = 0; r < nrhs; ++r) {
@@ -163,7 +174,7 @@ __global__ void __launch_bounds__(256) prolong_add_kernel(GridDims gf, GridDims 
   if (idx >= gf.size) return;
   int fi, fj, fk;
   node_coords(gf, idx, fi, fj, fk);
-  const double* wt = c_transfer_w[RW - 1];
+  const T* wt = TransferW<T>::get(RW);
   const long long sy = gc.N[0];
   const long long sz = (long long)gc.N[0] * gc.N[1];
   // coarse J with |f - 2J| <= RW along each axis; weight 2 * w(f - 2J) per axis

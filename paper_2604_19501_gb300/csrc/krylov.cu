@@ -296,14 +296,34 @@ __global__ void coef_df_kernel(FineOp op, const double* __restrict__ kap, float4
   }
 }
 
-// Per-thread double-float accumulators live in shared memory as float4 [value][thread];
-// each is turned into complex FP64 in place before the block reduction.
-__device__ __forceinline__ void df_to_double_inplace(double2* sacc, int nval) {
-  float4* sdf = reinterpret_cast<float4*>(sacc);
-  for (int i = 0; i < nval; ++i) {
-    const int s = i * blockDim.x + threadIdx.x;
-    sacc[s] = from_df(sdf[s]);
+// Reduction of per-thread double-float accumulators sdf[i * blockDim + tid] (nval sums):
+// warps reduce in double-float, the block partials go to part (as float4), and the last
+// block adds the partials in block order and converts each sum to FP64 once.
+__device__ void reduce_finish_df(float4* sdf, int nval, double2* __restrict__ part_raw,
+                                 unsigned* __restrict__ counter, double2* __restrict__ out) {
+  __shared__ bool s_last;
+  float4* part = reinterpret_cast<float4*>(part_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  __syncthreads();
+  for (int i = warp; i < nval; i += nwarp) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int t = lane; t < (int)blockDim.x; t += 32) df_acc_add(v, sdf[i * blockDim.x + t]);
+    v = df_warp_sum(v);
+    if (lane == 0) part[(long long)blockIdx.x * nval + i] = v;
   }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int i = warp; i < nval; i += nwarp) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int b = lane; b < (int)gridDim.x; b += 32) df_acc_add(v, __ldcg(part + (long long)b * nval + i));
+    v = df_warp_sum(v);
+    if (lane == 0) out[i] = from_df(v);
+  }
+  if (tid == 0) *counter = 0u;
 }
 
 __global__ void __launch_bounds__(kThreads) arnoldi_matvec_df_kernel(
@@ -322,8 +342,7 @@ __global__ void __launch_bounds__(kThreads) arnoldi_matvec_df_kernel(
     for (int q = 0; q < nv; ++q) df_cmacc(sdf[q * blockDim.x + tid], V[q * vstride + p], wv);
     df_cmacc(sdf[nv * blockDim.x + tid], wv, wv);
   }
-  df_to_double_inplace(sacc, nv + 1);
-  reduce_finish(sacc, nv + 1, part, counter, out);
+  reduce_finish_df(sdf, nv + 1, part, counter, out);
 }
 
 __global__ void __launch_bounds__(kThreads) arnoldi_update_df_kernel(
@@ -345,8 +364,7 @@ __global__ void __launch_bounds__(kThreads) arnoldi_update_df_kernel(
     for (int q = 0; q < nv; ++q) df_cmacc(sdf[q * blockDim.x + tid], V[q * vstride + p], w4);
     df_cmacc(sdf[nv * blockDim.x + tid], w4, w4);
   }
-  df_to_double_inplace(sacc, nv + 1);
-  reduce_finish(sacc, nv + 1, part, counter, out);
+  reduce_finish_df(sdf, nv + 1, part, counter, out);
 }
 
 __global__ void __launch_bounds__(kThreads) arnoldi_normalize_df_kernel(
