@@ -412,6 +412,8 @@ __global__ void __launch_bounds__(kFwdCols) fwd_colsum_kernel(
     const int2* __restrict__ ctb, const double2* __restrict__ factors, const double2* __restrict__ b,
     double2* __restrict__ uv, double2* __restrict__ w, double2* __restrict__ part,
     unsigned* __restrict__ counters, int nrhs, long long nodes, long long uv_total) {
+  pdl_trigger();
+  // job lists, fronts and factors are written at set-up: read before the wait
   const FwdJob job = jobs[blockIdx.x];
   const FrontDesc d = desc[job.front];
   const int nF = d.nS + d.nB;
@@ -421,6 +423,7 @@ __global__ void __launch_bounds__(kFwdCols) fwd_colsum_kernel(
   __shared__ double2 rs[kFwdMaxChunk];
   __shared__ float4 rsd[kFwdMaxChunk];
   __shared__ bool s_last;
+  pdl_wait();
   for (int r = 0; r < nrhs; ++r) {
     for (int q = tid; q < s1 - s0; q += blockDim.x) {
       const double2 v = front_rhs(d, Sidx, ctb, b, uv, s0 + q, r, nodes, uv_total);
@@ -434,11 +437,11 @@ __global__ void __launch_bounds__(kFwdCols) fwd_colsum_kernel(
       if (DF) {
         const float4* col = reinterpret_cast<const float4*>(factors + d.M_off) + (long long)s0 * nF + t;
 #pragma unroll 8
-        for (int s = 0; s < s1 - s0; ++s) df_cmac(a4, col[(long long)s * nF], rsd[s]);
+        for (int s = 0; s < s1 - s0; ++s) df_cmac(a4, __ldcs(col + (long long)s * nF), rsd[s]);
       } else {
         const double2* col = factors + d.M_off + (long long)s0 * nF + t;
 #pragma unroll 8
-        for (int s = 0; s < s1 - s0; ++s) acc = cmac(acc, col[(long long)s * nF], rs[s]);
+        for (int s = 0; s < s1 - s0; ++s) acc = cmac(acc, __ldcs(col + (long long)s * nF), rs[s]);
       }
     }
     if (job.nchunks == 1) {
@@ -489,11 +492,13 @@ __global__ void __launch_bounds__(512) bwd_matvec_kernel(const FrontDesc* __rest
                                                          double2* __restrict__ x, float4* __restrict__ xd,
                                                          int nrhs, long long nodes, int smem_cap) {
   extern __shared__ float4 xs[];
+  pdl_trigger();
   const int4 job = rows[blockIdx.x];
   const FrontDesc d = desc[job.x];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int* B = Bidx + d.B_off;
   const bool staged = d.nB <= smem_cap;
+  pdl_wait();
   for (int r = 0; r < nrhs; ++r) {
     if (staged) {
       for (int c = threadIdx.x; c < d.nB; c += blockDim.x) {
@@ -510,7 +515,7 @@ __global__ void __launch_bounds__(512) bwd_matvec_kernel(const FrontDesc* __rest
         float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (staged) {
 #pragma unroll 4
-          for (int c = lane; c < d.nB; c += 32) df_cmac(a4, G[c], xs[c]);
+          for (int c = lane; c < d.nB; c += 32) df_cmac(a4, __ldcs(G + c), xs[c]);
         } else {
           const float4* xr = xd + r * nodes;
           for (int c = lane; c < d.nB; c += 32) df_cmac(a4, G[c], xr[B[c]]);
@@ -522,7 +527,7 @@ __global__ void __launch_bounds__(512) bwd_matvec_kernel(const FrontDesc* __rest
         if (staged) {
           const double2* xs2 = reinterpret_cast<const double2*>(xs);
 #pragma unroll 4
-          for (int c = lane; c < d.nB; c += 32) acc = cmac(acc, G[c], xs2[c]);
+          for (int c = lane; c < d.nB; c += 32) acc = cmac(acc, __ldcs(G + c), xs2[c]);
         } else {
           const double2* xr = x + r * nodes;
           for (int c = lane; c < d.nB; c += 32) acc = cmac(acc, G[c], xr[B[c]]);
@@ -810,26 +815,20 @@ static int ensure_rhs(CoarseSolver& cs, int nrhs) {
 static int solve_sweeps(const CoarseSolver& cs, const double2* b, double2* e, int nrhs, double2* uv,
                         double2* w, double2* part, unsigned* counters, float4* xd, cudaStream_t s) {
   for (int h = 0; h < cs.nlevels; ++h) {
-    if (cs.df)
-      fwd_colsum_kernel<true><<<cs.n_fwd_jobs[h], kFwdCols, 0, s>>>(cs.d_desc, cs.d_fwd_jobs[h], cs.d_S, cs.d_ctb,
-                                                                    cs.d_factors, b, uv, w, part, counters, nrhs,
-                                                                    cs.g.size, cs.uv_total);
-    else
-      fwd_colsum_kernel<false><<<cs.n_fwd_jobs[h], kFwdCols, 0, s>>>(cs.d_desc, cs.d_fwd_jobs[h], cs.d_S, cs.d_ctb,
-                                                                     cs.d_factors, b, uv, w, part, counters, nrhs,
-                                                                     cs.g.size, cs.uv_total);
+    const cudaError_t le = launch_pdl(cs.df ? fwd_colsum_kernel<true> : fwd_colsum_kernel<false>,
+                                      dim3(cs.n_fwd_jobs[h]), dim3(kFwdCols), 0, s, cs.d_desc, cs.d_fwd_jobs[h],
+                                      cs.d_S, cs.d_ctb, cs.d_factors, b, uv, w, part, counters, nrhs, cs.g.size,
+                                      cs.uv_total);
+    if (le != cudaSuccess) { set_error(std::string("coarse forward launch: ") + cudaGetErrorString(le)); return HELM_ECUDA; }
     HELM_LAUNCH_CHECK();
   }
   for (int h = cs.nlevels - 1; h >= 0; --h) {
     const size_t sm = (size_t)std::min(cs.max_nB, kBwdSmemEntries) * sizeof(float4);
-    if (cs.df)
-      bwd_matvec_kernel<true><<<cs.n_bwd_rows[h], 32 * kRowsPerBlock, sm, s>>>(
-          cs.d_desc, cs.d_bwd_rows[h], cs.d_S, cs.d_B, cs.d_factors, w, e, xd, nrhs, cs.g.size,
-          kBwdSmemEntries);
-    else
-      bwd_matvec_kernel<false><<<cs.n_bwd_rows[h], 32 * kRowsPerBlock, sm, s>>>(
-          cs.d_desc, cs.d_bwd_rows[h], cs.d_S, cs.d_B, cs.d_factors, w, e, xd, nrhs, cs.g.size,
-          kBwdSmemEntries);
+    const cudaError_t le = launch_pdl(cs.df ? bwd_matvec_kernel<true> : bwd_matvec_kernel<false>,
+                                      dim3(cs.n_bwd_rows[h]), dim3(32 * kRowsPerBlock), sm, s, cs.d_desc,
+                                      cs.d_bwd_rows[h], cs.d_S, cs.d_B, cs.d_factors, w, e, xd, nrhs, cs.g.size,
+                                      kBwdSmemEntries);
+    if (le != cudaSuccess) { set_error(std::string("coarse backward launch: ") + cudaGetErrorString(le)); return HELM_ECUDA; }
     HELM_LAUNCH_CHECK();
   }
   return 0;

@@ -161,4 +161,29 @@ void set_error(const std::string& s);
 
 inline int blocks_for(long long n, int threads) { return (int)((n + threads - 1) / threads); }
 
+// ---------------------------------------------------------------- programmatic dependent launch
+// Kernels launched with launch_pdl may start while the previous kernel of the stream is
+// still running.  They call pdl_trigger() early (which lets the next kernel launch once
+// every block of this one has started) and pdl_wait() before they read anything an
+// earlier kernel wrote; pdl_wait returns once the previous kernel has completed and its
+// memory is visible.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 }  // namespace helm
