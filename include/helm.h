@@ -121,15 +121,20 @@ int helm_solve(helm_ctx* c, const void* q, void* p, int n_rhs, double tol, int m
                helm_stats* stats);
 
 /* Gradient of L = 1/2 sum_r ||P_rec p_r - d_r||^2 with respect to kappa^2, by
- * the adjoint-state method: H is complex-symmetric, so mu_r = conj(lambda_r)
- * solves H mu_r = conj(residual_r) with the same preconditioned solver, and
- * dL/dkappa^2_j = omega^2 sum_r Re((1 - i gamma_j) mu_{r,j} p_{r,j}).
- * p: c128 forward fields (n_rhs * nodes); resid: c128 receiver residuals
- * P_rec^T (P_rec p - d) on the full grid (zero off receivers); grad: real FP64
- * [nodes], ACCUMULATED into (caller zeroes it).  All device pointers.  stats as
- * for helm_solve (adjoint solves).  Synchronises the stream. */
+ * the adjoint-state method (the paper has no adjoint; standard derivation for the
+ * operator of Sec. 3.1).  H is complex-symmetric, so mu_r = conj(lambda_r)
+ * solves H mu_r = conj(resid_r) with the same preconditioned solver, and with the
+ * mass weights w_o of the stencil (coefficient mean on every mass coupling)
+ *   dL/dkappa^2_j = omega^2 sum_r Re((1 - i gamma_j) sum_o w_o (mu_j p_{j+o} + mu_{j+o} p_j) / 2),
+ * i.e. omega^2 sum_r Re((1 - i gamma_j) mu_{r,j} p_{r,j}) for the 5/7-point stencil.
+ * p: c128 forward fields (n_rhs * nodes); resid: c128 P_rec^T (P_rec p - d) on the
+ * full grid (zero off the receivers), or in general dL/dp in the convention
+ * dL = Re(sum conj(resid) dp); grad: real FP64 [nodes], ACCUMULATED into (the caller
+ * zeroes it); adj: optional c128 output of the adjoint fields mu (n_rhs * nodes), or
+ * NULL.  lambda = conj(mu) is the gradient with respect to the source q.  All device
+ * pointers.  stats as for helm_solve (the adjoint solves).  Synchronises the stream. */
 int helm_adjoint_grad(helm_ctx* c, const void* p, const void* resid, int n_rhs, double tol,
-                      int maxit, double* grad, helm_stats* stats);
+                      int maxit, double* grad, void* adj, helm_stats* stats);
 
 /* ---- Component entry points (one step of the method each; device pointers) ---- */
 

@@ -11,7 +11,7 @@ import ctypes
 from . import _ffi
 from ._ffi import HelmError, HelmOpts, HelmStats, check
 
-__all__ = ["Solver", "HelmError", "level_shape"]
+__all__ = ["Solver", "HelmError", "level_shape", "helmholtz_solve"]
 
 _lib = _ffi.load()
 
@@ -139,12 +139,13 @@ class Solver:
         return p, [dict(iterations=s.iterations, converged=bool(s.converged), relres=s.relres,
                         est_relres=s.est_relres) for s in stats]
 
-    def adjoint_grad(self, p, resid, grad, tol=1e-6, maxit=500):
-        """Accumulates dL/dkappa^2 into ``grad`` (helm_adjoint_grad)."""
+    def adjoint_grad(self, p, resid, grad, adj=None, tol=1e-6, maxit=500):
+        """Accumulates dL/dkappa^2 into ``grad`` (helm_adjoint_grad); ``adj`` optionally
+        receives the adjoint fields mu = conj(lambda).  Returns the adjoint-solve stats."""
         nrhs = self._nrhs(p)
         stats = (HelmStats * nrhs)()
         st = _lib.helm_adjoint_grad(self._ctx, _ptr(p), _ptr(resid), nrhs, float(tol), int(maxit),
-                                    _ptr(grad), stats)
+                                    _ptr(grad), _ptr(adj), stats)
         if st not in (_ffi.HELM_OK, _ffi.HELM_NOT_CONVERGED):
             check(st, "helm_adjoint_grad")
         return [dict(iterations=s.iterations, converged=bool(s.converged), relres=s.relres) for s in stats]
@@ -224,3 +225,51 @@ def _empty_like(x):
     import numpy as np
 
     return np.empty_like(x)
+
+
+def _autograd_function():
+    import torch
+
+    class HelmholtzSolve(torch.autograd.Function):
+        """p = H(kappa2)^-1 q with the adjoint-state backward.
+
+        forward: set-up for kappa2, then helm_solve.  backward: helm_adjoint_grad with
+        the incoming gradient as residual, giving dL/dkappa2 and, as conj(mu), dL/dq.
+        ``recompute=True`` keeps only q and solves for p again in the backward (less
+        memory, one more forward solve)."""
+
+        @staticmethod
+        def forward(ctx, kappa2, q, opts, tol, maxit, recompute):
+            solver = Solver(kappa2.detach().contiguous(), **opts)
+            qd = q.detach().contiguous()
+            p, _ = solver.solve(qd, tol=tol, maxit=maxit)
+            ctx.solver, ctx.tol, ctx.maxit, ctx.recompute = solver, tol, maxit, recompute
+            ctx.save_for_backward(qd if recompute else p)
+            return p
+
+        @staticmethod
+        def backward(ctx, grad_p):
+            (saved,) = ctx.saved_tensors
+            solver = ctx.solver
+            p = solver.solve(saved, tol=ctx.tol, maxit=ctx.maxit)[0] if ctx.recompute else saved
+            grad_k = torch.zeros(solver.shape(1), dtype=torch.float64, device=p.device)
+            adj = torch.empty_like(p)
+            solver.adjoint_grad(p, grad_p.contiguous(), grad_k, adj, tol=ctx.tol, maxit=ctx.maxit)
+            grad_q = adj.conj() if ctx.needs_input_grad[1] else None
+            solver.close()
+            return grad_k, grad_q, None, None, None, None
+
+    return HelmholtzSolve
+
+
+_HELMHOLTZ_SOLVE = None
+
+
+def helmholtz_solve(kappa2, q, n, omega, tol=1e-6, maxit=500, recompute=False, **opts):
+    """Differentiable p = H(kappa2)^-1 q (torch.autograd): the backward pass is the
+    adjoint solve of helm_adjoint_grad.  ``opts`` are Solver keywords."""
+    global _HELMHOLTZ_SOLVE
+    if _HELMHOLTZ_SOLVE is None:
+        _HELMHOLTZ_SOLVE = _autograd_function()
+    o = dict(opts, n=n, omega=omega)
+    return _HELMHOLTZ_SOLVE.apply(kappa2, q, o, tol, maxit, recompute)

@@ -62,7 +62,7 @@ SIGNATURES = {
     "helm_setup": (_I, [ctypes.POINTER(HelmOpts), _P, ctypes.POINTER(_P)]),
     "helm_destroy": (_I, [_P]),
     "helm_solve": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(HelmStats)]),
-    "helm_adjoint_grad": (_I, [_P, _P, _P, _I, _D, _I, _P, ctypes.POINTER(HelmStats)]),
+    "helm_adjoint_grad": (_I, [_P, _P, _P, _I, _D, _I, _P, _P, ctypes.POINTER(HelmStats)]),
     "helm_apply": (_I, [_P, _I, _I, _P, _P, _I]),
     "helm_smooth": (_I, [_P, _I, _I, _P, _P, _I]),
     "helm_residual": (_I, [_P, _I, _I, _P, _P, _P, _I]),

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/helm.h"
+#include "adjoint.cuh"
 #include "coarse.cuh"
 #include "galerkin.cuh"
 #include "gridops.cuh"
@@ -568,9 +569,37 @@ int helm_solve(helm_ctx* c, const void* q, void* p, int n_rhs, double tol, int m
 }
 
 int helm_adjoint_grad(helm_ctx* c, const void* p, const void* resid, int n_rhs, double tol, int maxit,
-                      double* grad, helm_stats* stats) {
-  (void)c; (void)p; (void)resid; (void)n_rhs; (void)tol; (void)maxit; (void)grad; (void)stats;
-  return fail(HELM_EINVAL, "adjoint gradient not built");
+                      double* grad, void* adj, helm_stats* stats) {
+  if (!c || !p || !resid || !grad) return fail(HELM_EINVAL, "null argument");
+  if (n_rhs < 1 || !(tol > 0) || maxit < 1) return fail(HELM_EINVAL, "bad n_rhs, tol or maxit");
+  if (!is_device_ptr(p) || !is_device_ptr(resid) || !is_device_ptr(grad) || (adj && !is_device_ptr(adj)))
+    return fail(HELM_EINVAL, "helm_adjoint_grad takes device pointers");
+  LaunchScope scope(c);
+  const long long n = c->g[0].size;
+  // one right-hand side of conj(residual) and one adjoint field at a time
+  if (2 * n > c->stage_cap) {
+    cudaFree(c->stage);
+    c->stage = nullptr;
+    c->stage_cap = 0;
+    if (int st = dmalloc(&c->stage, 2 * n * sizeof(double2))) return st;
+    c->stage_cap = 2 * n;
+  }
+  double2* rhs = c->stage;
+  double2* mu = c->stage + n;
+  int worst = HELM_OK;
+  for (int r = 0; r < n_rhs; ++r) {
+    const double2* pr = (const double2*)p + (size_t)r * n;
+    if (int st = launch_conj(n, (const double2*)resid + (size_t)r * n, rhs, c->s)) return st;
+    double2* m_out = adj ? (double2*)adj + (size_t)r * n : mu;
+    helm_stats one{};
+    if (int st = fgmres_one(c, rhs, m_out, tol, maxit, &one)) return st;
+    if (stats) stats[r] = one;
+    if (!one.converged) worst = HELM_NOT_CONVERGED;
+    if (int st = launch_gradient(c->fine, pr, m_out, grad, c->s)) return st;
+  }
+  HELM_CUDA_TRY(cudaStreamSynchronize(c->s));
+  if (worst != HELM_OK) set_error("adjoint solve not converged within maxit");
+  return worst;
 }
 
 int helm_apply(helm_ctx* c, int level, int dtype, const void* x, void* y, int n_rhs) {
