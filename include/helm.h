@@ -76,7 +76,9 @@ typedef struct {
   double rb_w;            /* relaxation weight of the red-black sweep */
   int precision;          /* helm_precision used by helm_solve / helm_cycle */
   int restart;            /* FGMRES restart length m (>= 1) */
-  int max_rhs;            /* largest n_rhs a solve will be given (sizes workspaces; grows on demand) */
+  int max_rhs;            /* right-hand sides per FGMRES block: helm_solve / helm_adjoint_grad run
+                             n_rhs in blocks of this size, each block sharing one cycle and one
+                             coarsest solve per iteration (operators read once per block) */
   void* stream;           /* cudaStream_t for all work of this context */
 } helm_opts;
 

@@ -54,8 +54,12 @@ struct helm_ctx {
   // Krylov workspaces (one right-hand side at a time)
   double2 *V = nullptr, *w = nullptr, *r = nullptr;
   void* Z = nullptr;
-  KrylovState ks;
-  double* h_scal = nullptr;                    // pinned copy of ks.scal
+  std::vector<KrylovState> ks;                // one FGMRES state per right-hand side of a block
+  double* d_scal = nullptr;                    // [block][KS_COUNT] scalars of the states
+  double* h_scal = nullptr;                    // pinned copy of d_scal
+  double2* d_kpart = nullptr;                  // reduction scratch shared by the states
+  unsigned* d_kcounter = nullptr;
+  int block = 1;                               // right-hand sides per FGMRES block
   // staging for host buffers
   double2* stage = nullptr;
   long long stage_cap = 0;
@@ -240,75 +244,125 @@ int run_cycle(helm_ctx* c, const void* v, Prec vs, void* z, Prec zs, int nrhs) {
   return launch_convert(P, zs, x, z, n1, c->s);
 }
 
-int sync_scal(helm_ctx* c) {
-  HELM_CUDA_TRY(cudaMemcpyAsync(c->h_scal, c->ks.scal, sizeof(double) * KS_COUNT, cudaMemcpyDeviceToHost, c->s));
+int sync_scal(helm_ctx* c, int B) {
+  HELM_CUDA_TRY(cudaMemcpyAsync(c->h_scal, c->d_scal, sizeof(double) * KS_COUNT * B, cudaMemcpyDeviceToHost, c->s));
   HELM_CUDA_TRY(cudaStreamSynchronize(c->s));
   return 0;
 }
 
-// FGMRES(m) for one right-hand side (device pointers).
-int fgmres_one(helm_ctx* c, const double2* q, double2* p, double tol, int maxit, helm_stats* out) {
+// FGMRES(m) for a block of B right-hand sides (device pointers, B * nodes each).  The
+// cycle and the coarsest solve run once per iteration for the whole block (operators
+// read once per block); each right-hand side keeps its own Arnoldi basis, Givens
+// rotations and convergence test, and leaves the block's Arnoldi steps once it has
+// converged.  Per right-hand side the arithmetic is that of a single solve.
+// Layouts: V [m+1][B][n], Z [m][B][n], w and r [B][n].
+int fgmres_block(helm_ctx* c, const double2* q, double2* p, int B, double tol, int maxit, helm_stats* out) {
   const long long n = c->g[0].size;
   const int m = c->o.restart;
   const Prec zp = cycle_prec(c);
   const size_t zes = esize(zp);
   // mixed precision: the basis V and w are double-float (float4), arithmetic on FP32 pipes
   const bool df = zp == P32;
-  float4* Vd = reinterpret_cast<float4*>(c->V);
-  float4* wd = reinterpret_cast<float4*>(c->w);
-  HELM_CUDA_TRY(cudaMemsetAsync(p, 0, n * sizeof(double2), c->s));
-  if (int st = k_norm(c->ks, n, q, c->r, c->s)) return st;
-  if (int st = sync_scal(c)) return st;
-  const double bnorm = c->h_scal[KS_BNORM];
-  helm_stats res{0, 1, 0.0, 0.0};
-  if (!std::isfinite(bnorm)) return fail(HELM_EINVAL, "right-hand side is not finite");
-  if (bnorm == 0.0) {
-    if (out) *out = res;
-    return 0;
+  const long long vstride = (long long)B * n;
+  auto Vp = [&](int i, int r) { return c->V + ((size_t)i * B + r) * n; };
+  auto Vd = [&](int i, int r) { return reinterpret_cast<float4*>(c->V) + ((size_t)i * B + r) * n; };
+  auto Zp = [&](int j, int r) { return (char*)c->Z + ((size_t)j * B + r) * n * zes; };
+  auto S = [&](int r) { return c->h_scal + (size_t)r * KS_COUNT; };
+  HELM_CUDA_TRY(cudaMemsetAsync(p, 0, (size_t)B * n * sizeof(double2), c->s));
+  for (int r = 0; r < B; ++r)
+    if (int st = k_norm(c->ks[r], n, q + (size_t)r * n, c->r + (size_t)r * n, c->s)) return st;
+  if (int st = sync_scal(c, B)) return st;
+  std::vector<double> bnorm(B), beta(B), est(B);
+  std::vector<int> its(B, 0), k(B, 0);
+  std::vector<char> done(B, 0), part(B, 0), act(B, 0);
+  for (int r = 0; r < B; ++r) {
+    bnorm[r] = S(r)[KS_BNORM];
+    beta[r] = S(r)[KS_BETA];
+    if (!std::isfinite(bnorm[r])) return fail(HELM_EINVAL, "right-hand side is not finite");
+    est[r] = bnorm[r] > 0 ? beta[r] / bnorm[r] : 0.0;
+    if (bnorm[r] == 0.0) done[r] = 1;
   }
-  double beta = c->h_scal[KS_BETA];
-  int its = 0;
-  double est = beta / bnorm;
   while (true) {
-    if (beta / bnorm < tol || its >= maxit) break;
-    if (df) {
-      if (int st = k_start_cycle_df(c->ks, n, c->r, Vd, c->s)) return st;
-    } else if (int st = k_start_cycle(c->ks, n, c->r, c->V, c->s)) {
-      return st;
+    int npart = 0;
+    for (int r = 0; r < B; ++r) {
+      part[r] = !done[r] && beta[r] / bnorm[r] >= tol && its[r] < maxit;
+      act[r] = part[r];
+      k[r] = 0;
+      npart += part[r];
     }
-    int k = 0;
-    for (int j = 0; j < m; ++j) {
-      void* zj = (char*)c->Z + (size_t)j * n * zes;
+    if (npart == 0) break;
+    for (int r = 0; r < B; ++r) {
+      if (!part[r]) continue;
       if (df) {
-        if (int st = run_cycle(c, Vd + (size_t)j * n, P_DF, zj, zp, 1)) return st;
-        if (int st = k_arnoldi_df(c->ks, c->fine, c->cdf, (const float2*)zj, wd, Vd, n, j, c->s)) return st;
-      } else {
-        if (int st = run_cycle(c, c->V + (size_t)j * n, P64, zj, zp, 1)) return st;
-        if (int st = k_arnoldi(c->ks, c->fine, c->kap64, zj, zp, c->w, c->V, n, j, c->s)) return st;
-      }
-      if (int st = sync_scal(c)) return st;
-      ++its;
-      k = j + 1;
-      est = c->h_scal[KS_EST];
-      if (!std::isfinite(est)) return fail(HELM_ENUMERIC, "non-finite residual estimate");
-      if (est < tol || its >= maxit || c->h_scal[KS_HN] == 0.0) break;
-      if (df) {
-        if (int st = k_normalize_df(c->ks, n, wd, Vd, n, j, Vd + (size_t)(j + 1) * n, c->s)) return st;
-      } else if (int st = k_normalize(c->ks, n, c->w, c->V, n, j, c->V + (size_t)(j + 1) * n, c->s)) {
+        if (int st = k_start_cycle_df(c->ks[r], n, c->r + (size_t)r * n, Vd(0, r), c->s)) return st;
+      } else if (int st = k_start_cycle(c->ks[r], n, c->r + (size_t)r * n, Vp(0, r), c->s)) {
         return st;
       }
     }
-    if (int st = k_update_solution(c->ks, n, p, c->Z, zp, n, k, c->s)) return st;
-    if (int st = k_true_residual(c->ks, c->fine, c->kap64, q, p, c->r, c->s)) return st;
-    if (int st = sync_scal(c)) return st;
-    beta = c->h_scal[KS_BETA];
-    if (!std::isfinite(beta)) return fail(HELM_ENUMERIC, "non-finite residual");
+    for (int j = 0; j < m; ++j) {
+      if (df) {
+        if (int st = run_cycle(c, Vd(j, 0), P_DF, Zp(j, 0), zp, B)) return st;
+      } else if (int st = run_cycle(c, Vp(j, 0), P64, Zp(j, 0), zp, B)) {
+        return st;
+      }
+      for (int r = 0; r < B; ++r) {
+        if (!act[r]) continue;
+        if (df) {
+          if (int st = k_arnoldi_df(c->ks[r], c->fine, c->cdf, (const float2*)Zp(j, r), reinterpret_cast<float4*>(c->w) + (size_t)r * n,
+                                    Vd(0, r), vstride, j, c->s))
+            return st;
+        } else if (int st = k_arnoldi(c->ks[r], c->fine, c->kap64, Zp(j, r), zp, c->w + (size_t)r * n, Vp(0, r),
+                                      vstride, j, c->s)) {
+          return st;
+        }
+      }
+      if (int st = sync_scal(c, B)) return st;
+      int nact = 0;
+      for (int r = 0; r < B; ++r) {
+        if (!act[r]) continue;
+        ++its[r];
+        k[r] = j + 1;
+        est[r] = S(r)[KS_EST];
+        if (!std::isfinite(est[r])) return fail(HELM_ENUMERIC, "non-finite residual estimate");
+        if (est[r] < tol || its[r] >= maxit || S(r)[KS_HN] == 0.0) act[r] = 0;
+        nact += act[r];
+      }
+      if (nact == 0) break;
+      for (int r = 0; r < B; ++r) {
+        if (!act[r]) continue;
+        if (df) {
+          if (int st = k_normalize_df(c->ks[r], n, reinterpret_cast<float4*>(c->w) + (size_t)r * n, Vd(0, r), vstride, j,
+                                      Vd(j + 1, r), c->s))
+            return st;
+        } else if (int st = k_normalize(c->ks[r], n, c->w + (size_t)r * n, Vp(0, r), vstride, j, Vp(j + 1, r), c->s)) {
+          return st;
+        }
+      }
+    }
+    for (int r = 0; r < B; ++r) {
+      if (!part[r]) continue;
+      if (int st = k_update_solution(c->ks[r], n, p + (size_t)r * n, Zp(0, r), zp, vstride, k[r], c->s)) return st;
+      if (int st = k_true_residual(c->ks[r], c->fine, c->kap64, q + (size_t)r * n, p + (size_t)r * n,
+                                   c->r + (size_t)r * n, c->s))
+        return st;
+    }
+    if (int st = sync_scal(c, B)) return st;
+    for (int r = 0; r < B; ++r) {
+      if (!part[r]) continue;
+      beta[r] = S(r)[KS_BETA];
+      if (!std::isfinite(beta[r])) return fail(HELM_ENUMERIC, "non-finite residual");
+    }
   }
-  res.iterations = its;
-  res.relres = beta / bnorm;
-  res.converged = res.relres < tol ? 1 : 0;
-  res.est_relres = est;
-  if (out) *out = res;
+  for (int r = 0; r < B; ++r) {
+    helm_stats res{0, 1, 0.0, 0.0};
+    if (bnorm[r] > 0) {
+      res.iterations = its[r];
+      res.relres = beta[r] / bnorm[r];
+      res.converged = res.relres < tol ? 1 : 0;
+      res.est_relres = est[r];
+    }
+    if (out) out[r] = res;
+  }
   return 0;
 }
 
@@ -497,16 +551,26 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
   // workspaces
   const int m = o->restart;
   if ((st = ensure_workspaces(c, o->max_rhs))) return bail(st);
-  if ((st = dmalloc(&c->V, (size_t)(m + 1) * n1 * sizeof(double2))) ||
-      (st = dmalloc(&c->Z, (size_t)m * n1 * esize(cycle_prec(c)))) ||
-      (st = dmalloc(&c->w, n1 * sizeof(double2))) || (st = dmalloc(&c->r, n1 * sizeof(double2))))
+  const int B = o->max_rhs;
+  c->block = B;
+  if ((st = dmalloc(&c->V, (size_t)(m + 1) * B * n1 * sizeof(double2))) ||
+      (st = dmalloc(&c->Z, (size_t)m * B * n1 * esize(cycle_prec(c)))) ||
+      (st = dmalloc(&c->w, (size_t)B * n1 * sizeof(double2))) || (st = dmalloc(&c->r, (size_t)B * n1 * sizeof(double2))))
     return bail(st);
-  if ((st = krylov_alloc(c->ks, m))) return bail(st);
+  if ((st = dmalloc(&c->d_scal, sizeof(double) * KS_COUNT * B)) ||
+      (st = dmalloc(&c->d_kpart, sizeof(double2) * krylov_part_entries(m))) ||
+      (st = dmalloc(&c->d_kcounter, sizeof(unsigned))))
+    return bail(st);
+  if (cudaMemset(c->d_kcounter, 0, sizeof(unsigned)) != cudaSuccess) return bail(fail(HELM_ECUDA, "memset"));
+  c->ks.resize(B);
+  for (int r = 0; r < B; ++r)
+    if ((st = krylov_alloc(c->ks[r], m, c->d_scal + (size_t)r * KS_COUNT, c->d_kpart, c->d_kcounter)))
+      return bail(st);
   if (o->precision == HELM_MIXED) {
     if ((st = dmalloc(&c->cdf, n1 * sizeof(float4)))) return bail(st);
     if ((st = k_coef_df(c->fine, c->kap64, c->cdf, c->s))) return bail(HELM_ECUDA);
   }
-  if (cudaMallocHost(&c->h_scal, sizeof(double) * KS_COUNT) != cudaSuccess) return bail(fail(HELM_ENOMEM, "pinned alloc"));
+  if (cudaMallocHost(&c->h_scal, sizeof(double) * KS_COUNT * B) != cudaSuccess) return bail(fail(HELM_ENOMEM, "pinned alloc"));
   if (cudaStreamSynchronize(c->s) != cudaSuccess) return bail(fail(HELM_ECUDA, cudaGetErrorString(cudaGetLastError())));
   *out = c;
   return HELM_OK;
@@ -518,11 +582,11 @@ int helm_destroy(helm_ctx* c) {
   else cudaDeviceSynchronize();
   free_workspaces(c);
   coarse_free(c->cs);
-  krylov_free(c->ks);
+  for (auto& k : c->ks) krylov_free(k);
   for (void* p : {(void*)c->d_gam, (void*)c->d_gam32, (void*)c->kap64, (void*)c->kap32, (void*)c->A2_64, (void*)c->A2_dinv64,
                   (void*)c->A2_32, (void*)c->A2_dinv32, (void*)c->Mk2, (void*)c->A3_64, (void*)c->A3_dinv64,
                   (void*)c->V, (void*)c->w, (void*)c->r, c->Z, (void*)c->stage, (void*)c->d_bad,
-                  (void*)c->cdf})
+                  (void*)c->cdf, (void*)c->d_scal, (void*)c->d_kpart, (void*)c->d_kcounter})
     cudaFree(p);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   delete[] c->h_gam;
@@ -554,11 +618,14 @@ int helm_solve(helm_ctx* c, const void* q, void* p, int n_rhs, double tol, int m
   }
   if (!pd) dp = sp;
   int worst = HELM_OK;
-  for (int r = 0; r < n_rhs; ++r) {
-    helm_stats one{};
-    if (int st = fgmres_one(c, dq + (size_t)r * n, dp + (size_t)r * n, tol, maxit, &one)) return st;
-    if (stats) stats[r] = one;
-    if (!one.converged) worst = HELM_NOT_CONVERGED;
+  std::vector<helm_stats> st_block(c->block);
+  for (int r0 = 0; r0 < n_rhs; r0 += c->block) {
+    const int B = std::min(c->block, n_rhs - r0);
+    if (int st = fgmres_block(c, dq + (size_t)r0 * n, dp + (size_t)r0 * n, B, tol, maxit, st_block.data())) return st;
+    for (int r = 0; r < B; ++r) {
+      if (stats) stats[r0 + r] = st_block[r];
+      if (!st_block[r].converged) worst = HELM_NOT_CONVERGED;
+    }
   }
   if (!pd) {
     HELM_CUDA_TRY(cudaMemcpyAsync(p, dp, n_rhs * n * sizeof(double2), cudaMemcpyDeviceToHost, c->s));
@@ -576,26 +643,31 @@ int helm_adjoint_grad(helm_ctx* c, const void* p, const void* resid, int n_rhs, 
     return fail(HELM_EINVAL, "helm_adjoint_grad takes device pointers");
   LaunchScope scope(c);
   const long long n = c->g[0].size;
-  // one right-hand side of conj(residual) and one adjoint field at a time
-  if (2 * n > c->stage_cap) {
+  // a block of conj(residual) right-hand sides and their adjoint fields at a time
+  const long long need = 2LL * c->block * n;
+  if (need > c->stage_cap) {
     cudaFree(c->stage);
     c->stage = nullptr;
     c->stage_cap = 0;
-    if (int st = dmalloc(&c->stage, 2 * n * sizeof(double2))) return st;
-    c->stage_cap = 2 * n;
+    if (int st = dmalloc(&c->stage, need * sizeof(double2))) return st;
+    c->stage_cap = need;
   }
   double2* rhs = c->stage;
-  double2* mu = c->stage + n;
+  double2* mu = c->stage + (size_t)c->block * n;
   int worst = HELM_OK;
-  for (int r = 0; r < n_rhs; ++r) {
-    const double2* pr = (const double2*)p + (size_t)r * n;
-    if (int st = launch_conj(n, (const double2*)resid + (size_t)r * n, rhs, c->s)) return st;
-    double2* m_out = adj ? (double2*)adj + (size_t)r * n : mu;
-    helm_stats one{};
-    if (int st = fgmres_one(c, rhs, m_out, tol, maxit, &one)) return st;
-    if (stats) stats[r] = one;
-    if (!one.converged) worst = HELM_NOT_CONVERGED;
-    if (int st = launch_gradient(c->fine, pr, m_out, grad, c->s)) return st;
+  std::vector<helm_stats> st_block(c->block);
+  for (int r0 = 0; r0 < n_rhs; r0 += c->block) {
+    const int B = std::min(c->block, n_rhs - r0);
+    if (int st = launch_conj((long long)B * n, (const double2*)resid + (size_t)r0 * n, rhs, c->s)) return st;
+    double2* m_out = adj ? (double2*)adj + (size_t)r0 * n : mu;
+    if (int st = fgmres_block(c, rhs, m_out, B, tol, maxit, st_block.data())) return st;
+    for (int r = 0; r < B; ++r) {
+      if (stats) stats[r0 + r] = st_block[r];
+      if (!st_block[r].converged) worst = HELM_NOT_CONVERGED;
+      // right-hand sides in order: the gradient sums over them deterministically
+      if (int st = launch_gradient(c->fine, (const double2*)p + (size_t)(r0 + r) * n, m_out + (size_t)r * n, grad, c->s))
+        return st;
+    }
   }
   HELM_CUDA_TRY(cudaStreamSynchronize(c->s));
   if (worst != HELM_OK) set_error("adjoint solve not converged within maxit");

@@ -405,8 +405,9 @@ int grid_blocks(long long n) {
 
 }  // namespace
 
-int krylov_alloc(KrylovState& st, int m) {
+int krylov_alloc(KrylovState& st, int m, double* scal, double2* part, unsigned* counter) {
   st.m = m;
+  st.owns_shared = false;
   HELM_CUDA_TRY(cudaMalloc(&st.H, sizeof(double2) * (m + 1) * m));
   HELM_CUDA_TRY(cudaMalloc(&st.g, sizeof(double2) * (m + 1)));
   HELM_CUDA_TRY(cudaMalloc(&st.sn, sizeof(double2) * m));
@@ -415,20 +416,20 @@ int krylov_alloc(KrylovState& st, int m) {
   HELM_CUDA_TRY(cudaMalloc(&st.h1, sizeof(double2) * (m + 2)));
   HELM_CUDA_TRY(cudaMalloc(&st.h2, sizeof(double2) * (m + 2)));
   HELM_CUDA_TRY(cudaMalloc(&st.red, sizeof(double2) * 4));
-  HELM_CUDA_TRY(cudaMalloc(&st.scal, sizeof(double) * KS_COUNT));
-  HELM_CUDA_TRY(cudaMalloc(&st.part, sizeof(double2) * 152 * 4 * (m + 2)));
-  HELM_CUDA_TRY(cudaMalloc(&st.counter, sizeof(unsigned)));
-  HELM_CUDA_TRY(cudaMemset(st.counter, 0, sizeof(unsigned)));
+  st.scal = scal;
+  st.part = part;
+  st.counter = counter;
   HELM_CUDA_TRY(cudaMemset(st.H, 0, sizeof(double2) * (m + 1) * m));
   return 0;
 }
 
 void krylov_free(KrylovState& st) {
   cudaFree(st.H); cudaFree(st.g); cudaFree(st.sn); cudaFree(st.cs); cudaFree(st.y);
-  cudaFree(st.h1); cudaFree(st.h2); cudaFree(st.red); cudaFree(st.scal); cudaFree(st.part);
-  cudaFree(st.counter);
+  cudaFree(st.h1); cudaFree(st.h2); cudaFree(st.red);
   st = KrylovState();
 }
+
+size_t krylov_part_entries(int m) { return (size_t)152 * 4 * (m + 2); }
 
 int k_norm(const KrylovState& st, long long n, const double2* b, double2* copy_to, cudaStream_t s) {
   const int bl = grid_blocks(n);

@@ -19,12 +19,17 @@ struct KrylovState {
   double2* h2 = nullptr;     // second pass (+ ||w||^2)
   double2* red = nullptr;    // reduction outputs
   double* scal = nullptr;    // KS_* scalars
-  double2* part = nullptr;   // per-block partial sums
+  double2* part = nullptr;   // per-block partial sums (shared by the states of a context)
   unsigned* counter = nullptr;
+  bool owns_shared = false;
 };
 
-int krylov_alloc(KrylovState& st, int m);
+// The small per-right-hand-side arrays; scal (KS_COUNT doubles), the partial-sum buffer
+// (krylov_part_entries(m) entries) and the zeroed counter are supplied by the caller:
+// the states of one context run on one stream, one after the other, and share them.
+int krylov_alloc(KrylovState& st, int m, double* scal, double2* part, unsigned* counter);
 void krylov_free(KrylovState& st);
+size_t krylov_part_entries(int m);
 
 // scal[KS_BNORM] = scal[KS_BETA] = ||b||; if copy_to, copy_to = b.
 int k_norm(const KrylovState& st, long long n, const double2* b, double2* copy_to, cudaStream_t s);
