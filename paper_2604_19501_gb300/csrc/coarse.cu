@@ -406,7 +406,7 @@ __device__ __forceinline__ void fwd_write(const FrontDesc& d, const int* __restr
 // r_S is assembled on the fly from b and the children's update vectors.  Fronts split
 // into several row chunks leave partial sums that the last block of the tile adds in
 // chunk order.
-template <bool DF>
+template <bool DF, int RG>
 __global__ void __launch_bounds__(kFwdCols) fwd_colsum_kernel(
     const FrontDesc* __restrict__ desc, const FwdJob* __restrict__ jobs, const int* __restrict__ Sidx,
     const int2* __restrict__ ctb, const double2* __restrict__ factors, const double2* __restrict__ b,
@@ -419,37 +419,61 @@ __global__ void __launch_bounds__(kFwdCols) fwd_colsum_kernel(
   const int nF = d.nS + d.nB;
   const int tid = threadIdx.x;
   const int t = job.tile * kFwdCols + tid;
-  const int s0 = job.s0, s1 = job.s1;
-  __shared__ double2 rs[kFwdMaxChunk];
-  __shared__ float4 rsd[kFwdMaxChunk];
+  const int s0 = job.s0, s1 = job.s1, nrow = s1 - s0;
+  // right-hand-side values of the chunk for a group of kRhsGroup right-hand sides
+  __shared__ double2 rs[kFwdMaxChunk][RG];
+  __shared__ float4 rsd[kFwdMaxChunk][RG];
   __shared__ bool s_last;
   pdl_wait();
-  for (int r = 0; r < nrhs; ++r) {
-    for (int q = tid; q < s1 - s0; q += blockDim.x) {
-      const double2 v = front_rhs(d, Sidx, ctb, b, uv, s0 + q, r, nodes, uv_total);
-      if (DF) rsd[q] = to_df(v);
-      else rs[q] = v;
+  for (int r0 = 0; r0 < nrhs; r0 += RG) {
+    const int nr = min(RG, nrhs - r0);
+    for (int q = tid; q < nrow * nr; q += blockDim.x) {
+      const int row = q / nr, rr = q % nr;
+      const double2 v = front_rhs(d, Sidx, ctb, b, uv, s0 + row, r0 + rr, nodes, uv_total);
+      if (DF) rsd[row][rr] = to_df(v);
+      else rs[row][rr] = v;
     }
     __syncthreads();
-    double2 acc = make_double2(0.0, 0.0);
-    float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // every factor entry is loaded once and applied to the whole group
+    double2 acc[RG];
+    float4 a4[RG];
+#pragma unroll
+    for (int rr = 0; rr < RG; ++rr) {
+      acc[rr] = make_double2(0.0, 0.0);
+      a4[rr] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     if (t < nF) {
       if (DF) {
         const float4* col = reinterpret_cast<const float4*>(factors + d.M_off) + (long long)s0 * nF + t;
 #pragma unroll 8
-        for (int s = 0; s < s1 - s0; ++s) df_cmac(a4, __ldcs(col + (long long)s * nF), rsd[s]);
+        for (int s = 0; s < nrow; ++s) {
+          const float4 m = __ldcs(col + (long long)s * nF);
+#pragma unroll
+          for (int rr = 0; rr < RG; ++rr)
+            if (RG == 1 || rr < nr) df_cmac(a4[rr], m, rsd[s][rr]);
+        }
       } else {
         const double2* col = factors + d.M_off + (long long)s0 * nF + t;
 #pragma unroll 8
-        for (int s = 0; s < s1 - s0; ++s) acc = cmac(acc, __ldcs(col + (long long)s * nF), rs[s]);
+        for (int s = 0; s < nrow; ++s) {
+          const double2 m = __ldcs(col + (long long)s * nF);
+#pragma unroll
+          for (int rr = 0; rr < RG; ++rr)
+            if (RG == 1 || rr < nr) acc[rr] = cmac(acc[rr], m, rs[s][rr]);
+        }
       }
     }
-    if (job.nchunks == 1) {
-      if (t < nF) fwd_write(d, Sidx, ctb, b, t, r, DF ? from_df(a4) : acc, uv, w, nodes, uv_total);
-    } else {
-      const long long pi = ((long long)(job.pbase + job.chunk) * nrhs + r) * kFwdCols + tid;
-      if (DF) reinterpret_cast<float4*>(part)[pi] = a4;
-      else part[pi] = acc;
+#pragma unroll
+    for (int rr = 0; rr < RG; ++rr) {
+      if (rr >= nr) break;
+      const int r = r0 + rr;
+      if (job.nchunks == 1) {
+        if (t < nF) fwd_write(d, Sidx, ctb, b, t, r, DF ? from_df(a4[rr]) : acc[rr], uv, w, nodes, uv_total);
+      } else {
+        const long long pi = ((long long)(job.pbase + job.chunk) * nrhs + r) * kFwdCols + tid;
+        if (DF) reinterpret_cast<float4*>(part)[pi] = a4[rr];
+        else part[pi] = acc[rr];
+      }
     }
     __syncthreads();
   }
@@ -479,10 +503,11 @@ __global__ void __launch_bounds__(kFwdCols) fwd_colsum_kernel(
 }
 
 // One warp per row of G: x_S[row] = w_S[row] - G[row, :] . x_B; a block handles a range
-// of rows of one front and first stages x_B in shared memory (as double-float with DF),
-// so the row loops stream G and read x_B without dependent gathers.  With DF
-// the factors are double-float and the sweep also writes the double-float copy xd of x.
-template <bool DF>
+// of rows of one front for a group of kRhsGroup right-hand sides.  x_B of the group is
+// first staged in shared memory (as double-float with DF) when it fits, so the row loops
+// stream G once for the whole group.  With DF the factors are double-float and the sweep
+// also writes the double-float copy xd of x.
+template <bool DF, int RG>
 __global__ void __launch_bounds__(512) bwd_matvec_kernel(const FrontDesc* __restrict__ desc,
                                                          const int4* __restrict__ rows,
                                                          const int* __restrict__ Sidx,
@@ -497,52 +522,69 @@ __global__ void __launch_bounds__(512) bwd_matvec_kernel(const FrontDesc* __rest
   const FrontDesc d = desc[job.x];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int* B = Bidx + d.B_off;
-  const bool staged = d.nB <= smem_cap;
   pdl_wait();
-  for (int r = 0; r < nrhs; ++r) {
+  for (int r0 = 0; r0 < nrhs; r0 += RG) {
+    const int nr = min(RG, nrhs - r0);
+    const bool staged = d.nB * nr <= smem_cap;
     if (staged) {
-      for (int c = threadIdx.x; c < d.nB; c += blockDim.x) {
-        if (DF) xs[c] = xd[r * nodes + B[c]];
-        else reinterpret_cast<double2*>(xs)[c] = x[r * nodes + B[c]];
+      for (int q = threadIdx.x; q < d.nB * nr; q += blockDim.x) {
+        const int rr = q / d.nB, c = q % d.nB;
+        const long long gi = (r0 + rr) * nodes + B[c];
+        if (DF) xs[rr * d.nB + c] = xd[gi];
+        else reinterpret_cast<double2*>(xs)[rr * d.nB + c] = x[gi];
       }
       __syncthreads();
     }
     for (int row = job.y + warp; row < job.z; row += nwarp) {
       const int node = Sidx[d.S_off + row];
-      double2 acc = make_double2(0.0, 0.0);
+      double2 acc[RG];
+      float4 a4[RG];
+#pragma unroll
+      for (int rr = 0; rr < RG; ++rr) {
+        acc[rr] = make_double2(0.0, 0.0);
+        a4[rr] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
       if (DF) {
         const float4* G = reinterpret_cast<const float4*>(factors + d.G_off) + (long long)row * d.g_ld;
-        float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (staged) {
 #pragma unroll 4
-          for (int c = lane; c < d.nB; c += 32) df_cmac(a4, __ldcs(G + c), xs[c]);
-        } else {
-          const float4* xr = xd + r * nodes;
-          for (int c = lane; c < d.nB; c += 32) df_cmac(a4, G[c], xr[B[c]]);
+        for (int c = lane; c < d.nB; c += 32) {
+          const float4 g = __ldcs(G + c);
+#pragma unroll
+          for (int rr = 0; rr < RG; ++rr)
+            if (RG == 1 || rr < nr) df_cmac(a4[rr], g, staged ? xs[rr * d.nB + c] : xd[(r0 + rr) * nodes + B[c]]);
         }
-        a4 = df_warp_sum(a4);
-        if (lane == 0) acc = from_df(a4);
       } else {
         const double2* G = factors + d.G_off + (long long)row * d.g_ld;
-        if (staged) {
-          const double2* xs2 = reinterpret_cast<const double2*>(xs);
+        const double2* xs2 = reinterpret_cast<const double2*>(xs);
 #pragma unroll 4
-          for (int c = lane; c < d.nB; c += 32) acc = cmac(acc, __ldcs(G + c), xs2[c]);
-        } else {
-          const double2* xr = x + r * nodes;
-          for (int c = lane; c < d.nB; c += 32) acc = cmac(acc, G[c], xr[B[c]]);
+        for (int c = lane; c < d.nB; c += 32) {
+          const double2 g = __ldcs(G + c);
+#pragma unroll
+          for (int rr = 0; rr < RG; ++rr)
+            if (RG == 1 || rr < nr) acc[rr] = cmac(acc[rr], g, staged ? xs2[rr * d.nB + c] : x[(r0 + rr) * nodes + B[c]]);
         }
       }
-      if (!DF)
-        for (int off = 16; off > 0; off >>= 1) {
-          acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
-          acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
+#pragma unroll
+      for (int rr = 0; rr < RG; ++rr) {
+        if (rr >= nr) break;
+        double2 v;
+        if (DF) {
+          const float4 sum = df_warp_sum(a4[rr]);
+          v = from_df(sum);
+        } else {
+          v = acc[rr];
+          for (int off = 16; off > 0; off >>= 1) {
+            v.x += __shfl_down_sync(0xffffffffu, v.x, off);
+            v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+          }
         }
-      if (lane == 0) {
-        const double2 wv = w[r * nodes + node];
-        const double2 xv = make_double2(wv.x - acc.x, wv.y - acc.y);
-        x[r * nodes + node] = xv;
-        if (DF) xd[r * nodes + node] = to_df(xv);
+        if (lane == 0) {
+          const long long gi = (r0 + rr) * nodes + node;
+          const double2 wv = w[gi];
+          const double2 xv = make_double2(wv.x - v.x, wv.y - v.y);
+          x[gi] = xv;
+          if (DF) xd[gi] = to_df(xv);
+        }
       }
     }
     if (staged) __syncthreads();
@@ -559,7 +601,7 @@ int upload(T** dst, const std::vector<T>& v) {
 
 constexpr int kRowsPerBlock = 16;  // warps per block in the backward sweep (minimum rows per block)
 constexpr int kTargetBlocks = 1024;   // blocks per tree level the sweeps aim for
-constexpr int kBwdSmemEntries = 3072;   // x_B entries staged in shared memory (48 KiB)
+constexpr int kBwdSmemEntries = 6144;   // x_B entries staged in shared memory (96 KiB)
 constexpr int kBigFront = 96;      // fronts with at least this many eliminated nodes use the grid-wide elimination
 
 }  // namespace
@@ -814,8 +856,19 @@ static int ensure_rhs(CoarseSolver& cs, int nrhs) {
 
 static int solve_sweeps(const CoarseSolver& cs, const double2* b, double2* e, int nrhs, double2* uv,
                         double2* w, double2* part, unsigned* counters, float4* xd, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    const int bytes = kBwdSmemEntries * (int)sizeof(float4);
+    cudaFuncSetAttribute(bwd_matvec_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(bwd_matvec_kernel<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(bwd_matvec_kernel<true, kRhsGroup>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(bwd_matvec_kernel<false, kRhsGroup>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    attr_set = true;
+  }
   for (int h = 0; h < cs.nlevels; ++h) {
-    const cudaError_t le = launch_pdl(cs.df ? fwd_colsum_kernel<true> : fwd_colsum_kernel<false>,
+    auto fk = nrhs == 1 ? (cs.df ? fwd_colsum_kernel<true, 1> : fwd_colsum_kernel<false, 1>)
+                        : (cs.df ? fwd_colsum_kernel<true, kRhsGroup> : fwd_colsum_kernel<false, kRhsGroup>);
+    const cudaError_t le = launch_pdl(fk,
                                       dim3(cs.n_fwd_jobs[h]), dim3(kFwdCols), 0, s, cs.d_desc, cs.d_fwd_jobs[h],
                                       cs.d_S, cs.d_ctb, cs.d_factors, b, uv, w, part, counters, nrhs, cs.g.size,
                                       cs.uv_total);
@@ -823,8 +876,11 @@ static int solve_sweeps(const CoarseSolver& cs, const double2* b, double2* e, in
     HELM_LAUNCH_CHECK();
   }
   for (int h = cs.nlevels - 1; h >= 0; --h) {
-    const size_t sm = (size_t)std::min(cs.max_nB, kBwdSmemEntries) * sizeof(float4);
-    const cudaError_t le = launch_pdl(cs.df ? bwd_matvec_kernel<true> : bwd_matvec_kernel<false>,
+    const size_t sm = (size_t)std::min((long long)cs.max_nB * std::min(nrhs, kRhsGroup), (long long)kBwdSmemEntries) *
+                      sizeof(float4);
+    auto bk = nrhs == 1 ? (cs.df ? bwd_matvec_kernel<true, 1> : bwd_matvec_kernel<false, 1>)
+                        : (cs.df ? bwd_matvec_kernel<true, kRhsGroup> : bwd_matvec_kernel<false, kRhsGroup>);
+    const cudaError_t le = launch_pdl(bk,
                                       dim3(cs.n_bwd_rows[h]), dim3(32 * kRowsPerBlock), sm, s, cs.d_desc,
                                       cs.d_bwd_rows[h], cs.d_S, cs.d_B, cs.d_factors, w, e, xd, nrhs, cs.g.size,
                                       kBwdSmemEntries);

@@ -8,7 +8,8 @@ namespace helm {
 
 constexpr int kFwdCols = 256;    // columns per block of the forward sweep
 constexpr int kFwdMinChunk = 16;   // rows per partial sum of the forward sweep: at least ...
-constexpr int kFwdMaxChunk = 256;  // ... and at most
+constexpr int kFwdMaxChunk = 128;  // ... and at most
+constexpr int kRhsGroup = 4;       // right-hand sides sharing each factor load in the sweeps
 
 struct FrontDesc {
   int nS, nB;             // eliminated (separator / leaf) nodes, boundary (ancestor) nodes
