@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mdof*solves/s to 1e-6 rel-res"
 UNIT = "Mdof*solves/s"
-FP64_PEAK_TFLOPS = 1.26   # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz (see DESIGN.md)
+FP64_PEAK_TFLOPS = 1.26   # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
 
 
 def parse():
@@ -279,14 +279,14 @@ def reference_arm(args):
 def kernel_model(info, its, restart, n1, n3):
     """Algorithmic bytes and flops per launch of the timed kernel classes.
 
-    coarse: the forward sweep reads every factor entry, the backward sweep the G blocks
-    again (16 B per complex entry, FP64 or double-float), plus the vectors (b, w, x and
+    coarse: the forward sweep reads M and the backward sweep G^T, every stored factor
+    entry once (16 B per complex entry, FP64 or double-float), plus the vectors (b, w, x and
     the update vectors, about 6 x 16 B per coarsest node).  Arnoldi kernels: one complex
     value of 16 B per basis vector and node, plus w, z and the coefficient."""
     nv_avg = sum((i % restart) + 1 for i in range(its)) / its
-    cb = 16.0 * (info["coarse_entries"] + info["coarse_bwd_entries"]) + 6 * 16.0 * n3
+    cb = 16.0 * info["coarse_entries"] + 6 * 16.0 * n3
     return {
-        "coarse": {"flops": 8.0 * (info["coarse_entries"] + info["coarse_bwd_entries"]), "bytes": cb},
+        "coarse": {"flops": 8.0 * info["coarse_entries"], "bytes": cb},
         "arnoldi_update": {"flops": 8.0 * 2 * nv_avg * n1, "bytes": (32.0 + 16.0 * nv_avg) * n1},
         "arnoldi_norm": {"flops": 8.0 * nv_avg * n1, "bytes": (32.0 + 16.0 * nv_avg) * n1},
         "arnoldi_matvec": {"flops": (8.0 * nv_avg + 40.0) * n1, "bytes": (40.0 + 16.0 * nv_avg) * n1},
@@ -389,7 +389,7 @@ def our_arm(args):
             roof = {"kernel": dom, "bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": fl / FP64_PEAK_TFLOPS, "traffic": None,
                     "algorithmic_bytes_per_launch": model[dom]["bytes"], "launches_timed": cnt,
-                    "peak_note": "FP64 ALU peak derived from unit counts and clock (DESIGN.md)"}
+                    "peak_note": "FP64 ALU peak: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz"}
 
     # ---- CPU oracle on a bounded sample
     cpu = None

@@ -182,14 +182,29 @@ int helm_coarse_solve(helm_ctx* c, const void* b, void* e, int n_rhs);
  * complex FP64 entries (16 MiB), which every GPU that loads the library holds
  * until the process exits.  A solve needs, per right-hand side, the update
  * vectors of all nested-dissection fronts, two vectors over the coarsest nodes
- * and the forward sweep's partial sums, plus one counter per split column
- * tile; larger requests return HELM_EINVAL and do nothing.  The first call on a device looks up the array's
+ * and the solve's partial sums, plus completion counters (two per front, one per
+ * output split across jobs); larger requests return HELM_EINVAL and do nothing.  The first call on a device looks up the array's
  * device address with that device current; later calls reuse it.  All calls
  * share the array: calls that may overlap on the GPU (two streams, two
  * contexts, two threads) race and corrupt each other's results, so serialise
  * them.  Nothing in the array needs to start at zero: every entry a call reads
  * is written earlier in the same call.  b, e: c128 device pointers. */
 int helm_coarse_solve_noalloc(helm_ctx* c, const void* b, void* e, int n_rhs);
+
+/* Plan of the coarsest-level direct solve, computed on the host only (no GPU and no
+ * context needed), as helm_setup builds it for a level-3 grid of n_nodes[0..dim-1]
+ * nodes and a stencil of radius `radius`: the nested-dissection tree (leaf boxes of at
+ * most leaf_max nodes; helm_setup uses 64), the front matrices, and the job list of the
+ * persistent solve kernel for `grid` resident blocks.  symmetric = 1 for a
+ * complex-symmetric operator (full-weighting or cubic transfers on both levels).
+ * The plan is checked against every extent the solve kernel indexes and for the job
+ * order its schedule needs; HELM_EINVAL (message in helm_last_error) if a check fails.
+ * stats (8 entries, caller-owned host memory): fronts, tree levels, jobs, factor
+ * entries, backward-sweep entries, partial-sum blocks, split outputs, largest boundary.
+ * Sec. 2 and 3.1 fix only that the coarsest level is solved exactly; the paper has no
+ * counterpart of the plan itself. */
+int helm_coarse_plan(int dim, const int n_nodes[3], int radius, int leaf_max, int symmetric, int grid,
+                     long long stats[8]);
 
 /* z = M^-1 v: one application of the 3-level cycle from a zero initial guess,
  * v and z in c128 (the mixed precision mode computes levels 1-2 in c64). */
@@ -205,7 +220,7 @@ typedef enum {
   HELM_INFO_NODES3 = 2,              /* nodes of level 3 (coarsest) */
   HELM_INFO_RADIUS2 = 3,             /* stencil radius of the level-2 operator */
   HELM_INFO_RADIUS3 = 4,             /* stencil radius of the level-3 operator */
-  HELM_INFO_COARSE_ENTRIES = 5,      /* complex entries of the coarsest factors read per solve */
+  HELM_INFO_COARSE_ENTRIES = 5,      /* complex entries of the coarsest factors (M and G^T), each read once per solve */
   HELM_INFO_COARSE_FRONTS = 6,       /* fronts of the nested-dissection tree */
   HELM_INFO_COARSE_LEVELS = 7,       /* levels of the nested-dissection tree */
   HELM_INFO_COARSE_BWD_ENTRIES = 8,  /* complex entries the backward sweep reads per solve */

@@ -11,7 +11,7 @@ import ctypes
 from . import _ffi
 from ._ffi import HelmError, HelmOpts, HelmStats, check
 
-__all__ = ["Solver", "HelmError", "level_shape", "helmholtz_solve"]
+__all__ = ["Solver", "HelmError", "level_shape", "helmholtz_solve", "coarse_plan"]
 
 _lib = _ffi.load()
 
@@ -208,6 +208,22 @@ class Solver:
         z = _empty_like(v) if z is None else z
         check(_lib.helm_cycle(self._ctx, _ptr(v), _ptr(z), self._nrhs(v)), "helm_cycle")
         return z
+
+
+PLAN_KEYS = ("fronts", "levels", "jobs", "factor_entries", "bwd_entries", "part_blocks", "split_outputs",
+             "max_boundary")
+
+
+def coarse_plan(n_nodes, radius, leaf_max=64, symmetric=True, grid=304):
+    """Host-only plan of the coarsest-level direct solve (helm_coarse_plan): the
+    nested-dissection tree and the solve kernel's job list for a level-3 grid of
+    ``n_nodes`` nodes per axis (x first), checked against the kernel's extents."""
+    dim = len(n_nodes)
+    nn = (ctypes.c_int * 3)(*(list(n_nodes) + [1] * (3 - dim)))
+    st = (ctypes.c_longlong * 8)()
+    check(_lib.helm_coarse_plan(dim, nn, int(radius), int(leaf_max), int(bool(symmetric)), int(grid), st),
+          "helm_coarse_plan")
+    return dict(zip(PLAN_KEYS, list(st)))
 
 
 def _numel(shape):

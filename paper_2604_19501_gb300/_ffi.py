@@ -72,6 +72,7 @@ SIGNATURES = {
     "helm_coarse_solve": (_I, [_P, _P, _P, _I]),
     "helm_coarse_solve_noalloc": (_I, [_P, _P, _P, _I]),
     "helm_cycle": (_I, [_P, _P, _P, _I]),
+    "helm_coarse_plan": (_I, [_I, ctypes.POINTER(_I), _I, _I, _I, _I, ctypes.POINTER(ctypes.c_longlong)]),
     "helm_launch_count": (ctypes.c_longlong, [_P]),
     "helm_info": (_I, [_P, _I, ctypes.POINTER(ctypes.c_longlong)]),
     "helm_timer_enable": (_I, [_P, ctypes.c_uint]),

@@ -363,7 +363,7 @@ int fgmres_block(helm_ctx* c, const double2* q, double2* p, int B, double tol, i
     }
     if (out) out[r] = res;
   }
-  return 0;
+  return coarse_status(c->cs, c->s);
 }
 
 int check_level(const helm_ctx* c, int level, int lo, int hi) {
@@ -741,6 +741,7 @@ int helm_coarse_solve(helm_ctx* c, const void* b, void* e, int n_rhs) {
   if (!c || !b || !e || n_rhs < 1) return fail(HELM_EINVAL, "bad argument");
   LaunchScope scope(c);
   if (int st = coarse_solve(c->cs, (const double2*)b, (double2*)e, n_rhs, c->s)) return st;
+  if (int st = coarse_status(c->cs, c->s)) return st;
   return HELM_OK;
 }
 
@@ -748,6 +749,7 @@ int helm_coarse_solve_noalloc(helm_ctx* c, const void* b, void* e, int n_rhs) {
   if (!c || !b || !e || n_rhs < 1) return fail(HELM_EINVAL, "bad argument");
   LaunchScope scope(c);
   if (int st = coarse_solve_noalloc(c->cs, (const double2*)b, (double2*)e, n_rhs, c->s)) return st;
+  if (int st = coarse_status(c->cs, c->s)) return st;
   return HELM_OK;
 }
 
@@ -755,6 +757,27 @@ int helm_cycle(helm_ctx* c, const void* v, void* z, int n_rhs) {
   if (!c || !v || !z || n_rhs < 1) return fail(HELM_EINVAL, "bad argument");
   LaunchScope scope(c);
   if (int st = run_cycle(c, v, P64, z, P64, n_rhs)) return st;
+  if (int st = coarse_status(c->cs, c->s)) return st;
+  return HELM_OK;
+}
+
+int helm_coarse_plan(int dim, const int n_nodes[3], int radius, int leaf_max, int symmetric, int grid,
+                     long long stats[8]) {
+  if (!n_nodes || !stats) return fail(HELM_EINVAL, "null argument");
+  if ((dim != 2 && dim != 3) || radius < 1 || radius > 3 || leaf_max < 1 || grid < 1)
+    return fail(HELM_EINVAL, "bad dim, radius, leaf_max or grid");
+  GridDims g{};
+  g.dim = dim;
+  long long size = 1;
+  for (int d = 0; d < 3; ++d) {
+    g.N[d] = d < dim ? n_nodes[d] : 1;
+    if (g.N[d] < 1) return fail(HELM_EINVAL, "bad node count");
+    size *= g.N[d];
+  }
+  if (size >= (1LL << 31)) return fail(HELM_EINVAL, "grid too large");
+  g.size = size;
+  finish_dims(g);
+  if (int st = coarse_plan_stats(g, radius, leaf_max, symmetric != 0, grid, stats)) return st;
   return HELM_OK;
 }
 

@@ -18,16 +18,17 @@
 //
 // Stored per front: M = [F_SS^-1 | F_SS^-1 F_SB] (|S| x |F|) when the coarsest operator is
 // complex-symmetric (full-weighting or cubic transfers on both levels), since then
-// F_BS F_SS^-1 = (F_SS^-1 F_SB)^T; otherwise M = [F_SS^-1 | -F_BS F_SS^-1]^T plus
-// G = F_SS^-1 F_SB.  Small fronts are eliminated by one thread block each; large fronts by
-// a pair of grid-wide kernels per pivot (pivot search + row swap/scale, elimination).
+// F_BS F_SS^-1 = (F_SS^-1 F_SB)^T; otherwise M = [F_SS^-1 | -F_BS F_SS^-1]^T.  Both cases
+// also keep G^T = (F_SS^-1 F_SB)^T (|B| x |S|).  Small fronts are eliminated by one thread
+// block each; large fronts by a pair of grid-wide kernels per pivot (pivot search + row
+// swap/scale, elimination).
 //
-// Solve: forward, leaves to root, every front turns its assembled right-hand side r_F
-// into w_S = F_SS^-1 r_S and the update vector r_B - F_BS F_SS^-1 r_S for its parent:
-// column sums over M, split into row chunks whose partial sums the last block of a column
-// tile adds in chunk order.  Backward, root to leaves, x_S = w_S - (F_SS^-1 F_SB) x_B
-// (row dot products).  The summation order is fixed, so results are reproducible bit
-// for bit.
+// Solve (coarse_sweep.cu): forward, leaves to root, every front turns its assembled
+// right-hand side r_F into w_S = F_SS^-1 r_S and the update vector r_B - F_BS F_SS^-1 r_S
+// for its parent, as column sums over M.  Backward, root to leaves,
+// x_S = w_S - (F_SS^-1 F_SB) x_B, as column sums over G^T.  Both are split into row chunks
+// whose partial sums the last job of a column tile adds in chunk order: the summation
+// order is fixed, so results are reproducible bit for bit.
 #include <algorithm>
 #include <mutex>
 #include <unordered_map>
@@ -354,12 +355,11 @@ __global__ void fact_extract_kernel(const FrontDesc* __restrict__ desc, const in
     else               // X^T, X = [F_SS^-1 ; -F_BS F_SS^-1]
       store_factor(M, t, A[(long long)col * ld + nF + row], df);
   }
-  if (d.bsign > 0) {
-    double2* G = factors + d.G_off;
-    for (long long t = threadIdx.x; t < (long long)nS * nB; t += blockDim.x) {
-      const int row = (int)(t / nB), col = (int)(t % nB);
-      store_factor(G, t, A[(long long)row * ld + nS + col], df);
-    }
+  // G^T = (F_SS^-1 F_SB)^T, [nB][nS], read by the backward sweep as column sums
+  double2* GT = factors + d.G_off;
+  for (long long t = threadIdx.x; t < (long long)nS * nB; t += blockDim.x) {
+    const int c = (int)(t / nS), row = (int)(t % nS);
+    store_factor(GT, t, A[(long long)row * ld + nS + c], df);
   }
   for (long long t = threadIdx.x; t < (long long)nB * nB; t += blockDim.x) {
     const int row = (int)(t / nB), col = (int)(t % nB);
@@ -367,229 +367,16 @@ __global__ void fact_extract_kernel(const FrontDesc* __restrict__ desc, const in
   }
 }
 
-// ------------------------------------------------------------------ solve kernels
-// Right-hand side of front position t: b at the eliminated nodes plus the entries of the
-// children's update vectors that map to t (at most one per child), added in child order.
-__device__ __forceinline__ double2 front_rhs(const FrontDesc& d, const int* __restrict__ Sidx,
-                                             const int2* __restrict__ ctb, const double2* __restrict__ b,
-                                             const double2* __restrict__ uv, int t, int r, long long nodes,
-                                             long long uv_total) {
-  double2 v = t < d.nS ? b[r * nodes + Sidx[d.S_off + t]] : make_double2(0.0, 0.0);
-  const int2 c = ctb[d.ctb_off + t];
-  if (c.x >= 0) {
-    const double2 u = uv[r * uv_total + c.x];
-    v.x += u.x;
-    v.y += u.y;
-  }
-  if (c.y >= 0) {
-    const double2 u = uv[r * uv_total + c.y];
-    v.x += u.x;
-    v.y += u.y;
-  }
-  return v;
-}
-
-// out_t < nS: w at node S[t]; t >= nS: the update vector r_B + bsign * out.
-__device__ __forceinline__ void fwd_write(const FrontDesc& d, const int* __restrict__ Sidx,
-                                          const int2* __restrict__ ctb, const double2* __restrict__ b, int t,
-                                          int r, double2 v, double2* __restrict__ uv, double2* __restrict__ w,
-                                          long long nodes, long long uv_total) {
-  if (t < d.nS) {
-    w[r * nodes + Sidx[d.S_off + t]] = v;
-  } else {
-    const double2 rb = front_rhs(d, Sidx, ctb, b, uv, t, r, nodes, uv_total);
-    uv[r * uv_total + d.uv_off + t - d.nS] = make_double2(rb.x + d.bsign * v.x, rb.y + d.bsign * v.y);
-  }
-}
-
-// Forward sweep of one level: out_t = sum_{s in [s0, s1)} M[s][t] r_S[s] for one column tile;
-// r_S is assembled on the fly from b and the children's update vectors.  Fronts split
-// into several row chunks leave partial sums that the last block of the tile adds in
-// chunk order.
-template <bool DF, int RG>
-__global__ void __launch_bounds__(kFwdCols) fwd_colsum_kernel(
-    const FrontDesc* __restrict__ desc, const FwdJob* __restrict__ jobs, const int* __restrict__ Sidx,
-    const int2* __restrict__ ctb, const double2* __restrict__ factors, const double2* __restrict__ b,
-    double2* __restrict__ uv, double2* __restrict__ w, double2* __restrict__ part,
-    unsigned* __restrict__ counters, int nrhs, long long nodes, long long uv_total) {
-  pdl_trigger();
-  // job lists, fronts and factors are written at set-up: read before the wait
-  const FwdJob job = jobs[blockIdx.x];
-  const FrontDesc d = desc[job.front];
-  const int nF = d.nS + d.nB;
-  const int tid = threadIdx.x;
-  const int t = job.tile * kFwdCols + tid;
-  const int s0 = job.s0, s1 = job.s1, nrow = s1 - s0;
-  // right-hand-side values of the chunk for a group of kRhsGroup right-hand sides
-  __shared__ double2 rs[kFwdMaxChunk][RG];
-  __shared__ float4 rsd[kFwdMaxChunk][RG];
-  __shared__ bool s_last;
-  pdl_wait();
-  for (int r0 = 0; r0 < nrhs; r0 += RG) {
-    const int nr = min(RG, nrhs - r0);
-    for (int q = tid; q < nrow * nr; q += blockDim.x) {
-      const int row = q / nr, rr = q % nr;
-      const double2 v = front_rhs(d, Sidx, ctb, b, uv, s0 + row, r0 + rr, nodes, uv_total);
-      if (DF) rsd[row][rr] = to_df(v);
-      else rs[row][rr] = v;
-    }
-    __syncthreads();
-    // every factor entry is loaded once and applied to the whole group
-    double2 acc[RG];
-    float4 a4[RG];
-#pragma unroll
-    for (int rr = 0; rr < RG; ++rr) {
-      acc[rr] = make_double2(0.0, 0.0);
-      a4[rr] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    if (t < nF) {
-      if (DF) {
-        const float4* col = reinterpret_cast<const float4*>(factors + d.M_off) + (long long)s0 * nF + t;
-#pragma unroll 8
-        for (int s = 0; s < nrow; ++s) {
-          const float4 m = __ldcs(col + (long long)s * nF);
-#pragma unroll
-          for (int rr = 0; rr < RG; ++rr)
-            if (RG == 1 || rr < nr) df_cmac(a4[rr], m, rsd[s][rr]);
-        }
-      } else {
-        const double2* col = factors + d.M_off + (long long)s0 * nF + t;
-#pragma unroll 8
-        for (int s = 0; s < nrow; ++s) {
-          const double2 m = __ldcs(col + (long long)s * nF);
-#pragma unroll
-          for (int rr = 0; rr < RG; ++rr)
-            if (RG == 1 || rr < nr) acc[rr] = cmac(acc[rr], m, rs[s][rr]);
-        }
-      }
-    }
-#pragma unroll
-    for (int rr = 0; rr < RG; ++rr) {
-      if (rr >= nr) break;
-      const int r = r0 + rr;
-      if (job.nchunks == 1) {
-        if (t < nF) fwd_write(d, Sidx, ctb, b, t, r, DF ? from_df(a4[rr]) : acc[rr], uv, w, nodes, uv_total);
-      } else {
-        const long long pi = ((long long)(job.pbase + job.chunk) * nrhs + r) * kFwdCols + tid;
-        if (DF) reinterpret_cast<float4*>(part)[pi] = a4[rr];
-        else part[pi] = acc[rr];
-      }
-    }
-    __syncthreads();
-  }
-  if (job.nchunks == 1) return;
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) s_last = (atomicAdd(&counters[job.slot], 1u) == (unsigned)job.nchunks - 1);
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  for (int r = 0; r < nrhs; ++r) {
-    double2 acc = make_double2(0.0, 0.0);
-    float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int q = 0; q < job.nchunks; ++q) {
-      const long long pi = ((long long)(job.pbase + q) * nrhs + r) * kFwdCols + tid;
-      if (DF) {
-        df_acc_add(a4, __ldcg(reinterpret_cast<const float4*>(part) + pi));
-      } else {
-        const double2 v = __ldcg(part + pi);
-        acc.x += v.x;
-        acc.y += v.y;
-      }
-    }
-    if (t < nF) fwd_write(d, Sidx, ctb, b, t, r, DF ? from_df(a4) : acc, uv, w, nodes, uv_total);
-  }
-  if (tid == 0) counters[job.slot] = 0u;
-}
-
-// One warp per row of G: x_S[row] = w_S[row] - G[row, :] . x_B; a block handles a range
-// of rows of one front for a group of kRhsGroup right-hand sides.  x_B of the group is
-// first staged in shared memory (as double-float with DF) when it fits, so the row loops
-// stream G once for the whole group.  With DF the factors are double-float and the sweep
-// also writes the double-float copy xd of x.
-template <bool DF, int RG>
-__global__ void __launch_bounds__(512) bwd_matvec_kernel(const FrontDesc* __restrict__ desc,
-                                                         const int4* __restrict__ rows,
-                                                         const int* __restrict__ Sidx,
-                                                         const int* __restrict__ Bidx,
-                                                         const double2* __restrict__ factors,
-                                                         const double2* __restrict__ w,
-                                                         double2* __restrict__ x, float4* __restrict__ xd,
-                                                         int nrhs, long long nodes, int smem_cap) {
-  extern __shared__ float4 xs[];
-  pdl_trigger();
-  const int4 job = rows[blockIdx.x];
-  const FrontDesc d = desc[job.x];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const int* B = Bidx + d.B_off;
-  pdl_wait();
-  for (int r0 = 0; r0 < nrhs; r0 += RG) {
-    const int nr = min(RG, nrhs - r0);
-    const bool staged = d.nB * nr <= smem_cap;
-    if (staged) {
-      for (int q = threadIdx.x; q < d.nB * nr; q += blockDim.x) {
-        const int rr = q / d.nB, c = q % d.nB;
-        const long long gi = (r0 + rr) * nodes + B[c];
-        if (DF) xs[rr * d.nB + c] = xd[gi];
-        else reinterpret_cast<double2*>(xs)[rr * d.nB + c] = x[gi];
-      }
-      __syncthreads();
-    }
-    for (int row = job.y + warp; row < job.z; row += nwarp) {
-      const int node = Sidx[d.S_off + row];
-      double2 acc[RG];
-      float4 a4[RG];
-#pragma unroll
-      for (int rr = 0; rr < RG; ++rr) {
-        acc[rr] = make_double2(0.0, 0.0);
-        a4[rr] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-      if (DF) {
-        const float4* G = reinterpret_cast<const float4*>(factors + d.G_off) + (long long)row * d.g_ld;
-#pragma unroll 4
-        for (int c = lane; c < d.nB; c += 32) {
-          const float4 g = __ldcs(G + c);
-#pragma unroll
-          for (int rr = 0; rr < RG; ++rr)
-            if (RG == 1 || rr < nr) df_cmac(a4[rr], g, staged ? xs[rr * d.nB + c] : xd[(r0 + rr) * nodes + B[c]]);
-        }
-      } else {
-        const double2* G = factors + d.G_off + (long long)row * d.g_ld;
-        const double2* xs2 = reinterpret_cast<const double2*>(xs);
-#pragma unroll 4
-        for (int c = lane; c < d.nB; c += 32) {
-          const double2 g = __ldcs(G + c);
-#pragma unroll
-          for (int rr = 0; rr < RG; ++rr)
-            if (RG == 1 || rr < nr) acc[rr] = cmac(acc[rr], g, staged ? xs2[rr * d.nB + c] : x[(r0 + rr) * nodes + B[c]]);
-        }
-      }
-#pragma unroll
-      for (int rr = 0; rr < RG; ++rr) {
-        if (rr >= nr) break;
-        double2 v;
-        if (DF) {
-          const float4 sum = df_warp_sum(a4[rr]);
-          v = from_df(sum);
-        } else {
-          v = acc[rr];
-          for (int off = 16; off > 0; off >>= 1) {
-            v.x += __shfl_down_sync(0xffffffffu, v.x, off);
-            v.y += __shfl_down_sync(0xffffffffu, v.y, off);
-          }
-        }
-        if (lane == 0) {
-          const long long gi = (r0 + rr) * nodes + node;
-          const double2 wv = w[gi];
-          const double2 xv = make_double2(wv.x - v.x, wv.y - v.y);
-          x[gi] = xv;
-          if (DF) xd[gi] = to_df(xv);
-        }
-      }
-    }
-    if (staged) __syncthreads();
-  }
-}
+// Host side of the set-up: the nested-dissection tree, the front descriptors and the solve
+// job list (no device work).
+struct CoarsePlan {
+  std::vector<FrontDesc> desc;
+  std::vector<int> Sall, Ball, kids, cmap;
+  std::vector<int2> ents, ctb;
+  std::vector<std::vector<int>> bigs, smalls;
+  std::vector<SweepJob> jobs;
+  long long aug_max = 0, upool = 0;
+};
 
 template <typename T>
 int upload(T** dst, const std::vector<T>& v) {
@@ -599,18 +386,82 @@ int upload(T** dst, const std::vector<T>& v) {
   return 0;
 }
 
-constexpr int kRowsPerBlock = 16;  // warps per block in the backward sweep (minimum rows per block)
-constexpr int kTargetBlocks = 1024;   // blocks per tree level the sweeps aim for
-constexpr int kBwdSmemEntries = 6144;   // x_B entries staged in shared memory (96 KiB)
+constexpr int kJobsPerBlockLevel = 1;   // solve jobs per resident block and tree level aimed for
 constexpr int kBigFront = 96;      // fronts with at least this many eliminated nodes use the grid-wide elimination
 
 }  // namespace
 
-int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef, int leaf_max,
-                 bool symmetric, bool df, cudaStream_t s) {
+// Host check of the solve plan against the extents the solve kernel indexes: every job's
+// factor rows and columns inside the factor pool, at most one stage of shared memory per
+// fill, partial blocks and slots inside their buffers, and every dependency of a job
+// listed before it (the condition under which the persistent schedule cannot deadlock).
+static int validate_plan(const CoarseSolver& cs, const CoarsePlan& P) {
+  auto bad = [](const std::string& m) {
+    set_error("coarsest solve plan: " + m);
+    return HELM_EINVAL;
+  };
+  const auto& D = P.desc;
+  std::vector<long long> first_fwd(cs.nfronts, -1), last_fwd(cs.nfronts, -1), first_bwd(cs.nfronts, -1),
+      last_bwd(cs.nfronts, -1);
+  std::vector<int> fwd_units_seen(cs.nfronts, 0), bwd_units_seen(cs.nfronts, 0);
+  for (size_t j = 0; j < P.jobs.size(); ++j) {
+    const SweepJob& J = P.jobs[j];
+    if (J.front < 0 || J.front >= cs.nfronts) return bad("front index");
+    const FrontDesc& d = D[J.front];
+    const int rows = J.r1 - J.r0, cols = J.c1 - J.c0;
+    if (J.nchunks < 1 || J.chunk < 0 || J.chunk >= J.nchunks) return bad("job chunks");
+    if (J.nchunks > 1 && (J.slot < 0 || J.slot >= cs.n_slots || J.pbase < 0 || J.pbase + J.nchunks > cs.part_blocks))
+      return bad("partial slot");
+    if (J.kind != 0 && J.kind != 1) return bad("job kind");
+    // forward: M [nS][nF]; backward: G^T [nB][nS]
+    const int nrows = J.kind == 0 ? d.nS : d.nB, ncols = J.kind == 0 ? d.nS + d.nB : d.nS;
+    const long long off = J.kind == 0 ? d.M_off : d.G_off;
+    if (J.kind == 1 && d.g_ld != d.nS) return bad("backward stride");
+    if (J.c0 < 0 || cols < 1 || J.c1 > ncols || cols > kTile || cols > kPartBlock) return bad("job columns");
+    if (nrows == 0) {
+      if (J.kind != 1 || J.r0 != 0 || J.r1 != 0 || J.srows != 0 || J.nchunks != 1) return bad("empty job");
+    } else {
+      if (J.r0 < 0 || rows < 1 || J.r1 > nrows || rows > kJobRows) return bad("job rows");
+      if (J.srows < 1 || (long long)J.srows * cols > kStageEntries) return bad("job stage");
+      if (off + (long long)(J.r1 - 1) * ncols + J.c1 > cs.factor_entries) return bad("factor extent");
+    }
+    auto& first = J.kind == 0 ? first_fwd : first_bwd;
+    auto& last = J.kind == 0 ? last_fwd : last_bwd;
+    auto& units = J.kind == 0 ? fwd_units_seen : bwd_units_seen;
+    if (first[J.front] < 0) first[J.front] = (long long)j;
+    last[J.front] = (long long)j;
+    if (J.chunk == 0) ++units[J.front];
+  }
+  for (int f = 0; f < cs.nfronts; ++f) {
+    const FrontDesc& d = D[f];
+    if (first_fwd[f] < 0 || first_bwd[f] < 0) return bad("front without jobs");
+    if (fwd_units_seen[f] != d.fwd_units || bwd_units_seen[f] != d.bwd_units) return bad("unit counts");
+    for (int q = 0; q < d.nkids; ++q)
+      if (last_fwd[P.kids[d.kid_off + q]] >= first_fwd[f]) return bad("forward dependency order");
+    if (d.parent < 0) {
+      if (last_fwd[f] >= first_bwd[f]) return bad("root dependency order");
+    } else if (last_bwd[d.parent] >= first_bwd[f]) {
+      return bad("backward dependency order");
+    }
+  }
+  return 0;
+}
+
+int coarse_plan(CoarseSolver& cs, CoarsePlan& P, const GridDims& g, int r, int leaf_max, bool symmetric,
+                int grid) {
   cs.g = g;
   cs.r = r;
-  cs.df = df;
+  cs.grid = grid;
+  auto& desc = P.desc;
+  auto& Sall = P.Sall;
+  auto& Ball = P.Ball;
+  auto& kids = P.kids;
+  auto& cmap = P.cmap;
+  auto& ents = P.ents;
+  auto& ctb = P.ctb;
+  auto& bigs = P.bigs;
+  auto& smalls = P.smalls;
+  auto& jobs = P.jobs;
   Builder bld;
   bld.dim = g.dim;
   for (int d = 0; d < 3; ++d) bld.N[d] = g.N[d];
@@ -627,9 +478,7 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
   for (int i = 0; i < cs.nfronts; ++i) cs.level_fronts[F[i].height].push_back(i);
 
   const int W = 2 * r + 1;
-  std::vector<FrontDesc> desc(cs.nfronts);
-  std::vector<int> Sall, Ball, kids, cmap;
-  std::vector<int2> ents;
+  desc.assign(cs.nfronts, FrontDesc{});
   long long xg = 0, uoff = 0, rfo = 0, uvo = 0;
   for (int i = 0; i < cs.nfronts; ++i) {
     HostFront& f = F[i];
@@ -644,14 +493,9 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
     d.bsign = symmetric ? -1 : 1;
     d.M_off = xg;
     xg += (long long)nF * d.nS;
-    if (symmetric) {
-      d.G_off = d.M_off + d.nS;
-      d.g_ld = nF;
-    } else {
-      d.G_off = xg;
-      d.g_ld = d.nB;
-      xg += (long long)d.nS * d.nB;
-    }
+    d.G_off = xg;       // G^T [nB][nS]
+    d.g_ld = d.nS;
+    xg += (long long)d.nS * d.nB;
     d.U_off = uoff;
     uoff += (long long)d.nB * d.nB;
     d.ctb_off = rfo;
@@ -660,6 +504,7 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
     uvo += d.nB;
     d.kid_off = (int)kids.size();
     d.nkids = (int)f.kids.size();
+    d.parent = f.parent;
     kids.insert(kids.end(), f.kids.begin(), f.kids.end());
   }
   // child maps and original entries need the position of a node inside a front
@@ -674,7 +519,7 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
       desc[k].cmap_off = (int)cmap.size();
       for (int node : F[k].B) {
         auto it = pos.find(node);
-        if (it == pos.end()) { set_error("nested dissection: child boundary outside parent front"); return HELM_ECUDA; }
+        if (it == pos.end()) { set_error("nested dissection: child boundary outside parent front"); return HELM_EINVAL; }
         cmap.push_back(it->second);
       }
     }
@@ -707,7 +552,7 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
   for (auto& d : desc) cs.max_nB = std::max(cs.max_nB, d.nB);
   cs.uv_total = uvo;
   // for every front position, the update-vector entries of the children that map to it
-  std::vector<int2> ctb(rfo, make_int2(-1, -1));
+  ctb.assign(rfo, make_int2(-1, -1));
   for (int i = 0; i < cs.nfronts; ++i) {
     const FrontDesc& d = desc[i];
     for (int c = 0; c < d.nkids; ++c) {
@@ -717,73 +562,132 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
         const int src = (int)(kd.uv_off + a);
         if (c == 0) slot.x = src;
         else if (c == 1) slot.y = src;
-        else { set_error("nested dissection: more than two children"); return HELM_ECUDA; }
+        else { set_error("nested dissection: more than two children"); return HELM_EINVAL; }
       }
     }
   }
-  // per-level augmented work offsets and solve job lists
+  // per-level augmented work offsets and fronts by elimination path
   long long aug_max = 0;
-  cs.d_level_list.resize(cs.nlevels);
-  cs.d_fwd_jobs.resize(cs.nlevels);
-  cs.d_bwd_rows.resize(cs.nlevels);
-  cs.n_fwd_jobs.resize(cs.nlevels);
-  cs.n_bwd_rows.resize(cs.nlevels);
-  cs.big_list.resize(cs.nlevels);
-  cs.small_list.resize(cs.nlevels);
-  cs.part_entries = 1;
-  cs.n_slots = 1;
-  std::vector<std::vector<int>> bigs(cs.nlevels), smalls(cs.nlevels);
-  std::vector<std::vector<FwdJob>> fjobs(cs.nlevels);
-  std::vector<std::vector<int4>> brows(cs.nlevels);
+  bigs.assign(cs.nlevels, {});
+  smalls.assign(cs.nlevels, {});
   for (int h = 0; h < cs.nlevels; ++h) {
     long long off = 0;
-    int slot = 0, pbase = 0;
-    // row chunks and backward rows per block sized so that a level has about
-    // kTargetBlocks blocks: small fronts are not split, large fronts are
-    long long work = 0, rows_total = 0;
-    for (int f : cs.level_fronts[h]) {
-      work += (long long)((desc[f].nS + desc[f].nB + kFwdCols - 1) / kFwdCols) * desc[f].nS;
-      rows_total += desc[f].nS;
-    }
-    int chunk_rows = (int)std::max<long long>(kFwdMinChunk, (work + kTargetBlocks - 1) / kTargetBlocks);
-    chunk_rows = std::min(kFwdMaxChunk, (chunk_rows + kFwdMinChunk - 1) / kFwdMinChunk * kFwdMinChunk);
-    const int bwd_rows = (int)std::max<long long>(kRowsPerBlock, (rows_total + kTargetBlocks - 1) / kTargetBlocks);
     for (int f : cs.level_fronts[h]) {
       desc[f].aug_off = off;
       const int nS = desc[f].nS, nF = nS + desc[f].nB;
       off += (long long)nF * (nF + nS);
       (nS >= kBigFront ? bigs[h] : smalls[h]).push_back(f);
-      const int tiles = (nF + kFwdCols - 1) / kFwdCols;
-      const int chunks = (nS + chunk_rows - 1) / chunk_rows;
-      for (int tl = 0; tl < tiles; ++tl) {
-        for (int ch = 0; ch < chunks; ++ch)
-          fjobs[h].push_back(FwdJob{f, tl, ch * chunk_rows, std::min(nS, (ch + 1) * chunk_rows), chunks, ch,
-                                    slot, pbase});
-        if (chunks > 1) {
-          pbase += chunks;
-          ++slot;
-        }
-      }
-      for (int r0 = 0; r0 < nS; r0 += bwd_rows) brows[h].push_back(make_int4(f, r0, std::min(nS, r0 + bwd_rows), 0));
     }
     aug_max = std::max(aug_max, off);
-    cs.part_entries = std::max<long long>(cs.part_entries, (long long)pbase * kFwdCols);
-    cs.n_slots = std::max(cs.n_slots, slot);
-    cs.n_fwd_jobs[h] = (int)fjobs[h].size();
-    cs.n_bwd_rows[h] = (int)brows[h].size();
   }
-  if (upload(&cs.d_desc, desc) || upload(&cs.d_S, Sall) || upload(&cs.d_B, Ball) ||
-      upload(&cs.d_kids, kids) || upload(&cs.d_cmap, cmap) || upload(&cs.d_ctb, ctb))
+  // solve jobs: forward by height from the leaves, then backward from the root.  Rows per
+  // job are sized so that a level has about kJobsPerBlockLevel jobs per resident block,
+  // and are a whole number of stages.
+  const long long target = (long long)kJobsPerBlockLevel * cs.grid;
+  auto job_rows = [&](long long level_rows, int srows) {
+    const long long want = std::max<long long>(srows, (level_rows + target - 1) / target);
+    const long long cap = (long long)(kJobRows / srows) * srows;
+    return (int)std::min(cap, (want + srows - 1) / srows * srows);
+  };
+  jobs.clear();
+  int slot = 0;
+  long long pbase = 0;
+  // column tiles of a front matrix with `nrows` rows and `ncols` columns, row chunks of
+  // each; rows are split beyond kJobRows only where the level has too few tiles to keep
+  // every resident block busy
+  auto add_tiles = [&](int f, int kind, int nrows, int ncols, long long level_rows, bool split) {
+    for (int c0 = 0; c0 < ncols; c0 += kTile) {
+      const int cols = std::min(kTile, ncols - c0);
+      if (nrows == 0) {   // the root's backward: x_S = w_S
+        jobs.push_back(SweepJob{f, kind, 0, 0, c0, c0 + cols, 0, 1, 0, -1, 0});
+        continue;
+      }
+      const int srows = std::min(kJobRows, std::max(1, kStageEntries / cols));
+      const int jr = split ? job_rows(level_rows, srows) : (kJobRows / srows) * srows;
+      const int nch = (nrows + jr - 1) / jr;
+      for (int ch = 0; ch < nch; ++ch)
+        jobs.push_back(SweepJob{f, kind, ch * jr, std::min(nrows, (ch + 1) * jr), c0, c0 + cols, srows, nch, ch,
+                                nch > 1 ? slot : -1, nch > 1 ? (int)pbase : 0});
+      if (nch > 1) {
+        ++slot;
+        pbase += nch;
+      }
+    }
+  };
+  for (int h = 0; h < cs.nlevels; ++h) {   // forward: M [nS][nF]
+    long long level_rows = 0, tiles = 0;
+    for (int f : cs.level_fronts[h]) {
+      const int t = (desc[f].nS + desc[f].nB + kTile - 1) / kTile;
+      level_rows += (long long)t * desc[f].nS;
+      tiles += t;
+    }
+    for (int f : cs.level_fronts[h]) {
+      desc[f].fwd_units = (desc[f].nS + desc[f].nB + kTile - 1) / kTile;
+      add_tiles(f, 0, desc[f].nS, desc[f].nS + desc[f].nB, level_rows, tiles < 2LL * grid);
+    }
+  }
+  for (int h = cs.nlevels - 1; h >= 0; --h) {   // backward: G^T [nB][nS]
+    long long level_rows = 0, tiles = 0;
+    for (int f : cs.level_fronts[h]) {
+      const int t = (desc[f].nS + kTile - 1) / kTile;
+      level_rows += (long long)t * desc[f].nB;
+      tiles += t;
+    }
+    for (int f : cs.level_fronts[h]) {
+      desc[f].bwd_units = (desc[f].nS + kTile - 1) / kTile;
+      add_tiles(f, 1, desc[f].nB, desc[f].nS, level_rows, tiles < 2LL * grid);
+    }
+  }
+  cs.njobs = (int)jobs.size();
+  cs.n_slots = slot;
+  cs.part_blocks = std::max<long long>(1, pbase);
+  cs.n_counters = 2LL * cs.nfronts + slot;
+  P.aug_max = aug_max;
+  P.upool = uoff;
+  return validate_plan(cs, P);
+}
+
+int coarse_plan_stats(const GridDims& g, int r, int leaf_max, bool symmetric, int grid, long long stats[8]) {
+  CoarseSolver cs;
+  CoarsePlan P;
+  if (int st = coarse_plan(cs, P, g, r, leaf_max, symmetric, grid)) return st;
+  stats[0] = cs.nfronts;
+  stats[1] = cs.nlevels;
+  stats[2] = cs.njobs;
+  stats[3] = cs.factor_entries;
+  stats[4] = cs.bwd_entries;
+  stats[5] = cs.part_blocks;
+  stats[6] = cs.n_slots;
+  stats[7] = cs.max_nB;
+  return 0;
+}
+
+int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef, int leaf_max,
+                 bool symmetric, bool df, cudaStream_t s) {
+  int grid = 0;
+  if (int st = sweep_grid_size(&grid)) return st;
+  CoarsePlan P;
+  if (int st = coarse_plan(cs, P, g, r, leaf_max, symmetric, grid)) return st;
+  cs.df = df;
+  const auto& desc = P.desc;
+  const auto& bigs = P.bigs;
+  const auto& smalls = P.smalls;
+  const long long aug_max = P.aug_max, uoff = P.upool;
+  cs.d_level_list.resize(cs.nlevels);
+  cs.big_list.resize(cs.nlevels);
+  cs.small_list.resize(cs.nlevels);
+  if (upload(&cs.d_desc, desc) || upload(&cs.d_S, P.Sall) || upload(&cs.d_B, P.Ball) ||
+      upload(&cs.d_kids, P.kids) || upload(&cs.d_cmap, P.cmap) || upload(&cs.d_ctb, P.ctb))
     return HELM_ECUDA;
   int2* d_ents = nullptr;
-  if (upload(&d_ents, ents)) return HELM_ECUDA;
+  if (upload(&d_ents, P.ents)) return HELM_ECUDA;
+  if (upload(&cs.d_jobs, P.jobs)) return HELM_ECUDA;
   for (int h = 0; h < cs.nlevels; ++h) {
-    if (upload(&cs.d_level_list[h], cs.level_fronts[h]) || upload(&cs.d_fwd_jobs[h], fjobs[h]) ||
-        upload(&cs.d_bwd_rows[h], brows[h]) || upload(&cs.big_list[h], bigs[h]) ||
+    if (upload(&cs.d_level_list[h], cs.level_fronts[h]) || upload(&cs.big_list[h], bigs[h]) ||
         upload(&cs.small_list[h], smalls[h]))
       return HELM_ECUDA;
   }
-  HELM_CUDA_TRY(cudaMalloc(&cs.d_factors, std::max<long long>(1, xg) * sizeof(double2)));
+  HELM_CUDA_TRY(cudaMalloc(&cs.d_factors, std::max<long long>(1, cs.factor_entries) * sizeof(double2)));
   HELM_CUDA_TRY(cudaMalloc(&cs.d_err, sizeof(int)));
   HELM_CUDA_TRY(cudaMemsetAsync(cs.d_err, 0, sizeof(int), s));
   double2 *d_aug = nullptr, *d_upool = nullptr, *d_akk = nullptr;
@@ -844,56 +748,34 @@ static int ensure_rhs(CoarseSolver& cs, int nrhs) {
   cudaFree(cs.d_part);
   cudaFree(cs.d_counters);
   cudaFree(cs.d_xd);
+  cs.d_uv = cs.d_w = cs.d_part = nullptr;
+  cs.d_counters = nullptr;
+  cs.d_xd = nullptr;
+  cs.rhs_cap = 0;
   HELM_CUDA_TRY(cudaMalloc(&cs.d_xd, cs.g.size * nrhs * sizeof(float4)));
   HELM_CUDA_TRY(cudaMalloc(&cs.d_uv, std::max<long long>(1, cs.uv_total) * nrhs * sizeof(double2)));
   HELM_CUDA_TRY(cudaMalloc(&cs.d_w, cs.g.size * nrhs * sizeof(double2)));
-  HELM_CUDA_TRY(cudaMalloc(&cs.d_part, cs.part_entries * nrhs * sizeof(double2)));
-  HELM_CUDA_TRY(cudaMalloc(&cs.d_counters, cs.n_slots * sizeof(unsigned)));
-  HELM_CUDA_TRY(cudaMemset(cs.d_counters, 0, cs.n_slots * sizeof(unsigned)));
+  HELM_CUDA_TRY(cudaMalloc(&cs.d_part, cs.part_blocks * kPartBlock * nrhs * sizeof(double2)));
+  HELM_CUDA_TRY(cudaMalloc(&cs.d_counters, std::max<long long>(1, cs.n_counters) * sizeof(unsigned)));
   cs.rhs_cap = nrhs;
-  return 0;
-}
-
-static int solve_sweeps(const CoarseSolver& cs, const double2* b, double2* e, int nrhs, double2* uv,
-                        double2* w, double2* part, unsigned* counters, float4* xd, cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    const int bytes = kBwdSmemEntries * (int)sizeof(float4);
-    cudaFuncSetAttribute(bwd_matvec_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(bwd_matvec_kernel<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(bwd_matvec_kernel<true, kRhsGroup>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(bwd_matvec_kernel<false, kRhsGroup>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    attr_set = true;
-  }
-  for (int h = 0; h < cs.nlevels; ++h) {
-    auto fk = nrhs == 1 ? (cs.df ? fwd_colsum_kernel<true, 1> : fwd_colsum_kernel<false, 1>)
-                        : (cs.df ? fwd_colsum_kernel<true, kRhsGroup> : fwd_colsum_kernel<false, kRhsGroup>);
-    const cudaError_t le = launch_pdl(fk,
-                                      dim3(cs.n_fwd_jobs[h]), dim3(kFwdCols), 0, s, cs.d_desc, cs.d_fwd_jobs[h],
-                                      cs.d_S, cs.d_ctb, cs.d_factors, b, uv, w, part, counters, nrhs, cs.g.size,
-                                      cs.uv_total);
-    if (le != cudaSuccess) { set_error(std::string("coarse forward launch: ") + cudaGetErrorString(le)); return HELM_ECUDA; }
-    HELM_LAUNCH_CHECK();
-  }
-  for (int h = cs.nlevels - 1; h >= 0; --h) {
-    const size_t sm = (size_t)std::min((long long)cs.max_nB * std::min(nrhs, kRhsGroup), (long long)kBwdSmemEntries) *
-                      sizeof(float4);
-    auto bk = nrhs == 1 ? (cs.df ? bwd_matvec_kernel<true, 1> : bwd_matvec_kernel<false, 1>)
-                        : (cs.df ? bwd_matvec_kernel<true, kRhsGroup> : bwd_matvec_kernel<false, kRhsGroup>);
-    const cudaError_t le = launch_pdl(bk,
-                                      dim3(cs.n_bwd_rows[h]), dim3(32 * kRowsPerBlock), sm, s, cs.d_desc,
-                                      cs.d_bwd_rows[h], cs.d_S, cs.d_B, cs.d_factors, w, e, xd, nrhs, cs.g.size,
-                                      kBwdSmemEntries);
-    if (le != cudaSuccess) { set_error(std::string("coarse backward launch: ") + cudaGetErrorString(le)); return HELM_ECUDA; }
-    HELM_LAUNCH_CHECK();
-  }
   return 0;
 }
 
 int coarse_solve(CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaStream_t s) {
   if (int st = ensure_rhs(cs, nrhs)) return st;
   KernelTimer kt(HELM_K_COARSE, s);
-  return solve_sweeps(cs, b, e, nrhs, cs.d_uv, cs.d_w, cs.d_part, cs.d_counters, cs.d_xd, s);
+  return sweep_launch(cs, b, e, nrhs, cs.d_uv, cs.d_w, cs.d_part, cs.d_counters, cs.d_xd, s);
+}
+
+int coarse_status(const CoarseSolver& cs, cudaStream_t s) {
+  if (!cs.d_err) return 0;
+  HELM_CUDA_TRY(cudaStreamSynchronize(s));
+  int herr = 0;
+  HELM_CUDA_TRY(cudaMemcpy(&herr, cs.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr == kErrSweepWait) { set_error("coarsest solve: a front dependency did not complete in time"); return HELM_ECUDA; }
+  if (herr == kErrSweepCopy) { set_error("coarsest solve: a factor copy did not complete in time"); return HELM_ECUDA; }
+  if (herr) { set_error("coarsest solver in error state"); return HELM_ECUDA; }
+  return 0;
 }
 
 // ------------------------------------------------------------------ allocation-free variant
@@ -911,8 +793,8 @@ double2* g_noalloc_addr[kMaxDevices] = {};
 }  // namespace
 
 int coarse_solve_noalloc(const CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaStream_t s) {
-  const long long per_rhs = cs.uv_total + cs.g.size + cs.part_entries + cs.g.size;
-  const long long counter_entries = (cs.n_slots * (long long)sizeof(unsigned) + sizeof(double2) - 1) / sizeof(double2);
+  const long long per_rhs = cs.uv_total + cs.g.size + cs.part_blocks * kPartBlock + cs.g.size;
+  const long long counter_entries = (cs.n_counters * (long long)sizeof(unsigned) + sizeof(double2) - 1) / sizeof(double2);
   if (nrhs < 1 || per_rhs * nrhs + counter_entries > kNoAllocScratchEntries) {
     set_error("allocation-free coarsest solve needs " + std::to_string(per_rhs * nrhs + counter_entries) +
               " complex scratch entries; the static array holds " + std::to_string(kNoAllocScratchEntries));
@@ -936,17 +818,16 @@ int coarse_solve_noalloc(const CoarseSolver& cs, const double2* b, double2* e, i
     }
     base = g_noalloc_addr[dev];
   }
-  // The column-tile counters must start at zero and are cleared here; every other
-  // scratch entry that is read is written earlier in the same call (update vectors and
-  // partial sums by the kernels that produce them, w and its double-float copy for
-  // every eliminated node).
+  // The completion counters must start at zero and are cleared by sweep_launch; every
+  // other scratch entry that is read is written earlier in the same call (update vectors
+  // and partial sums by the jobs that produce them, w and its double-float copy for every
+  // eliminated node).
   unsigned* counters = reinterpret_cast<unsigned*>(base);
-  HELM_CUDA_TRY(cudaMemsetAsync(counters, 0, cs.n_slots * sizeof(unsigned), s));
   double2* uv = base + counter_entries;
   double2* w = uv + cs.uv_total * nrhs;
   double2* part = w + cs.g.size * nrhs;
-  float4* xd = reinterpret_cast<float4*>(part + cs.part_entries * nrhs);   // float4 and double2 are both 16 bytes
-  return solve_sweeps(cs, b, e, nrhs, uv, w, part, counters, xd, s);
+  float4* xd = reinterpret_cast<float4*>(part + cs.part_blocks * kPartBlock * nrhs);   // float4 and double2 are both 16 bytes
+  return sweep_launch(cs, b, e, nrhs, uv, w, part, counters, xd, s);
 }
 
 void coarse_free(CoarseSolver& cs) {
@@ -958,8 +839,7 @@ void coarse_free(CoarseSolver& cs) {
   cudaFree(cs.d_factors);
   cudaFree(cs.d_err);
   for (auto p : cs.d_level_list) cudaFree(p);
-  for (auto p : cs.d_fwd_jobs) cudaFree(p);
-  for (auto p : cs.d_bwd_rows) cudaFree(p);
+  cudaFree(cs.d_jobs);
   for (auto p : cs.big_list) cudaFree(p);
   for (auto p : cs.small_list) cudaFree(p);
   cudaFree(cs.d_part);

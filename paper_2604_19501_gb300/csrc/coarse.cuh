@@ -6,17 +6,29 @@
 
 namespace helm {
 
-constexpr int kFwdCols = 256;    // columns per block of the forward sweep
-constexpr int kFwdMinChunk = 16;   // rows per partial sum of the forward sweep: at least ...
-constexpr int kFwdMaxChunk = 128;  // ... and at most
-constexpr int kRhsGroup = 4;       // right-hand sides sharing each factor load in the sweeps
+// The solve runs as one persistent kernel (coarse_sweep.cu): a list of jobs, forward
+// (leaves to root) then backward (root to leaves), dealt round-robin to resident blocks.
+// Each block streams its jobs' factor rows through a ring of shared-memory stages filled
+// by bulk asynchronous copies, so a job's factors arrive while it waits for the fronts it
+// depends on.
+constexpr int kSweepThreads = 256;   // threads per block
+constexpr int kStageEntries = 1024;  // 16-byte factor entries per stage (16 KiB)
+constexpr int kJobRows = 128;        // most factor rows of one job
+constexpr int kTile = 256;           // output columns of one job (one thread each at most)
+constexpr int kPartBlock = 256;      // partial-sum entries per chunk and right-hand side
+constexpr int kRhsGroup = 4;         // right-hand sides sharing each staged factor entry
+
+// Error codes the solve kernel leaves in CoarseSolver::d_err.
+constexpr int kErrPivot = 1;       // factorisation: zero or non-finite pivot
+constexpr int kErrSweepWait = 2;   // solve: a dependency did not complete in time
+constexpr int kErrSweepCopy = 3;   // solve: a factor copy did not complete in time
 
 struct FrontDesc {
   int nS, nB;             // eliminated (separator / leaf) nodes, boundary (ancestor) nodes
   int S_off, B_off;       // offsets into the S / B node-index arrays
   long long M_off;        // forward matrix [nS][nS+nB], read as column sums (see coarse.cu)
-  long long G_off;        // backward matrix F_SS^-1 F_SB, rows of stride g_ld
-  int g_ld;
+  long long G_off;        // backward matrix (F_SS^-1 F_SB)^T [nB][nS], read as column sums
+  int g_ld;               // its row stride (nS)
   int bsign;              // -1: M = [F_SS^-1 | G] (symmetric operator); +1: M = X^T
   long long aug_off;      // augmented front [nF][nF+nS] within the level work buffer
   long long U_off;        // update matrix   [nB][nB] = F_BB - F_BS F_SS^-1 F_SB
@@ -25,12 +37,22 @@ struct FrontDesc {
   int cmap_off;           // this front's boundary positions inside its parent's front
   long long ctb_off;      // per front position: the children's update-vector entries added to it
   long long uv_off;       // solve scratch: update vector (nB entries)
+  int parent;             // parent front, -1 for the root
+  int fwd_units;          // forward output units (column tiles of M) of the front
+  int bwd_units;          // backward output units (column tiles of G^T) of the front
 };
 
-struct FwdJob {
-  int front, tile, s0, s1;           // column tile and rows [s0, s1) of one front
-  int nchunks, chunk;                // row chunks of the tile and the index of this one
-  int slot, pbase;                   // counter of the tile; first partial-sum slot of the tile
+// One job of the solve kernel: partial column sums over rows [r0, r1) of a front matrix,
+// for its columns [c0, c1).  Kind 0 (forward): M, rows = eliminated positions s, columns =
+// front positions t.  Kind 1 (backward): G^T, rows = boundary positions, columns =
+// eliminated positions.  An output unit (a column tile) is split into nchunks jobs over
+// the rows; their partial sums go to consecutive blocks of the partial buffer from pbase
+// on and the last job to finish (counted in slot) adds them in chunk order.
+struct SweepJob {
+  int front, kind;
+  int r0, r1, c0, c1;
+  int srows;              // rows per stage (0: the job reads no factor entries)
+  int nchunks, chunk, slot, pbase;
 };
 
 struct CoarseSolver {
@@ -48,17 +70,17 @@ struct CoarseSolver {
   long long factor_entries = 0;
   long long bwd_entries = 0;          // entries of the G blocks (read again by the backward sweep)
   std::vector<int*> d_level_list;     // per level: front ids
-  std::vector<FwdJob*> d_fwd_jobs;    // per level: forward-sweep blocks
-  std::vector<int> n_fwd_jobs;
   std::vector<int*> big_list, small_list;   // per level: fronts by elimination path
-  long long part_entries = 1;         // partial sums of the forward sweep (per right-hand side)
-  int n_slots = 1;                    // column-tile counters
+  SweepJob* d_jobs = nullptr;         // the solve kernel's job list
+  int njobs = 0;
+  int grid = 0;                       // resident blocks of the solve kernel
+  long long part_blocks = 1;          // partial-sum blocks (kPartBlock entries per right-hand side)
+  int n_slots = 0;                    // output units split into several jobs
+  long long n_counters = 0;           // forward and backward completion counts, then the slots
   double2* d_part = nullptr;
   unsigned* d_counters = nullptr;
   bool df = false;                    // factors stored and applied in double-float arithmetic
   float4* d_xd = nullptr;             // double-float copy of the backward-sweep result
-  std::vector<int4*> d_bwd_rows;      // per level: (front, first row, end row) blocks
-  std::vector<int> n_bwd_rows;
   long long uv_total = 0;
   int2* d_ctb = nullptr;              // children's contributions per front position
   double2* d_uv = nullptr;            // [nrhs][uv_total]
@@ -82,6 +104,19 @@ int coarse_solve(CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaS
 // The same solve with its scratch in a static device array of fixed size (no
 // allocation); HELM_EINVAL when the problem needs more scratch than the array holds.
 int coarse_solve_noalloc(const CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaStream_t s);
+
+// Host only: the plan coarse_setup builds (tree, fronts, solve jobs for `grid` resident
+// blocks), checked; stats as documented for helm_coarse_plan.
+int coarse_plan_stats(const GridDims& g, int r, int leaf_max, bool symmetric, int grid, long long stats[8]);
+
+// Waits for the stream and reports an error a solve kernel left in d_err.
+int coarse_status(const CoarseSolver& cs, cudaStream_t s);
+
+// Solve kernel (coarse_sweep.cu): resident blocks on this device, and one launch over
+// the job list with the given scratch (counters cleared first).
+int sweep_grid_size(int* grid);
+int sweep_launch(const CoarseSolver& cs, const double2* b, double2* e, int nrhs, double2* uv, double2* w,
+                 double2* part, unsigned* counters, float4* xd, cudaStream_t s);
 
 void coarse_free(CoarseSolver& cs);
 
