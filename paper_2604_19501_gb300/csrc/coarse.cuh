@@ -13,7 +13,7 @@ namespace helm {
 // depends on.
 constexpr int kSweepThreads = 256;   // threads per block
 constexpr int kStageEntries = 1024;  // 16-byte factor entries per stage (16 KiB)
-constexpr int kJobRows = 128;        // most factor rows of one job
+constexpr int kJobRows = 256;        // most factor rows of one job
 constexpr int kTile = 256;           // output columns of one job (one thread each at most)
 constexpr int kPartBlock = 256;      // partial-sum entries per chunk and right-hand side
 constexpr int kRhsGroup = 4;         // right-hand sides sharing each staged factor entry

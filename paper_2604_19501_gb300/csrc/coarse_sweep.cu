@@ -35,15 +35,19 @@ namespace helm {
 namespace {
 
 constexpr int kSplitMax = 16;                              // forward row parts per column
-constexpr unsigned long long kWaitNs = 2000000000ull;      // 2 s limit on any wait
+// Limit on any wait, in cycles of the waiting multiprocessor's clock (clock64 is
+// monotonic per multiprocessor): about 2 s at the maximum SM clock, longer below it.
+constexpr long long kWaitCycles = 4000000000LL;
 constexpr int kStageBytes = kStageEntries * 16;
-// per-job shared scratch: row values v [kJobRows][RG], row-part sums [threads][RG],
-// forward r_B at the job's columns [kTile][RG]
 // The ring is deeper for single right-hand sides, whose per-job scratch is smaller.
 template <int RG>
 __host__ __device__ constexpr int ring_stages() { return RG == 1 ? 6 : 4; }
+// per-job scratch: row values [kJobRows][RG] (reused for the row-part sums
+// [kSweepThreads][RG] once the job's stages are consumed) and forward r_B [kTile][RG]
 template <int RG>
-__host__ __device__ constexpr int local_bytes() { return (kJobRows + kSweepThreads + kTile) * RG * 16; }
+__host__ __device__ constexpr int local_bytes() {
+  return ((kJobRows > kSweepThreads ? kJobRows : kSweepThreads) + kTile) * RG * 16;
+}
 template <int RG>
 __host__ __device__ constexpr int smem_bytes() { return ring_stages<RG>() * kStageBytes + local_bytes<RG>() + 2048; }
 static_assert(smem_bytes<kRhsGroup>() * 2 + 2048 <= 233472, "two blocks per multiprocessor");
@@ -92,11 +96,7 @@ __device__ __forceinline__ double2 ldcg(const double2* p) { return __ldcg(p); }
 __device__ __forceinline__ float4 ldcg(const float4* p) { return __ldcg(p); }
 
 // ---- synchronisation primitives
-__device__ __forceinline__ unsigned long long now_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
+__device__ __forceinline__ bool expired(long long t0) { return clock64() - t0 > kWaitCycles; }
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -112,12 +112,12 @@ __device__ __forceinline__ int ld_relaxed(const int* p) {
 // block has already recorded an error.
 __device__ bool wait_count(const unsigned* p, unsigned target, int* err) {
   if (ld_acquire(p) >= target) return true;
-  const unsigned long long t0 = now_ns();
+  const long long t0 = clock64();
   while (true) {
     __nanosleep(64);
     if (ld_acquire(p) >= target) return true;
     if (ld_relaxed(err)) return false;
-    if (now_ns() - t0 > kWaitNs) {
+    if (expired(t0)) {
       atomicCAS(err, 0, kErrSweepWait);
       return false;
     }
@@ -145,9 +145,9 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 // The stage's copies have landed within the time limit.
 __device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = now_ns();
+  const long long t0 = clock64();
   while (!mbar_try(bar, parity))
-    if (now_ns() - t0 > kWaitNs) return false;
+    if (expired(t0)) return false;
   return true;
 }
 __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
@@ -216,9 +216,6 @@ __device__ __forceinline__ double2 front_rhs(const SweepArgs& a, const FrontDesc
   if (c.y >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + c.y));
   return v;
 }
-// Gather items a consumer thread handles per pass: the job's rows x group, its columns x group.
-constexpr int kRowItems = (kJobRows * kRhsGroup + kSweepThreads - 1) / kSweepThreads;
-constexpr int kColItems = (kTile * kRhsGroup + kSweepThreads - 1) / kSweepThreads;
 constexpr int kBlockThreads = kSweepThreads + 32;   // consumers + one producer warp
 
 __device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kSweepThreads) : "memory"); }
@@ -232,14 +229,17 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 template <bool DF, int RG>
 __global__ void __launch_bounds__(kBlockThreads, 2) sweep_kernel(const SweepArgs a) {
   using E = typename std::conditional<DF, float4, double2>::type;
+  // gather items a consumer thread handles per pass: the job's rows x group, its columns x group
+  constexpr int kRowItems = (kJobRows * RG + kSweepThreads - 1) / kSweepThreads;
+  constexpr int kColItems = (kTile * RG + kSweepThreads - 1) / kSweepThreads;
   constexpr int NST = ring_stages<RG>();
   constexpr int kLocalBytes = local_bytes<RG>();
   extern __shared__ __align__(128) unsigned char smem[];
   E* const stage = reinterpret_cast<E*>(smem);
   unsigned char* const local = smem + NST * kStageBytes;
-  E* const vs = reinterpret_cast<E*>(local);                           // row values [kJobRows][RG]
-  E* const red = vs + kJobRows * RG;                                   // row-part sums [threads][RG]
-  double2* const rbs = reinterpret_cast<double2*>(red + kSweepThreads * RG);   // forward r_B [kTile][RG]
+  E* const vs = reinterpret_cast<E*>(local);   // row values [kJobRows][RG]
+  E* const red = vs;                           // row-part sums [threads][RG], after the stages
+  double2* const rbs = reinterpret_cast<double2*>(vs + (kJobRows > kSweepThreads ? kJobRows : kSweepThreads) * RG);   // forward r_B [kTile][RG]
   uint64_t* const full = reinterpret_cast<uint64_t*>(local + kLocalBytes);
   uint64_t* const empty = full + NST;
   volatile int* const flag = reinterpret_cast<volatile int*>(empty + NST);
@@ -442,6 +442,7 @@ __global__ void __launch_bounds__(kBlockThreads, 2) sweep_kernel(const SweepArgs
           }
         });
       }
+      consumer_sync();   // every thread is done with the row values red overwrites
       if (ok && act)
 #pragma unroll
         for (int rr = 0; rr < RG; ++rr) red[tid * RG + rr] = acc[rr];
