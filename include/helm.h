@@ -80,6 +80,10 @@ typedef struct {
                              n_rhs in blocks of this size, each block sharing one cycle and one
                              coarsest solve per iteration (operators read once per block) */
   void* stream;           /* cudaStream_t for all work of this context */
+  int fuse_cycle;         /* 1: the 2D mixed-precision V(1,1) Jacobi cycle runs as fused tile
+                             passes (fine down, level-2 residual, restriction to level 3,
+                             level-2 up, fine up); 0: one kernel per step.  Other
+                             configurations always take one kernel per step. */
 } helm_opts;
 
 /* Per-solve statistics, one entry per right-hand side. */
@@ -94,7 +98,7 @@ typedef struct helm_ctx helm_ctx;
 
 /* Fills *o with defaults: 2D, h = 1, gamma_max = 1, alpha2 = alpha3 = 1,
  * 2nd-order stencil, FW transfers, V(1,1), Jacobi w = (0.8, 0.8), rb_w = 1,
- * FP64, restart 10, max_rhs 1, default stream.  The caller sets dim, n,
+ * FP64, restart 10, max_rhs 1, default stream, fuse_cycle 1.  The caller sets dim, n,
  * omega, abc_width and the shifts. */
 int helm_default_opts(helm_opts* o);
 

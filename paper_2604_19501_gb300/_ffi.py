@@ -40,6 +40,7 @@ class HelmOpts(ctypes.Structure):
         ("restart", ctypes.c_int),
         ("max_rhs", ctypes.c_int),
         ("stream", ctypes.c_void_p),
+        ("fuse_cycle", ctypes.c_int),
     ]
 
 

@@ -11,6 +11,7 @@
 #include "adjoint.cuh"
 #include "coarse.cuh"
 #include "galerkin.cuh"
+#include "cycle2d.cuh"
 #include "gridops.cuh"
 #include "krylov.cuh"
 #include "timer.cuh"
@@ -223,9 +224,45 @@ int visit_level2(helm_ctx* c, Prec P, void** x, void** t, bool first, int nrhs) 
   return smooth(c, 1, P, c->l2b, P, x, t, c->o.nu2, false, nrhs);
 }
 
+// The fused 2D cycle applies: mixed precision (double-float input, c64 output), V(1,1)
+// with damped Jacobi.
+bool fused_cycle(const helm_ctx* c, Prec vs, Prec zs) {
+  const helm_opts& o = c->o;
+  return o.fuse_cycle && o.dim == 2 && o.precision == HELM_MIXED && vs == P_DF && zs == P32 &&
+         o.cycle == HELM_CYCLE_V && o.smoother == HELM_SMOOTHER_JACOBI && o.nu1 == 1 && o.nu2 == 1 &&
+         (c->r2 == 1 || c->r2 == 2);
+}
+
+int run_cycle_fused(helm_ctx* c, const void* v, void* z, int nrhs) {
+  Cycle2D cy;
+  cy.fine = c->fine;
+  cy.kap = c->kap32;
+  cy.g2 = c->g[1];
+  cy.g3 = c->g[2];
+  cy.r2 = c->r2;
+  cy.coef2 = c->A2_32;
+  cy.dinv2 = c->A2_dinv32;
+  cy.rw1 = c->tR1.radius;
+  cy.rw2 = c->tR2.radius;
+  cy.pw2 = c->tP2.radius;
+  cy.w1 = (float)c->o.jacobi_w[0];
+  cy.w2 = (float)c->o.jacobi_w[1];
+  const float4* vd = static_cast<const float4*>(v);
+  float2* r2 = static_cast<float2*>(c->l2b);
+  float2* s2 = static_cast<float2*>(c->l2r);
+  float2* y2 = static_cast<float2*>(c->l2a);
+  if (int st = cycle2d_fine_down(cy, vd, r2, nrhs, c->s)) return st;
+  if (int st = cycle2d_l2_resid(cy, r2, s2, nrhs, c->s)) return st;
+  if (int st = cycle2d_l2_restrict(cy, s2, c->l3b, nrhs, c->s)) return st;
+  if (int st = coarse_solve(c->cs, c->l3b, c->l3e, nrhs, c->s)) return st;
+  if (int st = cycle2d_l2_up(cy, r2, c->l3e, y2, nrhs, c->s)) return st;
+  return cycle2d_fine_up(cy, vd, y2, static_cast<float2*>(z), nrhs, c->s);
+}
+
 // z = M^-1 v from a zero initial guess.  v has storage vs, z storage zs.
 int run_cycle(helm_ctx* c, const void* v, Prec vs, void* z, Prec zs, int nrhs) {
   if (int st = ensure_workspaces(c, nrhs)) return st;
+  if (fused_cycle(c, vs, zs)) return run_cycle_fused(c, v, z, nrhs);
   const Prec P = cycle_prec(c);
   void* x = c->l1a;
   void* t = c->l1b;
@@ -398,6 +435,7 @@ int helm_default_opts(helm_opts* o) {
   o->restart = 10;
   o->max_rhs = 1;
   o->stream = nullptr;
+  o->fuse_cycle = 1;
   return HELM_OK;
 }
 
@@ -756,7 +794,16 @@ int helm_coarse_solve_noalloc(helm_ctx* c, const void* b, void* e, int n_rhs) {
 int helm_cycle(helm_ctx* c, const void* v, void* z, int n_rhs) {
   if (!c || !v || !z || n_rhs < 1) return fail(HELM_EINVAL, "bad argument");
   LaunchScope scope(c);
-  if (int st = run_cycle(c, v, P64, z, P64, n_rhs)) return st;
+  if (fused_cycle(c, P_DF, P32)) {
+    // the fused mixed-precision cycle reads the double-float form of v and writes c64
+    if (int st = ensure_workspaces(c, n_rhs)) return st;
+    const long long n = c->g[0].size * n_rhs;
+    if (int st = launch_convert(P64, P_DF, v, c->l1r, n, c->s)) return st;
+    if (int st = run_cycle(c, c->l1r, P_DF, c->l1a, P32, n_rhs)) return st;
+    if (int st = launch_convert(P32, P64, c->l1a, z, n, c->s)) return st;
+  } else if (int st = run_cycle(c, v, P64, z, P64, n_rhs)) {
+    return st;
+  }
   if (int st = coarse_status(c->cs, c->s)) return st;
   return HELM_OK;
 }

@@ -241,11 +241,22 @@ __global__ void convert_kernel(const c2<S>* __restrict__ x, c2<D>* __restrict__ 
     y[i] = cvt<D>(x[i]);
 }
 
+// c128 -> double-float (hi, lo) per component
+__global__ void to_df_kernel(const double2* __restrict__ x, float4* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = x[i];
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    y[i] = make_float4(rh, ih, __double2float_rn(v.x - (double)rh), __double2float_rn(v.y - (double)ih));
+  }
+}
+
 int launch_convert(Prec from, Prec to, const void* x, void* y, long long n, cudaStream_t s) {
   const int th = 256;
   const int bl = (int)std::min<long long>(blocks_for(n, th), 152LL * 16);
   KernelTimer kt(HELM_K_TRANSFER, s);
-  if (from == P64 && to == P32) convert_kernel<double, float><<<bl, th, 0, s>>>((const double2*)x, (float2*)y, n);
+  if (from == P64 && to == P_DF) to_df_kernel<<<bl, th, 0, s>>>((const double2*)x, (float4*)y, n);
+  else if (from == P_DF || to == P_DF) { set_error("unsupported conversion"); return 1; }
+  else if (from == P64 && to == P32) convert_kernel<double, float><<<bl, th, 0, s>>>((const double2*)x, (float2*)y, n);
   else if (from == P32 && to == P64) convert_kernel<float, double><<<bl, th, 0, s>>>((const float2*)x, (double2*)y, n);
   else if (from == P64) convert_kernel<double, double><<<bl, th, 0, s>>>((const double2*)x, (double2*)y, n);
   else convert_kernel<float, float><<<bl, th, 0, s>>>((const float2*)x, (float2*)y, n);
