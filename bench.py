@@ -13,8 +13,11 @@ One JSON line on stdout (rank 0).  Diagnostics go to stderr.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 The reference arm (--impl reference) times the CPU oracle on the host cores: every
-step is a bounded sample of FGMRES iterations of the same workload, scaled by the
-oracle's own iteration count to the metric's unit.
+step is one full oracle solve (to the same tolerance) of the same workload generator at
+--cpu-n interior cells (default 512: 576^2 cells with the layer); the value is that
+instance's nodes per solve second.  The full-size instance is out of the oracle's reach
+(its SuperLU factorisation of the coarsest operator alone takes minutes).  The same
+sample gives the cpu_baseline object of the GPU arm.
 """
 import argparse
 import json
@@ -24,6 +27,12 @@ import subprocess
 import sys
 import threading
 import time
+
+# the CPU oracle runs single-threaded (SciPy sparse products and SuperLU solves are; this
+# pins the BLAS pool used by its vector reductions too), before numpy is imported
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+ORACLE_THREADS = int(os.environ["OPENBLAS_NUM_THREADS"])
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -36,7 +45,7 @@ FP64_PEAK_TFLOPS = 1.26   # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=25)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=2048, help="interior cells per axis")
@@ -51,7 +60,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--maxit", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-iters", type=int, default=3, help="oracle FGMRES iterations per CPU sample")
+    ap.add_argument("--cpu-n", type=int, default=512,
+                    help="interior cells per axis of the workload instance the CPU oracle solves")
     ap.add_argument("--sources", type=int, default=1,
                     help="right-hand sides per step: 1 = the centre source; K > 1 = K seeded surface sources")
     ap.add_argument("--block", type=int, default=0, help="right-hand sides per FGMRES block (0 = all)")
@@ -186,34 +196,45 @@ def max_over_ranks(world, value, device=None):
 
 
 # ------------------------------------------------------------------ oracle timing
-def oracle_sample(args, wl, iters, log):
-    """Oracle set-up, one full solve for its iteration count, then timed samples of
-    `iters` FGMRES iterations.  Returns (seconds per iteration list, full iteration count)."""
-    import numpy as np
+def oracle_sample(args, log):
+    """Oracle set-up for the bounded CPU sample: the workload generator of the timed run
+    (same medium recipe, absorbing layer, points per wavelength, method and shifts) at
+    --cpu-n interior cells.  The full-size instance is out of reach of the oracle: its
+    SuperLU factorisation of the coarsest operator alone takes minutes."""
+    import argparse
 
     from oracle import cycle as OC
     from oracle import grid as OG
     from oracle import hierarchy as OH
-    from oracle import krylov as OK
 
+    sargs = argparse.Namespace(**vars(args))
+    sargs.n = args.cpu_n
+    wl = workload(sargs)
     grid = OG.Grid(wl["n"])
     gamma = OG.abc_profile(grid, OG.uniform_widths(2, wl["pad"]), 1.0)
     t0 = time.perf_counter()
     h = OH.Hierarchy(grid, wl["kappa2"], wl["omega"], gamma, wl["order"], wl["intergrid"], alpha3=wl["alpha3"])
     h.coarsest_lu
     cy = OC.Cycle(h, cycle=args.cycle, weights=(wl["jacobi"], wl["jacobi"]))
-    log(f"oracle set-up {time.perf_counter() - t0:.1f} s")
-    A = h.A[0]
-    q = wl["q"].ravel()
-    return h, cy, A, q
+    log(f"oracle set-up {time.perf_counter() - t0:.1f} s ({wl['n'][0]}^2 cells)")
+    nodes = (wl["n"][0] + 1) * (wl["n"][1] + 1)
+    return dict(h=h, cy=cy, A=h.A[0], q=wl["q"].ravel(), nodes=nodes, cells=wl["n"][0], n=args.cpu_n)
 
 
-def run_oracle_iters(A, q, cy, iters, restart, tol):
+def oracle_solve(smp, args):
+    """One oracle FGMRES solve of the sample to the run's tolerance: (seconds, iterations)."""
     from oracle import krylov as OK
 
     t = time.perf_counter()
-    _, info = OK.fgmres(lambda v: A @ v, q, cy, tol=tol, maxit=iters, restart=restart)
-    return (time.perf_counter() - t), info
+    _, info = OK.fgmres(lambda v: smp["A"] @ v, smp["q"], smp["cy"], tol=args.tol, maxit=args.maxit,
+                        restart=args.restart)
+    return time.perf_counter() - t, info["iterations"]
+
+
+def cpu_sample_note(smp, its, t):
+    return (f"oracle (NumPy/SciPy sparse, FP64, {ORACLE_THREADS} thread(s)) full FGMRES solve to the run's tolerance of the "
+            f"same workload at {smp['n']}^2 cells + absorbing layer ({smp['cells']}^2 cells, {smp['nodes']} nodes): "
+            f"{its} iterations in {t:.2f} s, set-up excluded; value = sample nodes / solve time")
 
 
 def hbm_peak_gbs():
@@ -225,22 +246,6 @@ def hbm_peak_gbs():
         return 6800.0
 
 
-def cpu_cores():
-    try:
-        return len(os.sched_getaffinity(0))
-    except AttributeError:
-        return os.cpu_count()
-
-
-def blas_threads():
-    try:
-        from threadpoolctl import threadpool_info
-
-        return max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
-    except Exception:
-        return int(os.environ.get("OMP_NUM_THREADS", "0")) or None
-
-
 # ------------------------------------------------------------------ reference arm
 def reference_arm(args):
     world, rank, _ = dist_init(args)
@@ -248,26 +253,20 @@ def reference_arm(args):
         return 0
     log = lambda m: print(m, file=sys.stderr, flush=True)
     wl = workload(args)
-    nodes = (wl["n"][0] + 1) * (wl["n"][1] + 1)
-    h, cy, A, q = oracle_sample(args, wl, args.cpu_iters, log)
-    t_full, info = run_oracle_iters(A, q, cy, args.maxit, args.restart, args.tol)
-    its = info["iterations"]
-    log(f"oracle full solve: {its} iterations, relres {info['relres']:.2e}, {t_full:.1f} s")
+    smp = oracle_sample(args, log)
     for _ in range(args.warmup):
-        run_oracle_iters(A, q, cy, args.cpu_iters, args.restart, args.tol)
-    times = [run_oracle_iters(A, q, cy, args.cpu_iters, args.restart, args.tol)[0] for _ in range(args.steps)]
-    per_iter = sum(times) / (args.steps * args.cpu_iters)
-    solve_s = per_iter * its
-    value = nodes / 1e6 / solve_s
-    cores = blas_threads() or cpu_cores()
+        oracle_solve(smp, args)
+    runs = [oracle_solve(smp, args) for _ in range(args.steps)]
+    t_step = sum(t for t, _ in runs) / len(runs)
+    its = runs[-1][1]
+    value = smp["nodes"] / 1e6 / t_step
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": describe(args, wl),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{args.cpu_iters} FGMRES iterations per step, scaled by the oracle's own "
-                                   f"{its}-iteration full solve"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": ORACLE_THREADS, "kind": "oracle",
+                         "sample": cpu_sample_note(smp, its, t_step)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "iterations": its,
     }
@@ -394,14 +393,10 @@ def our_arm(args):
     # ---- CPU oracle on a bounded sample
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        h, cy, A, qo = oracle_sample(args, wl, args.cpu_iters, log)
-        dt, _ = run_oracle_iters(A, qo, cy, args.cpu_iters, args.restart, args.tol)
-        per_iter = dt / args.cpu_iters
-        cpu_solve = per_iter * its_one
-        cpu = {"value": nodes / 1e6 / cpu_solve, "unit": UNIT, "cores": blas_threads() or cpu_cores(),
-               "kind": "oracle",
-               "sample": f"{args.cpu_iters} oracle FGMRES iterations on the full workload ({per_iter:.2f} s each), "
-                         f"scaled to the {its_one}-iteration solve"}
+        smp = oracle_sample(args, log)
+        t_cpu, its_cpu = oracle_solve(smp, args)
+        cpu = {"value": smp["nodes"] / 1e6 / t_cpu, "unit": UNIT, "cores": ORACLE_THREADS, "kind": "oracle",
+               "sample": cpu_sample_note(smp, its_cpu, t_cpu)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
