@@ -26,6 +26,11 @@ constexpr int kTX = 32, kTY = 8;     // level-2 passes: tile of level-2 nodes
 constexpr int kFX = 32, kFY = 16;    // fine up pass: tile of fine nodes
 
 __device__ __forceinline__ float2 z2() { return make_float2(0.f, 0.f); }
+// 1 / d as conj(d) / |d|^2 with one IEEE round-to-nearest reciprocal
+__device__ __forceinline__ float2 rcp_c(float2 d) {
+  const float r = __frcp_rn(fmaf(d.x, d.x, d.y * d.y));
+  return make_float2(d.x * r, -d.y * r);
+}
 
 // coefficient c = omega^2 kappa^2 (1 - i gamma) and diagonal of the fine operator at (x, y)
 template <int ORDER>
@@ -104,7 +109,7 @@ __global__ void __launch_bounds__(kThreads) fine_down_kernel(const Cycle2D c, co
       vv = make_float2(t.x, t.y);
       float2 diag;
       fine_cd<ORDER>(c, idx, gx, gy, cc, diag);
-      xx = cscale(cmul(crecip(diag), vv), w1);
+      xx = cscale(cmul(rcp_c(diag), vv), w1);
     }
     sv[q] = vv;
     sc[q] = cc;
@@ -223,40 +228,36 @@ __global__ void __launch_bounds__(kThreads) l2_restrict_kernel(const Cycle2D c, 
   }
 }
 
-// Prolongation of a coarse field ec (held in a tile) to the fine tile positions
-// [X0, X0 + NX) x [Y0, Y0 + NY): separable, P = 4 R^T, weights 2 w per axis.
+// Prolongation of a coarse field (held in a tile) to the fine tile positions
+// [X0, X0 + NX) x [Y0, Y0 + NY): separable, P = 4 R^T, i.e. weights 2 w per axis.  Along
+// an axis, fine node f = 2J takes 2w[PW] of J and, for cubic transfers, 2w[PW -+ 2] of J -+ 1;
+// f = 2J + 1 takes 2w[PW - 1] = 2w[PW + 1] of J and J + 1:
+//   full weighting:  even (1) of J;            odd (1/2, 1/2)
+//   cubic:           even (1/8, 3/4, 1/8);     odd (1/2, 1/2)
 //   ce: coarse tile with origin (J0x, J0y), size MX x MY; u: scratch [MY][NX]; out: [NY][NX]
+template <int PW>
+__device__ __forceinline__ float2 prolong_1d(const float2* __restrict__ e, int f, int J0, int stride) {
+  const int J = f >> 1;   // floor division
+  const float2* p = e + (J - J0) * stride;
+  if (f & 1) return cscale(p[0] + p[stride], 0.5f);
+  if (PW == 1) return p[0];
+  float2 acc = cscale(p[0], 0.75f);
+  acc.x = fmaf(0.125f, p[-stride].x + p[stride].x, acc.x);
+  acc.y = fmaf(0.125f, p[-stride].y + p[stride].y, acc.y);
+  return acc;
+}
 template <int PW>
 __device__ __forceinline__ void prolong_tile(const float2* __restrict__ ce, int J0x, int J0y, int MX, int MY,
                                              float2* __restrict__ u, float2* __restrict__ out, int X0, int Y0,
                                              int NX, int NY) {
-  const float* w = c_w[PW - 1];
   for (int q = threadIdx.x; q < MY * NX; q += kThreads) {
     const int jy = q / NX, lx = q % NX;
-    const int f = X0 + lx;
-    const int i0 = (f - PW + 1) >> 1, i1 = (f + PW) >> 1;
-    float2 acc = z2();
-    for (int I = i0; I <= i1; ++I) {
-      const float wt = 2.f * w[f - 2 * I + PW];
-      const float2 e = ce[jy * MX + (I - J0x)];
-      acc.x = fmaf(wt, e.x, acc.x);
-      acc.y = fmaf(wt, e.y, acc.y);
-    }
-    u[q] = acc;
+    u[q] = prolong_1d<PW>(ce + jy * MX, X0 + lx, J0x, 1);
   }
   __syncthreads();
   for (int q = threadIdx.x; q < NY * NX; q += kThreads) {
     const int ly = q / NX, lx = q % NX;
-    const int f = Y0 + ly;
-    const int j0 = (f - PW + 1) >> 1, j1 = (f + PW) >> 1;
-    float2 acc = z2();
-    for (int J = j0; J <= j1; ++J) {
-      const float wt = 2.f * w[f - 2 * J + PW];
-      const float2 e = u[(J - J0y) * NX + lx];
-      acc.x = fmaf(wt, e.x, acc.x);
-      acc.y = fmaf(wt, e.y, acc.y);
-    }
-    out[q] = acc;
+    out[q] = prolong_1d<PW>(u + lx, Y0 + ly, J0y, NX);
   }
 }
 
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(kThreads) fine_up_kernel(const Cycle2D c, cons
   __shared__ float2 sv[NX * NY];
   __shared__ float2 sc[NX * NY];
   __shared__ float2 sx[NX * NY];
-  __shared__ float2 sp[NX * NY];
+  __shared__ float2 sp[NX * NY];   // P y2, then 1 / diagonal
   __shared__ float2 se[MX * MY];
   __shared__ float2 su[MY * NX];
   const GridDims& g = c.fine.g;
@@ -352,18 +353,20 @@ __global__ void __launch_bounds__(kThreads) fine_up_kernel(const Cycle2D c, cons
   __syncthreads();
   for (int q = threadIdx.x; q < NX * NY; q += kThreads) {
     const int gx = X0 + q % NX, gy = Y0 + q / NX;
-    float2 vv = z2(), cc = z2(), xx = z2();
+    float2 vv = z2(), cc = z2(), xx = z2(), di = z2();
     if (gx >= 0 && gx < N0 && gy >= 0 && gy < N1) {
       const long long idx = gx + (long long)N0 * gy;
       const float4 t = vb[idx];
       vv = make_float2(t.x, t.y);
       float2 diag;
       fine_cd<ORDER>(c, idx, gx, gy, cc, diag);
-      xx = cscale(cmul(crecip(diag), vv), w1) + sp[q];
+      di = rcp_c(diag);
+      xx = cscale(cmul(di, vv), w1) + sp[q];
     }
     sv[q] = vv;
     sc[q] = cc;
     sx[q] = xx;
+    sp[q] = di;
   }
   __syncthreads();
   for (int q = threadIdx.x; q < kFX * kFY; q += kThreads) {
@@ -373,7 +376,7 @@ __global__ void __launch_bounds__(kThreads) fine_up_kernel(const Cycle2D c, cons
     const int li = (tx + 1) + NX * (ty + 1);
     const float2 diag = fine_diag_of<ORDER>(c, sc[li]);
     const float2 res = sv[li] - fine_apply_tile<ORDER>(sx, sc, li, NX, ih2, diag);
-    z[rhs * g.size + gx + (long long)N0 * gy] = sx[li] + cscale(cmul(crecip(diag), res), w1);
+    z[rhs * g.size + gx + (long long)N0 * gy] = sx[li] + cscale(cmul(sp[li], res), w1);
   }
 }
 

@@ -384,6 +384,100 @@ __global__ void __launch_bounds__(kThreads) arnoldi_normalize_df_kernel(
   }
 }
 
+// Arnoldi step for a basis of NV <= kMaxNV vectors with register accumulators.
+// First CGS pass: w = H z in double-float, h1 = V^H w from the high parts in FP32.  The
+// second pass (update kernel, double-float) orthogonalises against whatever the first
+// pass left, so h1 needs only to remove the bulk of w's components along V; the stored
+// column of the Hessenberg matrix is h1 + h2.
+constexpr int kMaxNV = 10;
+
+template <int NV>
+__global__ void __launch_bounds__(kThreads, 2) arnoldi_matvec_df_t(FineOp op, DfConsts K, const float4* __restrict__ cdf,
+                                                                const float2* __restrict__ z, float4* __restrict__ w,
+                                                                const float4* __restrict__ V, long long vstride,
+                                                                double2* __restrict__ part,
+                                                                unsigned* __restrict__ counter,
+                                                                double2* __restrict__ out) {
+  extern __shared__ double2 sacc[];
+  float4* sdf = reinterpret_cast<float4*>(sacc);
+  const int tid = threadIdx.x;
+  float2 acc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) acc[q] = make_float2(0.f, 0.f);
+  for (long long p = blockIdx.x * (long long)blockDim.x + tid; p < op.g.size; p += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    node_coords(op.g, p, i, j, k);
+    const float4 wv = cdd_store(fine_apply_df(op, cdf, z, p, i, j, k, K.ih2, K.ih2_6, K.inv24));
+    w[p] = wv;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const float4 v = V[q * vstride + p];   // acc += conj(v) w, high parts
+      acc[q].x = fmaf(v.x, wv.x, acc[q].x);
+      acc[q].x = fmaf(v.y, wv.y, acc[q].x);
+      acc[q].y = fmaf(v.x, wv.y, acc[q].y);
+      acc[q].y = fmaf(-v.y, wv.x, acc[q].y);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NV; ++q) sdf[q * blockDim.x + tid] = make_float4(acc[q].x, acc[q].y, 0.f, 0.f);
+  reduce_finish_df(sdf, NV, part, counter, out);
+}
+
+// Second CGS pass: w' = w - V h1 and h2 = V^H w', |w'|^2 (double-float), accumulators in
+// registers (the dot pass re-reads V right after the subtraction read it: L1 hits).
+template <int NV>
+__global__ void __launch_bounds__(kThreads, 2) arnoldi_update_df_t(long long n, float4* __restrict__ w,
+                                                                   const float4* __restrict__ V, long long vstride,
+                                                                   const double2* __restrict__ h1,
+                                                                   double2* __restrict__ part,
+                                                                   unsigned* __restrict__ counter,
+                                                                   double2* __restrict__ out) {
+  extern __shared__ double2 sacc[];
+  float4* sdf = reinterpret_cast<float4*>(sacc);
+  __shared__ float4 sh[NV];
+  const int tid = threadIdx.x;
+  float4 acc[NV + 1];
+#pragma unroll
+  for (int q = 0; q <= NV; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = tid; i < NV; i += blockDim.x) sh[i] = cdd_store(cdd_make(h1[i]));
+  __syncthreads();
+  for (long long p = blockIdx.x * (long long)blockDim.x + tid; p < n; p += (long long)gridDim.x * blockDim.x) {
+    cdd wv = cdd_load(w[p]);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) wv = cdd_sub(wv, cdd_mul(cdd_load(sh[q]), cdd_load(V[q * vstride + p])));
+    const float4 w4 = cdd_store(wv);
+    w[p] = w4;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) df_cmacc(acc[q], V[q * vstride + p], w4);
+    df_cmacc(acc[NV], w4, w4);
+  }
+#pragma unroll
+  for (int q = 0; q <= NV; ++q) sdf[q * blockDim.x + tid] = acc[q];
+  reduce_finish_df(sdf, NV + 1, part, counter, out);
+}
+
+template <int NV>
+int arnoldi_df_launch(int bl, size_t sm, const FineOp& op, const DfConsts& K, const float4* cdf, const float2* z,
+                      float4* w, const float4* V, long long vstride, const KrylovState& st, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(arnoldi_matvec_df_t<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(arnoldi_update_df_t<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  {
+    KernelTimer kt(HELM_K_ARNOLDI_MATVEC, s);
+    arnoldi_matvec_df_t<NV><<<bl, kThreads, sm, s>>>(op, K, cdf, z, w, V, vstride, st.part, st.counter, st.h1);
+    HELM_LAUNCH_CHECK();
+  }
+  {
+    KernelTimer kt(HELM_K_ARNOLDI_UPDATE, s);
+    arnoldi_update_df_t<NV><<<bl, kThreads, sm, s>>>(op.g.size, w, V, vstride, st.h1, st.part, st.counter, st.h2);
+    HELM_LAUNCH_CHECK();
+  }
+  return 0;
+}
+
 // v = r / beta into double-float storage; resets g = (beta, 0, ...)
 __global__ void __launch_bounds__(kThreads) start_cycle_df_kernel(long long n, const double2* __restrict__ r,
                                                                   float4* __restrict__ v, KrylovState st, int m) {
@@ -526,15 +620,26 @@ int k_arnoldi_df(const KrylovState& st, const FineOp& op, const float4* cdf, con
     attr_set = true;
   }
   const DfConsts K = df_consts(op);
-  {
-    KernelTimer kt(HELM_K_ARNOLDI_MATVEC, s);
-    arnoldi_matvec_df_kernel<<<bl, kThreads, sm, s>>>(op, K, cdf, z, w, V, vstride, nv, st.part, st.counter, st.h1);
-    HELM_LAUNCH_CHECK();
-  }
-  {
-    KernelTimer kt(HELM_K_ARNOLDI_UPDATE, s);
-    arnoldi_update_df_kernel<<<bl, kThreads, sm, s>>>(n, w, V, vstride, nv, st.h1, st.part, st.counter, st.h2);
-    HELM_LAUNCH_CHECK();
+  if (nv <= kMaxNV) {
+    int st2 = 0;
+    switch (nv) {
+#define HELM_NV(N) \
+  case N: st2 = arnoldi_df_launch<N>(bl, sm, op, K, cdf, z, w, V, vstride, st, s); break;
+      HELM_NV(1) HELM_NV(2) HELM_NV(3) HELM_NV(4) HELM_NV(5) HELM_NV(6) HELM_NV(7) HELM_NV(8) HELM_NV(9) HELM_NV(10)
+#undef HELM_NV
+    }
+    if (st2) return st2;
+  } else {
+    {
+      KernelTimer kt(HELM_K_ARNOLDI_MATVEC, s);
+      arnoldi_matvec_df_kernel<<<bl, kThreads, sm, s>>>(op, K, cdf, z, w, V, vstride, nv, st.part, st.counter, st.h1);
+      HELM_LAUNCH_CHECK();
+    }
+    {
+      KernelTimer kt(HELM_K_ARNOLDI_UPDATE, s);
+      arnoldi_update_df_kernel<<<bl, kThreads, sm, s>>>(n, w, V, vstride, nv, st.h1, st.part, st.counter, st.h2);
+      HELM_LAUNCH_CHECK();
+    }
   }
   KernelTimer kt(HELM_K_KRYLOV_OTHER, s);
   arnoldi_small_kernel<<<1, 32, 0, s>>>(st, j, st.m);
