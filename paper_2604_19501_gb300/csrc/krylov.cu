@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(kThreads) arnoldi_normalize_df_kernel(
 constexpr int kMaxNV = 10;
 
 template <int NV>
-__global__ void __launch_bounds__(kThreads, 2) arnoldi_matvec_df_t(FineOp op, DfConsts K, const float4* __restrict__ cdf,
+__global__ void __launch_bounds__(kThreads, 4) arnoldi_matvec_df_t(FineOp op, DfConsts K, const float4* __restrict__ cdf,
                                                                 const float2* __restrict__ z, float4* __restrict__ w,
                                                                 const float4* __restrict__ V, long long vstride,
                                                                 double2* __restrict__ part,
