@@ -40,6 +40,9 @@ sys.path.insert(0, ROOT)
 METRIC = "Mdof*solves/s to 1e-6 rel-res"
 UNIT = "Mdof*solves/s"
 FP64_PEAK_TFLOPS = 1.26   # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
+# DRAM read + write bytes of one coarsest-solve launch (sweep_kernel) on the default
+# workload, from one ncu capture of the current kernel (profiles/sweep_kernel_2112_traffic.md)
+SWEEP_TRAFFIC_DEFAULT = 2.99e9 + 54.4e6
 
 
 def parse():
@@ -95,6 +98,12 @@ def workload(args):
         q = workloads.surface_sources(n, args.sources, args.pad, seed=0)
     return dict(n=n, kappa2=kappa2, omega=omega, q=q, order=order, intergrid=ig, alpha3=alpha3,
                 jacobi=jw, pad=args.pad, vmin=vmin)
+
+
+def default_workload(args):
+    """The configuration the sweep traffic figure was captured on."""
+    return (args.n, args.pad, args.ppw, args.method, args.precision, args.cycle, args.sources) == \
+        (2048, 32, 12, "paper", "mixed", "V", 1)
 
 
 def describe(args, wl):
@@ -286,10 +295,24 @@ def kernel_model(info, its, restart, n1, n3):
     cb = 16.0 * info["coarse_entries"] + 6 * 16.0 * n3
     return {
         "coarse": {"flops": 8.0 * info["coarse_entries"], "bytes": cb},
+        "cycle": {"bytes": cycle_bytes(info, n1, n3)},
         "arnoldi_update": {"flops": 8.0 * 2 * nv_avg * n1, "bytes": (32.0 + 16.0 * nv_avg) * n1},
         "arnoldi_norm": {"flops": 8.0 * nv_avg * n1, "bytes": (32.0 + 16.0 * nv_avg) * n1},
         "arnoldi_matvec": {"flops": (8.0 * nv_avg + 40.0) * n1, "bytes": (40.0 + 16.0 * nv_avg) * n1},
     }
+
+
+def cycle_bytes(info, n1, n3):
+    """Algorithmic HBM bytes of one fused 2D cycle (levels 1-2 and the level-3 transfers):
+    fine down reads v (16 B) and kappa (4 B) per fine node and writes r2 (8 B per level-2
+    node); level-2 residual and level-2 up each read the stencil (8 B per coefficient),
+    1/diag and r2 and write 8 B per level-2 node, s2 is read once more by the restriction;
+    the restriction writes and the up pass reads 16 B per level-3 node; fine up reads v,
+    kappa and y2 and writes z (8 B per fine node)."""
+    n2 = info["nodes2"]
+    ncoef = (2 * info["radius2"] + 1) ** 2
+    level2 = 8 + 2 * (8 * ncoef + 8 + 8 + 8) + 8 + 8
+    return n1 * (20 + 20 + 8) + n2 * level2 + n3 * 32
 
 
 def our_arm(args):
@@ -390,6 +413,18 @@ def our_arm(args):
                     "algorithmic_bytes_per_launch": model[dom]["bytes"], "launches_timed": cnt,
                     "peak_note": "FP64 ALU peak: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz"}
 
+    if roof is not None and dom == "coarse" and default_workload(args):
+        roof["traffic"] = SWEEP_TRAFFIC_DEFAULT
+    # cycle kernels (fine, level-2, transfers) against the HBM roofline, per cycle
+    cyc = None
+    if info.get("double_float") and all(k in prof for k in ("fine", "stencil", "transfer")):
+        n_cyc = prof["fine"][1] / 2.0   # two fine passes per cycle
+        t_cyc = sum(prof[k][0] for k in ("fine", "stencil", "transfer")) / 1e3 / n_cyc
+        gbs = model["cycle"]["bytes"] / t_cyc / 1e9
+        peak = hbm_peak_gbs()
+        cyc = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+               "algorithmic_bytes_per_cycle": model["cycle"]["bytes"], "ms_per_cycle": t_cyc * 1e3}
+
     # ---- CPU oracle on a bounded sample
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -411,6 +446,7 @@ def our_arm(args):
         "gpu_launches": launches,
         "roofline": roof,
         "kernels": kernels,
+        "cycle_roofline": cyc,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
