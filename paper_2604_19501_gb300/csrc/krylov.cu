@@ -218,6 +218,26 @@ __global__ void __launch_bounds__(kThreads) solution_update_kernel(long long n, 
   }
 }
 
+// x += Z y for a c64 basis Z: the correction sum_q y_q z_q is formed in double-float (z_q
+// are exact floats, y_q rounded to about 48 bits) and added to x in FP64.
+__global__ void __launch_bounds__(kThreads) solution_update_df_kernel(long long n, double2* __restrict__ x,
+                                                                      const float2* __restrict__ Z,
+                                                                      long long zstride, int k,
+                                                                      const double2* __restrict__ y) {
+  __shared__ float4 sy[64];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sy[i] = cdd_store(cdd_make(y[i]));
+  __syncthreads();
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    cdd acc = cdd_zero();
+    for (int q = 0; q < k; ++q) acc = cdd_add(acc, cdd_mulf(cdd_load(sy[q]), Z[q * zstride + p]));
+    double2 xv = x[p];
+    xv.x += (double)acc.re.hi + (double)acc.re.lo;
+    xv.y += (double)acc.im.hi + (double)acc.im.lo;
+    x[p] = xv;
+  }
+}
+
 // r = b - H x (FP64) and ||r||^2 (in out[0].x)
 __global__ void __launch_bounds__(kThreads) true_residual_kernel(FineOp op, const double* __restrict__ kap,
                                                                  const double2* __restrict__ b,
@@ -673,7 +693,7 @@ int k_update_solution(const KrylovState& st, long long n, double2* x, const void
   if (zp == P64)
     solution_update_kernel<double><<<grid_blocks(n), kThreads, 0, s>>>(n, x, (const double2*)Z, zstride, k, st.y);
   else
-    solution_update_kernel<float><<<grid_blocks(n), kThreads, 0, s>>>(n, x, (const float2*)Z, zstride, k, st.y);
+    solution_update_df_kernel<<<grid_blocks(n), kThreads, 0, s>>>(n, x, (const float2*)Z, zstride, k, st.y);
   HELM_LAUNCH_CHECK();
   return 0;
 }
