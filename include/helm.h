@@ -234,6 +234,22 @@ typedef enum {
 /* *value = the quantity selected by key. */
 int helm_info(const helm_ctx* c, int key, long long* value);
 
+/* Right-hand-side blocking of helm_solve / helm_adjoint_grad (the batched cycle of the
+ * survey's configuration 4; the paper solves one source at a time).  The context holds
+ * FGMRES state for at most max_rhs right-hand sides per block (helm_opts.max_rhs).
+ *
+ * helm_set_block: solve in blocks of `block` (1 <= block <= max_rhs).
+ *
+ * helm_autotune_block: time one FGMRES restart cycle (helm_opts.restart iterations, or
+ * probe_iters if > 0) of blocks of 1, 2, 4, ... up to min(max_rhs, n_rhs) right-hand
+ * sides taken from q (device, c128, [n_rhs][nodes]), pick the size with the least time
+ * per right-hand side and iteration, and set it as the block size.  *best receives it,
+ * ms_per_rhs_iter (optional, caller-owned host array of at least 7 entries) the measured
+ * cost of each candidate in order.  Allocates scratch for the candidate solutions. */
+int helm_set_block(helm_ctx* c, int block);
+int helm_autotune_block(helm_ctx* c, const void* q, int n_rhs, int probe_iters, int* best,
+                        double* ms_per_rhs_iter);
+
 /* ---- Launch timer (tracing) ---- */
 
 /* Kernel classes of the launch timer. */

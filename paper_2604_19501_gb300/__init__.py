@@ -66,6 +66,7 @@ class Solver:
         o.precision = _ffi.PRECISION[precision]
         o.restart = int(restart)
         o.max_rhs = int(max_rhs)
+        self.max_rhs = int(max_rhs)
         o.fuse_cycle = int(bool(fuse_cycle))
         if stream is None:
             import torch
@@ -199,6 +200,28 @@ class Solver:
         check(_lib.helm_get_stencil(self._ctx, level, ctypes.c_void_p(out.ctypes.data), ctypes.byref(r)),
               "helm_get_stencil")
         return out, r.value
+
+    def set_block(self, block):
+        """Solve in FGMRES blocks of ``block`` right-hand sides (<= max_rhs)."""
+        check(_lib.helm_set_block(self._ctx, int(block)), "helm_set_block")
+
+    def autotune_block(self, q, probe_iters=0):
+        """Time one FGMRES restart cycle for blocks of 1, 2, 4, ... right-hand sides of
+        ``q`` (device tensor [n_rhs, ...]) and keep the fastest per right-hand side.
+        Returns (block, {block: ms per right-hand side and iteration})."""
+        n_rhs = self._nrhs(q)
+        best = ctypes.c_int(0)
+        costs = (ctypes.c_double * 7)()
+        check(_lib.helm_autotune_block(self._ctx, _ptr(q), n_rhs, int(probe_iters), ctypes.byref(best), costs),
+              "helm_autotune_block")
+        cap = min(self.max_rhs, n_rhs)
+        cands = []
+        b = 1
+        while b < cap:
+            cands.append(b)
+            b *= 2
+        cands.append(cap)
+        return best.value, {c: costs[i] for i, c in enumerate(cands[:7])}
 
     def coarse_solve(self, b, e=None):
         e = _empty_like(b) if e is None else e

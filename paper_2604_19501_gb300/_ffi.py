@@ -73,6 +73,8 @@ SIGNATURES = {
     "helm_coarse_solve": (_I, [_P, _P, _P, _I]),
     "helm_coarse_solve_noalloc": (_I, [_P, _P, _P, _I]),
     "helm_cycle": (_I, [_P, _P, _P, _I]),
+    "helm_set_block": (_I, [_P, _I]),
+    "helm_autotune_block": (_I, [_P, _P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "helm_coarse_plan": (_I, [_I, ctypes.POINTER(_I), _I, _I, _I, _I, ctypes.POINTER(ctypes.c_longlong)]),
     "helm_launch_count": (ctypes.c_longlong, [_P]),
     "helm_info": (_I, [_P, _I, ctypes.POINTER(ctypes.c_longlong)]),

@@ -830,6 +830,73 @@ int helm_coarse_plan(int dim, const int n_nodes[3], int radius, int leaf_max, in
 
 long long helm_launch_count(const helm_ctx* c) { return c ? c->launches : 0; }
 
+int helm_set_block(helm_ctx* c, int block) {
+  if (!c) return fail(HELM_EINVAL, "null context");
+  if (block < 1 || block > (int)c->ks.size()) return fail(HELM_EINVAL, "block must be in [1, max_rhs]");
+  c->block = block;
+  return HELM_OK;
+}
+
+int helm_autotune_block(helm_ctx* c, const void* q, int n_rhs, int probe_iters, int* best, double* ms_per_rhs_iter) {
+  if (!c || !q || !best) return fail(HELM_EINVAL, "null argument");
+  if (n_rhs < 1) return fail(HELM_EINVAL, "n_rhs must be >= 1");
+  if (!is_device_ptr(q)) return fail(HELM_EINVAL, "helm_autotune_block takes a device pointer");
+  LaunchScope scope(c);
+  const int iters = probe_iters > 0 ? probe_iters : c->o.restart;
+  const int cap = std::min((int)c->ks.size(), n_rhs);
+  const long long n = c->g[0].size;
+  if ((long long)cap * n > c->stage_cap) {
+    cudaFree(c->stage);
+    c->stage = nullptr;
+    c->stage_cap = 0;
+    if (int st = dmalloc(&c->stage, (long long)cap * n * sizeof(double2))) return st;
+    c->stage_cap = (long long)cap * n;
+  }
+  std::vector<int> cands;
+  for (int b = 1; b < cap; b *= 2) cands.push_back(b);
+  cands.push_back(cap);
+  cudaEvent_t e0, e1;
+  HELM_CUDA_TRY(cudaEventCreate(&e0));
+  HELM_CUDA_TRY(cudaEventCreate(&e1));
+  std::vector<helm_stats> st(cap);
+  double best_cost = 0.0;
+  int best_b = 1;
+  int status = HELM_OK;
+  const int saved = c->block;
+  for (size_t i = 0; i < cands.size(); ++i) {
+    const int b = cands[i];
+    c->block = b;
+    // a first run allocates what a block of this size needs; the second is timed.  A
+    // tolerance of zero keeps every right-hand side iterating for exactly `iters` steps.
+    for (int rep = 0; rep < 2 && status == HELM_OK; ++rep) {
+      if (rep == 1) cudaEventRecord(e0, c->s);
+      status = fgmres_block(c, (const double2*)q, c->stage, b, 0.0, iters, st.data());
+      if (rep == 1) cudaEventRecord(e1, c->s);
+    }
+    if (status != HELM_OK) break;
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      status = fail(HELM_ECUDA, "autotune timing failed");
+      break;
+    }
+    const double cost = ms / ((double)b * iters);
+    if (ms_per_rhs_iter && i < 7) ms_per_rhs_iter[i] = cost;
+    if (i == 0 || cost < best_cost) {
+      best_cost = cost;
+      best_b = b;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status != HELM_OK) {
+    c->block = saved;
+    return status;
+  }
+  c->block = best_b;
+  *best = best_b;
+  return HELM_OK;
+}
+
 int helm_info(const helm_ctx* c, int key, long long* value) {
   if (!c || !value) return fail(HELM_EINVAL, "null argument");
   switch (key) {

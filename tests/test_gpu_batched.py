@@ -57,3 +57,25 @@ def test_block_adjoint_equals_single():
     assert torch.equal(out[0][0], out[1][0])
     assert torch.equal(out[0][1], out[1][1])
     assert torch.equal(out[0][2], out[1][2])
+
+
+def test_autotune_block_picks_a_candidate_and_keeps_results():
+    """The RHS-block autotuner times blocks of 1, 2, 4, ... and keeps the fastest; the
+    solves that follow are those of any block size (identical per right-hand side)."""
+    c = Case((64, 64), abc=6, alpha3=1.0045, G_ppw=12, order="4th", intergrid="cubic", seed=5)
+    q = _sources(c, 6, 8)
+    qd = torch.from_numpy(q).cuda()
+    s = c.solver(max_rhs=4, precision="mixed", jacobi_w=(0.89, 0.89))
+    best, costs = s.autotune_block(qd)
+    assert best in (1, 2, 4) and set(costs) == {1, 2, 4}
+    assert all(v > 0 for v in costs.values())
+    assert costs[best] == min(costs.values())
+    pb, stb = s.solve(qd, tol=1e-8, maxit=300)
+    s.set_block(1)
+    p1, st1 = s.solve(qd, tol=1e-8, maxit=300)
+    torch.cuda.synchronize()
+    assert [a["iterations"] for a in stb] == [a["iterations"] for a in st1]
+    assert torch.equal(pb, p1)
+    with pytest.raises(Exception):
+        s.set_block(5)
+    s.close()
