@@ -84,6 +84,12 @@ typedef struct {
                              passes (fine down, level-2 residual, restriction to level 3,
                              level-2 up, fine up); 0: one kernel per step.  Other
                              configurations always take one kernel per step. */
+  int graphs;             /* 1: helm_solve / helm_adjoint_grad replay each FGMRES iteration (the
+                             block's cycle, Arnoldi kernels and the read-back of the
+                             convergence scalars) as a CUDA graph, captured on the second
+                             use of each (iteration, block, active set); 0 (default): plain
+                             launches.  Not while the launch timer is enabled.  If capture
+                             fails the context keeps plain launches (HELM_INFO_GRAPHS = -1). */
 } helm_opts;
 
 /* Per-solve statistics, one entry per right-hand side. */
@@ -228,7 +234,8 @@ typedef enum {
   HELM_INFO_COARSE_FRONTS = 6,       /* fronts of the nested-dissection tree */
   HELM_INFO_COARSE_LEVELS = 7,       /* levels of the nested-dissection tree */
   HELM_INFO_COARSE_BWD_ENTRIES = 8,  /* complex entries the backward sweep reads per solve */
-  HELM_INFO_DOUBLE_FLOAT = 9         /* 1 if the coarsest factors and Krylov basis are double-float */
+  HELM_INFO_DOUBLE_FLOAT = 9,        /* 1 if the coarsest factors and Krylov basis are double-float */
+  HELM_INFO_GRAPHS = 10              /* CUDA graphs instantiated (helm_opts.graphs); -1 after a failed capture */
 } helm_info_key;
 
 /* *value = the quantity selected by key. */

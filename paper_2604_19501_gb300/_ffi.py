@@ -13,7 +13,7 @@ SMOOTHER = {"jacobi": 0, "redblack": 1, "rb": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 DTYPE = {"c128": 0, "c64": 1}
 INFO_KEYS = ["nodes1", "nodes2", "nodes3", "radius2", "radius3", "coarse_entries", "coarse_fronts",
-             "coarse_levels", "coarse_bwd_entries", "double_float"]
+             "coarse_levels", "coarse_bwd_entries", "double_float", "graphs"]
 KERNEL_CLASSES = ["fine", "stencil", "transfer", "coarse", "arnoldi_matvec", "arnoldi_update",
                   "arnoldi_norm", "krylov_other", "setup"]
 
@@ -41,6 +41,7 @@ class HelmOpts(ctypes.Structure):
         ("max_rhs", ctypes.c_int),
         ("stream", ctypes.c_void_p),
         ("fuse_cycle", ctypes.c_int),
+        ("graphs", ctypes.c_int),
     ]
 
 

@@ -2,6 +2,10 @@
 // the 3-level cycle (Algorithm TwoGrid applied recursively, Sec. 2) and the FGMRES
 // driver (Sec. 5).
 #include <cmath>
+#include <functional>
+#include <map>
+#include <set>
+#include <tuple>
 #include <cstring>
 #include <string>
 #include <utility>
@@ -64,6 +68,15 @@ struct helm_ctx {
   // staging for host buffers
   double2* stage = nullptr;
   long long stage_cap = 0;
+  // CUDA graphs of FGMRES iterations, by (iteration, block size, active right-hand sides)
+  struct GraphEntry {
+    cudaGraphExec_t exec;
+    long long launches;   // kernels in the graph (for the launch count)
+  };
+  std::map<std::tuple<int, int, unsigned long long>, GraphEntry> graphs;
+  std::set<std::tuple<int, int, unsigned long long>> graph_seen;
+  std::pair<int, int> graph_caps{-1, -1};   // workspace capacities the graphs were captured with
+  bool graphs_broken = false;
   long long launches = 0;
   int* d_bad = nullptr;
   LaunchTimer timer;
@@ -287,6 +300,56 @@ int sync_scal(helm_ctx* c, int B) {
   return 0;
 }
 
+void drop_graphs(helm_ctx* c) {
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.second.exec);
+  c->graphs.clear();
+  c->graph_seen.clear();
+}
+
+// Issues one FGMRES iteration's work (issue()), as plain launches or as a CUDA graph:
+// a key is run plainly on first use (which also makes every allocation it needs), captured
+// and replayed from its second use on.  Graphs are dropped when workspaces were
+// reallocated since their capture; a failed capture leaves the context on plain launches.
+int run_iteration(helm_ctx* c, const std::tuple<int, int, unsigned long long>& key, const std::function<int()>& issue) {
+  if (!c->o.graphs || c->graphs_broken || c->timer.mask != 0) return issue();
+  const std::pair<int, int> caps{c->rhs_cap, c->cs.rhs_cap};
+  if (caps != c->graph_caps) {
+    drop_graphs(c);
+    c->graph_caps = caps;
+  }
+  auto it = c->graphs.find(key);
+  if (it != c->graphs.end()) {
+    HELM_CUDA_TRY(cudaGraphLaunch(it->second.exec, c->s));
+    c->launches += it->second.launches;
+    return 0;
+  }
+  if (!c->graph_seen.count(key)) {
+    c->graph_seen.insert(key);
+    return issue();
+  }
+  const long long before = c->launches;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  bool ok = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    const int st = issue();
+    ok = cudaStreamEndCapture(c->s, &g) == cudaSuccess && st == 0 && g != nullptr &&
+         cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+  }
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    // the work was only recorded, not run: run it plainly and stay on plain launches
+    cudaGetLastError();
+    c->graphs_broken = true;
+    drop_graphs(c);
+    c->launches = before;
+    return issue();
+  }
+  c->graphs[key] = helm_ctx::GraphEntry{ex, c->launches - before};
+  HELM_CUDA_TRY(cudaGraphLaunch(ex, c->s));
+  return 0;
+}
+
 // FGMRES(m) for a block of B right-hand sides (device pointers, B * nodes each).  The
 // cycle and the coarsest solve run once per iteration for the whole block (operators
 // read once per block); each right-hand side keeps its own Arnoldi basis, Givens
@@ -337,23 +400,35 @@ int fgmres_block(helm_ctx* c, const double2* q, double2* p, int B, double tol, i
       }
     }
     for (int j = 0; j < m; ++j) {
-      if (df) {
-        if (int st = run_cycle(c, Vd(j, 0), P_DF, Zp(j, 0), zp, B)) return st;
-      } else if (int st = run_cycle(c, Vp(j, 0), P64, Zp(j, 0), zp, B)) {
-        return st;
-      }
-      for (int r = 0; r < B; ++r) {
-        if (!act[r]) continue;
+      // the iteration's device work: cycle for the block, Arnoldi steps, scalars to the host
+      auto issue = [&]() -> int {
         if (df) {
-          if (int st = k_arnoldi_df(c->ks[r], c->fine, c->cdf, (const float2*)Zp(j, r), reinterpret_cast<float4*>(c->w) + (size_t)r * n,
-                                    Vd(0, r), vstride, j, c->s))
-            return st;
-        } else if (int st = k_arnoldi(c->ks[r], c->fine, c->kap64, Zp(j, r), zp, c->w + (size_t)r * n, Vp(0, r),
-                                      vstride, j, c->s)) {
+          if (int st = run_cycle(c, Vd(j, 0), P_DF, Zp(j, 0), zp, B)) return st;
+        } else if (int st = run_cycle(c, Vp(j, 0), P64, Zp(j, 0), zp, B)) {
           return st;
         }
+        for (int r = 0; r < B; ++r) {
+          if (!act[r]) continue;
+          if (df) {
+            if (int st = k_arnoldi_df(c->ks[r], c->fine, c->cdf, (const float2*)Zp(j, r),
+                                      reinterpret_cast<float4*>(c->w) + (size_t)r * n, Vd(0, r), vstride, j, c->s))
+              return st;
+          } else if (int st = k_arnoldi(c->ks[r], c->fine, c->kap64, Zp(j, r), zp, c->w + (size_t)r * n, Vp(0, r),
+                                        vstride, j, c->s)) {
+            return st;
+          }
+        }
+        HELM_CUDA_TRY(cudaMemcpyAsync(c->h_scal, c->d_scal, sizeof(double) * KS_COUNT * B, cudaMemcpyDeviceToHost, c->s));
+        return 0;
+      };
+      unsigned long long mask = 0;
+      for (int r = 0; r < B && r < 64; ++r) mask |= (unsigned long long)(act[r] != 0) << r;
+      if (B > 64) {
+        if (int st = issue()) return st;
+      } else if (int st = run_iteration(c, std::make_tuple(j, B, mask), issue)) {
+        return st;
       }
-      if (int st = sync_scal(c, B)) return st;
+      HELM_CUDA_TRY(cudaStreamSynchronize(c->s));
       int nact = 0;
       for (int r = 0; r < B; ++r) {
         if (!act[r]) continue;
@@ -436,6 +511,7 @@ int helm_default_opts(helm_opts* o) {
   o->max_rhs = 1;
   o->stream = nullptr;
   o->fuse_cycle = 1;
+  o->graphs = 0;
   return HELM_OK;
 }
 
@@ -618,6 +694,7 @@ int helm_destroy(helm_ctx* c) {
   if (!c) return HELM_OK;
   if (c->s) cudaStreamSynchronize(c->s);
   else cudaDeviceSynchronize();
+  drop_graphs(c);
   free_workspaces(c);
   coarse_free(c->cs);
   for (auto& k : c->ks) krylov_free(k);
@@ -910,6 +987,7 @@ int helm_info(const helm_ctx* c, int key, long long* value) {
     case HELM_INFO_COARSE_LEVELS: *value = c->cs.nlevels; break;
     case HELM_INFO_COARSE_BWD_ENTRIES: *value = c->cs.bwd_entries; break;
     case HELM_INFO_DOUBLE_FLOAT: *value = c->cs.df ? 1 : 0; break;
+    case HELM_INFO_GRAPHS: *value = c->graphs_broken ? -1 : (long long)c->graphs.size(); break;
     default: return fail(HELM_EINVAL, "unknown info key");
   }
   return HELM_OK;

@@ -79,3 +79,27 @@ def test_autotune_block_picks_a_candidate_and_keeps_results():
     with pytest.raises(Exception):
         s.set_block(5)
     s.close()
+
+
+@pytest.mark.parametrize("max_rhs,prec", [(1, "mixed"), (3, "mixed"), (1, "fp64")])
+def test_graph_replay_equals_plain_launches(max_rhs, prec):
+    """helm_opts.graphs: three solves in a row (plain, capture, replay) give the plain
+    solve's result bit for bit; the context reports its graphs, or -1 if the capture
+    was refused and it stayed on plain launches."""
+    c = Case((64, 64), abc=6, alpha3=1.0045, G_ppw=12, order="4th", intergrid="cubic", seed=7)
+    q = _sources(c, 3, 9) if max_rhs > 1 else workloads.point_source(c.n)
+    qd = torch.from_numpy(q).cuda()
+    s0 = c.solver(max_rhs=max_rhs, precision=prec, jacobi_w=(0.89, 0.89))
+    p0, st0 = s0.solve(qd, tol=1e-8, maxit=300)
+    torch.cuda.synchronize()
+    sg = c.solver(max_rhs=max_rhs, precision=prec, jacobi_w=(0.89, 0.89), graphs=True)
+    for _ in range(3):
+        pg, stg = sg.solve(qd, tol=1e-8, maxit=300)
+        torch.cuda.synchronize()
+        assert [a["iterations"] for a in stg] == [a["iterations"] for a in st0]
+        assert torch.equal(pg, p0)
+    ng = sg.info()["graphs"]
+    print("graphs instantiated:", ng)
+    assert ng != 0
+    s0.close()
+    sg.close()
