@@ -68,6 +68,10 @@ def parse():
     ap.add_argument("--sources", type=int, default=1,
                     help="right-hand sides per step: 1 = the centre source; K > 1 = K seeded surface sources")
     ap.add_argument("--block", type=int, default=0, help="right-hand sides per FGMRES block (0 = all)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the FGMRES block size with helm_autotune_block before the warm-up")
+    ap.add_argument("--graphs", action="store_true",
+                    help="replay FGMRES iterations as CUDA graphs (the launch timer stays off)")
     return ap.parse_args()
 
 
@@ -334,7 +338,7 @@ def our_arm(args):
     s = Solver(kap, wl["n"], wl["omega"], abc_width=wl["pad"], alpha3=wl["alpha3"], stencil=wl["order"],
                intergrid=wl["intergrid"], cycle=args.cycle, jacobi_w=(wl["jacobi"], wl["jacobi"]),
                precision=args.precision, restart=args.restart, stream=stream.cuda_stream,
-               max_rhs=max(1, args.block or args.sources))
+               max_rhs=max(1, args.block or args.sources), graphs=args.graphs)
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
     info = s.info()
@@ -342,14 +346,19 @@ def our_arm(args):
     q = torch.from_numpy(wl["q"]).to(dev)
     p = torch.empty_like(q)
     stats = None
+    tuned = None
+    if args.autotune:
+        tuned = s.autotune_block(q)
+        log(f"autotuned block: {tuned[0]} (ms per rhs and iteration: {tuned[1]})")
     for _ in range(args.warmup):
         p, stats = s.solve(q, p, tol=args.tol, maxit=args.maxit)
     its = stats[0]["iterations"] if stats else None
     log(f"warm-up: {stats}")
 
     # ---- device-resident timed region
-    s.timer_enable(["coarse", "arnoldi_update", "arnoldi_matvec", "arnoldi_norm", "fine", "stencil",
-                    "transfer", "krylov_other"])
+    if not args.graphs:
+        s.timer_enable(["coarse", "arnoldi_update", "arnoldi_matvec", "arnoldi_norm", "fine", "stencil",
+                        "transfer", "krylov_other"])
     sampler = ClockSampler(local).start()
     l0 = s.launches
     barrier(world)
@@ -392,7 +401,7 @@ def our_arm(args):
     total_ms = t_dev * 1e3
     kernels = {k: {"ms_per_solve": v[0] / (args.steps * nsrc), "launches_per_solve": v[1] / (args.steps * nsrc),
                    "share": v[0] / total_ms} for k, v in prof.items() if v[1]}
-    dom = max(kernels, key=lambda k: kernels[k]["ms_per_solve"])
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_solve"]) if kernels else None
     its_one = its if nsrc == 1 else max(x["iterations"] for x in all_stats[-nsrc:])
     model = kernel_model(info, its_one, args.restart, nodes, info["nodes3"])
     roof = None
@@ -447,6 +456,8 @@ def our_arm(args):
         "roofline": roof,
         "kernels": kernels,
         "cycle_roofline": cyc,
+        "graphs": s.info()["graphs"] if args.graphs else None,
+        "autotuned_block": tuned[0] if tuned else None,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
