@@ -426,7 +426,7 @@ def our_arm(args):
         roof["traffic"] = SWEEP_TRAFFIC_DEFAULT
     # cycle kernels (fine, level-2, transfers) against the HBM roofline, per cycle
     cyc = None
-    if info.get("double_float") and all(k in prof for k in ("fine", "stencil", "transfer")):
+    if info.get("double_float") and all(prof.get(k, (0, 0))[1] for k in ("fine", "stencil", "transfer")):
         n_cyc = prof["fine"][1] / 2.0   # two fine passes per cycle
         t_cyc = sum(prof[k][0] for k in ("fine", "stencil", "transfer")) / 1e3 / n_cyc
         gbs = model["cycle"]["bytes"] / t_cyc / 1e9

@@ -77,6 +77,7 @@ struct helm_ctx {
   std::set<std::tuple<int, int, unsigned long long>> graph_seen;
   std::pair<int, int> graph_caps{-1, -1};   // workspace capacities the graphs were captured with
   bool graphs_broken = false;
+  cudaStream_t cap_stream = nullptr;         // capture stream (the context's stream may be the legacy one)
   long long launches = 0;
   int* d_bad = nullptr;
   LaunchTimer timer;
@@ -330,10 +331,16 @@ int run_iteration(helm_ctx* c, const std::tuple<int, int, unsigned long long>& k
   const long long before = c->launches;
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ex = nullptr;
-  bool ok = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  // The work is recorded on a private stream (the legacy default stream cannot be
+  // captured) and the graph launched on the context's stream, which keeps its order.
+  bool ok = c->cap_stream || cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+  const cudaStream_t user = c->s;
+  if (ok) ok = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
   if (ok) {
+    c->s = c->cap_stream;
     const int st = issue();
-    ok = cudaStreamEndCapture(c->s, &g) == cudaSuccess && st == 0 && g != nullptr &&
+    c->s = user;
+    ok = cudaStreamEndCapture(c->cap_stream, &g) == cudaSuccess && st == 0 && g != nullptr &&
          cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
   }
   if (g) cudaGraphDestroy(g);
@@ -695,6 +702,7 @@ int helm_destroy(helm_ctx* c) {
   if (c->s) cudaStreamSynchronize(c->s);
   else cudaDeviceSynchronize();
   drop_graphs(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   free_workspaces(c);
   coarse_free(c->cs);
   for (auto& k : c->ks) krylov_free(k);
