@@ -88,8 +88,9 @@ typedef struct {
                              block's cycle, Arnoldi kernels and the read-back of the
                              convergence scalars) as a CUDA graph, captured on the second
                              use of each (iteration, block, active set); 0 (default): plain
-                             launches.  Not while the launch timer is enabled.  If capture
-                             fails the context keeps plain launches (HELM_INFO_GRAPHS = -1). */
+                             launches.  The launch timer reads the events a graph records
+                             after each replay.  If capture fails the context keeps plain
+                             launches (HELM_INFO_GRAPHS = -1). */
 } helm_opts;
 
 /* Per-solve statistics, one entry per right-hand side. */

@@ -71,11 +71,13 @@ struct helm_ctx {
   // CUDA graphs of FGMRES iterations, by (iteration, block size, active right-hand sides)
   struct GraphEntry {
     cudaGraphExec_t exec;
-    long long launches;   // kernels in the graph (for the launch count)
+    long long launches;                          // kernels in the graph (for the launch count)
+    std::vector<LaunchTimer::Pending> timed;     // launch-timer event pairs recorded by the graph
   };
   std::map<std::tuple<int, int, unsigned long long>, GraphEntry> graphs;
   std::set<std::tuple<int, int, unsigned long long>> graph_seen;
-  std::pair<int, int> graph_caps{-1, -1};   // workspace capacities the graphs were captured with
+  std::tuple<int, int, unsigned> graph_caps{-1, -1, 0u};   // workspace capacities and timer mask at capture
+  const std::vector<LaunchTimer::Pending>* graph_timed = nullptr;   // pairs of the graph last launched
   bool graphs_broken = false;
   cudaStream_t cap_stream = nullptr;         // capture stream (the context's stream may be the legacy one)
   long long launches = 0;
@@ -302,18 +304,40 @@ int sync_scal(helm_ctx* c, int B) {
 }
 
 void drop_graphs(helm_ctx* c) {
-  for (auto& g : c->graphs) cudaGraphExecDestroy(g.second.exec);
+  for (auto& g : c->graphs) {
+    cudaGraphExecDestroy(g.second.exec);
+    for (auto& p : g.second.timed) {
+      c->timer.pool.push_back(p.a);
+      c->timer.pool.push_back(p.b);
+    }
+  }
   c->graphs.clear();
   c->graph_seen.clear();
+  c->graph_timed = nullptr;
+}
+
+// After the stream has completed a replayed graph: add its launch-timer pairs.
+void collect_graph_timing(helm_ctx* c) {
+  if (!c->graph_timed) return;
+  for (const auto& p : *c->graph_timed) {
+    float ms = 0.f;
+    if ((c->timer.mask >> p.cls & 1u) && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->timer.total_ms[p.cls] += ms;
+      c->timer.count[p.cls] += 1;
+    }
+  }
+  c->graph_timed = nullptr;
 }
 
 // Issues one FGMRES iteration's work (issue()), as plain launches or as a CUDA graph:
 // a key is run plainly on first use (which also makes every allocation it needs), captured
 // and replayed from its second use on.  Graphs are dropped when workspaces were
-// reallocated since their capture; a failed capture leaves the context on plain launches.
+// reallocated or the launch timer's classes changed since their capture; the timer's event
+// pairs recorded by a graph are read back after every replay (collect_graph_timing).  A
+// failed capture leaves the context on plain launches.
 int run_iteration(helm_ctx* c, const std::tuple<int, int, unsigned long long>& key, const std::function<int()>& issue) {
-  if (!c->o.graphs || c->graphs_broken || c->timer.mask != 0) return issue();
-  const std::pair<int, int> caps{c->rhs_cap, c->cs.rhs_cap};
+  if (!c->o.graphs || c->graphs_broken) return issue();
+  const std::tuple<int, int, unsigned> caps{c->rhs_cap, c->cs.rhs_cap, c->timer.mask};
   if (caps != c->graph_caps) {
     drop_graphs(c);
     c->graph_caps = caps;
@@ -322,6 +346,7 @@ int run_iteration(helm_ctx* c, const std::tuple<int, int, unsigned long long>& k
   if (it != c->graphs.end()) {
     HELM_CUDA_TRY(cudaGraphLaunch(it->second.exec, c->s));
     c->launches += it->second.launches;
+    c->graph_timed = &it->second.timed;
     return 0;
   }
   if (!c->graph_seen.count(key)) {
@@ -336,6 +361,8 @@ int run_iteration(helm_ctx* c, const std::tuple<int, int, unsigned long long>& k
   bool ok = c->cap_stream || cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
   const cudaStream_t user = c->s;
   if (ok) ok = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  const size_t p0 = c->timer.pending.size();
+  std::vector<LaunchTimer::Pending> timed;
   if (ok) {
     c->s = c->cap_stream;
     const int st = issue();
@@ -343,17 +370,28 @@ int run_iteration(helm_ctx* c, const std::tuple<int, int, unsigned long long>& k
     ok = cudaStreamEndCapture(c->cap_stream, &g) == cudaSuccess && st == 0 && g != nullptr &&
          cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
   }
+  // timer pairs issued during the capture belong to the graph, not to the plain timeline
+  if (c->timer.pending.size() > p0) {
+    timed.assign(c->timer.pending.begin() + p0, c->timer.pending.end());
+    c->timer.pending.resize(p0);
+  }
   if (g) cudaGraphDestroy(g);
   if (!ok) {
     // the work was only recorded, not run: run it plainly and stay on plain launches
     cudaGetLastError();
+    for (auto& p : timed) {
+      c->timer.pool.push_back(p.a);
+      c->timer.pool.push_back(p.b);
+    }
     c->graphs_broken = true;
     drop_graphs(c);
     c->launches = before;
     return issue();
   }
-  c->graphs[key] = helm_ctx::GraphEntry{ex, c->launches - before};
+  auto& entry = c->graphs[key];
+  entry = helm_ctx::GraphEntry{ex, c->launches - before, std::move(timed)};
   HELM_CUDA_TRY(cudaGraphLaunch(ex, c->s));
+  c->graph_timed = &entry.timed;
   return 0;
 }
 
@@ -436,6 +474,7 @@ int fgmres_block(helm_ctx* c, const double2* q, double2* p, int B, double tol, i
         return st;
       }
       HELM_CUDA_TRY(cudaStreamSynchronize(c->s));
+      collect_graph_timing(c);
       int nact = 0;
       for (int r = 0; r < B; ++r) {
         if (!act[r]) continue;

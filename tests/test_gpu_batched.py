@@ -93,6 +93,7 @@ def test_graph_replay_equals_plain_launches(max_rhs, prec):
     p0, st0 = s0.solve(qd, tol=1e-8, maxit=300)
     torch.cuda.synchronize()
     sg = c.solver(max_rhs=max_rhs, precision=prec, jacobi_w=(0.89, 0.89), graphs=True)
+    sg.timer_enable(["coarse", "arnoldi_matvec"])
     for _ in range(3):
         pg, stg = sg.solve(qd, tol=1e-8, maxit=300)
         torch.cuda.synchronize()
@@ -100,6 +101,10 @@ def test_graph_replay_equals_plain_launches(max_rhs, prec):
         assert torch.equal(pg, p0)
     ng = sg.info()["graphs"]
     print("graphs instantiated:", ng)
-    assert ng != 0
+    assert ng > 0
+    # the launch timer sees every iteration, replayed or not: one coarsest solve per iteration
+    prof = sg.timer_read()
+    assert prof["coarse"][1] == 3 * max(a["iterations"] for a in st0)
+    assert prof["coarse"][0] > 0
     s0.close()
     sg.close()
