@@ -321,9 +321,12 @@ void collect_graph_timing(helm_ctx* c) {
   if (!c->graph_timed) return;
   for (const auto& p : *c->graph_timed) {
     float ms = 0.f;
-    if ((c->timer.mask >> p.cls & 1u) && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+    if (!(c->timer.mask >> p.cls & 1u)) continue;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       c->timer.total_ms[p.cls] += ms;
       c->timer.count[p.cls] += 1;
+    } else {
+      cudaGetLastError();   // an unreadable pair is skipped, not left as the next launch's error
     }
   }
   c->graph_timed = nullptr;

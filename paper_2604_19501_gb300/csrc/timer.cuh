@@ -21,6 +21,16 @@ struct LaunchTimer {
 
 extern thread_local LaunchTimer* g_timer;
 
+// Records an event on s; while s is being captured into a CUDA graph the record becomes
+// a graph node (an external record), so the graph's replays record the event.
+inline void record_event(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, s);
+}
+
 // Records an event pair around the launches issued during its lifetime.
 struct KernelTimer {
   LaunchTimer* t;
@@ -30,7 +40,7 @@ struct KernelTimer {
   KernelTimer(int cls_, cudaStream_t s_) : t(g_timer), cls(cls_), s(s_) {
     if (t && (t->mask >> cls & 1u)) {
       a = t->get();
-      cudaEventRecord(a, s);
+      record_event(a, s);
     } else {
       t = nullptr;
     }
@@ -38,7 +48,7 @@ struct KernelTimer {
   ~KernelTimer() {
     if (!t) return;
     cudaEvent_t b = t->get();
-    cudaEventRecord(b, s);
+    record_event(b, s);
     t->pending.push_back({cls, a, b});
     if (t->pending.size() >= 4096) t->resolve();
   }
