@@ -14,6 +14,13 @@ Oracle module (test infrastructure only).
 Reading: the real shift scales k^2 = omega^2 kappa^2 only, not the absorbing
 term i gamma k^2 (the literal Eq. realShift with H_h including the layer).
 
+RS-CGC + CSLP (Sec. 5, second experiment: the combination suggested for 10 points
+per wavelength, with a complex shift of 0.03 k^2): with beta > 0 the cycle's
+operators are built from the complex-shifted fine operator
+H_h^beta = -Lap_h - k^2 (1 - i gamma - i beta) M_h = H_h + i beta K,
+the shift entering like the absorbing term; the outer (Krylov) operator stays H_h.
+The real shift of level 3 then acts on H_h^beta.
+
 Transfers per level ("intergrid"):
   "fw"     full weighting / bilinear on both levels;
   "cubic"  Eq. intergrid on both levels;
@@ -41,11 +48,13 @@ class Hierarchy:
     Parameters: ``grid`` (:class:`Grid`), ``kappa2`` slowness squared on the
     nodes, ``omega`` angular frequency, ``gamma`` absorbing-layer profile,
     ``order`` "2nd" | "4th", ``intergrid`` "fw" | "cubic" | "levdep",
-    ``alpha2`` / ``alpha3`` real shifts of levels 2 and 3.
+    ``alpha2`` / ``alpha3`` real shifts of levels 2 and 3, ``beta`` the complex
+    shift of the cycle (0: plain RS-CGC).  ``A[0]`` is the cycle's fine operator,
+    ``A_outer`` the operator the outer iteration solves.
     """
 
     def __init__(self, grid, kappa2, omega, gamma, order="2nd", intergrid="fw",
-                 alpha2=1.0, alpha3=1.0):
+                 alpha2=1.0, alpha3=1.0, beta=0.0):
         self.grids = [grid, grid.coarse(), grid.coarse().coarse()]
         self.omega = float(omega)
         self.order = order
@@ -55,6 +64,11 @@ class Hierarchy:
         k2 = omega**2 * self.kappa2
         H1 = operators.helmholtz(grid, c, order)
         K1 = operators.mass(grid, k2, order)
+        self.A_outer = H1.tocsr()
+        if beta != 0.0:
+            # the complex shift enters like the absorbing term: gamma -> gamma + beta
+            c_beta = grid_mod.coefficient(self.kappa2, omega, self.gamma + beta)
+            H1 = operators.helmholtz(grid, c_beta, order)
         (r1, p1), (r2, p2) = INTERGRID[intergrid]
         self.R = [transfers.restriction(self.grids[0], r1),
                   transfers.restriction(self.grids[1], r2)]

@@ -55,3 +55,35 @@ def test_cycle_equals_recursive_two_grid_matrix(kind, cyc, nu):
     M = (I1 - E1) @ np.linalg.inv(A[0])
     cols = np.stack([cy(e) for e in np.eye(grid.size, dtype=np.complex128)], axis=1)
     np.testing.assert_allclose(cols, M, atol=1e-9 * np.max(np.abs(M)))
+
+
+@pytest.mark.parametrize("order", ["2nd", "4th"])
+def test_cslp_shift_of_the_cycle_operator(order):
+    """RS-CGC + CSLP (Sec. 5): the cycle's fine operator is the outer operator plus
+    i beta k^2 times the mass stencil.  Closed forms: for the 5-point operator the shift
+    is diagonal with entries i beta omega^2 kappa^2; for the compact 4th-order operator
+    (mass stencil weights summing to one) the interior row sums of the shift are
+    i beta omega^2 kappa^2 in a constant medium.  The outer operator is unshifted."""
+    import numpy as np
+    from oracle import grid as G
+    from oracle import hierarchy as Hy
+
+    grid = G.Grid((16, 12))
+    rng = np.random.default_rng(3)
+    kappa2 = 1.0 + 0.0 * rng.random(grid.shape) if order == "4th" else 0.5 + rng.random(grid.shape)
+    omega, beta = 0.7, 0.03
+    gamma = G.abc_profile(grid, G.uniform_widths(2, 3), 1.0)
+    h0 = Hy.Hierarchy(grid, kappa2, omega, gamma, order, "fw", alpha3=1.1)
+    hb = Hy.Hierarchy(grid, kappa2, omega, gamma, order, "fw", alpha3=1.1, beta=beta)
+    assert abs(hb.A_outer - h0.A[0]).max() == 0
+    assert abs(h0.A_outer - h0.A[0]).max() == 0
+    D = (hb.A[0] - hb.A_outer).toarray()
+    k2 = omega**2 * kappa2.ravel()
+    if order == "2nd":
+        np.testing.assert_allclose(D, np.diag(1j * beta * k2), atol=1e-14)
+    else:
+        interior = [x + grid.nodes[0] * y for y in range(1, grid.nodes[1] - 1) for x in range(1, grid.nodes[0] - 1)]
+        np.testing.assert_allclose(D.sum(axis=1)[interior], 1j * beta * k2[interior], rtol=1e-12)
+        assert np.all(D.real == 0)
+    # the coarse levels are built from the shifted operator: they change too
+    assert abs(hb.A[1] - h0.A[1]).max() > 0 and abs(hb.A[2] - h0.A[2]).max() > 0
