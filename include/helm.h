@@ -91,6 +91,12 @@ typedef struct {
                              launches.  The launch timer reads the events a graph records
                              after each replay.  If capture fails the context keeps plain
                              launches (HELM_INFO_GRAPHS = -1). */
+  double cslp_beta;       /* RS-CGC + CSLP (Sec. 5: a complex shift of 0.03 k^2 with RS-CGC for 10
+                             points per wavelength): the cycle's operators are built from
+                             H_h + i cslp_beta k^2 M_h (the shift enters like the absorbing
+                             term), the outer FGMRES operator stays H_h.  Level-1 component
+                             calls (helm_apply, helm_residual, helm_smooth) use the cycle's
+                             operator.  Default 0: plain RS-CGC. */
 } helm_opts;
 
 /* Per-solve statistics, one entry per right-hand side. */

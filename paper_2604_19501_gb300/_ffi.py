@@ -42,6 +42,7 @@ class HelmOpts(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("fuse_cycle", ctypes.c_int),
         ("graphs", ctypes.c_int),
+        ("cslp_beta", ctypes.c_double),
     ]
 
 

@@ -38,6 +38,9 @@ struct helm_ctx {
   FineOp fine{};
   double* d_gam = nullptr;
   float* d_gam32 = nullptr;
+  FineOp fine_cyc{};                           // the cycle's fine operator (with the CSLP shift)
+  double* d_gam_cyc = nullptr;                 // shifted absorbing tables (CSLP only)
+  float* d_gam32_cyc = nullptr;
   double* kap64 = nullptr;
   float* kap32 = nullptr;
   double* h_gam = nullptr;                     // host copy of the per-axis profiles
@@ -182,7 +185,7 @@ Prec cycle_prec(const helm_ctx* c) { return c->o.precision == HELM_MIXED ? P32 :
 int row_op(helm_ctx* c, int level, Prec arith, int mode, Prec xs, Prec bs, Prec ys, const void* x,
            const void* b, void* y, int nrhs, double w, int colour) {
   if (level == 0)
-    return launch_fine_row(c->fine, mode, arith, xs, bs, ys, arith == P64 ? (const void*)c->kap64 : (const void*)c->kap32,
+    return launch_fine_row(c->fine_cyc, mode, arith, xs, bs, ys, arith == P64 ? (const void*)c->kap64 : (const void*)c->kap32,
                            x, b, y, nrhs, w, colour, c->s);
   if (level == 1)
     return launch_stencil_row(c->g[1], c->r2, arith, arith == P64 ? (const void*)c->A2_64 : (const void*)c->A2_32,
@@ -251,7 +254,7 @@ bool fused_cycle(const helm_ctx* c, Prec vs, Prec zs) {
 
 int run_cycle_fused(helm_ctx* c, const void* v, void* z, int nrhs) {
   Cycle2D cy;
-  cy.fine = c->fine;
+  cy.fine = c->fine_cyc;
   cy.kap = c->kap32;
   cy.g2 = c->g[1];
   cy.g3 = c->g[2];
@@ -561,6 +564,7 @@ int helm_default_opts(helm_opts* o) {
   o->stream = nullptr;
   o->fuse_cycle = 1;
   o->graphs = 0;
+  o->cslp_beta = 0.0;
   return HELM_OK;
 }
 
@@ -574,7 +578,8 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
     return fail(HELM_EINVAL, "h must be > 0 and omega >= 0, both finite");
   for (int f = 0; f < 2 * o->dim; ++f)
     if (o->abc_width[f] < 0 || o->abc_width[f] > o->n[f / 2]) return fail(HELM_EINVAL, "bad absorbing-layer width");
-  if (!std::isfinite(o->alpha2) || !std::isfinite(o->alpha3) || !std::isfinite(o->abc_gamma_max))
+  if (!std::isfinite(o->alpha2) || !std::isfinite(o->alpha3) || !std::isfinite(o->abc_gamma_max) ||
+      !std::isfinite(o->cslp_beta) || o->cslp_beta < 0.0)
     return fail(HELM_EINVAL, "non-finite shift or layer amplitude");
   if (o->stencil != HELM_STENCIL_2ND && o->stencil != HELM_STENCIL_4TH) return fail(HELM_EINVAL, "bad stencil");
   if (o->intergrid < HELM_INTERGRID_FW || o->intergrid > HELM_INTERGRID_LEVDEP)
@@ -658,6 +663,23 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
     c->fine.gam32[1] = c->d_gam32 + c->g[0].N[0];
     c->fine.gam32[2] = c->d_gam32 + c->g[0].N[0] + c->g[0].N[1];
   }
+  // the cycle's operator: with the CSLP shift the x-axis table carries gamma + beta, so
+  // that gamma_x + gamma_y (+ gamma_z) + beta enters every coefficient
+  c->fine_cyc = c->fine;
+  if (o->cslp_beta != 0.0) {
+    std::vector<double> gs(gam);
+    for (int i = 0; i < c->g[0].N[0]; ++i) gs[i] += o->cslp_beta;
+    std::vector<float> gs32(gs.begin(), gs.end());
+    if (int st = dmalloc(&c->d_gam_cyc, tot * sizeof(double))) return bail(st);
+    if (int st = dmalloc(&c->d_gam32_cyc, tot * sizeof(float))) return bail(st);
+    if (cudaMemcpy(c->d_gam_cyc, gs.data(), tot * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_gam32_cyc, gs32.data(), tot * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(fail(HELM_ECUDA, "uploading the shifted absorbing profile"));
+    for (int a = 0, off2 = 0; a < 3; off2 += c->g[0].N[a], ++a) {
+      c->fine_cyc.gam[a] = c->d_gam_cyc + off2;
+      c->fine_cyc.gam32[a] = c->d_gam32_cyc + off2;
+    }
+  }
 
   // transfers: full weighting / linear everywhere (FW); the cubic stencil of Eq.
   // intergrid everywhere (cubic); cubic except the restriction to level 3 (Eq. levdep)
@@ -675,7 +697,7 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
   double2* H20 = nullptr;
   if (int st = dmalloc(&H20, c->nc2 * n2 * sizeof(double2))) return bail(st);
   if (int st = dmalloc(&c->Mk2, c->nc2 * n2 * sizeof(double))) { cudaFree(H20); return bail(st); }
-  int st = assemble_level2(c->fine, c->kap64, c->g[1], c->tR1.radius, c->tP1.radius, H20, c->Mk2, &c->r2, c->s);
+  int st = assemble_level2(c->fine_cyc, c->kap64, c->g[1], c->tR1.radius, c->tP1.radius, H20, c->Mk2, &c->r2, c->s);
   if (st) { cudaFree(H20); return bail(HELM_ECUDA); }
   // level-2 operator of the cycle: H_2h + (1 - alpha2^2) R1 K P1
   if ((st = dmalloc(&c->A2_64, c->nc2 * n2 * sizeof(double2)))) { cudaFree(H20); return bail(st); }
@@ -748,7 +770,7 @@ int helm_destroy(helm_ctx* c) {
   free_workspaces(c);
   coarse_free(c->cs);
   for (auto& k : c->ks) krylov_free(k);
-  for (void* p : {(void*)c->d_gam, (void*)c->d_gam32, (void*)c->kap64, (void*)c->kap32, (void*)c->A2_64, (void*)c->A2_dinv64,
+  for (void* p : {(void*)c->d_gam, (void*)c->d_gam32, (void*)c->d_gam_cyc, (void*)c->d_gam32_cyc, (void*)c->kap64, (void*)c->kap32, (void*)c->A2_64, (void*)c->A2_dinv64,
                   (void*)c->A2_32, (void*)c->A2_dinv32, (void*)c->Mk2, (void*)c->A3_64, (void*)c->A3_dinv64,
                   (void*)c->V, (void*)c->w, (void*)c->r, c->Z, (void*)c->stage, (void*)c->d_bad,
                   (void*)c->cdf, (void*)c->d_scal, (void*)c->d_kpart, (void*)c->d_kcounter})

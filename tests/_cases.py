@@ -17,8 +17,9 @@ def medium(n, seed=0, lo=0.3, hi=1.0):
 
 class Case:
     def __init__(self, n, omega=None, abc=3, gamma_max=1.0, alpha2=1.0, alpha3=1.0, seed=0, kappa2=None,
-                 G_ppw=10.0, order="2nd", intergrid="fw"):
+                 G_ppw=10.0, order="2nd", intergrid="fw", beta=0.0):
         self.order, self.intergrid = order, intergrid
+        self.beta = beta
         self.n = tuple(n)
         self.dim = len(n)
         self.grid = G.Grid(self.n)
@@ -36,7 +37,7 @@ class Case:
     def hier(self):
         if self._hier is None:
             self._hier = Hy.Hierarchy(self.grid, self.kappa2, self.omega, self.gamma, self.order,
-                                      self.intergrid, alpha2=self.alpha2, alpha3=self.alpha3)
+                                      self.intergrid, alpha2=self.alpha2, alpha3=self.alpha3, beta=self.beta)
         return self._hier
 
     def solver(self, **kw):
@@ -45,7 +46,8 @@ class Case:
 
         k = torch.from_numpy(self.kappa2).cuda()
         return Solver(k, self.n, self.omega, abc_width=self.abc, abc_gamma_max=self.gamma_max,
-                      alpha2=self.alpha2, alpha3=self.alpha3, stencil=self.order, intergrid=self.intergrid, **kw)
+                      alpha2=self.alpha2, alpha3=self.alpha3, stencil=self.order, intergrid=self.intergrid,
+                      cslp_beta=self.beta, **kw)
 
 
 def rand_complex(shape, seed, dtype=np.complex128):
