@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--block", type=int, default=0, help="right-hand sides per FGMRES block (0 = all)")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the FGMRES block size with helm_autotune_block before the warm-up")
+    ap.add_argument("--cslp", type=float, default=0.0,
+                    help="complex shift beta of the cycle (RS-CGC + CSLP, Sec. 5: 0.03 for 10 ppw); 0 = RS-CGC")
     ap.add_argument("--graphs", action="store_true",
                     help="replay FGMRES iterations as CUDA graphs")
     return ap.parse_args()
@@ -106,8 +108,8 @@ def workload(args):
 
 def default_workload(args):
     """The configuration the sweep traffic figure was captured on."""
-    return (args.n, args.pad, args.ppw, args.method, args.precision, args.cycle, args.sources) == \
-        (2048, 32, 12, "paper", "mixed", "V", 1)
+    return (args.n, args.pad, args.ppw, args.method, args.precision, args.cycle, args.sources, args.cslp) == \
+        (2048, 32, 12, "paper", "mixed", "V", 1, 0.0)
 
 
 def describe(args, wl):
@@ -115,7 +117,8 @@ def describe(args, wl):
         "workload": (f"2D heterogeneous layered/faulted medium (1.5-4.5 km/s, seeded) {args.n}^2 cells "
                      f"+ {args.pad}-cell absorbing layer per side = {wl['n'][0]}^2 cells "
                      f"({(wl['n'][0] + 1) ** 2} nodes), {args.ppw} points per wavelength, centre point source"),
-        "method": (f"RS-CGC {args.cycle}(1,1) damped Jacobi w={wl['jacobi']}, "
+        "method": (f"RS-CGC{' + CSLP (complex shift %g k^2)' % args.cslp if args.cslp else ''} "
+                   f"{args.cycle}(1,1) damped Jacobi w={wl['jacobi']}, "
                    f"{'4th-order 9-point + cubic transfers' if wl['order'] == '4th' else '5-point + FW/bilinear'}, "
                    f"alpha3={wl['alpha3']}, FGMRES({args.restart}), tol {args.tol}"),
         "precision": ("FP32 cycle on levels 1-2; FGMRES basis, Arnoldi streams and coarsest solve in "
@@ -338,7 +341,7 @@ def our_arm(args):
     s = Solver(kap, wl["n"], wl["omega"], abc_width=wl["pad"], alpha3=wl["alpha3"], stencil=wl["order"],
                intergrid=wl["intergrid"], cycle=args.cycle, jacobi_w=(wl["jacobi"], wl["jacobi"]),
                precision=args.precision, restart=args.restart, stream=stream.cuda_stream,
-               max_rhs=max(1, args.block or args.sources), graphs=args.graphs)
+               max_rhs=max(1, args.block or args.sources), graphs=args.graphs, cslp_beta=args.cslp)
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
     info = s.info()
