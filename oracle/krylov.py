@@ -84,3 +84,24 @@ def fgmres(apply_A, b, apply_M, tol=1e-6, maxit=200, restart=None, x0=None,
     relres = beta / bnorm
     return x, dict(iterations=its, converged=bool(relres < tol), relres=float(relres),
                    history=hist)
+
+
+def stationary(apply_A, b, apply_M, tol=1e-6, maxit=200):
+    """RS-CGC as a solver (Sec. 5, the parenthesised counts of Table 3): the iteration
+    x_{k+1} = x_k + M (b - A x_k) from x_0 = 0, stopped once the relative residual
+    ||b - A x|| / ||b|| is below tol or after maxit applications of M.  The iteration
+    count is the number of applications of M."""
+    b = np.asarray(b, dtype=np.complex128)
+    bnorm = np.linalg.norm(b)
+    x = np.zeros_like(b)
+    if bnorm == 0:
+        return x, dict(iterations=0, converged=True, relres=0.0)
+    r = b.copy()
+    relres = 1.0
+    its = 0
+    while its < maxit and relres >= tol:
+        x = x + apply_M(r)
+        r = b - apply_A(x)
+        relres = np.linalg.norm(r) / bnorm
+        its += 1
+    return x, dict(iterations=its, converged=bool(relres < tol), relres=float(relres))

@@ -72,3 +72,31 @@ def test_preconditioned_helmholtz_matches_direct(cyc):
     xd = spla.spsolve(hier.A[0].tocsc(), b)
     assert info["converged"]
     np.testing.assert_allclose(x, xd, atol=1e-9 * np.max(np.abs(xd)))
+
+
+def test_stationary_exact_preconditioner_one_step():
+    """With M = A^-1 the stationary iteration solves in one step."""
+    import numpy as np
+    from oracle import krylov as K
+
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((12, 12)) + 1j * rng.standard_normal((12, 12)) + 6 * np.eye(12)
+    b = rng.standard_normal(12) + 1j * rng.standard_normal(12)
+    Ainv = np.linalg.inv(A)
+    x, info = K.stationary(lambda v: A @ v, b, lambda v: Ainv @ v, tol=1e-10, maxit=5)
+    assert info["iterations"] == 1 and info["converged"]
+    np.testing.assert_allclose(A @ x, b, atol=1e-10)
+
+
+def test_stationary_diagonal_contraction():
+    """Closed form: for A = diag(d) and M = I / d_max the residual component i after k
+    steps is (1 - d_i / d_max)^k b_i."""
+    import numpy as np
+    from oracle import krylov as K
+
+    d = np.array([1.0, 2.0, 4.0, 8.0])
+    b = np.array([1.0, -2.0, 0.5, 3.0]) + 0j
+    for k in range(1, 6):
+        x, info = K.stationary(lambda v: d * v, b, lambda v: v / 8.0, tol=0.0, maxit=k)
+        assert info["iterations"] == k
+        np.testing.assert_allclose(b - d * x, (1 - d / 8.0) ** k * b, rtol=1e-14, atol=1e-15)
