@@ -74,6 +74,9 @@ def parse():
                     help="complex shift beta of the cycle (RS-CGC + CSLP, Sec. 5: 0.03 for 10 ppw); 0 = RS-CGC")
     ap.add_argument("--graphs", action="store_true",
                     help="replay FGMRES iterations as CUDA graphs")
+    ap.add_argument("--solver", default="fgmres", choices=["fgmres", "cycle"],
+                    help="fgmres: FGMRES preconditioned by the cycle; cycle: RS-CGC as a solver "
+                         "(stationary cycle iteration, Sec. 5)")
     return ap.parse_args()
 
 
@@ -108,8 +111,8 @@ def workload(args):
 
 def default_workload(args):
     """The configuration the sweep traffic figure was captured on."""
-    return (args.n, args.pad, args.ppw, args.method, args.precision, args.cycle, args.sources, args.cslp) == \
-        (2048, 32, 12, "paper", "mixed", "V", 1, 0.0)
+    return (args.n, args.pad, args.ppw, args.method, args.precision, args.cycle, args.sources, args.cslp,
+            args.solver) == (2048, 32, 12, "paper", "mixed", "V", 1, 0.0, "fgmres")
 
 
 def describe(args, wl):
@@ -120,7 +123,9 @@ def describe(args, wl):
         "method": (f"RS-CGC{' + CSLP (complex shift %g k^2)' % args.cslp if args.cslp else ''} "
                    f"{args.cycle}(1,1) damped Jacobi w={wl['jacobi']}, "
                    f"{'4th-order 9-point + cubic transfers' if wl['order'] == '4th' else '5-point + FW/bilinear'}, "
-                   f"alpha3={wl['alpha3']}, FGMRES({args.restart}), tol {args.tol}"),
+                   f"alpha3={wl['alpha3']}, "
+                   f"{'FGMRES(%d)' % args.restart if args.solver == 'fgmres' else 'stationary cycle iteration'}, "
+                   f"tol {args.tol}"),
         "precision": ("FP32 cycle on levels 1-2; FGMRES basis, Arnoldi streams and coarsest solve in "
                       "double-FP32 arithmetic (about 48 significant bits); Givens, solution update and true "
                       "residual in FP64" if args.precision == "mixed" else "FP64 throughout"),
@@ -229,26 +234,33 @@ def oracle_sample(args, log):
     grid = OG.Grid(wl["n"])
     gamma = OG.abc_profile(grid, OG.uniform_widths(2, wl["pad"]), 1.0)
     t0 = time.perf_counter()
-    h = OH.Hierarchy(grid, wl["kappa2"], wl["omega"], gamma, wl["order"], wl["intergrid"], alpha3=wl["alpha3"])
+    h = OH.Hierarchy(grid, wl["kappa2"], wl["omega"], gamma, wl["order"], wl["intergrid"], alpha3=wl["alpha3"],
+                     beta=args.cslp)
     h.coarsest_lu
     cy = OC.Cycle(h, cycle=args.cycle, weights=(wl["jacobi"], wl["jacobi"]))
     log(f"oracle set-up {time.perf_counter() - t0:.1f} s ({wl['n'][0]}^2 cells)")
     nodes = (wl["n"][0] + 1) * (wl["n"][1] + 1)
-    return dict(h=h, cy=cy, A=h.A[0], q=wl["q"].ravel(), nodes=nodes, cells=wl["n"][0], n=args.cpu_n)
+    return dict(h=h, cy=cy, A=h.A_outer, q=wl["q"].ravel(), nodes=nodes, cells=wl["n"][0], n=args.cpu_n,
+                solver=args.solver)
 
 
 def oracle_solve(smp, args):
-    """One oracle FGMRES solve of the sample to the run's tolerance: (seconds, iterations)."""
+    """One oracle solve of the sample to the run's tolerance, by the run's solver:
+    (seconds, iterations)."""
     from oracle import krylov as OK
 
     t = time.perf_counter()
-    _, info = OK.fgmres(lambda v: smp["A"] @ v, smp["q"], smp["cy"], tol=args.tol, maxit=args.maxit,
-                        restart=args.restart)
+    if args.solver == "cycle":
+        _, info = OK.stationary(lambda v: smp["A"] @ v, smp["q"], smp["cy"], tol=args.tol, maxit=args.maxit)
+    else:
+        _, info = OK.fgmres(lambda v: smp["A"] @ v, smp["q"], smp["cy"], tol=args.tol, maxit=args.maxit,
+                            restart=args.restart)
     return time.perf_counter() - t, info["iterations"]
 
 
 def cpu_sample_note(smp, its, t):
-    return (f"oracle (NumPy/SciPy sparse, FP64, {ORACLE_THREADS} thread(s)) full FGMRES solve to the run's tolerance of the "
+    return (f"oracle (NumPy/SciPy sparse, FP64, {ORACLE_THREADS} thread(s)) full {'FGMRES' if smp['solver'] == 'fgmres' else 'cycle-iteration'} "
+            f"solve to the run's tolerance of the "
             f"same workload at {smp['n']}^2 cells + absorbing layer ({smp['cells']}^2 cells, {smp['nodes']} nodes): "
             f"{its} iterations in {t:.2f} s, set-up excluded; value = sample nodes / solve time")
 
@@ -341,7 +353,8 @@ def our_arm(args):
     s = Solver(kap, wl["n"], wl["omega"], abc_width=wl["pad"], alpha3=wl["alpha3"], stencil=wl["order"],
                intergrid=wl["intergrid"], cycle=args.cycle, jacobi_w=(wl["jacobi"], wl["jacobi"]),
                precision=args.precision, restart=args.restart, stream=stream.cuda_stream,
-               max_rhs=max(1, args.block or args.sources), graphs=args.graphs, cslp_beta=args.cslp)
+               max_rhs=max(1, args.block or args.sources), graphs=args.graphs, cslp_beta=args.cslp,
+               solver=args.solver)
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
     info = s.info()

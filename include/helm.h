@@ -54,6 +54,12 @@ typedef enum { HELM_SMOOTHER_JACOBI = 0, HELM_SMOOTHER_REDBLACK = 1 } helm_smoot
  * the true residual and the coarsest solve in complex FP64. */
 typedef enum { HELM_FP64 = 0, HELM_MIXED = 1 } helm_precision;
 typedef enum { HELM_C128 = 0, HELM_C64 = 1 } helm_dtype;
+/* HELM_SOLVER_FGMRES: FGMRES(restart) preconditioned by the cycle (Sec. 5).
+ * HELM_SOLVER_CYCLE: RS-CGC as a solver (Sec. 5, the iteration counts Table 3 gives
+ * in parentheses): p <- p + M^-1 (q - H p) from p = 0, M^-1 one cycle, the correction
+ * added and the true residual formed in FP64; helm_stats.iterations counts cycles and
+ * est_relres equals relres. */
+typedef enum { HELM_SOLVER_FGMRES = 0, HELM_SOLVER_CYCLE = 1 } helm_solver;
 
 /* Problem and method options; fill with helm_default_opts() first. */
 typedef struct {
@@ -97,6 +103,7 @@ typedef struct {
                              term), the outer FGMRES operator stays H_h.  Level-1 component
                              calls (helm_apply, helm_residual, helm_smooth) use the cycle's
                              operator.  Default 0: plain RS-CGC. */
+  int solver;             /* helm_solver used by helm_solve / helm_adjoint_grad */
 } helm_opts;
 
 /* Per-solve statistics, one entry per right-hand side. */
@@ -111,7 +118,8 @@ typedef struct helm_ctx helm_ctx;
 
 /* Fills *o with defaults: 2D, h = 1, gamma_max = 1, alpha2 = alpha3 = 1,
  * 2nd-order stencil, FW transfers, V(1,1), Jacobi w = (0.8, 0.8), rb_w = 1,
- * FP64, restart 10, max_rhs 1, default stream, fuse_cycle 1.  The caller sets dim, n,
+ * FP64, restart 10, max_rhs 1, default stream, fuse_cycle 1, graphs 0,
+ * cslp_beta 0, solver FGMRES.  The caller sets dim, n,
  * omega, abc_width and the shifts. */
 int helm_default_opts(helm_opts* o);
 

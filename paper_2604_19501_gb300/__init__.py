@@ -42,7 +42,8 @@ class Solver:
     def __init__(self, kappa2, n, omega, h=1.0, abc_width=0, abc_gamma_max=1.0, alpha2=1.0,
                  alpha3=1.0, stencil="2nd", intergrid="fw", cycle="V", nu=(1, 1),
                  smoother="jacobi", jacobi_w=(0.8, 0.8), rb_w=1.0, precision="fp64", restart=10,
-                 max_rhs=1, stream=None, fuse_cycle=True, graphs=False, cslp_beta=0.0):
+                 max_rhs=1, stream=None, fuse_cycle=True, graphs=False, cslp_beta=0.0,
+                 solver="fgmres"):
         self.n = tuple(int(v) for v in n)
         self.dim = len(self.n)
         o = HelmOpts()
@@ -70,6 +71,7 @@ class Solver:
         o.fuse_cycle = int(bool(fuse_cycle))
         o.graphs = int(bool(graphs))
         o.cslp_beta = float(cslp_beta)
+        o.solver = _ffi.SOLVER[solver]
         if stream is None:
             import torch
 

@@ -12,6 +12,7 @@ CYCLE = {"V": 0, "W": 1}
 SMOOTHER = {"jacobi": 0, "redblack": 1, "rb": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 DTYPE = {"c128": 0, "c64": 1}
+SOLVER = {"fgmres": 0, "cycle": 1}
 INFO_KEYS = ["nodes1", "nodes2", "nodes3", "radius2", "radius3", "coarse_entries", "coarse_fronts",
              "coarse_levels", "coarse_bwd_entries", "double_float", "graphs"]
 KERNEL_CLASSES = ["fine", "stencil", "transfer", "coarse", "arnoldi_matvec", "arnoldi_update",
@@ -43,6 +44,7 @@ class HelmOpts(ctypes.Structure):
         ("fuse_cycle", ctypes.c_int),
         ("graphs", ctypes.c_int),
         ("cslp_beta", ctypes.c_double),
+        ("solver", ctypes.c_int),
     ]
 
 

@@ -530,6 +530,100 @@ int fgmres_block(helm_ctx* c, const double2* q, double2* p, int B, double tol, i
   return coarse_status(c->cs, c->s);
 }
 
+// RS-CGC as a solver (Sec. 5, the parenthesised iteration counts of Table 3): the
+// stationary iteration p <- p + M^-1 (q - H p) from p = 0, M^-1 one cycle, until the true
+// relative residual ||q - H p|| / ||q|| (FP64) is below tol or maxit cycles ran.  The cycle
+// runs once per iteration for the whole block; a right-hand side that has converged keeps
+// its iterate (its correction is not added) and its residual.  The correction is added
+// and the residual formed in FP64 in both precision modes.  The iteration works on context
+// buffers only, so that a captured iteration replays for any q and p: the iterate x in
+// w [B][n], a copy of q in V slot 1, the residual r [B][n]; the cycle reads its double-
+// float input from V slot 0 (mixed precision) and writes Z [B][n].
+int stationary_block(helm_ctx* c, const double2* q, double2* p, int B, double tol, int maxit, helm_stats* out) {
+  const long long n = c->g[0].size;
+  const Prec zp = cycle_prec(c);
+  const bool df = zp == P32;
+  const size_t zes = esize(zp);
+  const size_t bytes = (size_t)B * n * sizeof(double2);
+  double2* x = c->w;
+  double2* qc = c->V + (size_t)B * n;
+  auto S = [&](int r) { return c->h_scal + (size_t)r * KS_COUNT; };
+  HELM_CUDA_TRY(cudaMemsetAsync(x, 0, bytes, c->s));
+  for (int r = 0; r < B; ++r)
+    if (int st = k_norm(c->ks[r], n, q + (size_t)r * n, qc + (size_t)r * n, c->s)) return st;
+  HELM_CUDA_TRY(cudaMemcpyAsync(c->r, qc, bytes, cudaMemcpyDeviceToDevice, c->s));
+  if (int st = sync_scal(c, B)) return st;
+  std::vector<double> bnorm(B), beta(B);
+  std::vector<int> its(B, 0);
+  std::vector<char> act(B, 0);
+  for (int r = 0; r < B; ++r) {
+    bnorm[r] = S(r)[KS_BNORM];
+    beta[r] = S(r)[KS_BETA];
+    if (!std::isfinite(bnorm[r])) return fail(HELM_EINVAL, "right-hand side is not finite");
+  }
+  while (true) {
+    int nact = 0;
+    unsigned long long mask = 0;
+    for (int r = 0; r < B; ++r) {
+      act[r] = bnorm[r] > 0 && beta[r] / bnorm[r] >= tol && its[r] < maxit;
+      nact += act[r];
+      if (r < 64) mask |= (unsigned long long)(act[r] != 0) << r;
+    }
+    if (nact == 0) break;
+    // the iteration's device work: cycle for the block, corrections and residuals of the
+    // active right-hand sides, residual norms to the host
+    auto issue = [&]() -> int {
+      if (df) {
+        float4* vd = reinterpret_cast<float4*>(c->V);
+        if (int st = launch_convert(P64, P_DF, c->r, vd, (long long)B * n, c->s)) return st;
+        if (int st = run_cycle(c, vd, P_DF, c->Z, zp, B)) return st;
+      } else if (int st = run_cycle(c, c->r, P64, c->Z, zp, B)) {
+        return st;
+      }
+      for (int r = 0; r < B; ++r) {
+        if (!act[r]) continue;
+        double2* xr = x + (size_t)r * n;
+        if (int st = k_add_correction(n, xr, (const char*)c->Z + (size_t)r * n * zes, zp, c->s)) return st;
+        if (int st = k_true_residual(c->ks[r], c->fine, c->kap64, qc + (size_t)r * n, xr, c->r + (size_t)r * n, c->s))
+          return st;
+      }
+      HELM_CUDA_TRY(cudaMemcpyAsync(c->h_scal, c->d_scal, sizeof(double) * KS_COUNT * B, cudaMemcpyDeviceToHost, c->s));
+      return 0;
+    };
+    if (B > 64) {
+      if (int st = issue()) return st;
+    } else if (int st = run_iteration(c, std::make_tuple(-1, B, mask), issue)) {
+      return st;
+    }
+    HELM_CUDA_TRY(cudaStreamSynchronize(c->s));
+    collect_graph_timing(c);
+    for (int r = 0; r < B; ++r) {
+      if (!act[r]) continue;
+      ++its[r];
+      beta[r] = S(r)[KS_BETA];
+      if (!std::isfinite(beta[r])) return fail(HELM_ENUMERIC, "non-finite residual");
+    }
+  }
+  for (int r = 0; r < B; ++r) {
+    helm_stats res{0, 1, 0.0, 0.0};
+    if (bnorm[r] > 0) {
+      res.iterations = its[r];
+      res.relres = beta[r] / bnorm[r];
+      res.converged = res.relres < tol ? 1 : 0;
+      res.est_relres = res.relres;
+    }
+    if (out) out[r] = res;
+  }
+  HELM_CUDA_TRY(cudaMemcpyAsync(p, x, bytes, cudaMemcpyDeviceToDevice, c->s));
+  return coarse_status(c->cs, c->s);
+}
+
+// One block of right-hand sides by the context's solver (helm_opts.solver).
+int solve_block(helm_ctx* c, const double2* q, double2* p, int B, double tol, int maxit, helm_stats* out) {
+  if (c->o.solver == HELM_SOLVER_CYCLE) return stationary_block(c, q, p, B, tol, maxit, out);
+  return fgmres_block(c, q, p, B, tol, maxit, out);
+}
+
 int check_level(const helm_ctx* c, int level, int lo, int hi) {
   if (level < lo || level > hi) return fail(HELM_EINVAL, "level out of range");
   return 0;
@@ -565,6 +659,7 @@ int helm_default_opts(helm_opts* o) {
   o->fuse_cycle = 1;
   o->graphs = 0;
   o->cslp_beta = 0.0;
+  o->solver = HELM_SOLVER_FGMRES;
   return HELM_OK;
 }
 
@@ -581,6 +676,7 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
   if (!std::isfinite(o->alpha2) || !std::isfinite(o->alpha3) || !std::isfinite(o->abc_gamma_max) ||
       !std::isfinite(o->cslp_beta) || o->cslp_beta < 0.0)
     return fail(HELM_EINVAL, "non-finite shift or layer amplitude");
+  if (o->solver != HELM_SOLVER_FGMRES && o->solver != HELM_SOLVER_CYCLE) return fail(HELM_EINVAL, "bad solver");
   if (o->stencil != HELM_STENCIL_2ND && o->stencil != HELM_STENCIL_4TH) return fail(HELM_EINVAL, "bad stencil");
   if (o->intergrid < HELM_INTERGRID_FW || o->intergrid > HELM_INTERGRID_LEVDEP)
     return fail(HELM_EINVAL, "bad intergrid transfer");
@@ -808,7 +904,7 @@ int helm_solve(helm_ctx* c, const void* q, void* p, int n_rhs, double tol, int m
   std::vector<helm_stats> st_block(c->block);
   for (int r0 = 0; r0 < n_rhs; r0 += c->block) {
     const int B = std::min(c->block, n_rhs - r0);
-    if (int st = fgmres_block(c, dq + (size_t)r0 * n, dp + (size_t)r0 * n, B, tol, maxit, st_block.data())) return st;
+    if (int st = solve_block(c, dq + (size_t)r0 * n, dp + (size_t)r0 * n, B, tol, maxit, st_block.data())) return st;
     for (int r = 0; r < B; ++r) {
       if (stats) stats[r0 + r] = st_block[r];
       if (!st_block[r].converged) worst = HELM_NOT_CONVERGED;
@@ -847,7 +943,7 @@ int helm_adjoint_grad(helm_ctx* c, const void* p, const void* resid, int n_rhs, 
     const int B = std::min(c->block, n_rhs - r0);
     if (int st = launch_conj((long long)B * n, (const double2*)resid + (size_t)r0 * n, rhs, c->s)) return st;
     double2* m_out = adj ? (double2*)adj + (size_t)r0 * n : mu;
-    if (int st = fgmres_block(c, rhs, m_out, B, tol, maxit, st_block.data())) return st;
+    if (int st = solve_block(c, rhs, m_out, B, tol, maxit, st_block.data())) return st;
     for (int r = 0; r < B; ++r) {
       if (stats) stats[r0 + r] = st_block[r];
       if (!st_block[r].converged) worst = HELM_NOT_CONVERGED;
@@ -1019,7 +1115,7 @@ int helm_autotune_block(helm_ctx* c, const void* q, int n_rhs, int probe_iters, 
     // tolerance of zero keeps every right-hand side iterating for exactly `iters` steps.
     for (int rep = 0; rep < 2 && status == HELM_OK; ++rep) {
       if (rep == 1) cudaEventRecord(e0, c->s);
-      status = fgmres_block(c, (const double2*)q, c->stage, b, 0.0, iters, st.data());
+      status = solve_block(c, (const double2*)q, c->stage, b, 0.0, iters, st.data());
       if (rep == 1) cudaEventRecord(e1, c->s);
     }
     if (status != HELM_OK) break;

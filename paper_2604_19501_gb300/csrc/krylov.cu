@@ -201,6 +201,21 @@ __global__ void lsq_kernel(KrylovState st, int k, int m) {
   }
 }
 
+// x += z with the sum in FP64 (z c128 or c64): the correction step of the stationary
+// cycle iteration, one right-hand side per call.
+template <typename TZ>
+__global__ void __launch_bounds__(kThreads) add_correction_kernel(long long n, double2* __restrict__ x,
+                                                                  const c2<TZ>* __restrict__ z) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const c2<double> d = cvt<double>(z[p]);
+    double2 v = x[p];
+    v.x += d.x;
+    v.y += d.y;
+    x[p] = v;
+  }
+}
+
 // x += sum_i y_i z_i
 template <typename TZ>
 __global__ void __launch_bounds__(kThreads) solution_update_kernel(long long n, double2* __restrict__ x,
@@ -694,6 +709,16 @@ int k_update_solution(const KrylovState& st, long long n, double2* x, const void
     solution_update_kernel<double><<<grid_blocks(n), kThreads, 0, s>>>(n, x, (const double2*)Z, zstride, k, st.y);
   else
     solution_update_df_kernel<<<grid_blocks(n), kThreads, 0, s>>>(n, x, (const float2*)Z, zstride, k, st.y);
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
+int k_add_correction(long long n, double2* x, const void* z, Prec zp, cudaStream_t s) {
+  KernelTimer kt(HELM_K_KRYLOV_OTHER, s);
+  if (zp == P64)
+    add_correction_kernel<double><<<grid_blocks(n), kThreads, 0, s>>>(n, x, (const double2*)z);
+  else
+    add_correction_kernel<float><<<grid_blocks(n), kThreads, 0, s>>>(n, x, (const float2*)z);
   HELM_LAUNCH_CHECK();
   return 0;
 }

@@ -51,6 +51,8 @@ int k_normalize_df(const KrylovState& st, long long n, const float4* w, const fl
 // y = R^-1 g (k x k) and x += Z y.
 int k_update_solution(const KrylovState& st, long long n, double2* x, const void* Z, Prec zp,
                       long long zstride, int k, cudaStream_t s);
+// x += z (z c128 or c64), summed in FP64.
+int k_add_correction(long long n, double2* x, const void* z, Prec zp, cudaStream_t s);
 // r = b - H x in FP64, scal[KS_BETA] = ||r||.
 int k_true_residual(const KrylovState& st, const FineOp& op, const double* kap64, const double2* b,
                     const double2* x, double2* r, cudaStream_t s);

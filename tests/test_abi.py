@@ -57,3 +57,40 @@ def test_host_only_calls(lib):
     o.dim, o.n[0], o.n[1] = 2, 6, 8
     assert l.helm_setup(ctypes.byref(o), ctypes.cast(k, ctypes.c_void_p), ctypes.byref(ctx)) == _ffi.HELM_EINVAL
     assert l.helm_destroy(None) == 0
+
+
+def _header_opts_fields():
+    src = open(HEADER).read()
+    body = re.search(r"typedef struct \{(.*?)\} helm_opts;", src, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        for part in decl.split(",") if "," in decl else [decl]:
+            m = re.search(r"(\w+)\s*(\[\d+\])?\s*$", part.strip())
+            names.append(m.group(1))
+    return names
+
+
+def test_binding_opts_layout_follows_header():
+    from paper_2604_19501_gb300 import _ffi
+
+    assert [f[0] for f in _ffi.HelmOpts._fields_] == _header_opts_fields()
+
+
+def test_solver_option_defaults_and_validation(lib):
+    from paper_2604_19501_gb300 import _ffi
+
+    l = _ffi.load()
+    o = _ffi.HelmOpts()
+    assert l.helm_default_opts(ctypes.byref(o)) == 0
+    assert o.solver == _ffi.SOLVER["fgmres"] and o.fuse_cycle == 1 and o.graphs == 0 and o.cslp_beta == 0.0
+    ctx = ctypes.c_void_p()
+    k = (ctypes.c_double * 81)()
+    o.dim, o.n[0], o.n[1] = 2, 8, 8
+    o.solver = 7
+    assert l.helm_setup(ctypes.byref(o), ctypes.cast(k, ctypes.c_void_p), ctypes.byref(ctx)) == _ffi.HELM_EINVAL
+    assert b"solver" in l.helm_last_error()
+    assert not ctx.value
