@@ -74,6 +74,11 @@ def parse():
                     help="complex shift beta of the cycle (RS-CGC + CSLP, Sec. 5: 0.03 for 10 ppw); 0 = RS-CGC")
     ap.add_argument("--graphs", action="store_true",
                     help="replay FGMRES iterations as CUDA graphs")
+    ap.add_argument("--medium", default="layered", choices=["layered", "linear", "wedge"],
+                    help="layered: seeded layered/faulted medium, centre source; linear / wedge: the "
+                         "2D heterogeneous models of Sec. 5.1 (Table 3), source at the top centre")
+    ap.add_argument("--kappa-min", type=float, default=0.5,
+                    help="smallest slowness of the linear / wedge model (Table 3: 0.5 or 0.1)")
     ap.add_argument("--solver", default="fgmres", choices=["fgmres", "cycle"],
                     help="fgmres: FGMRES preconditioned by the cycle; cycle: RS-CGC as a solver "
                          "(stationary cycle iteration, Sec. 5)")
@@ -88,7 +93,11 @@ def workload(args):
 
     N = args.n + 2 * args.pad
     n = (N, N)
-    kappa2 = workloads.layered_faulted_2d(args.n, args.pad, seed=0)
+    if args.medium == "layered":
+        kappa2 = workloads.layered_faulted_2d(args.n, args.pad, seed=0)
+    else:
+        gen = workloads.linear_2d if args.medium == "linear" else workloads.wedge_2d
+        kappa2 = gen(args.n, args.pad, args.kappa_min)
     vmin = 1.0 / float(np.sqrt(kappa2.max()))
     omega = workloads.omega_for_ppw(args.ppw, vmin)
     with open(os.path.join(ROOT, "workloads", "shifts.json")) as f:
@@ -102,7 +111,7 @@ def workload(args):
         alpha3 = shifts["2nd"]["fw"][str(args.ppw)]["alpha3"]
         jw = 0.8 if args.jacobi is None else args.jacobi
     if args.sources <= 1:
-        q = workloads.point_source(n)
+        q = workloads.point_source(n, node=None if args.medium == "layered" else (N // 2, args.pad))
     else:
         q = workloads.surface_sources(n, args.sources, args.pad, seed=0)
     return dict(n=n, kappa2=kappa2, omega=omega, q=q, order=order, intergrid=ig, alpha3=alpha3,
@@ -112,14 +121,21 @@ def workload(args):
 def default_workload(args):
     """The configuration the sweep traffic figure was captured on."""
     return (args.n, args.pad, args.ppw, args.method, args.precision, args.cycle, args.sources, args.cslp,
-            args.solver) == (2048, 32, 12, "paper", "mixed", "V", 1, 0.0, "fgmres")
+            args.solver, args.medium) == (2048, 32, 12, "paper", "mixed", "V", 1, 0.0, "fgmres", "layered")
+
+
+def medium_name(args):
+    if args.medium == "layered":
+        return "2D heterogeneous layered/faulted medium (1.5-4.5 km/s, seeded)"
+    return f"2D {args.medium} model of Sec. 5.1 / Table 3 (slowness in [{args.kappa_min:g}, 1])"
 
 
 def describe(args, wl):
     return {
-        "workload": (f"2D heterogeneous layered/faulted medium (1.5-4.5 km/s, seeded) {args.n}^2 cells "
+        "workload": (f"{medium_name(args)} {args.n}^2 cells "
                      f"+ {args.pad}-cell absorbing layer per side = {wl['n'][0]}^2 cells "
-                     f"({(wl['n'][0] + 1) ** 2} nodes), {args.ppw} points per wavelength, centre point source"),
+                     f"({(wl['n'][0] + 1) ** 2} nodes), {args.ppw} points per wavelength, "
+                     f"{'centre' if args.medium == 'layered' else 'top-centre'} point source"),
         "method": (f"RS-CGC{' + CSLP (complex shift %g k^2)' % args.cslp if args.cslp else ''} "
                    f"{args.cycle}(1,1) damped Jacobi w={wl['jacobi']}, "
                    f"{'4th-order 9-point + cubic transfers' if wl['order'] == '4th' else '5-point + FW/bilinear'}, "

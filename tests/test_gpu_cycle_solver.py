@@ -134,3 +134,35 @@ def test_bad_solver_is_rejected():
             _case((16, 16)).solver(solver="bogus")
     finally:
         del _ffi.SOLVER["bogus"]
+
+
+@pytest.mark.parametrize("model,kmin,prec", [("linear", 0.1, "fp64"), ("wedge", 0.5, "mixed")])
+def test_table3_models_match_oracle(model, kmin, prec):
+    """The 2D heterogeneous models of Sec. 5.1 (Table 3) at 128^2 cells + 20-cell layer,
+    W(1,1): FGMRES and the cycle solver take the oracle's iteration counts (mixed: +-1)."""
+    from oracle import grid as OG
+    from oracle import hierarchy as OH
+
+    cells, pad = 128, 20
+    f = {"linear": workloads.linear_2d, "wedge": workloads.wedge_2d}[model]
+    kappa2 = f(cells, pad, kmin)
+    N = cells + 2 * pad
+    c = Case((N, N), abc=pad, alpha3=1.0045, order="4th", intergrid="cubic", kappa2=kappa2, G_ppw=12)
+    q = workloads.point_source(c.n, node=(N // 2, pad))
+    qd = torch.from_numpy(q).cuda()
+    cy = OC.Cycle(c.hier, cycle="W", weights=W)
+    A = lambda v: c.hier.A_outer @ v
+    for solver in ("fgmres", "cycle"):
+        s = c.solver(precision=prec, cycle="W", jacobi_w=W, solver=solver, restart=60)
+        p, st = s.solve(qd, tol=1e-6, maxit=60)
+        s.close()
+        if solver == "fgmres":
+            x, info = OK.fgmres(A, q.ravel(), cy, tol=1e-6, maxit=60, restart=60)
+        else:
+            x, info = OK.stationary(A, q.ravel(), cy, tol=1e-6, maxit=60)
+        assert st[0]["converged"] and info["converged"]
+        if prec == "fp64":
+            assert st[0]["iterations"] == info["iterations"]
+            assert rel(_n(p).ravel(), x) < 1e-9
+        else:
+            assert abs(st[0]["iterations"] - info["iterations"]) <= 1

@@ -22,6 +22,8 @@ __all__ = [
     "constant_medium",
     "layered_faulted_2d",
     "layered_3d",
+    "linear_2d",
+    "wedge_2d",
     "point_source",
     "surface_sources",
 ]
@@ -115,6 +117,39 @@ def layered_3d(n_interior, pad, seed=0, v_range=(1.5, 4.5), n_layers=8,
     v = np.clip(v, vmin, vmax)
     v = np.pad(v, int(pad), mode="edge")
     return (1.0 / v**2).astype(np.float64)
+
+
+def _unit_square(n_interior):
+    """Node coordinates (x, z) of an ``n_interior``-cell grid on the unit square."""
+    t = np.linspace(0.0, 1.0, int(n_interior) + 1)
+    return np.meshgrid(t, t, indexing="xy")
+
+
+def linear_2d(n_interior, pad, kappa_min=0.5, kappa_max=1.0):
+    """The linear model of Section 5 (heterogeneous 2D media): slowness kappa varying
+    linearly with depth over the unit square, from ``kappa_max`` at the surface to
+    ``kappa_min`` at the bottom (velocity increasing with depth), padded by edge
+    extension.  Returns kappa^2 on the nodes, shape ``(N+1, N+1)``,
+    ``N = n_interior + 2 pad``."""
+    _, z = _unit_square(n_interior)
+    kappa = kappa_max + (kappa_min - kappa_max) * z
+    return np.pad(kappa, int(pad), mode="edge") ** 2
+
+
+def wedge_2d(n_interior, pad, kappa_min=0.5, kappa_max=1.0):
+    """A wedge model for Section 5 (heterogeneous 2D media): three regions of constant
+    slowness on the unit square separated by two straight interfaces,
+    z1(x) = 0.4 + 0.2 x and z2(x) = 0.8 - 0.4 x, which meet at x = 2/3 and enclose a
+    wedge of the slowest material (``kappa_max``) on the left.  Above the wedge the
+    slowness is (kappa_min + kappa_max) / 2, below it ``kappa_min`` (for [0.5, 1] the
+    slowness ratios of 2000 / 1500 / 3000 m/s layers).  Padded by edge extension;
+    returns kappa^2 on the nodes, shape ``(N+1, N+1)``."""
+    x, z = _unit_square(n_interior)
+    z1 = 0.4 + 0.2 * x
+    z2 = 0.8 - 0.4 * x
+    kappa = np.where(z < z1, 0.5 * (kappa_min + kappa_max), kappa_min)
+    kappa = np.where((z >= z1) & (z < z2), kappa_max, kappa)
+    return np.pad(kappa, int(pad), mode="edge") ** 2
 
 
 def point_source(n, h=1.0, node=None):
