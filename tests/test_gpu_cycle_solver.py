@@ -153,7 +153,7 @@ def test_table3_models_match_oracle(model, kmin, prec):
     cy = OC.Cycle(c.hier, cycle="W", weights=W)
     A = lambda v: c.hier.A_outer @ v
     for solver in ("fgmres", "cycle"):
-        s = c.solver(precision=prec, cycle="W", jacobi_w=W, solver=solver, restart=60)
+        s = c.solver(precision=prec, cycle="W", jacobi_w=W, solver=solver, restart=40)
         p, st = s.solve(qd, tol=1e-6, maxit=60)
         s.close()
         if solver == "fgmres":
