@@ -375,6 +375,7 @@ struct CoarsePlan {
   std::vector<int2> ents, ctb;
   std::vector<std::vector<int>> bigs, smalls;
   std::vector<SweepJob> jobs;
+  std::vector<SweepMeta> meta;
   long long aug_max = 0, upool = 0;
 };
 
@@ -644,7 +645,57 @@ int coarse_plan(CoarseSolver& cs, CoarsePlan& P, const GridDims& g, int r, int l
   cs.n_counters = 2LL * cs.nfronts + slot;
   P.aug_max = aug_max;
   P.upool = uoff;
-  return validate_plan(cs, P);
+  if (int st = validate_plan(cs, P)) return st;
+  // the kernel's job records; counters: forward completions [0, nfronts), backward
+  // completions [nfronts, 2 nfronts), chunk slots after them
+  P.meta.assign(jobs.size(), SweepMeta{});
+  for (size_t j = 0; j < jobs.size(); ++j) {
+    const SweepJob& J = jobs[j];
+    const FrontDesc& d = desc[J.front];
+    SweepMeta& m = P.meta[j];
+    m.kind = J.kind;
+    m.r0 = J.r0;
+    m.r1 = J.r1;
+    m.c0 = J.c0;
+    m.c1 = J.c1;
+    m.srows = J.srows;
+    m.nchunks = J.nchunks;
+    m.chunk = J.chunk;
+    m.slot = J.nchunks > 1 ? 2 * cs.nfronts + J.slot : -1;
+    m.pbase = J.pbase;
+    m.nS = d.nS;
+    m.nB = d.nB;
+    m.S_off = d.S_off;
+    m.B_off = d.B_off;
+    m.bsign = d.bsign;
+    m.front = J.front;
+    m.ld = J.kind == 0 ? d.nS + d.nB : d.g_ld;
+    m.src = (J.kind == 0 ? d.M_off : d.G_off) + (long long)J.r0 * m.ld + J.c0;
+    m.ctb_off = d.ctb_off;
+    m.uv_off = d.uv_off;
+    m.done = J.kind == 0 ? J.front : cs.nfronts + J.front;
+    if (J.kind == 0) {
+      if (d.nkids > 2) {
+        set_error("coarsest solve plan: a front with more than two children");
+        return HELM_EINVAL;
+      }
+      m.nwait = d.nkids;
+      for (int q = 0; q < d.nkids; ++q) {
+        const int k = P.kids[d.kid_off + q];
+        m.wait[q] = k;
+        m.target[q] = desc[k].fwd_units;
+      }
+    } else if (d.parent < 0) {
+      m.nwait = 1;
+      m.wait[0] = J.front;
+      m.target[0] = d.fwd_units;
+    } else {
+      m.nwait = 1;
+      m.wait[0] = cs.nfronts + d.parent;
+      m.target[0] = desc[d.parent].bwd_units;
+    }
+  }
+  return 0;
 }
 
 int coarse_plan_stats(const GridDims& g, int r, int leaf_max, bool symmetric, int grid, long long stats[8]) {
@@ -681,7 +732,7 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
     return HELM_ECUDA;
   int2* d_ents = nullptr;
   if (upload(&d_ents, P.ents)) return HELM_ECUDA;
-  if (upload(&cs.d_jobs, P.jobs)) return HELM_ECUDA;
+  if (upload(&cs.d_meta, P.meta)) return HELM_ECUDA;
   for (int h = 0; h < cs.nlevels; ++h) {
     if (upload(&cs.d_level_list[h], cs.level_fronts[h]) || upload(&cs.big_list[h], bigs[h]) ||
         upload(&cs.small_list[h], smalls[h]))
@@ -839,7 +890,7 @@ void coarse_free(CoarseSolver& cs) {
   cudaFree(cs.d_factors);
   cudaFree(cs.d_err);
   for (auto p : cs.d_level_list) cudaFree(p);
-  cudaFree(cs.d_jobs);
+  cudaFree(cs.d_meta);
   for (auto p : cs.big_list) cudaFree(p);
   for (auto p : cs.small_list) cudaFree(p);
   cudaFree(cs.d_part);

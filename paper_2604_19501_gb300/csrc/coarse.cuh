@@ -55,6 +55,22 @@ struct SweepJob {
   int nchunks, chunk, slot, pbase;
 };
 
+// Everything the solve kernel reads about one job, flattened on the host from the job and
+// its front so that a job costs one 128-byte read; a block reads its next job's record
+// while it runs the current one.
+struct alignas(16) SweepMeta {
+  int kind, r0, r1, c0;            // as SweepJob
+  int c1, srows, nchunks, chunk;
+  int slot, pbase, nS, nB;         // slot and pbase as SweepJob; the front's sizes
+  int S_off, B_off, bsign, nwait;  // the front's node-index offsets and update sign; dependencies (0-2)
+  int wait[2], target[2];          // counter indices and the counts they must reach before the job runs
+  int done, ld;                    // counter the job's output unit completes; factor row stride
+  long long src;                   // factor entry of row r0, column c0
+  long long ctb_off, uv_off;       // the front's child-contribution map and update-vector offsets
+  int front, pad[3];
+};
+static_assert(sizeof(SweepMeta) == 128, "one 128-byte record per job");
+
 struct CoarseSolver {
   GridDims g;
   int r = 1;                          // stencil radius of the coarsest operator
@@ -71,7 +87,7 @@ struct CoarseSolver {
   long long bwd_entries = 0;          // entries of the G blocks (read again by the backward sweep)
   std::vector<int*> d_level_list;     // per level: front ids
   std::vector<int*> big_list, small_list;   // per level: fronts by elimination path
-  SweepJob* d_jobs = nullptr;         // the solve kernel's job list
+  SweepMeta* d_meta = nullptr;        // the solve kernel's job list
   int njobs = 0;
   int grid = 0;                       // resident blocks of the solve kernel
   long long part_blocks = 1;          // partial-sum blocks (kPartBlock entries per right-hand side)

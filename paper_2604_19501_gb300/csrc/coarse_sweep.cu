@@ -26,6 +26,7 @@
 // split into a fixed number of interleaved parts per column, combined in part order, and
 // job partial sums in chunk order.  None of it depends on the number of right-hand sides
 // solved together.
+#include <cstddef>
 #include <type_traits>
 #include "coarse.cuh"
 #include "df64.cuh"
@@ -48,19 +49,26 @@ template <int RG>
 __host__ __device__ constexpr int local_bytes() {
   return ((kJobRows > kSweepThreads ? kJobRows : kSweepThreads) + kTile) * RG * 16;
 }
+// after the local scratch: two job records, the ring's mbarriers, two flags and the
+// output columns' nodes of the current and the next job
 template <int RG>
-__host__ __device__ constexpr int smem_bytes() { return ring_stages<RG>() * kStageBytes + local_bytes<RG>() + 2048; }
+__host__ __device__ constexpr int tail_bytes() {
+  return 2 * (int)sizeof(SweepMeta) + 2 * ring_stages<RG>() * 8 + 16 + 2 * kTile * 4;
+}
+template <int RG>
+__host__ __device__ constexpr int smem_bytes() {
+  return ring_stages<RG>() * kStageBytes + local_bytes<RG>() + (tail_bytes<RG>() + 127) / 128 * 128;
+}
+static_assert(offsetof(SweepMeta, ld) == 21 * 4 && offsetof(SweepMeta, src) == 22 * 4, "record words read by the producer");
 static_assert(smem_bytes<kRhsGroup>() * 2 + 2048 <= 233472, "two blocks per multiprocessor");
 static_assert(kTile <= kPartBlock, "partial block");
 static_assert(kTile <= kSweepThreads, "one thread per output column at least");
 
 struct SweepArgs {
-  const FrontDesc* desc;
-  const SweepJob* jobs;
+  const SweepMeta* meta;
   int njobs;
   const int* S;
   const int* B;
-  const int* kids;
   const int2* ctb;
   const double2* factors;
   const double2* b;
@@ -69,9 +77,7 @@ struct SweepArgs {
   double2* x;
   float4* xd;
   double2* part;
-  unsigned* fwd_done;
-  unsigned* bwd_done;
-  unsigned* slots;
+  unsigned* counters;   // forward completions, backward completions, chunk slots
   int* err;
   int nrhs;
   long long nodes;
@@ -106,6 +112,18 @@ __device__ __forceinline__ int ld_relaxed(const int* p) {
   int v;
   asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+
+// Completion counts.  A block publishes its writes by a barrier over its consumer threads
+// followed by one release increment; a waiter's acquire load followed by the same barrier
+// makes them visible to all its consumer threads.
+__device__ __forceinline__ void red_release(unsigned* p) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p) : "memory");
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+  return old;
 }
 
 // *p >= target within the time limit; false on a timeout (recorded) or when another
@@ -159,36 +177,37 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
 // ---- the block's sequence of stage fills: its jobs with factor rows, every pass over
 // the right-hand-side groups, every stage of the job.  The cursor keeps the current job's
 // copy source so that a fill reads no job data from memory.
-__device__ __forceinline__ int job_stages(const SweepJob& J) {
-  return J.srows ? (J.r1 - J.r0 + J.srows - 1) / J.srows : 0;
-}
+__device__ __forceinline__ int job_stages(int rows, int srows) { return srows ? (rows + srows - 1) / srows : 0; }
 struct Cursor {
   int j, pass, k, nst;
   int rows, cols, srows;
   long long ld;
   const double2* src;   // factor row r0 of the job, column c0
 };
-__device__ void cursor_load(Cursor& c, const SweepArgs& a) {
+// The producer warp's next job with factor rows: lane l reads word l of the record.
+__device__ void cursor_load(Cursor& c, const SweepArgs& a, int lane) {
   for (; c.j < a.njobs; c.j += gridDim.x) {
-    const SweepJob J = a.jobs[c.j];
-    c.nst = job_stages(J);
+    const int w = reinterpret_cast<const int*>(a.meta + c.j)[lane];
+    auto f = [&](int i) { return __shfl_sync(0xffffffffu, w, i); };
+    const int r0 = f(1), r1 = f(2), c0 = f(3), c1 = f(4), srows = f(5);
+    c.nst = job_stages(r1 - r0, srows);
     if (!c.nst) continue;
-    const FrontDesc& d = a.desc[J.front];
-    c.rows = J.r1 - J.r0;
-    c.cols = J.c1 - J.c0;
-    c.srows = J.srows;
-    c.ld = J.kind == 0 ? (long long)(d.nS + d.nB) : (long long)d.g_ld;
-    c.src = a.factors + (J.kind == 0 ? d.M_off : d.G_off) + (long long)J.r0 * c.ld + J.c0;
+    c.rows = r1 - r0;
+    c.cols = c1 - c0;
+    c.srows = srows;
+    c.ld = f(21);
+    const long long src = (long long)(unsigned)f(22) | ((long long)f(23) << 32);
+    c.src = a.factors + src;
     return;
   }
 }
-__device__ void cursor_next(Cursor& c, const SweepArgs& a, int npass) {
+__device__ void cursor_next(Cursor& c, const SweepArgs& a, int npass, int lane) {
   if (++c.k < c.nst) return;
   c.k = 0;
   if (++c.pass < npass) return;
   c.pass = 0;
   c.j += gridDim.x;
-  cursor_load(c, a);
+  cursor_load(c, a, lane);
 }
 // Warp 0: copy the factor rows of the cursor's stage into shared memory at dst.
 __device__ void issue_stage(const Cursor& c, uint32_t dst, uint32_t bar, int lane) {
@@ -207,15 +226,6 @@ __device__ void issue_stage(const Cursor& c, uint32_t dst, uint32_t bar, int lan
   }
 }
 
-// r_F at front position t: b at the eliminated nodes plus the children's update-vector
-// entries mapped to t (at most one per child), added in child order.
-__device__ __forceinline__ double2 front_rhs(const SweepArgs& a, const FrontDesc& d, int t, int r) {
-  double2 v = t < d.nS ? a.b[r * a.nodes + a.S[d.S_off + t]] : make_double2(0.0, 0.0);
-  const int2 c = a.ctb[d.ctb_off + t];
-  if (c.x >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + c.x));
-  if (c.y >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + c.y));
-  return v;
-}
 constexpr int kBlockThreads = kSweepThreads + 32;   // consumers + one producer warp
 
 __device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kSweepThreads) : "memory"); }
@@ -234,17 +244,19 @@ __global__ void __launch_bounds__(kBlockThreads, 2) sweep_kernel(const SweepArgs
   constexpr int kColItems = (kTile * RG + kSweepThreads - 1) / kSweepThreads;
   constexpr int NST = ring_stages<RG>();
   constexpr int kLocalBytes = local_bytes<RG>();
+  constexpr int kMetaWarp = kSweepThreads / 32 - 1;   // the consumer warp that reads job records
   extern __shared__ __align__(128) unsigned char smem[];
   E* const stage = reinterpret_cast<E*>(smem);
   unsigned char* const local = smem + NST * kStageBytes;
   E* const vs = reinterpret_cast<E*>(local);   // row values [kJobRows][RG]
   E* const red = vs;                           // row-part sums [threads][RG], after the stages
   double2* const rbs = reinterpret_cast<double2*>(vs + (kJobRows > kSweepThreads ? kJobRows : kSweepThreads) * RG);   // forward r_B [kTile][RG]
-  uint64_t* const full = reinterpret_cast<uint64_t*>(local + kLocalBytes);
+  SweepMeta* const metas = reinterpret_cast<SweepMeta*>(local + kLocalBytes);   // [2]: current and next job
+  uint64_t* const full = reinterpret_cast<uint64_t*>(metas + 2);
   uint64_t* const empty = full + NST;
   volatile int* const flag = reinterpret_cast<volatile int*>(empty + NST);
   volatile int* const abort_copy = flag + 1;
-  int* const sidx = const_cast<int*>(flag) + 4;                         // node of each output column [kTile]
+  int* const sidx2 = const_cast<int*>(flag) + 4;   // node of each output column [2][kTile]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int npass = (a.nrhs + RG - 1) / RG;
 
@@ -257,6 +269,8 @@ __global__ void __launch_bounds__(kBlockThreads, 2) sweep_kernel(const SweepArgs
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
+  if (warp == kMetaWarp && (int)blockIdx.x < a.njobs)
+    reinterpret_cast<int*>(metas)[lane] = reinterpret_cast<const int*>(a.meta + blockIdx.x)[lane];
   __syncthreads();
 
   if (warp == kSweepThreads / 32) {
@@ -264,7 +278,7 @@ __global__ void __launch_bounds__(kBlockThreads, 2) sweep_kernel(const SweepArgs
     Cursor pc;
     pc.j = blockIdx.x;
     pc.pass = pc.k = 0;
-    cursor_load(pc, a);
+    cursor_load(pc, a, lane);
     long long i = 0;
     for (; pc.j < a.njobs; ++i) {
       const int q = (int)(i % NST);
@@ -275,7 +289,7 @@ __global__ void __launch_bounds__(kBlockThreads, 2) sweep_kernel(const SweepArgs
       }
       if (*abort_copy) break;
       issue_stage(pc, smem_u32(stage + q * kStageEntries), smem_u32(&full[q]), lane);
-      cursor_next(pc, a, npass);
+      cursor_next(pc, a, npass, lane);
     }
     // copies still in flight must land before the block may exit (bounded)
     for (long long q = i > NST ? i - NST : 0; q < i; ++q)
@@ -301,113 +315,89 @@ __global__ void __launch_bounds__(kBlockThreads, 2) sweep_kernel(const SweepArgs
     if (lane == 0) mbar_arrive(smem_u32(&empty[q]));
   };
 
-  for (int j = blockIdx.x; j < a.njobs; j += gridDim.x) {
-    const SweepJob J = a.jobs[j];
-    const FrontDesc d = a.desc[J.front];
-    const bool fwd = J.kind == 0;
-    const int nst = job_stages(J);
-    const int rows = J.r1 - J.r0, cols = J.c1 - J.c0;
-
-    // Gathers of one pass, split into what is known before the dependencies complete
-    // (right-hand side b, node and child-map indices) and what other blocks of this
-    // launch write (children's update vectors; the ancestors' x_B).
-    double2 pv[kRowItems];
-    int2 pc2[kRowItems], qc2[kColItems];
-    auto gather_pre = [&](int r0, int nr) {
-      for (int q = tid; q < cols; q += kSweepThreads) {
-        const int t = J.c0 + q;
-        sidx[q] = (!fwd || t < d.nS) ? a.S[d.S_off + t] : -1;
-      }
+  // Gathers of one pass in three steps: indices (node and child-map entries, known
+  // before the job runs), the right-hand side b at the row nodes (forward; also known
+  // before), and what other blocks of this launch write (children's update vectors; the
+  // ancestors' x_B and this front's w), read once the job's dependencies have completed.
+  // The first two steps of a job's first pass run while the block finishes its previous
+  // job.
+  int sI[kColItems];            // node of output column item
+  int pI[kRowItems];            // forward: node of row item; backward: node of boundary row item
+  int2 pc2[kRowItems], qc2[kColItems];
+  double2 pv[kRowItems];
+  auto gather_idx = [&](const SweepMeta& m, int r0, int nr) {
+    const bool fw = m.kind == 0;
+    const int rows = m.r1 - m.r0, cols = m.c1 - m.c0;
 #pragma unroll
-      for (int i = 0; i < kRowItems; ++i) {
-        const int q = tid + i * kSweepThreads;
-        if (q < rows * nr) {
-          const int t = J.r0 + q / nr, r = r0 + q % nr;
-          if (fwd) {
-            pv[i] = a.b[r * a.nodes + a.S[d.S_off + t]];
-            pc2[i] = a.ctb[d.ctb_off + t];
-          } else {
-            pc2[i].x = a.B[d.B_off + t];
-          }
-        }
+    for (int i = 0; i < kColItems; ++i) {
+      const int q = tid + i * kSweepThreads;
+      if (q < cols) {
+        const int t = m.c0 + q;
+        sI[i] = (!fw || t < m.nS) ? a.S[m.S_off + t] : -1;
       }
-      if (fwd)
+    }
 #pragma unroll
-        for (int i = 0; i < kColItems; ++i) {
-          const int q = tid + i * kSweepThreads;
-          if (q < cols * nr) {
-            const int t = J.c0 + q / nr;
-            qc2[i] = t >= d.nS ? a.ctb[d.ctb_off + t] : make_int2(-1, -1);
-          }
-        }
-    };
-    auto gather_post = [&](int r0, int nr) {
-#pragma unroll
-      for (int i = 0; i < kRowItems; ++i) {
-        const int q = tid + i * kSweepThreads;
-        if (q < rows * nr) {
-          const int r = r0 + q % nr;
-          E* dst = vs + (q / nr) * RG + q % nr;
-          if (fwd) {
-            double2 v = pv[i];
-            if (pc2[i].x >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + pc2[i].x));
-            if (pc2[i].y >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + pc2[i].y));
-            from_c128(*dst, v);
-          } else {
-            const long long gi = r * a.nodes + pc2[i].x;
-            if (DF) *reinterpret_cast<float4*>(dst) = __ldcg(a.xd + gi);
-            else *reinterpret_cast<double2*>(dst) = __ldcg(a.x + gi);
-          }
-        }
-      }
-      if (fwd)
-#pragma unroll
-        for (int i = 0; i < kColItems; ++i) {
-          const int q = tid + i * kSweepThreads;
-          if (q < cols * nr) {
-            const int r = r0 + q % nr;
-            double2 v = make_double2(0.0, 0.0);
-            if (qc2[i].x >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + qc2[i].x));
-            if (qc2[i].y >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + qc2[i].y));
-            rbs[(q / nr) * RG + q % nr] = v;
-          }
-        }
-    };
-    // result v of column c for right-hand side r: forward, w at node S[t] (t = c0 + c < nS)
-    // or the update-vector entry r_B + bsign v; backward, x_S = w_S - v
-    auto write_out = [&](int c, int r, double2 v, double2 rb) {
-      const int t = J.c0 + c;
-      if (fwd && t >= d.nS) {
-        a.uv[r * a.uv_total + d.uv_off + t - d.nS] = make_double2(rb.x + d.bsign * v.x, rb.y + d.bsign * v.y);
-        return;
-      }
-      const long long gi = r * a.nodes + sidx[c];
-      if (fwd) {
-        a.w[gi] = v;
-      } else {
-        const double2 wv = __ldcg(a.w + gi);
-        const double2 xv = make_double2(wv.x - v.x, wv.y - v.y);
-        a.x[gi] = xv;
-        if (DF) a.xd[gi] = to_df(xv);
-      }
-    };
-
-    gather_pre(0, min(RG, a.nrhs));
-    // dependencies
-    if (tid == 0) {
-      bool good = ok && !ld_relaxed(a.err);
-      if (good) {
-        if (fwd) {
-          for (int q = 0; q < d.nkids && good; ++q) {
-            const int k = a.kids[d.kid_off + q];
-            good = wait_count(a.fwd_done + k, (unsigned)a.desc[k].fwd_units, a.err);
-          }
-        } else if (d.parent < 0) {
-          good = wait_count(a.fwd_done + J.front, (unsigned)d.fwd_units, a.err);
+    for (int i = 0; i < kRowItems; ++i) {
+      const int q = tid + i * kSweepThreads;
+      if (q < rows * nr) {
+        const int t = m.r0 + q / nr;
+        if (fw) {
+          pI[i] = a.S[m.S_off + t];
+          pc2[i] = a.ctb[m.ctb_off + t];
         } else {
-          good = wait_count(a.bwd_done + d.parent, (unsigned)a.desc[d.parent].bwd_units, a.err);
+          pI[i] = a.B[m.B_off + t];
         }
-        __threadfence();
+      }
+    }
+    if (fw)
+#pragma unroll
+      for (int i = 0; i < kColItems; ++i) {
+        const int q = tid + i * kSweepThreads;
+        if (q < cols * nr) {
+          const int t = m.c0 + q / nr;
+          qc2[i] = t >= m.nS ? a.ctb[m.ctb_off + t] : make_int2(-1, -1);
+        }
+      }
+  };
+  auto gather_b = [&](const SweepMeta& m, int r0, int nr) {
+    if (m.kind != 0) return;
+    const int rows = m.r1 - m.r0;
+#pragma unroll
+    for (int i = 0; i < kRowItems; ++i) {
+      const int q = tid + i * kSweepThreads;
+      if (q < rows * nr) pv[i] = a.b[(r0 + q % nr) * a.nodes + pI[i]];
+    }
+  };
+
+  bool pre_done = false;   // the current job's first-pass indices and b are already in registers
+  int cur = 0;
+  for (int j = blockIdx.x; j < a.njobs; j += gridDim.x, cur ^= 1) {
+    const SweepMeta& m = metas[cur];
+    int* const sidx = sidx2 + cur * kTile;
+    const bool fwd = m.kind == 0;
+    const int r0j = m.r0, c0j = m.c0, nS = m.nS;
+    const int rows = m.r1 - r0j, cols = m.c1 - c0j;
+    const int nst = job_stages(rows, m.srows);
+    const int nchunks = m.nchunks;
+    const int jn = j + gridDim.x;
+    // the next job's record, read now and stored after this job's stages
+    int next_word = 0;
+    if (warp == kMetaWarp && jn < a.njobs) next_word = reinterpret_cast<const int*>(a.meta + jn)[lane];
+
+    if (!pre_done) {
+      gather_idx(m, 0, min(RG, a.nrhs));
+      gather_b(m, 0, min(RG, a.nrhs));
+    }
+#pragma unroll
+    for (int i = 0; i < kColItems; ++i)
+      if (tid + i * kSweepThreads < cols) sidx[tid + i * kSweepThreads] = sI[i];
+    // dependencies: acquire loads of the completion counters (tid 0), then the barrier
+    if (tid == 0) {
+      bool good = ok;
+      if (good && m.nwait > 0) {
+        good = !ld_relaxed(a.err);
+        for (int q = 0; q < m.nwait && good; ++q)
+          good = wait_count(a.counters + m.wait[q], (unsigned)m.target[q], a.err);
       }
       *flag = good;
     }
@@ -420,10 +410,51 @@ __global__ void __launch_bounds__(kBlockThreads, 2) sweep_kernel(const SweepArgs
     const int nsplit = min(kSplitMax, kSweepThreads / cols);
     const int c = tid % cols, part = tid / cols;
     const bool act = part < nsplit;
+    double2 wv[RG];   // backward: w at this thread's output column
     for (int p = 0; p < npass; ++p) {
       const int r0 = p * RG, nr = min(RG, a.nrhs - r0);
-      if (p > 0) gather_pre(r0, nr);
-      if (ok) gather_post(r0, nr);
+      if (p > 0) {
+        gather_idx(m, r0, nr);
+        gather_b(m, r0, nr);
+      }
+      if (ok) {
+        // values written by other blocks of this launch
+#pragma unroll
+        for (int i = 0; i < kRowItems; ++i) {
+          const int q = tid + i * kSweepThreads;
+          if (q < rows * nr) {
+            const int r = r0 + q % nr;
+            E* dst = vs + (q / nr) * RG + q % nr;
+            if (fwd) {
+              double2 v = pv[i];
+              if (pc2[i].x >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + pc2[i].x));
+              if (pc2[i].y >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + pc2[i].y));
+              from_c128(*dst, v);
+            } else {
+              const long long gi = r * a.nodes + pI[i];
+              if (DF) *reinterpret_cast<float4*>(dst) = __ldcg(a.xd + gi);
+              else *reinterpret_cast<double2*>(dst) = __ldcg(a.x + gi);
+            }
+          }
+        }
+        if (fwd) {
+#pragma unroll
+          for (int i = 0; i < kColItems; ++i) {
+            const int q = tid + i * kSweepThreads;
+            if (q < cols * nr) {
+              const int r = r0 + q % nr;
+              double2 v = make_double2(0.0, 0.0);
+              if (qc2[i].x >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + qc2[i].x));
+              if (qc2[i].y >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + qc2[i].y));
+              rbs[(q / nr) * RG + q % nr] = v;
+            }
+          }
+        } else if (nchunks == 1 && tid < cols) {
+#pragma unroll
+          for (int rr = 0; rr < RG; ++rr)
+            if (rr < nr) wv[rr] = __ldcg(a.w + (r0 + rr) * a.nodes + sI[0]);
+        }
+      }
       consumer_sync();
       E acc[RG];
 #pragma unroll
@@ -431,31 +462,49 @@ __global__ void __launch_bounds__(kBlockThreads, 2) sweep_kernel(const SweepArgs
       for (int k = 0; k < nst; ++k) {
         consume([&](const E* st) {
           if (!act) return;
-          const int base = k * J.srows, n = min(J.srows, rows - base);
+          const int base = k * m.srows, n = min(m.srows, rows - base);
 #pragma unroll 2
           for (int q = part; q < n; q += nsplit) {
-            const E m = st[q * cols + c];
+            const E mv = st[q * cols + c];
             const E* rv = vs + (base + q) * RG;
 #pragma unroll
             for (int rr = 0; rr < RG; ++rr)
-              if (RG == 1 || rr < nr) mac(acc[rr], m, rv[rr]);
+              if (RG == 1 || rr < nr) mac(acc[rr], mv, rv[rr]);
           }
         });
       }
-      consumer_sync();   // every thread is done with the row values red overwrites
+      const bool last = p == npass - 1;
+      if (last && warp == kMetaWarp && jn < a.njobs) reinterpret_cast<int*>(metas + (cur ^ 1))[lane] = next_word;
+      consumer_sync();   // every thread is done with the row values red overwrites; the next record is in place
       if (ok && act)
 #pragma unroll
         for (int rr = 0; rr < RG; ++rr) red[tid * RG + rr] = acc[rr];
+      // the next job's indices, read while this one finishes (its b once they have arrived)
+      pre_done = last && jn < a.njobs;
+      if (pre_done) gather_idx(metas[cur ^ 1], 0, min(RG, a.nrhs));
       consumer_sync();
       if (ok && tid < cols) {
         for (int rr = 0; rr < nr; ++rr) {
           E v = red[tid * RG + rr];
           for (int pp = 1; pp < nsplit; ++pp) addto(v, red[(pp * cols + tid) * RG + rr]);
           const int r = r0 + rr;
-          if (J.nchunks == 1)
-            write_out(tid, r, to_c128(v), fwd ? rbs[tid * RG + rr] : make_double2(0.0, 0.0));
-          else
-            reinterpret_cast<E*>(a.part)[((long long)(J.pbase + J.chunk) * a.nrhs + r) * kPartBlock + tid] = v;
+          if (nchunks == 1) {
+            const double2 o = to_c128(v);
+            const int t = c0j + tid;
+            if (fwd && t >= nS) {
+              const double2 rb = rbs[tid * RG + rr];
+              a.uv[r * a.uv_total + m.uv_off + t - nS] = make_double2(rb.x + m.bsign * o.x, rb.y + m.bsign * o.y);
+            } else if (fwd) {
+              a.w[r * a.nodes + sidx[tid]] = o;
+            } else {
+              const long long gi = r * a.nodes + sidx[tid];
+              const double2 xv = make_double2(wv[rr].x - o.x, wv[rr].y - o.y);
+              a.x[gi] = xv;
+              if (DF) a.xd[gi] = to_df(xv);
+            }
+          } else {
+            reinterpret_cast<E*>(a.part)[((long long)(m.pbase + m.chunk) * a.nrhs + r) * kPartBlock + tid] = v;
+          }
         }
       }
       consumer_sync();
@@ -463,43 +512,55 @@ __global__ void __launch_bounds__(kBlockThreads, 2) sweep_kernel(const SweepArgs
     ok = ok && !*abort_copy;
 
     // ---- output unit: the last of its jobs adds the partial sums in chunk order
-    bool finalized = J.nchunks == 1;
+    bool finalized = nchunks == 1;
     if (!finalized) {
-      __threadfence();
-      consumer_sync();
-      if (tid == 0) *flag = ok && atomicAdd(a.slots + J.slot, 1u) == (unsigned)J.nchunks - 1;
+      if (tid == 0) *flag = ok && atom_add_acq_rel(a.counters + m.slot) == (unsigned)nchunks - 1;
       consumer_sync();
       finalized = *flag;
       consumer_sync();
       if (finalized) {
-        __threadfence();
         const E* P = reinterpret_cast<const E*>(a.part);
         const long long step = (long long)a.nrhs * kPartBlock;
         for (int q = tid; q < cols * a.nrhs; q += kSweepThreads) {
           const int i = q % cols, r = q / cols;
-          const E* src = P + ((long long)J.pbase * a.nrhs + r) * kPartBlock + i;
+          const E* src = P + ((long long)m.pbase * a.nrhs + r) * kPartBlock + i;
           E v;
           zero(v);
           int ch = 0;
-          for (; ch + 8 <= J.nchunks; ch += 8) {
-            E t[8];
+          for (; ch + 8 <= nchunks; ch += 8) {
+            E t8[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) t[u] = ldcg(src + (ch + u) * step);
+            for (int u = 0; u < 8; ++u) t8[u] = ldcg(src + (ch + u) * step);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) addto(v, t[u]);
+            for (int u = 0; u < 8; ++u) addto(v, t8[u]);
           }
-          for (; ch < J.nchunks; ++ch) addto(v, ldcg(src + ch * step));
-          const int t = J.c0 + i;
-          write_out(i, r, to_c128(v), fwd && t >= d.nS ? front_rhs(a, d, t, r) : make_double2(0.0, 0.0));
+          for (; ch < nchunks; ++ch) addto(v, ldcg(src + ch * step));
+          const double2 o = to_c128(v);
+          const int t = c0j + i;
+          if (fwd && t >= nS) {
+            // r_F at t: the children's update-vector entries mapped to t (t is a boundary position)
+            double2 rb = make_double2(0.0, 0.0);
+            const int2 cc = a.ctb[m.ctb_off + t];
+            if (cc.x >= 0) addto(rb, __ldcg(a.uv + r * a.uv_total + cc.x));
+            if (cc.y >= 0) addto(rb, __ldcg(a.uv + r * a.uv_total + cc.y));
+            a.uv[r * a.uv_total + m.uv_off + t - nS] = make_double2(rb.x + m.bsign * o.x, rb.y + m.bsign * o.y);
+          } else {
+            const long long gi = r * a.nodes + sidx[i];
+            if (fwd) {
+              a.w[gi] = o;
+            } else {
+              const double2 wv1 = __ldcg(a.w + gi);
+              const double2 xv = make_double2(wv1.x - o.x, wv1.y - o.y);
+              a.x[gi] = xv;
+              if (DF) a.xd[gi] = to_df(xv);
+            }
+          }
         }
       }
     }
-    if (finalized && ok) {
-      __threadfence();
-      consumer_sync();
-      if (tid == 0) atomicAdd((fwd ? a.fwd_done : a.bwd_done) + J.front, 1u);
-    }
     consumer_sync();
+    if (finalized && ok && tid == 0) red_release(a.counters + m.done);
+    if (pre_done) gather_b(metas[cur ^ 1], 0, min(RG, a.nrhs));
   }
 }
 
@@ -554,12 +615,10 @@ int sweep_launch(const CoarseSolver& cs, const double2* b, double2* e, int nrhs,
                  double2* part, unsigned* counters, float4* xd, cudaStream_t s) {
   HELM_CUDA_TRY(cudaMemsetAsync(counters, 0, cs.n_counters * sizeof(unsigned), s));
   SweepArgs a;
-  a.desc = cs.d_desc;
-  a.jobs = cs.d_jobs;
+  a.meta = cs.d_meta;
   a.njobs = cs.njobs;
   a.S = cs.d_S;
   a.B = cs.d_B;
-  a.kids = cs.d_kids;
   a.ctb = cs.d_ctb;
   a.factors = cs.d_factors;
   a.b = b;
@@ -568,9 +627,7 @@ int sweep_launch(const CoarseSolver& cs, const double2* b, double2* e, int nrhs,
   a.x = e;
   a.xd = xd;
   a.part = part;
-  a.fwd_done = counters;
-  a.bwd_done = counters + cs.nfronts;
-  a.slots = counters + 2 * cs.nfronts;
+  a.counters = counters;
   a.err = cs.d_err;
   a.nrhs = nrhs;
   a.nodes = cs.g.size;
