@@ -11,11 +11,11 @@ namespace helm {
 // Each block streams its jobs' factor rows through a ring of shared-memory stages filled
 // by bulk asynchronous copies, so a job's factors arrive while it waits for the fronts it
 // depends on.
-constexpr int kSweepThreads = 256;   // threads per block
+constexpr int kSweepThreads = 128;   // consumer threads per block
 constexpr int kStageEntries = 1024;  // 16-byte factor entries per stage (16 KiB)
-constexpr int kJobRows = 256;        // most factor rows of one job
-constexpr int kTile = 256;           // output columns of one job (one thread each at most)
-constexpr int kPartBlock = 256;      // partial-sum entries per chunk and right-hand side
+constexpr int kJobRows = 128;        // most factor rows of one job
+constexpr int kTile = 128;           // output columns of one job (one thread each at most)
+constexpr int kPartBlock = 128;      // partial-sum entries per chunk and right-hand side
 constexpr int kRhsGroup = 4;         // right-hand sides sharing each staged factor entry
 
 // Error codes the solve kernel leaves in CoarseSolver::d_err.

@@ -40,9 +40,13 @@ constexpr int kSplitMax = 16;                              // forward row parts 
 // monotonic per multiprocessor): about 2 s at the maximum SM clock, longer below it.
 constexpr long long kWaitCycles = 4000000000LL;
 constexpr int kStageBytes = kStageEntries * 16;
-// The ring is deeper for single right-hand sides, whose per-job scratch is smaller.
+// Resident blocks per multiprocessor the kernel is shaped for: enough jobs in flight that
+// one job's fixed latencies (dependency wait, gathers, write-back) overlap the others'
+// streaming.  The rings of the blocks together keep 192 KiB (one right-hand side) of
+// factor rows in flight per multiprocessor.
+constexpr int kSweepBlocksPerSM = 4;
 template <int RG>
-__host__ __device__ constexpr int ring_stages() { return RG == 1 ? 6 : 4; }
+__host__ __device__ constexpr int ring_stages() { return RG == 1 ? 3 : 2; }
 // per-job scratch: row values [kJobRows][RG] (reused for the row-part sums
 // [kSweepThreads][RG] once the job's stages are consumed) and forward r_B [kTile][RG]
 template <int RG>
@@ -60,7 +64,9 @@ __host__ __device__ constexpr int smem_bytes() {
   return ring_stages<RG>() * kStageBytes + local_bytes<RG>() + (tail_bytes<RG>() + 127) / 128 * 128;
 }
 static_assert(offsetof(SweepMeta, ld) == 21 * 4 && offsetof(SweepMeta, src) == 22 * 4, "record words read by the producer");
-static_assert(smem_bytes<kRhsGroup>() * 2 + 2048 <= 233472, "two blocks per multiprocessor");
+static_assert((smem_bytes<1>() + 1024) * kSweepBlocksPerSM <= 233472 &&
+                  (smem_bytes<kRhsGroup>() + 1024) * kSweepBlocksPerSM <= 233472,
+              "kSweepBlocksPerSM blocks per multiprocessor");
 static_assert(kTile <= kPartBlock, "partial block");
 static_assert(kTile <= kSweepThreads, "one thread per output column at least");
 
@@ -233,11 +239,11 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// Block layout: warps 0-7 consume (compute), warp 8 produces (copies factor rows into the
-// ring).  Stage i of the block's fill sequence uses slot i mod NST; full[slot] completes
+// Block layout: the first kSweepThreads / 32 warps consume (compute), the last warp
+// produces (copies factor rows into the ring).  Stage i of the block's fill sequence uses slot i mod NST; full[slot] completes
 // when its copies land, empty[slot] when all consumer warps are done with it.
 template <bool DF, int RG>
-__global__ void __launch_bounds__(kBlockThreads, 2) sweep_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(kBlockThreads, kSweepBlocksPerSM) sweep_kernel(const SweepArgs a) {
   using E = typename std::conditional<DF, float4, double2>::type;
   // gather items a consumer thread handles per pass: the job's rows x group, its columns x group
   constexpr int kRowItems = (kJobRows * RG + kSweepThreads - 1) / kSweepThreads;
