@@ -715,10 +715,11 @@ int coarse_plan_stats(const GridDims& g, int r, int leaf_max, bool symmetric, in
 
 int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef, int leaf_max,
                  bool symmetric, bool df, cudaStream_t s) {
-  int grid = 0;
-  if (int st = sweep_grid_size(&grid)) return st;
+  int grid = 0, grid_group = 0;
+  if (int st = sweep_grid_size(&grid, &grid_group)) return st;
   CoarsePlan P;
   if (int st = coarse_plan(cs, P, g, r, leaf_max, symmetric, grid)) return st;
+  cs.grid_group = grid_group;
   cs.df = df;
   const auto& desc = P.desc;
   const auto& bigs = P.bigs;

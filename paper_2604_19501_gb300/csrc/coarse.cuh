@@ -13,7 +13,7 @@ namespace helm {
 // depends on.
 constexpr int kSweepThreads = 128;   // consumer threads per block
 constexpr int kStageEntries = 1024;  // 16-byte factor entries per stage (16 KiB)
-constexpr int kJobRows = 128;        // most factor rows of one job
+constexpr int kJobRows = 256;        // most factor rows of one job
 constexpr int kTile = 128;           // output columns of one job (one thread each at most)
 constexpr int kPartBlock = 128;      // partial-sum entries per chunk and right-hand side
 constexpr int kRhsGroup = 4;         // right-hand sides sharing each staged factor entry
@@ -89,7 +89,8 @@ struct CoarseSolver {
   std::vector<int*> big_list, small_list;   // per level: fronts by elimination path
   SweepMeta* d_meta = nullptr;        // the solve kernel's job list
   int njobs = 0;
-  int grid = 0;                       // resident blocks of the solve kernel
+  int grid = 0;                       // resident blocks of the solve kernel (one right-hand side)
+  int grid_group = 0;                 // resident blocks for right-hand-side groups
   long long part_blocks = 1;          // partial-sum blocks (kPartBlock entries per right-hand side)
   int n_slots = 0;                    // output units split into several jobs
   long long n_counters = 0;           // forward and backward completion counts, then the slots
@@ -130,7 +131,7 @@ int coarse_status(const CoarseSolver& cs, cudaStream_t s);
 
 // Solve kernel (coarse_sweep.cu): resident blocks on this device, and one launch over
 // the job list with the given scratch (counters cleared first).
-int sweep_grid_size(int* grid);
+int sweep_grid_size(int* grid, int* grid_group);
 int sweep_launch(const CoarseSolver& cs, const double2* b, double2* e, int nrhs, double2* uv, double2* w,
                  double2* part, unsigned* counters, float4* xd, cudaStream_t s);
 

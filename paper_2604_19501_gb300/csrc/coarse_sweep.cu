@@ -42,11 +42,13 @@ constexpr long long kWaitCycles = 4000000000LL;
 constexpr int kStageBytes = kStageEntries * 16;
 // Resident blocks per multiprocessor the kernel is shaped for: enough jobs in flight that
 // one job's fixed latencies (dependency wait, gathers, write-back) overlap the others'
-// streaming.  The rings of the blocks together keep 192 KiB (one right-hand side) of
-// factor rows in flight per multiprocessor.
-constexpr int kSweepBlocksPerSM = 4;
+// streaming.  Single right-hand sides run four blocks, groups (with four times the
+// per-job scratch) three; the rings keep 192 KiB or 144 KiB of factor rows in flight
+// per multiprocessor.
 template <int RG>
-__host__ __device__ constexpr int ring_stages() { return RG == 1 ? 3 : 2; }
+__host__ __device__ constexpr int blocks_per_sm_target() { return RG == 1 ? 4 : 3; }
+template <int RG>
+__host__ __device__ constexpr int ring_stages() { return 3; }
 // per-job scratch: row values [kJobRows][RG] (reused for the row-part sums
 // [kSweepThreads][RG] once the job's stages are consumed) and forward r_B [kTile][RG]
 template <int RG>
@@ -64,9 +66,9 @@ __host__ __device__ constexpr int smem_bytes() {
   return ring_stages<RG>() * kStageBytes + local_bytes<RG>() + (tail_bytes<RG>() + 127) / 128 * 128;
 }
 static_assert(offsetof(SweepMeta, ld) == 21 * 4 && offsetof(SweepMeta, src) == 22 * 4, "record words read by the producer");
-static_assert((smem_bytes<1>() + 1024) * kSweepBlocksPerSM <= 233472 &&
-                  (smem_bytes<kRhsGroup>() + 1024) * kSweepBlocksPerSM <= 233472,
-              "kSweepBlocksPerSM blocks per multiprocessor");
+static_assert((smem_bytes<1>() + 1024) * blocks_per_sm_target<1>() <= 233472 &&
+                  (smem_bytes<kRhsGroup>() + 1024) * blocks_per_sm_target<kRhsGroup>() <= 233472,
+              "the targeted blocks per multiprocessor fit in shared memory");
 static_assert(kTile <= kPartBlock, "partial block");
 static_assert(kTile <= kSweepThreads, "one thread per output column at least");
 
@@ -243,7 +245,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // produces (copies factor rows into the ring).  Stage i of the block's fill sequence uses slot i mod NST; full[slot] completes
 // when its copies land, empty[slot] when all consumer warps are done with it.
 template <bool DF, int RG>
-__global__ void __launch_bounds__(kBlockThreads, kSweepBlocksPerSM) sweep_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) sweep_kernel(const SweepArgs a) {
   using E = typename std::conditional<DF, float4, double2>::type;
   // gather items a consumer thread handles per pass: the job's rows x group, its columns x group
   constexpr int kRowItems = (kJobRows * RG + kSweepThreads - 1) / kSweepThreads;
@@ -572,6 +574,8 @@ __global__ void __launch_bounds__(kBlockThreads, kSweepBlocksPerSM) sweep_kernel
 
 template <bool DF, int RG>
 cudaError_t launch_one(const SweepArgs& a, int grid, cudaStream_t s) {
+  // every block of the grid must be resident (cooperative launch): the schedule's waits
+  // rely on it; any such grid size is correct, the job sizes were planned for cs.grid
   static bool attr = false;
   if (!attr) {
     const cudaError_t e = cudaFuncSetAttribute(sweep_kernel<DF, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<RG>());
@@ -603,17 +607,18 @@ int blocks_per_sm() {
 
 }  // namespace
 
-int sweep_grid_size(int* grid) {
+int sweep_grid_size(int* grid, int* grid_group) {
   int dev = 0, sms = 0;
   HELM_CUDA_TRY(cudaGetDevice(&dev));
   HELM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int per_sm = std::min(std::min(blocks_per_sm<true, 1>(), blocks_per_sm<true, kRhsGroup>()),
-                              std::min(blocks_per_sm<false, 1>(), blocks_per_sm<false, kRhsGroup>()));
-  if (per_sm < 1) {
+  const int per_sm = std::min(blocks_per_sm<true, 1>(), blocks_per_sm<false, 1>());
+  const int per_sm_group = std::min(blocks_per_sm<true, kRhsGroup>(), blocks_per_sm<false, kRhsGroup>());
+  if (per_sm < 1 || per_sm_group < 1) {
     set_error("coarsest solve kernel does not fit on a multiprocessor");
     return HELM_ECUDA;
   }
   *grid = per_sm * sms;
+  *grid_group = per_sm_group * sms;
   return 0;
 }
 
@@ -640,7 +645,7 @@ int sweep_launch(const CoarseSolver& cs, const double2* b, double2* e, int nrhs,
   a.uv_total = cs.uv_total;
   cudaError_t le;
   if (nrhs == 1) le = cs.df ? launch_one<true, 1>(a, cs.grid, s) : launch_one<false, 1>(a, cs.grid, s);
-  else le = cs.df ? launch_one<true, kRhsGroup>(a, cs.grid, s) : launch_one<false, kRhsGroup>(a, cs.grid, s);
+  else le = cs.df ? launch_one<true, kRhsGroup>(a, cs.grid_group, s) : launch_one<false, kRhsGroup>(a, cs.grid_group, s);
   if (le != cudaSuccess) {
     set_error(std::string("coarsest solve launch: ") + cudaGetErrorString(le));
     return HELM_ECUDA;
