@@ -74,6 +74,13 @@ def parse():
                     help="complex shift beta of the cycle (RS-CGC + CSLP, Sec. 5: 0.03 for 10 ppw); 0 = RS-CGC")
     ap.add_argument("--graphs", action="store_true",
                     help="replay FGMRES iterations as CUDA graphs")
+    ap.add_argument("--dim", type=int, default=2, choices=[2, 3],
+                    help="3: the 3D configuration (Sec. 5.2 set-up: lev-dep transfers, Jacobi 0.6/0.4, "
+                         "no layer on the top face, source at the centre of the top face)")
+    ap.add_argument("--cells3", default="192,192,72",
+                    help="3D grid in cells incl. the absorbing layer (Table 4's largest: 192,192,72)")
+    ap.add_argument("--pad3", type=int, default=16, help="3D absorbing layer on the sides and the bottom")
+    ap.add_argument("--cpu-cells3", default="64,64,32", help="3D grid of the bounded CPU oracle sample")
     ap.add_argument("--medium", default="layered", choices=["layered", "linear", "wedge"],
                     help="layered: seeded layered/faulted medium, centre source; linear / wedge: the "
                          "2D heterogeneous models of Sec. 5.1 (Table 3), source at the top centre")
@@ -91,6 +98,8 @@ def workload(args):
 
     import workloads
 
+    if args.dim == 3:
+        return workload3(args)
     N = args.n + 2 * args.pad
     n = (N, N)
     if args.medium == "layered":
@@ -115,13 +124,45 @@ def workload(args):
     else:
         q = workloads.surface_sources(n, args.sources, args.pad, seed=0)
     return dict(n=n, kappa2=kappa2, omega=omega, q=q, order=order, intergrid=ig, alpha3=alpha3,
-                jacobi=jw, pad=args.pad, vmin=vmin)
+                jacobi=jw, jw=(jw, jw), pad=args.pad, vmin=vmin, widths6=args.pad,
+                owidths=[(args.pad, args.pad)] * 2)
+
+
+def workload3(args):
+    """3D instance: seeded layered medium (workloads.layered_3d) on the grid's interior,
+    extended by edge values into a layer on the sides and the bottom; the top face (depth
+    index 0) has no layer and carries the source at its centre (the set-up of Sec. 5.2)."""
+    import numpy as np
+
+    import workloads
+
+    cx, cy, cz = (int(v) for v in args.cells3.split(","))
+    p = args.pad3
+    kappa2 = workloads.layered_3d((cx - 2 * p, cy - 2 * p, cz - p), 0, seed=0)
+    kappa2 = np.ascontiguousarray(np.pad(kappa2, ((0, p), (p, p), (p, p)), mode="edge"))
+    n = (cx, cy, cz)
+    vmin = 1.0 / float(np.sqrt(kappa2.max()))
+    omega = workloads.omega_for_ppw(args.ppw, vmin)
+    with open(os.path.join(ROOT, "workloads", "shifts.json")) as f:
+        alpha3 = json.load(f)["3d"]["4th"]["levdep"][str(args.ppw)]
+    jw = (0.6, 0.4) if args.jacobi is None else (args.jacobi, args.jacobi)
+    q = workloads.point_source(n, node=(cx // 2, cy // 2, 0))
+    return dict(n=n, kappa2=kappa2, omega=omega, q=q, order="4th", intergrid="levdep", alpha3=alpha3,
+                jacobi=jw[0], jw=jw, pad=p, vmin=vmin, widths6=[p, p, p, p, 0, p],
+                owidths=[(p, p), (p, p), (0, p)])
+
+
+def n_nodes(wl):
+    out = 1
+    for v in wl["n"]:
+        out *= v + 1
+    return out
 
 
 def default_workload(args):
     """The configuration the sweep traffic figure was captured on."""
-    return (args.n, args.pad, args.ppw, args.method, args.precision, args.cycle, args.sources, args.cslp,
-            args.solver, args.medium) == (2048, 32, 12, "paper", "mixed", "V", 1, 0.0, "fgmres", "layered")
+    return (args.dim, args.n, args.pad, args.ppw, args.method, args.precision, args.cycle, args.sources, args.cslp,
+            args.solver, args.medium) == (2, 2048, 32, 12, "paper", "mixed", "V", 1, 0.0, "fgmres", "layered")
 
 
 def medium_name(args):
@@ -131,6 +172,22 @@ def medium_name(args):
 
 
 def describe(args, wl):
+    if args.dim == 3:
+        return {
+            "workload": (f"3D seeded layered medium (1.5-4.5 km/s, smoothed 5% perturbation) "
+                         f"{'x'.join(str(v) for v in wl['n'])} cells incl. a {wl['pad']}-cell absorbing layer on "
+                         f"the sides and the bottom, none on the top face ({n_nodes(wl)} nodes), "
+                         f"{args.ppw} points per wavelength, point source at the centre of the top face"),
+            "method": (f"RS-CGC {args.cycle}(1,1) damped Jacobi w={wl['jw'][0]}/{wl['jw'][1]}, compact 4th-order "
+                       f"19-point stencil + lev-dep transfers, alpha3={wl['alpha3']}, "
+                       f"{'FGMRES(%d)' % args.restart if args.solver == 'fgmres' else 'stationary cycle iteration'}, "
+                       f"tol {args.tol}"),
+            "precision": ("FP32 cycle on levels 1-2 (one kernel per step); FGMRES basis, Arnoldi streams and "
+                          "coarsest solve in double-FP32 arithmetic; Givens, solution update and true residual in "
+                          "FP64" if args.precision == "mixed" else "FP64 throughout"),
+            "l2": "inputs larger than L2 (Krylov basis and operators: several GB per solve)",
+            "setup": "excluded from the timed region, reported as setup_ms",
+        }
     return {
         "workload": (f"{medium_name(args)} {args.n}^2 cells "
                      f"+ {args.pad}-cell absorbing layer per side = {wl['n'][0]}^2 cells "
@@ -246,18 +303,19 @@ def oracle_sample(args, log):
 
     sargs = argparse.Namespace(**vars(args))
     sargs.n = args.cpu_n
+    sargs.cells3 = args.cpu_cells3
     wl = workload(sargs)
     grid = OG.Grid(wl["n"])
-    gamma = OG.abc_profile(grid, OG.uniform_widths(2, wl["pad"]), 1.0)
+    gamma = OG.abc_profile(grid, wl["owidths"], 1.0)
     t0 = time.perf_counter()
     h = OH.Hierarchy(grid, wl["kappa2"], wl["omega"], gamma, wl["order"], wl["intergrid"], alpha3=wl["alpha3"],
                      beta=args.cslp)
     h.coarsest_lu
-    cy = OC.Cycle(h, cycle=args.cycle, weights=(wl["jacobi"], wl["jacobi"]))
-    log(f"oracle set-up {time.perf_counter() - t0:.1f} s ({wl['n'][0]}^2 cells)")
-    nodes = (wl["n"][0] + 1) * (wl["n"][1] + 1)
-    return dict(h=h, cy=cy, A=h.A_outer, q=wl["q"].ravel(), nodes=nodes, cells=wl["n"][0], n=args.cpu_n,
-                solver=args.solver)
+    cy = OC.Cycle(h, cycle=args.cycle, weights=wl["jw"])
+    shape = "x".join(str(v) for v in wl["n"])
+    log(f"oracle set-up {time.perf_counter() - t0:.1f} s ({shape} cells)")
+    return dict(h=h, cy=cy, A=h.A_outer, q=wl["q"].ravel(), nodes=n_nodes(wl), cells=shape,
+                n=args.cpu_cells3 if args.dim == 3 else args.cpu_n, solver=args.solver)
 
 
 def oracle_solve(smp, args):
@@ -277,7 +335,9 @@ def oracle_solve(smp, args):
 def cpu_sample_note(smp, its, t):
     return (f"oracle (NumPy/SciPy sparse, FP64, {ORACLE_THREADS} thread(s)) full {'FGMRES' if smp['solver'] == 'fgmres' else 'cycle-iteration'} "
             f"solve to the run's tolerance of the "
-            f"same workload at {smp['n']}^2 cells + absorbing layer ({smp['cells']}^2 cells, {smp['nodes']} nodes): "
+            + (f"same workload at {smp['cells']} cells incl. the layer ({smp['nodes']} nodes): " if "x" in str(smp['cells'])
+               and str(smp['cells']).count("x") == 2 else
+               f"same workload at {smp['n']}^2 cells + absorbing layer ({smp['cells']} cells, {smp['nodes']} nodes): ") +
             f"{its} iterations in {t:.2f} s, set-up excluded; value = sample nodes / solve time")
 
 
@@ -319,16 +379,24 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------------ our arm
-def kernel_model(info, its, restart, n1, n3):
+def kernel_model(info, its, restart, n1, n3, dim=2, elem=8):
     """Algorithmic bytes and flops per launch of the timed kernel classes.
 
     coarse: the forward sweep reads M and the backward sweep G^T, every stored factor
     entry once (16 B per complex entry, FP64 or double-float), plus the vectors (b, w, x and
     the update vectors, about 6 x 16 B per coarsest node).  Arnoldi kernels: one complex
-    value of 16 B per basis vector and node, plus w, z and the coefficient."""
+    value of 16 B per basis vector and node, plus w, z and the coefficient.  stencil (one
+    level-2 row operation of the per-step cycle, averaged over a level-2 visit of the (1,1)
+    Jacobi cycle: of its three row operations the residual and the second sweep read every
+    stencil coefficient plane once, the first sweep from zero only the diagonal; each also
+    moves about three vectors (x, b, result), elem bytes per complex value (8 in the mixed
+    cycle, 16 in FP64)."""
     nv_avg = sum((i % restart) + 1 for i in range(its)) / its
     cb = 16.0 * info["coarse_entries"] + 6 * 16.0 * n3
+    ncoef2 = (2 * info["radius2"] + 1) ** dim
     return {
+        "stencil": {"flops": 8.0 * ncoef2 * info["nodes2"] * 2.0 / 3.0,
+                    "bytes": elem * (ncoef2 * 2.0 / 3.0 + 3.0) * info["nodes2"]},
         "coarse": {"flops": 8.0 * info["coarse_entries"], "bytes": cb},
         "cycle": {"bytes": cycle_bytes(info, n1, n3)},
         "arnoldi_update": {"flops": 8.0 * 2 * nv_avg * n1, "bytes": (32.0 + 16.0 * nv_avg) * n1},
@@ -361,13 +429,13 @@ def our_arm(args):
     from paper_2604_19501_gb300 import Solver
 
     wl = workload(args)
-    nodes = (wl["n"][0] + 1) * (wl["n"][1] + 1)
+    nodes = n_nodes(wl)
     stream = torch.cuda.current_stream(dev)
     kap = torch.from_numpy(wl["kappa2"]).to(dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    s = Solver(kap, wl["n"], wl["omega"], abc_width=wl["pad"], alpha3=wl["alpha3"], stencil=wl["order"],
-               intergrid=wl["intergrid"], cycle=args.cycle, jacobi_w=(wl["jacobi"], wl["jacobi"]),
+    s = Solver(kap, wl["n"], wl["omega"], abc_width=wl["widths6"], alpha3=wl["alpha3"], stencil=wl["order"],
+               intergrid=wl["intergrid"], cycle=args.cycle, jacobi_w=wl["jw"],
                precision=args.precision, restart=args.restart, stream=stream.cuda_stream,
                max_rhs=max(1, args.block or args.sources), graphs=args.graphs, cslp_beta=args.cslp,
                solver=args.solver)
@@ -437,7 +505,8 @@ def our_arm(args):
                    "share": v[0] / total_ms} for k, v in prof.items() if v[1]}
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_solve"]) if kernels else None
     its_one = its if nsrc == 1 else max(x["iterations"] for x in all_stats[-nsrc:])
-    model = kernel_model(info, its_one, args.restart, nodes, info["nodes3"])
+    model = kernel_model(info, its_one, args.restart, nodes, info["nodes3"], dim=args.dim,
+                         elem=8 if args.precision == "mixed" else 16)
     roof = None
     if dom in model:
         ms, cnt = prof[dom]
@@ -460,7 +529,7 @@ def our_arm(args):
         roof["traffic"] = SWEEP_TRAFFIC_DEFAULT
     # cycle kernels (fine, level-2, transfers) against the HBM roofline, per cycle
     cyc = None
-    if info.get("double_float") and all(prof.get(k, (0, 0))[1] for k in ("fine", "stencil", "transfer")):
+    if args.dim == 2 and info.get("double_float") and all(prof.get(k, (0, 0))[1] for k in ("fine", "stencil", "transfer")):
         n_cyc = prof["fine"][1] / 2.0   # two fine passes per cycle
         t_cyc = sum(prof[k][0] for k in ("fine", "stencil", "transfer")) / 1e3 / n_cyc
         gbs = model["cycle"]["bytes"] / t_cyc / 1e9
