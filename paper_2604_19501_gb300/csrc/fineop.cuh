@@ -91,6 +91,52 @@ __device__ __forceinline__ c2<T> fine_apply_at(const FineOp& op, c2<T> diag, con
 //     L   = wc z_c - wf sum_f z_f - sum_e z_e       (wc, wf = 20, 4 in 2D; 24, 2 in 3D)
 //     Mz  = mc z_c + sum_f z_f,  Mcz = mc c_c z_c + sum_f c_f z_f   (mc = 8 in 2D, 6 in 3D)
 // (f: face neighbours, e: the other non-zero offsets, i.e. 2D corners and 3D edges).
+// Sums are running accumulators (racc): the high part is carried by Knuth's two-sum, the
+// rounding errors of sums and of Dekker products collect in the low part, and each
+// accumulator is normalised once, where it leaves the sum.
+struct racc {
+  float hi, lo;
+};
+__device__ __forceinline__ void racc_add(racc& a, float t) {   // + t, t an exact float
+  float s, e;
+  two_sum(a.hi, t, s, e);
+  a.hi = s;
+  a.lo += e;
+}
+__device__ __forceinline__ void racc_add_prod(racc& a, float x, float y) {   // + x y
+  const float p = x * y;
+  const float pe = fmaf(x, y, -p);
+  float s, e;
+  two_sum(a.hi, p, s, e);
+  a.hi = s;
+  a.lo += e + pe;
+}
+__device__ __forceinline__ void racc_add_ddf(racc& a, dd x, float y) {   // + x y, y an exact float
+  const float p = x.hi * y;
+  const float pe = fmaf(x.hi, y, -p) + x.lo * y;
+  float s, e;
+  two_sum(a.hi, p, s, e);
+  a.hi = s;
+  a.lo += e + pe;
+}
+__device__ __forceinline__ void racc_add_dd(racc& a, dd x, dd y) {   // + x y (y may be unnormalised)
+  const float p = x.hi * y.hi;
+  const float pe = fmaf(x.hi, y.hi, -p) + fmaf(x.hi, y.lo, x.lo * y.hi);
+  float s, e;
+  two_sum(a.hi, p, s, e);
+  a.hi = s;
+  a.lo += e + pe;
+}
+__device__ __forceinline__ dd racc_dd(racc a) { return dd_norm(a.hi, a.lo); }
+__device__ __forceinline__ dd dd_of(racc a) { return dd{a.hi, a.lo}; }
+// a += x z for a double-float complex x and a complex z of exact floats (sign s = +-1)
+__device__ __forceinline__ void cacc_add_cz(racc& re, racc& im, cdd x, float2 z, float s) {
+  racc_add_ddf(re, x.re, s * z.x);
+  racc_add_ddf(re, x.im, -s * z.y);
+  racc_add_ddf(im, x.re, s * z.y);
+  racc_add_ddf(im, x.im, s * z.x);
+}
+
 __device__ __forceinline__ cdd fine_apply_df(const FineOp& op, const float4* __restrict__ cdf,
                                              const float2* __restrict__ z, long long p, int i, int j, int k,
                                              dd ih2, dd ih2_6, dd inv24) {
@@ -100,22 +146,41 @@ __device__ __forceinline__ cdd fine_apply_df(const FineOp& op, const float4* __r
   const float2 zc = z[p];
   const bool is3 = op.g.dim == 3;
   if (op.order == 0) {
-    cdd L = cdd_wz(2.0f * op.g.dim, zc);
-    if (i > 0) L = cdd_sub(L, cdd_wz(1.f, z[p - 1]));
-    if (i < op.g.N[0] - 1) L = cdd_sub(L, cdd_wz(1.f, z[p + 1]));
-    if (j > 0) L = cdd_sub(L, cdd_wz(1.f, z[p - sy]));
-    if (j < op.g.N[1] - 1) L = cdd_sub(L, cdd_wz(1.f, z[p + sy]));
+    const float wc = 2.0f * op.g.dim;
+    racc Lr{0.f, 0.f}, Li{0.f, 0.f};
+    racc_add_prod(Lr, wc, zc.x);
+    racc_add_prod(Li, wc, zc.y);
+    auto face = [&](long long q) {
+      const float2 zq = z[q];
+      racc_add(Lr, -zq.x);
+      racc_add(Li, -zq.y);
+    };
+    if (i > 0) face(p - 1);
+    if (i < op.g.N[0] - 1) face(p + 1);
+    if (j > 0) face(p - sy);
+    if (j < op.g.N[1] - 1) face(p + sy);
     if (is3) {
-      if (k > 0) L = cdd_sub(L, cdd_wz(1.f, z[p - sz]));
-      if (k < op.g.N[2] - 1) L = cdd_sub(L, cdd_wz(1.f, z[p + sz]));
+      if (k > 0) face(p - sz);
+      if (k < op.g.N[2] - 1) face(p + sz);
     }
-    return cdd_sub(cdd_scale(L, ih2), cdd_mulf(cc, zc));
+    const dd lr = dd_mul(racc_dd(Lr), ih2), li = dd_mul(racc_dd(Li), ih2);
+    racc Wr{lr.hi, lr.lo}, Wi{li.hi, li.lo};
+    cacc_add_cz(Wr, Wi, cc, zc, -1.f);
+    return cdd{racc_dd(Wr), racc_dd(Wi)};
   }
   const float wc = is3 ? 24.f : 20.f, wf = is3 ? 2.f : 4.f, mc = is3 ? 6.f : 8.f;
-  cdd L = cdd_wz(wc, zc);
-  cdd Mz = cdd_wz(mc, zc);
-  const cdd czc = cdd_mulf(cc, zc);
-  cdd Mcz = cdd{dd_mulf(czc.re, mc), dd_mulf(czc.im, mc)};
+  racc Lr{0.f, 0.f}, Li{0.f, 0.f}, Zr{0.f, 0.f}, Zi{0.f, 0.f}, Mr{0.f, 0.f}, Mi{0.f, 0.f};
+  racc_add_prod(Lr, wc, zc.x);
+  racc_add_prod(Li, wc, zc.y);
+  racc_add_prod(Zr, mc, zc.x);
+  racc_add_prod(Zi, mc, zc.y);
+  // mc c_c z_c with mc z_c = p + e exact: c_c p + c_c e
+  {
+    const float pr = mc * zc.x, pi = mc * zc.y;
+    const float2 ez = make_float2(fmaf(mc, zc.x, -pr), fmaf(mc, zc.y, -pi));
+    cacc_add_cz(Mr, Mi, cc, make_float2(pr, pi), 1.f);
+    cacc_add_cz(Mr, Mi, cc, ez, 1.f);
+  }
   const int zlo = is3 ? -1 : 0, zhi = is3 ? 1 : 0;
   for (int dz = zlo; dz <= zhi; ++dz) {
     const int kk = k + dz;
@@ -131,16 +196,25 @@ __device__ __forceinline__ cdd fine_apply_df(const FineOp& op, const float4* __r
         const long long q = p + dx + dy * sy + dz * sz;
         const float2 zq = z[q];
         if (nz == 1) {
-          L = cdd_sub(L, cdd_wz(wf, zq));
-          Mz = cdd_add(Mz, cdd_wz(1.f, zq));
-          Mcz = cdd_add(Mcz, cdd_mulf(cdd_load(cdf[q]), zq));
+          racc_add(Lr, -wf * zq.x);   // wf a power of two: exact
+          racc_add(Li, -wf * zq.y);
+          racc_add(Zr, zq.x);
+          racc_add(Zi, zq.y);
+          cacc_add_cz(Mr, Mi, cdd_load(cdf[q]), zq, 1.f);
         } else {
-          L = cdd_sub(L, cdd_wz(1.f, zq));
+          racc_add(Lr, -zq.x);
+          racc_add(Li, -zq.y);
         }
       }
     }
   }
-  const cdd mass = cdd_add(cdd_mul(cc, Mz), Mcz);
+  // mass = c_c Mz + Mcz
+  racc_add_dd(Mr, cc.re, dd_of(Zr));
+  racc_add_dd(Mr, dd_neg(cc.im), dd_of(Zi));
+  racc_add_dd(Mi, cc.re, dd_of(Zi));
+  racc_add_dd(Mi, cc.im, dd_of(Zr));
+  const cdd L{racc_dd(Lr), racc_dd(Li)};
+  const cdd mass{racc_dd(Mr), racc_dd(Mi)};
   return cdd_sub(cdd_scale(L, ih2_6), cdd_scale(mass, inv24));
 }
 
