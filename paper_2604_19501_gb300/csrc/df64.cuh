@@ -149,4 +149,58 @@ __device__ __forceinline__ cdd cdd_scale(cdd a, dd s) { return cdd{dd_mul(a.re, 
 __device__ __forceinline__ cdd cdd_wz(float w, float2 z) { return cdd{dd_prodf(w, z.x), dd_prodf(w, z.y)}; }
 __device__ __forceinline__ cdd cdd_zero() { return cdd{dd{0.f, 0.f}, dd{0.f, 0.f}}; }
 
+// ---- running accumulators: the high part is carried by Knuth's two-sum, the rounding
+// errors of sums and of Dekker products collect in the low part, and the sum is
+// normalised once, where it leaves the accumulator.
+struct racc {
+  float hi, lo;
+};
+__device__ __forceinline__ void racc_add(racc& a, float t) {   // + t, t an exact float
+  float s, e;
+  two_sum(a.hi, t, s, e);
+  a.hi = s;
+  a.lo += e;
+}
+__device__ __forceinline__ void racc_add_prod(racc& a, float x, float y) {   // + x y
+  const float p = x * y;
+  const float pe = fmaf(x, y, -p);
+  float s, e;
+  two_sum(a.hi, p, s, e);
+  a.hi = s;
+  a.lo += e + pe;
+}
+__device__ __forceinline__ void racc_add_ddf(racc& a, dd x, float y) {   // + x y, y an exact float
+  const float p = x.hi * y;
+  const float pe = fmaf(x.hi, y, -p) + x.lo * y;
+  float s, e;
+  two_sum(a.hi, p, s, e);
+  a.hi = s;
+  a.lo += e + pe;
+}
+__device__ __forceinline__ void racc_add_dd(racc& a, dd x, dd y) {   // + x y (y may be unnormalised)
+  const float p = x.hi * y.hi;
+  const float pe = fmaf(x.hi, y.hi, -p) + fmaf(x.hi, y.lo, x.lo * y.hi);
+  float s, e;
+  two_sum(a.hi, p, s, e);
+  a.hi = s;
+  a.lo += e + pe;
+}
+__device__ __forceinline__ dd racc_dd(racc a) { return dd_norm(a.hi, a.lo); }
+__device__ __forceinline__ dd dd_of(racc a) { return dd{a.hi, a.lo}; }
+// a += x z for a double-float complex x and a complex z of exact floats (sign s = +-1)
+__device__ __forceinline__ void cacc_add_cz(racc& re, racc& im, cdd x, float2 z, float s) {
+  racc_add_ddf(re, x.re, s * z.x);
+  racc_add_ddf(re, x.im, -s * z.y);
+  racc_add_ddf(im, x.re, s * z.y);
+  racc_add_ddf(im, x.im, s * z.x);
+}
+
+// a -= h v for double-float complex h and v (re, im accumulators)
+__device__ __forceinline__ void cacc_sub_cdd(racc& re, racc& im, cdd h, cdd v) {
+  racc_add_dd(re, dd_neg(h.re), v.re);
+  racc_add_dd(re, h.im, v.im);
+  racc_add_dd(im, dd_neg(h.re), v.im);
+  racc_add_dd(im, dd_neg(h.im), v.re);
+}
+
 }  // namespace helm

@@ -91,52 +91,7 @@ __device__ __forceinline__ c2<T> fine_apply_at(const FineOp& op, c2<T> diag, con
 //     L   = wc z_c - wf sum_f z_f - sum_e z_e       (wc, wf = 20, 4 in 2D; 24, 2 in 3D)
 //     Mz  = mc z_c + sum_f z_f,  Mcz = mc c_c z_c + sum_f c_f z_f   (mc = 8 in 2D, 6 in 3D)
 // (f: face neighbours, e: the other non-zero offsets, i.e. 2D corners and 3D edges).
-// Sums are running accumulators (racc): the high part is carried by Knuth's two-sum, the
-// rounding errors of sums and of Dekker products collect in the low part, and each
-// accumulator is normalised once, where it leaves the sum.
-struct racc {
-  float hi, lo;
-};
-__device__ __forceinline__ void racc_add(racc& a, float t) {   // + t, t an exact float
-  float s, e;
-  two_sum(a.hi, t, s, e);
-  a.hi = s;
-  a.lo += e;
-}
-__device__ __forceinline__ void racc_add_prod(racc& a, float x, float y) {   // + x y
-  const float p = x * y;
-  const float pe = fmaf(x, y, -p);
-  float s, e;
-  two_sum(a.hi, p, s, e);
-  a.hi = s;
-  a.lo += e + pe;
-}
-__device__ __forceinline__ void racc_add_ddf(racc& a, dd x, float y) {   // + x y, y an exact float
-  const float p = x.hi * y;
-  const float pe = fmaf(x.hi, y, -p) + x.lo * y;
-  float s, e;
-  two_sum(a.hi, p, s, e);
-  a.hi = s;
-  a.lo += e + pe;
-}
-__device__ __forceinline__ void racc_add_dd(racc& a, dd x, dd y) {   // + x y (y may be unnormalised)
-  const float p = x.hi * y.hi;
-  const float pe = fmaf(x.hi, y.hi, -p) + fmaf(x.hi, y.lo, x.lo * y.hi);
-  float s, e;
-  two_sum(a.hi, p, s, e);
-  a.hi = s;
-  a.lo += e + pe;
-}
-__device__ __forceinline__ dd racc_dd(racc a) { return dd_norm(a.hi, a.lo); }
-__device__ __forceinline__ dd dd_of(racc a) { return dd{a.hi, a.lo}; }
-// a += x z for a double-float complex x and a complex z of exact floats (sign s = +-1)
-__device__ __forceinline__ void cacc_add_cz(racc& re, racc& im, cdd x, float2 z, float s) {
-  racc_add_ddf(re, x.re, s * z.x);
-  racc_add_ddf(re, x.im, -s * z.y);
-  racc_add_ddf(im, x.re, s * z.y);
-  racc_add_ddf(im, x.im, s * z.x);
-}
-
+// Sums are running accumulators (racc, df64.cuh), normalised once where they leave the sum.
 __device__ __forceinline__ cdd fine_apply_df(const FineOp& op, const float4* __restrict__ cdf,
                                              const float2* __restrict__ z, long long p, int i, int j, int k,
                                              dd ih2, dd ih2_6, dd inv24) {

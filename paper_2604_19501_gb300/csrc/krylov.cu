@@ -392,9 +392,10 @@ __global__ void __launch_bounds__(kThreads) arnoldi_update_df_kernel(
   for (int i = tid; i < nv; i += blockDim.x) sh[i] = cdd_store(cdd_make(h1[i]));
   __syncthreads();
   for (long long p = blockIdx.x * (long long)blockDim.x + tid; p < n; p += (long long)gridDim.x * blockDim.x) {
-    cdd wv = cdd_load(w[p]);
-    for (int q = 0; q < nv; ++q) wv = cdd_sub(wv, cdd_mul(cdd_load(sh[q]), cdd_load(V[q * vstride + p])));
-    const float4 w4 = cdd_store(wv);
+    const float4 w0 = w[p];
+    racc re{w0.x, w0.z}, im{w0.y, w0.w};
+    for (int q = 0; q < nv; ++q) cacc_sub_cdd(re, im, cdd_load(sh[q]), cdd_load(V[q * vstride + p]));
+    const float4 w4 = cdd_store(cdd{racc_dd(re), racc_dd(im)});
     w[p] = w4;
     for (int q = 0; q < nv; ++q) df_cmacc(sdf[q * blockDim.x + tid], V[q * vstride + p], w4);
     df_cmacc(sdf[nv * blockDim.x + tid], w4, w4);
@@ -413,9 +414,10 @@ __global__ void __launch_bounds__(kThreads) arnoldi_normalize_df_kernel(
   const dd sc = s_inv;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
-    cdd wv = cdd_load(w[p]);
-    for (int q = 0; q < nv; ++q) wv = cdd_sub(wv, cdd_mul(cdd_load(sh[q]), cdd_load(V[q * vstride + p])));
-    vout[p] = cdd_store(cdd_scale(wv, sc));
+    const float4 w0 = w[p];
+    racc re{w0.x, w0.z}, im{w0.y, w0.w};
+    for (int q = 0; q < nv; ++q) cacc_sub_cdd(re, im, cdd_load(sh[q]), cdd_load(V[q * vstride + p]));
+    vout[p] = cdd_store(cdd_scale(cdd{racc_dd(re), racc_dd(im)}, sc));
   }
 }
 
@@ -477,10 +479,11 @@ __global__ void __launch_bounds__(kThreads, 2) arnoldi_update_df_t(long long n, 
   for (int i = tid; i < NV; i += blockDim.x) sh[i] = cdd_store(cdd_make(h1[i]));
   __syncthreads();
   for (long long p = blockIdx.x * (long long)blockDim.x + tid; p < n; p += (long long)gridDim.x * blockDim.x) {
-    cdd wv = cdd_load(w[p]);
+    const float4 w0 = w[p];
+    racc re{w0.x, w0.z}, im{w0.y, w0.w};
 #pragma unroll
-    for (int q = 0; q < NV; ++q) wv = cdd_sub(wv, cdd_mul(cdd_load(sh[q]), cdd_load(V[q * vstride + p])));
-    const float4 w4 = cdd_store(wv);
+    for (int q = 0; q < NV; ++q) cacc_sub_cdd(re, im, cdd_load(sh[q]), cdd_load(V[q * vstride + p]));
+    const float4 w4 = cdd_store(cdd{racc_dd(re), racc_dd(im)});
     w[p] = w4;
 #pragma unroll
     for (int q = 0; q < NV; ++q) df_cmacc(acc[q], V[q * vstride + p], w4);
