@@ -81,6 +81,12 @@ def parse():
                     help="3D grid in cells incl. the absorbing layer (Table 4's largest: 192,192,72)")
     ap.add_argument("--pad3", type=int, default=16, help="3D absorbing layer on the sides and the bottom")
     ap.add_argument("--cpu-cells3", default="64,64,32", help="3D grid of the bounded CPU oracle sample")
+    ap.add_argument("--uneven", type=int, default=0,
+                    help="K > 0: the uneven-grid batch (config 4, second part): K instances with interior "
+                         "grids drawn from 256^2-1536^2, each its own context and stream, solved at the same "
+                         "time (solve_concurrent) and, for comparison, one after another")
+    ap.add_argument("--share", type=int, default=152,
+                    help="uneven batch: resident blocks of each instance's coarsest solve (coarse_blocks)")
     ap.add_argument("--medium", default="layered", choices=["layered", "linear", "wedge"],
                     help="layered: seeded layered/faulted medium, centre source; linear / wedge: the "
                          "2D heterogeneous models of Sec. 5.1 (Table 3), source at the top centre")
@@ -103,7 +109,7 @@ def workload(args):
     N = args.n + 2 * args.pad
     n = (N, N)
     if args.medium == "layered":
-        kappa2 = workloads.layered_faulted_2d(args.n, args.pad, seed=0)
+        kappa2 = workloads.layered_faulted_2d(args.n, args.pad, seed=getattr(args, "seed", 0))
     else:
         gen = workloads.linear_2d if args.medium == "linear" else workloads.wedge_2d
         kappa2 = gen(args.n, args.pad, args.kappa_min)
@@ -570,10 +576,155 @@ def our_arm(args):
     return 0
 
 
+def uneven_sizes(args):
+    """Interior cells per axis of the uneven batch: seeded, uniform in [256, 1536], multiples of 4."""
+    import numpy as np
+
+    rng = np.random.default_rng(0)
+    return sorted(int(v) // 4 * 4 for v in rng.integers(256, 1537, size=args.uneven))
+
+
+def uneven_arm(args):
+    """Config 4, second part: instances of uneven size (seeded layered media, 12 ppw, paper
+    method, mixed precision, one centre source each), each with its own context, stream and
+    a share of the device for its coarsest solve, solved at the same time through
+    solve_concurrent; the same contexts solved one after another give the comparison."""
+    import argparse
+    from concurrent.futures import ThreadPoolExecutor
+
+    import torch
+
+    world, rank, local = dist_init(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    log = (lambda m: print(m, file=sys.stderr, flush=True)) if rank == 0 else (lambda m: None)
+    from paper_2604_19501_gb300 import Solver, solve_concurrent
+
+    sizes = uneven_sizes(args)
+    solvers, qs, ps, wls, streams = [], [], [], [], []
+    for k, n in enumerate(sizes):
+        sargs = argparse.Namespace(**vars(args))
+        sargs.n, sargs.seed = n, k
+        wl = workload(sargs)
+        st = torch.cuda.Stream(dev)
+        solvers.append(Solver(torch.from_numpy(wl["kappa2"]).to(dev), wl["n"], wl["omega"], abc_width=wl["widths6"],
+                              alpha3=wl["alpha3"], stencil=wl["order"], intergrid=wl["intergrid"], cycle=args.cycle,
+                              jacobi_w=wl["jw"], precision=args.precision, restart=args.restart,
+                              stream=st.cuda_stream, coarse_blocks=args.share))
+        qs.append(torch.from_numpy(wl["q"]).to(dev))
+        ps.append(torch.empty_like(qs[-1]))
+        wls.append(wl)
+        streams.append(st)
+    torch.cuda.synchronize()
+    nodes = [n_nodes(w) for w in wls]
+    log(f"uneven batch: {len(sizes)} instances, interior cells {sizes}, {sum(nodes)} nodes")
+    ex = ThreadPoolExecutor(max_workers=len(solvers))
+    classes = ["coarse", "arnoldi_update", "arnoldi_matvec", "arnoldi_norm", "fine", "stencil", "transfer",
+               "krylov_other"]
+    for s_ in solvers:
+        s_.timer_enable(classes)
+
+    def rounds(concurrent, steps):
+        """Device time of `steps` rounds (max over the instances' streams)."""
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e0.record(streams[0])
+        for st in streams[1:]:
+            st.wait_event(e0)
+        stats = None
+        for _ in range(steps):
+            if concurrent:
+                out = solve_concurrent(solvers, qs, ps, tol=args.tol, maxit=args.maxit, executor=ex)
+            else:
+                out = [s_.solve(q, p, tol=args.tol, maxit=args.maxit) for s_, q, p in zip(solvers, qs, ps)]
+            stats = [o[1][0] for o in out]
+        ends = []
+        for st in streams:
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(st)
+            ends.append(e)
+        torch.cuda.synchronize()
+        return max(e0.elapsed_time(e) for e in ends) / 1e3, stats
+
+    for _ in range(args.warmup):
+        rounds(True, 1)
+    for s_ in solvers:
+        s_.timer_enable(classes)
+    sampler = ClockSampler(local).start()
+    l0 = sum(s_.launches for s_ in solvers)
+    t_conc, stats = rounds(True, args.steps)
+    clocks = sampler.stop()
+    launches = sum(s_.launches for s_ in solvers) - l0
+    profs = [s_.timer_read() for s_ in solvers]
+    for s_ in solvers:
+        s_.timer_enable([])
+    t_seq, _ = rounds(False, args.steps)
+    value = args.steps * sum(nodes) / 1e6 / t_conc
+    seq_value = args.steps * sum(nodes) / 1e6 / t_seq
+    # end to end with pinned host buffers
+    qh = [torch.from_numpy(w["q"]).pin_memory() for w in wls]
+    ph = [torch.empty_like(q).pin_memory() for q in qh]
+    solve_concurrent(solvers, qh, ph, tol=args.tol, maxit=args.maxit, executor=ex)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        solve_concurrent(solvers, qh, ph, tol=args.tol, maxit=args.maxit, executor=ex)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    qbytes = sum(q.numel() * q.element_size() for q in qh)
+    # coarsest solve against the HBM roofline: algorithmic bytes over the mean launch time
+    tot_bytes = tot_ms = tot_cnt = 0.0
+    for s_, prof, st_, w in zip(solvers, profs, stats, wls):
+        info = s_.info()
+        model = kernel_model(info, max(1, st_["iterations"]), args.restart, n_nodes(w), info["nodes3"])
+        ms, cnt = prof["coarse"]
+        tot_bytes += model["coarse"]["bytes"] * cnt
+        tot_ms += ms
+        tot_cnt += cnt
+    gbs = tot_bytes / (tot_ms / 1e3) / 1e9 if tot_ms else 0.0
+    peak = hbm_peak_gbs()
+    cpu = None
+    if not args.no_cpu_baseline:
+        smp = oracle_sample(args, log)
+        t_cpu, its_cpu = oracle_solve(smp, args)
+        cpu = {"value": smp["nodes"] / 1e6 / t_cpu, "unit": UNIT, "cores": ORACLE_THREADS, "kind": "oracle",
+               "sample": cpu_sample_note(smp, its_cpu, t_cpu)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_conc / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": (f"uneven batch of {len(sizes)} 2D layered/faulted media (seeded), interior "
+                                f"cells {sizes} + {args.pad}-cell layer, {sum(nodes)} nodes in all, "
+                                f"{args.ppw} points per wavelength, centre point source each"),
+                   "method": (f"RS-CGC V(1,1) Jacobi 0.89, 4th-order 9-point + cubic transfers, FGMRES"
+                              f"({args.restart}), tol {args.tol}; one context and stream per instance, "
+                              f"coarsest solve on {args.share} resident blocks each, solved at the same time"),
+                   "l2": "inputs larger than L2", "setup": "excluded from the timed region"},
+        "iterations": [x["iterations"] for x in stats],
+        "converged": all(x["converged"] for x in stats),
+        "sequential": {"value": seq_value, "ms_per_step": t_seq / args.steps * 1e3,
+                       "note": "the same contexts solved one after another"},
+        "e2e": {"value": args.steps * sum(nodes) / 1e6 / t_e2e, "unit": UNIT, "h2d_bytes_per_step": qbytes,
+                "d2h_bytes_per_step": qbytes},
+        "gpu_launches": launches,
+        "roofline": {"kernel": "coarse", "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                     "frac": gbs / peak, "traffic": None,
+                     "note": "algorithmic bytes over the mean coarsest-solve launch time, launches overlapping"},
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    ex.shutdown()
+    for s_ in solvers:
+        s_.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.uneven > 0:
+        return uneven_arm(args)
     return our_arm(args)
 
 

@@ -104,6 +104,11 @@ typedef struct {
                              calls (helm_apply, helm_residual, helm_smooth) use the cycle's
                              operator.  Default 0: plain RS-CGC. */
   int solver;             /* helm_solver used by helm_solve / helm_adjoint_grad */
+  int coarse_blocks;      /* resident thread blocks of the coarsest-solve kernel: 0 (default) =
+                             every block that fits on the device (fastest for one solve at a
+                             time); a smaller count leaves the rest of the GPU to contexts
+                             solving at the same time on other streams.  Results do not
+                             depend on it. */
 } helm_opts;
 
 /* Per-solve statistics, one entry per right-hand side. */
@@ -119,7 +124,7 @@ typedef struct helm_ctx helm_ctx;
 /* Fills *o with defaults: 2D, h = 1, gamma_max = 1, alpha2 = alpha3 = 1,
  * 2nd-order stencil, FW transfers, V(1,1), Jacobi w = (0.8, 0.8), rb_w = 1,
  * FP64, restart 10, max_rhs 1, default stream, fuse_cycle 1, graphs 0,
- * cslp_beta 0, solver FGMRES.  The caller sets dim, n,
+ * cslp_beta 0, solver FGMRES, coarse_blocks 0.  The caller sets dim, n,
  * omega, abc_width and the shifts. */
 int helm_default_opts(helm_opts* o);
 

@@ -11,7 +11,7 @@ import ctypes
 from . import _ffi
 from ._ffi import HelmError, HelmOpts, HelmStats, check
 
-__all__ = ["Solver", "HelmError", "level_shape", "helmholtz_solve", "coarse_plan"]
+__all__ = ["Solver", "HelmError", "level_shape", "helmholtz_solve", "coarse_plan", "solve_concurrent"]
 
 _lib = _ffi.load()
 
@@ -43,7 +43,7 @@ class Solver:
                  alpha3=1.0, stencil="2nd", intergrid="fw", cycle="V", nu=(1, 1),
                  smoother="jacobi", jacobi_w=(0.8, 0.8), rb_w=1.0, precision="fp64", restart=10,
                  max_rhs=1, stream=None, fuse_cycle=True, graphs=False, cslp_beta=0.0,
-                 solver="fgmres"):
+                 solver="fgmres", coarse_blocks=0):
         self.n = tuple(int(v) for v in n)
         self.dim = len(self.n)
         o = HelmOpts()
@@ -72,6 +72,7 @@ class Solver:
         o.graphs = int(bool(graphs))
         o.cslp_beta = float(cslp_beta)
         o.solver = _ffi.SOLVER[solver]
+        o.coarse_blocks = int(coarse_blocks)
         if stream is None:
             import torch
 
@@ -240,6 +241,27 @@ class Solver:
 
 PLAN_KEYS = ("fronts", "levels", "jobs", "factor_entries", "bwd_entries", "part_blocks", "split_outputs",
              "max_boundary")
+
+
+def solve_concurrent(solvers, qs, ps=None, tol=1e-6, maxit=500, executor=None):
+    """Solves one problem per context at the same time (grids of different sizes, for
+    instance): each helm_solve runs from its own host thread on its context's stream (the
+    library is called with the interpreter lock released), so the kernels of different
+    contexts overlap on the GPU.  Give the contexts distinct streams and, so that their
+    coarsest solves can run side by side, a share of the device each (``coarse_blocks``).
+    ``ps``: optional output tensors; ``executor``: an optional thread pool to reuse.
+    Returns ``[(p, stats)]`` in the order of ``solvers``."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    ps = list(ps) if ps is not None else [None] * len(solvers)
+    own = executor is None
+    ex = ThreadPoolExecutor(max_workers=max(1, len(solvers))) if own else executor
+    try:
+        futs = [ex.submit(s.solve, q, p, tol, maxit) for s, q, p in zip(solvers, qs, ps)]
+        return [f.result() for f in futs]
+    finally:
+        if own:
+            ex.shutdown()
 
 
 def coarse_plan(n_nodes, radius, leaf_max=64, symmetric=True, grid=304):

@@ -45,6 +45,7 @@ class HelmOpts(ctypes.Structure):
         ("graphs", ctypes.c_int),
         ("cslp_beta", ctypes.c_double),
         ("solver", ctypes.c_int),
+        ("coarse_blocks", ctypes.c_int),
     ]
 
 

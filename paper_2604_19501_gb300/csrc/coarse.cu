@@ -714,12 +714,19 @@ int coarse_plan_stats(const GridDims& g, int r, int leaf_max, bool symmetric, in
 }
 
 int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef, int leaf_max,
-                 bool symmetric, bool df, cudaStream_t s) {
+                 bool symmetric, bool df, cudaStream_t s, int blocks) {
   int grid = 0, grid_group = 0;
   if (int st = sweep_grid_size(&grid, &grid_group)) return st;
   CoarsePlan P;
   if (int st = coarse_plan(cs, P, g, r, leaf_max, symmetric, grid)) return st;
   cs.grid_group = grid_group;
+  // a share of the device, e.g. for solves running side by side: the job list stays the
+  // one planned for the whole device (and with it every summation order), only fewer
+  // blocks run it
+  if (blocks > 0) {
+    cs.grid = std::min(cs.grid, blocks);
+    cs.grid_group = std::min(cs.grid_group, blocks);
+  }
   cs.df = df;
   const auto& desc = P.desc;
   const auto& bigs = P.bigs;

@@ -112,8 +112,9 @@ struct CoarseSolver {
 // assembled stencil coef (c128, [ncoef][nodes]) of radius r.  leaf_max: largest leaf box.
 // symmetric: the operator is complex-symmetric (A = A^T), which halves the stored coupling.
 // df: store the factors as double-float and apply them on the FP32 pipes.
+// blocks: resident blocks of the solve kernel (0: all that fit on the device).
 int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef, int leaf_max,
-                 bool symmetric, bool df, cudaStream_t s);
+                 bool symmetric, bool df, cudaStream_t s, int blocks = 0);
 
 // e = A^-1 b for nrhs vectors (c128, [nrhs][nodes]).
 int coarse_solve(CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaStream_t s);
