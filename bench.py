@@ -85,8 +85,9 @@ def parse():
                     help="K > 0: the uneven-grid batch (config 4, second part): K instances with interior "
                          "grids drawn from 256^2-1536^2, each its own context and stream, solved at the same "
                          "time (solve_concurrent) and, for comparison, one after another")
-    ap.add_argument("--share", type=int, default=152,
-                    help="uneven batch: resident blocks of each instance's coarsest solve (coarse_blocks)")
+    ap.add_argument("--share", type=int, default=0,
+                    help="uneven batch: resident blocks of each instance's coarsest solve (coarse_blocks; "
+                         "0 = all)")
     ap.add_argument("--medium", default="layered", choices=["layered", "linear", "wedge"],
                     help="layered: seeded layered/faulted medium, centre source; linear / wedge: the "
                          "2D heterogeneous models of Sec. 5.1 (Table 3), source at the top centre")
@@ -697,7 +698,7 @@ def uneven_arm(args):
                                 f"{args.ppw} points per wavelength, centre point source each"),
                    "method": (f"RS-CGC V(1,1) Jacobi 0.89, 4th-order 9-point + cubic transfers, FGMRES"
                               f"({args.restart}), tol {args.tol}; one context and stream per instance, "
-                              f"coarsest solve on {args.share} resident blocks each, solved at the same time"),
+                              f"coarsest solve on {args.share or 'all'} resident blocks each, solved at the same time"),
                    "l2": "inputs larger than L2", "setup": "excluded from the timed region"},
         "iterations": [x["iterations"] for x in stats],
         "converged": all(x["converged"] for x in stats),
