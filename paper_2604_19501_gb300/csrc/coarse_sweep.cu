@@ -336,13 +336,13 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
   auto gather_idx = [&](const SweepMeta& m, int r0, int nr) {
     const bool fw = m.kind == 0;
     const int rows = m.r1 - m.r0, cols = m.c1 - m.c0;
+    // loads go straight into pre-set registers (no select on a loaded value, which would
+    // wait for the load here instead of where the value is used)
 #pragma unroll
     for (int i = 0; i < kColItems; ++i) {
       const int q = tid + i * kSweepThreads;
-      if (q < cols) {
-        const int t = m.c0 + q;
-        sI[i] = (!fw || t < m.nS) ? a.S[m.S_off + t] : -1;
-      }
+      sI[i] = -1;
+      if (q < cols && (!fw || m.c0 + q < m.nS)) sI[i] = a.S[m.S_off + m.c0 + q];
     }
 #pragma unroll
     for (int i = 0; i < kRowItems; ++i) {
@@ -361,10 +361,8 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
 #pragma unroll
       for (int i = 0; i < kColItems; ++i) {
         const int q = tid + i * kSweepThreads;
-        if (q < cols * nr) {
-          const int t = m.c0 + q / nr;
-          qc2[i] = t >= m.nS ? a.ctb[m.ctb_off + t] : make_int2(-1, -1);
-        }
+        qc2[i] = make_int2(-1, -1);
+        if (q < cols * nr && m.c0 + q / nr >= m.nS) qc2[i] = a.ctb[m.ctb_off + m.c0 + q / nr];
       }
   };
   auto gather_b = [&](const SweepMeta& m, int r0, int nr) {
