@@ -49,6 +49,37 @@ __device__ __forceinline__ float2 fine_diag_of(const Cycle2D& c, float2 cc) {
   return make_float2(float(20.0 / 6.0) * ih2 - float(8.0 / 12.0) * cc.x, -float(8.0 / 12.0) * cc.y);
 }
 
+// (H x) at the centre of a 3 x 3 window of x and c held in registers ([row][column]), in
+// the order of fine_apply_tile
+template <int ORDER>
+__device__ __forceinline__ float2 fine_apply_win(const float2 (&wx)[3][3], const float2 (&wc)[3][3], float ih2,
+                                                 float2 diag) {
+  if (ORDER == 0) {
+    float2 s = wx[1][0] + wx[1][2];
+    s = s + wx[0][1];
+    s = s + wx[2][1];
+    return cmul(diag, wx[1][1]) - cscale(s, ih2);
+  }
+  const float2 ci = wc[1][1];
+  float2 acc = cmul(diag, wx[1][1]);
+  const float wface = float(-4.0 / 6.0) * ih2, wedge = float(-1.0 / 6.0) * ih2;
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+      if (dx == 0 && dy == 0) continue;
+      const float2 xv = wx[1 + dy][1 + dx];
+      if (dx == 0 || dy == 0) {
+        const float2 cj = wc[1 + dy][1 + dx];
+        const float2 m = make_float2(wface - float(1.0 / 24.0) * (ci.x + cj.x), -float(1.0 / 24.0) * (ci.y + cj.y));
+        acc = cmac(acc, m, xv);
+      } else {
+        acc = acc + cscale(xv, wedge);
+      }
+    }
+  return acc;
+}
+
 // (H x) at tile position li (row stride S) from tiles of x and c
 template <int ORDER>
 __device__ __forceinline__ float2 fine_apply_tile(const float2* __restrict__ sx, const float2* __restrict__ sc, int li,
@@ -116,15 +147,44 @@ __global__ void __launch_bounds__(kThreads) fine_down_kernel(const Cycle2D c, co
     sx[q] = xx;
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < NF * NF; q += kThreads) {
-    const int lx = q % NF + 1, ly = q / NF + 1;
-    const int gx = X0 + lx, gy = Y0 + ly;
-    float2 r = z2();
-    if (gx >= 0 && gx < N0 && gy >= 0 && gy < N1) {
-      const int li = lx + NX * ly;
-      r = sv[li] - fine_apply_tile<ORDER>(sx, sc, li, NX, ih2, fine_diag_of<ORDER>(c, sc[li]));
+  // residual on the NF x NF region: each thread walks RS consecutive rows of one column
+  // with a three-row window of x and c in registers (a third of the shared-memory reads of
+  // a gather per node)
+  {
+    constexpr int SEG = kThreads / NF;              // row segments per column
+    constexpr int RS = (NF + SEG - 1) / SEG;        // rows per segment
+    const int lx = threadIdx.x % NF + 1, sg = threadIdx.x / NF;
+    if (sg < SEG) {
+      const int y0 = 1 + sg * RS, y1 = min(NF + 1, y0 + RS);
+      float2 wx[3][3], wc[3][3];   // [row - (ly - 1)][column - (lx - 1)]
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          wx[r][d] = sx[(lx - 1 + d) + NX * (y0 - 1 + r)];
+          wc[r][d] = sc[(lx - 1 + d) + NX * (y0 - 1 + r)];
+        }
+      const int gx = X0 + lx;
+      for (int ly = y0; ly < y1; ++ly) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          wx[2][d] = sx[(lx - 1 + d) + NX * (ly + 1)];
+          wc[2][d] = sc[(lx - 1 + d) + NX * (ly + 1)];
+        }
+        const int gy = Y0 + ly;
+        float2 r = z2();
+        if (gx >= 0 && gx < N0 && gy >= 0 && gy < N1)
+          r = sv[lx + NX * ly] - fine_apply_win<ORDER>(wx, wc, ih2, fine_diag_of<ORDER>(c, wc[1][1]));
+        sr[(ly - 1) * NF + lx - 1] = r;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          wx[0][d] = wx[1][d];
+          wx[1][d] = wx[2][d];
+          wc[0][d] = wc[1][d];
+          wc[1][d] = wc[2][d];
+        }
+      }
     }
-    sr[q] = r;
   }
   __syncthreads();
   const float* w = c_w[RW - 1];
