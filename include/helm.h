@@ -50,8 +50,11 @@ typedef enum { HELM_INTERGRID_FW = 0, HELM_INTERGRID_CUBIC = 1, HELM_INTERGRID_L
 typedef enum { HELM_CYCLE_V = 0, HELM_CYCLE_W = 1 } helm_cycle_kind;
 typedef enum { HELM_SMOOTHER_JACOBI = 0, HELM_SMOOTHER_REDBLACK = 1 } helm_smoother;
 /* HELM_FP64: every step in complex FP64.  HELM_MIXED: the cycle on levels 1-2
- * (smoothing, residuals, transfers) in complex FP32; FGMRES, the outer matvec,
- * the true residual and the coarsest solve in complex FP64. */
+ * (smoothing, residuals, transfers) in complex FP32; the coarsest solve, the FGMRES
+ * basis and the Arnoldi kernels (outer matvec, orthogonalisation) in double-float
+ * arithmetic (an unevaluated sum of two FP32 values, about 48 significant bits, on the
+ * FP32 pipes); the Givens rotations, the solution and the true residual in complex
+ * FP64.  The coarsest factorisation itself is computed in FP64 in both modes. */
 typedef enum { HELM_FP64 = 0, HELM_MIXED = 1 } helm_precision;
 typedef enum { HELM_C128 = 0, HELM_C64 = 1 } helm_dtype;
 /* HELM_SOLVER_FGMRES: FGMRES(restart) preconditioned by the cycle (Sec. 5).

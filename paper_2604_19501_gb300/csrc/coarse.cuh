@@ -1,5 +1,6 @@
 // Direct solver of the coarsest (level-3) operator: nested dissection with dense
-// frontal matrices (multifrontal), factorised and applied on the device in complex FP64.
+// frontal matrices (multifrontal), factorised on the device in complex FP64 and applied
+// in FP64 or, in the mixed-precision mode, from double-float copies of the factors.
 #pragma once
 #include <vector>
 #include "common.cuh"

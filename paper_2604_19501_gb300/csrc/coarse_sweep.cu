@@ -25,7 +25,8 @@
 // Reproducibility.  Every sum is taken in an order fixed by the job list: a job's rows
 // split into a fixed number of interleaved parts per column, combined in part order, and
 // job partial sums in chunk order.  None of it depends on the number of right-hand sides
-// solved together.
+// solved together, nor on how many resident blocks run the list (a context may run it on
+// a share of the device, helm_opts.coarse_blocks).
 #include <cstddef>
 #include <type_traits>
 #include "coarse.cuh"
