@@ -140,8 +140,7 @@ __global__ void __launch_bounds__(kThreads) arnoldi_normalize_kernel(
 }
 
 // Hessenberg column j, Givens rotations and the residual estimate (one thread).
-__global__ void arnoldi_small_kernel(KrylovState st, int j, int m) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void arnoldi_small_body(const KrylovState& st, int j, int m) {
   double2* H = st.H;   // [(m+1) x m], column j at H[i * m + j]
   double hs2 = 0.0;
   for (int i = 0; i <= j; ++i) {
@@ -183,6 +182,9 @@ __global__ void arnoldi_small_kernel(KrylovState st, int j, int m) {
   st.scal[KS_HN] = hn;
   st.scal[KS_INV_HN] = hn > 0.0 ? 1.0 / hn : 0.0;
   st.scal[KS_EST] = hypot(st.g[j + 1].x, st.g[j + 1].y) / st.scal[KS_BNORM];
+}
+__global__ void arnoldi_small_kernel(KrylovState st, int j, int m) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) arnoldi_small_body(st, j, m);
 }
 
 // y = R^-1 g on the k x k leading block of the rotated Hessenberg matrix (one thread).
@@ -334,7 +336,9 @@ __global__ void coef_df_kernel(FineOp op, const double* __restrict__ kap, float4
 // Reduction of per-thread double-float accumulators sdf[i * blockDim + tid] (nval sums):
 // warps reduce in double-float, the block partials go to part (as float4), and the last
 // block adds the partials in block order and converts each sum to FP64 once.
-__device__ void reduce_finish_df(float4* sdf, int nval, double2* __restrict__ part_raw,
+// Returns true in the block that finished the sums (after they are in out, visible to
+// the block's threads).
+__device__ bool reduce_finish_df(float4* sdf, int nval, double2* __restrict__ part_raw,
                                  unsigned* __restrict__ counter, double2* __restrict__ out) {
   __shared__ bool s_last;
   float4* part = reinterpret_cast<float4*>(part_raw);
@@ -350,7 +354,7 @@ __device__ void reduce_finish_df(float4* sdf, int nval, double2* __restrict__ pa
   __syncthreads();
   if (tid == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
   __syncthreads();
-  if (!s_last) return;
+  if (!s_last) return false;
   __threadfence();
   for (int i = warp; i < nval; i += nwarp) {
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -359,6 +363,8 @@ __device__ void reduce_finish_df(float4* sdf, int nval, double2* __restrict__ pa
     if (lane == 0) out[i] = from_df(v);
   }
   if (tid == 0) *counter = 0u;
+  __syncthreads();
+  return true;
 }
 
 __global__ void __launch_bounds__(kThreads) arnoldi_matvec_df_kernel(
@@ -462,13 +468,15 @@ __global__ void __launch_bounds__(kThreads, 4) arnoldi_matvec_df_t(FineOp op, Df
 
 // Second CGS pass: w' = w - V h1 and h2 = V^H w', |w'|^2 (double-float), accumulators in
 // registers (the dot pass re-reads V right after the subtraction read it: L1 hits).
+// The block that finishes the reduction also forms the Hessenberg column, its Givens
+// rotation and the residual estimate (the small step, no separate launch).
 template <int NV>
 __global__ void __launch_bounds__(kThreads, 2) arnoldi_update_df_t(long long n, float4* __restrict__ w,
                                                                    const float4* __restrict__ V, long long vstride,
                                                                    const double2* __restrict__ h1,
                                                                    double2* __restrict__ part,
                                                                    unsigned* __restrict__ counter,
-                                                                   double2* __restrict__ out) {
+                                                                   double2* __restrict__ out, KrylovState st) {
   extern __shared__ double2 sacc[];
   float4* sdf = reinterpret_cast<float4*>(sacc);
   __shared__ float4 sh[NV];
@@ -491,7 +499,7 @@ __global__ void __launch_bounds__(kThreads, 2) arnoldi_update_df_t(long long n, 
   }
 #pragma unroll
   for (int q = 0; q <= NV; ++q) sdf[q * blockDim.x + tid] = acc[q];
-  reduce_finish_df(sdf, NV + 1, part, counter, out);
+  if (reduce_finish_df(sdf, NV + 1, part, counter, out) && tid == 0) arnoldi_small_body(st, NV - 1, st.m);
 }
 
 template <int NV>
@@ -510,7 +518,7 @@ int arnoldi_df_launch(int bl, size_t sm, const FineOp& op, const DfConsts& K, co
   }
   {
     KernelTimer kt(HELM_K_ARNOLDI_UPDATE, s);
-    arnoldi_update_df_t<NV><<<bl, kThreads, sm, s>>>(op.g.size, w, V, vstride, st.h1, st.part, st.counter, st.h2);
+    arnoldi_update_df_t<NV><<<bl, kThreads, sm, s>>>(op.g.size, w, V, vstride, st.h1, st.part, st.counter, st.h2, st);
     HELM_LAUNCH_CHECK();
   }
   return 0;
@@ -678,9 +686,10 @@ int k_arnoldi_df(const KrylovState& st, const FineOp& op, const float4* cdf, con
       arnoldi_update_df_kernel<<<bl, kThreads, sm, s>>>(n, w, V, vstride, nv, st.h1, st.part, st.counter, st.h2);
       HELM_LAUNCH_CHECK();
     }
+    // the templated update kernels above do the small step in their last block
+    KernelTimer kt(HELM_K_KRYLOV_OTHER, s);
+    arnoldi_small_kernel<<<1, 32, 0, s>>>(st, j, st.m);
   }
-  KernelTimer kt(HELM_K_KRYLOV_OTHER, s);
-  arnoldi_small_kernel<<<1, 32, 0, s>>>(st, j, st.m);
   HELM_LAUNCH_CHECK();
   return 0;
 }
