@@ -88,6 +88,9 @@ def parse():
     ap.add_argument("--share", type=int, default=0,
                     help="uneven batch: resident blocks of each instance's coarsest solve (coarse_blocks; "
                          "0 = all)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="config 5: a least-squares gradient per step (forward solves of --sources sources, "
+                         "adjoint solves and the gradient dL/dkappa^2), receivers on the top interior row")
     ap.add_argument("--medium", default="layered", choices=["layered", "linear", "wedge"],
                     help="layered: seeded layered/faulted medium, centre source; linear / wedge: the "
                          "2D heterogeneous models of Sec. 5.1 (Table 3), source at the top centre")
@@ -720,12 +723,144 @@ def uneven_arm(args):
     return 0
 
 
+def adjoint_arm(args):
+    """Config 5 (differentiation): the layered medium at --n interior cells (512 for the
+    survey's 2D case), --sources seeded surface sources solved as one block, receivers on
+    the top interior row, data from a seeded perturbed medium (2% smoothed perturbation).
+    A step is one gradient of L = 1/2 sum |P_r p - d|^2: the forward solves, the receiver
+    residual (the user's loss, a torch elementwise op), and helm_adjoint_grad (the adjoint
+    solves on the conjugated residuals plus the fused gradient kernel).  Throughput counts
+    forward and adjoint solves; the same gradient through torch.autograd
+    (helmholtz_solve, which sets the context up again for every medium) is timed beside it."""
+    import numpy as np
+    import torch
+
+    import workloads
+
+    world, rank, local = dist_init(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    log = lambda m: print(m, file=sys.stderr, flush=True)
+    from paper_2604_19501_gb300 import Solver, helmholtz_solve
+
+    nsrc = max(1, args.sources)
+    wl = workload(args)
+    n, pad = wl["n"], args.pad
+    q = workloads.surface_sources(n, nsrc, pad, seed=0) if nsrc > 1 else wl["q"][None]
+    rng = np.random.default_rng(1)
+    from scipy.ndimage import gaussian_filter
+
+    pert = gaussian_filter(rng.standard_normal(wl["kappa2"].shape), 8.0)
+    kap_true = wl["kappa2"] * (1.0 + 0.02 * pert / np.abs(pert).max())
+    mask = np.zeros(wl["kappa2"].shape, dtype=bool)
+    mask[pad, pad:n[0] - pad + 1] = True
+    opts = dict(abc_width=wl["widths6"], alpha3=wl["alpha3"], stencil=wl["order"], intergrid=wl["intergrid"],
+                cycle=args.cycle, jacobi_w=wl["jw"], precision=args.precision, restart=args.restart,
+                max_rhs=nsrc)
+    qd = torch.from_numpy(q).to(dev)
+    md = torch.from_numpy(mask).to(dev)
+    s_true = Solver(torch.from_numpy(kap_true).to(dev), n, wl["omega"], **opts)
+    d = s_true.solve(qd, tol=1e-8, maxit=args.maxit)[0] * md
+    s_true.close()
+    kap = torch.from_numpy(wl["kappa2"]).to(dev)
+    s = Solver(kap, n, wl["omega"], **opts)
+    nodes = n_nodes(wl)
+    p = torch.empty_like(qd)
+    grad = torch.zeros(wl["kappa2"].shape, dtype=torch.float64, device=dev)
+    classes = ["coarse", "arnoldi_update", "arnoldi_matvec", "arnoldi_norm", "fine", "stencil", "transfer",
+               "krylov_other"]
+    s.timer_enable(classes)
+
+    def step():
+        p_, st = s.solve(qd, p, tol=args.tol, maxit=args.maxit)
+        resid = (p_ - d) * md
+        grad.zero_()
+        sa = s.adjoint_grad(p_, resid, grad, tol=args.tol, maxit=args.maxit)
+        return st, sa
+
+    for _ in range(args.warmup):
+        st, sa = step()
+    s.timer_enable(classes)
+    sampler = ClockSampler(local).start()
+    l0 = s.launches
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        st, sa = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t = e0.elapsed_time(e1) / 1e3
+    launches = s.launches - l0
+    prof = s.timer_read()
+    its_f = [x["iterations"] for x in st]
+    its_a = [x["iterations"] for x in sa]
+    value = args.steps * 2 * nsrc * nodes / 1e6 / t
+    info = s.info()
+    model = kernel_model(info, max(1, max(its_f)), args.restart, nodes, info["nodes3"])
+    ms, cnt = prof["coarse"]
+    gbs = model["coarse"]["bytes"] / (ms / 1e3 / cnt) / 1e9 if cnt else 0.0
+    peak = hbm_peak_gbs()
+    s.timer_enable([])
+    s.close()
+    # the same gradient through torch.autograd, set-up included (a new medium every step)
+    ka = kap.clone().requires_grad_(True)
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps // 2)):
+        pa = helmholtz_solve(ka, qd, n, wl["omega"], tol=args.tol, maxit=args.maxit, **opts)
+        loss = 0.5 * (((pa - d) * md).abs() ** 2).sum()
+        ka.grad = None
+        loss.backward()
+    torch.cuda.synchronize()
+    t_auto = (time.perf_counter() - t0) / max(1, args.steps // 2)
+    # end to end with pinned host buffers: sources in, gradient out
+    qh = torch.from_numpy(q).pin_memory()
+    gh = torch.empty(grad.shape, dtype=torch.float64).pin_memory()
+    s = Solver(kap, n, wl["omega"], **opts)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        p_, _ = s.solve(qh.to(dev, non_blocking=True), p, tol=args.tol, maxit=args.maxit)
+        grad.zero_()
+        s.adjoint_grad(p_, (p_ - d) * md, grad, tol=args.tol, maxit=args.maxit)
+        gh.copy_(grad, non_blocking=True)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    s.close()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": (f"config 5: {describe(args, wl)['workload']}; {nsrc} seeded surface sources as one "
+                                f"block, receivers on the top interior row, data from a 2%-perturbed medium"),
+                   "method": describe(args, wl)["method"] + "; adjoint solves on the conjugated receiver residuals "
+                             "and the fused gradient kernel (helm_adjoint_grad)",
+                   "step": "one gradient: forward + adjoint solves of every source (value counts both)"},
+        "iterations": {"forward": its_f, "adjoint": its_a},
+        "gradients_per_s": args.steps / t,
+        "autograd_ms_per_gradient": t_auto * 1e3,
+        "e2e": {"value": args.steps * 2 * nsrc * nodes / 1e6 / t_e2e, "unit": UNIT,
+                "h2d_bytes_per_step": qh.numel() * qh.element_size(),
+                "d2h_bytes_per_step": gh.numel() * gh.element_size()},
+        "gpu_launches": launches,
+        "roofline": {"kernel": "coarse", "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                     "frac": gbs / peak, "traffic": None},
+        "clocks": clocks,
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
     if args.uneven > 0:
         return uneven_arm(args)
+    if args.adjoint:
+        return adjoint_arm(args)
     return our_arm(args)
 
 
