@@ -331,9 +331,14 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
   // The first two steps of a job's first pass run while the block finishes its previous
   // job.
   int sI[kColItems];            // node of output column item
-  int pI[kRowItems];            // forward: node of row item; backward: node of boundary row item
-  int2 pc2[kRowItems], qc2[kColItems];
-  double2 pv[kRowItems];
+  // Single right-hand sides stage the row gathers in registers across the dependency
+  // wait; groups (kRowItems times more items) gather straight into shared memory after
+  // it, which keeps their registers for the accumulators.
+  constexpr bool kPre = RG == 1;
+  constexpr int kPreItems = kPre ? kRowItems : 1;
+  int pI[kPreItems];            // forward: node of row item; backward: node of boundary row item
+  int2 pc2[kPreItems], qc2[kColItems];
+  double2 pv[kPreItems];
   auto gather_idx = [&](const SweepMeta& m, int r0, int nr) {
     const bool fw = m.kind == 0;
     const int rows = m.r1 - m.r0, cols = m.c1 - m.c0;
@@ -345,16 +350,18 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
       sI[i] = -1;
       if (q < cols && (!fw || m.c0 + q < m.nS)) sI[i] = a.S[m.S_off + m.c0 + q];
     }
+    if constexpr (kPre) {
 #pragma unroll
-    for (int i = 0; i < kRowItems; ++i) {
-      const int q = tid + i * kSweepThreads;
-      if (q < rows * nr) {
-        const int t = m.r0 + q / nr;
-        if (fw) {
-          pI[i] = a.S[m.S_off + t];
-          pc2[i] = a.ctb[m.ctb_off + t];
-        } else {
-          pI[i] = a.B[m.B_off + t];
+      for (int i = 0; i < kRowItems; ++i) {
+        const int q = tid + i * kSweepThreads;
+        if (q < rows * nr) {
+          const int t = m.r0 + q / nr;
+          if (fw) {
+            pI[i] = a.S[m.S_off + t];
+            pc2[i] = a.ctb[m.ctb_off + t];
+          } else {
+            pI[i] = a.B[m.B_off + t];
+          }
         }
       }
     }
@@ -367,7 +374,7 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
       }
   };
   auto gather_b = [&](const SweepMeta& m, int r0, int nr) {
-    if (m.kind != 0) return;
+    if (!kPre || m.kind != 0) return;
     const int rows = m.r1 - m.r0;
 #pragma unroll
     for (int i = 0; i < kRowItems; ++i) {
@@ -426,19 +433,37 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
       }
       if (ok) {
         // values written by other blocks of this launch
+        if constexpr (kPre) {
 #pragma unroll
-        for (int i = 0; i < kRowItems; ++i) {
-          const int q = tid + i * kSweepThreads;
-          if (q < rows * nr) {
-            const int r = r0 + q % nr;
+          for (int i = 0; i < kRowItems; ++i) {
+            const int q = tid + i * kSweepThreads;
+            if (q < rows * nr) {
+              const int r = r0 + q % nr;
+              E* dst = vs + (q / nr) * RG + q % nr;
+              if (fwd) {
+                double2 v = pv[i];
+                if (pc2[i].x >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + pc2[i].x));
+                if (pc2[i].y >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + pc2[i].y));
+                from_c128(*dst, v);
+              } else {
+                const long long gi = r * a.nodes + pI[i];
+                if (DF) *reinterpret_cast<float4*>(dst) = __ldcg(a.xd + gi);
+                else *reinterpret_cast<double2*>(dst) = __ldcg(a.x + gi);
+              }
+            }
+          }
+        } else {
+          for (int q = tid; q < rows * nr; q += kSweepThreads) {
+            const int t = r0j + q / nr, r = r0 + q % nr;
             E* dst = vs + (q / nr) * RG + q % nr;
             if (fwd) {
-              double2 v = pv[i];
-              if (pc2[i].x >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + pc2[i].x));
-              if (pc2[i].y >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + pc2[i].y));
+              double2 v = a.b[r * a.nodes + a.S[m.S_off + t]];
+              const int2 cc = a.ctb[m.ctb_off + t];
+              if (cc.x >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + cc.x));
+              if (cc.y >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + cc.y));
               from_c128(*dst, v);
             } else {
-              const long long gi = r * a.nodes + pI[i];
+              const long long gi = r * a.nodes + a.B[m.B_off + t];
               if (DF) *reinterpret_cast<float4*>(dst) = __ldcg(a.xd + gi);
               else *reinterpret_cast<double2*>(dst) = __ldcg(a.x + gi);
             }
