@@ -82,14 +82,14 @@ def parse():
     ap.add_argument("--pad3", type=int, default=16, help="3D absorbing layer on the sides and the bottom")
     ap.add_argument("--cpu-cells3", default="64,64,32", help="3D grid of the bounded CPU oracle sample")
     ap.add_argument("--uneven", type=int, default=0,
-                    help="K > 0: the uneven-grid batch (config 4, second part): K instances with interior "
+                    help="K > 0: the uneven-grid batch: K instances with interior "
                          "grids drawn from 256^2-1536^2, each its own context and stream, solved at the same "
                          "time (solve_concurrent) and, for comparison, one after another")
     ap.add_argument("--share", type=int, default=0,
                     help="uneven batch: resident blocks of each instance's coarsest solve (coarse_blocks; "
                          "0 = all)")
     ap.add_argument("--adjoint", action="store_true",
-                    help="config 5: a least-squares gradient per step (forward solves of --sources sources, "
+                    help="the differentiation workload: a least-squares gradient per step (forward solves of --sources sources, "
                          "adjoint solves and the gradient dL/dkappa^2), receivers on the top interior row")
     ap.add_argument("--medium", default="layered", choices=["layered", "linear", "wedge"],
                     help="layered: seeded layered/faulted medium, centre source; linear / wedge: the "
@@ -589,7 +589,7 @@ def uneven_sizes(args):
 
 
 def uneven_arm(args):
-    """Config 4, second part: instances of uneven size (seeded layered media, 12 ppw, paper
+    """The uneven-grid batch: instances of uneven size (seeded layered media, 12 ppw, paper
     method, mixed precision, one centre source each), each with its own context, stream and
     a share of the device for its coarsest solve, solved at the same time through
     solve_concurrent; the same contexts solved one after another give the comparison."""
@@ -724,8 +724,8 @@ def uneven_arm(args):
 
 
 def adjoint_arm(args):
-    """Config 5 (differentiation): the layered medium at --n interior cells (512 for the
-    survey's 2D case), --sources seeded surface sources solved as one block, receivers on
+    """The differentiation workload: the layered medium at --n interior cells (512 in the
+    2D case), --sources seeded surface sources solved as one block, receivers on
     the top interior row, data from a seeded perturbed medium (2% smoothed perturbation).
     A step is one gradient of L = 1/2 sum |P_r p - d|^2: the forward solves, the receiver
     residual (the user's loss, a torch elementwise op), and helm_adjoint_grad (the adjoint
@@ -838,7 +838,7 @@ def adjoint_arm(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": (f"config 5: {describe(args, wl)['workload']}; {nsrc} seeded surface sources as one "
+        "config": {"workload": (f"differentiation: {describe(args, wl)['workload']}; {nsrc} seeded surface sources as one "
                                 f"block, receivers on the top interior row, data from a 2%-perturbed medium"),
                    "method": describe(args, wl)["method"] + "; adjoint solves on the conjugated receiver residuals "
                              "and the fused gradient kernel (helm_adjoint_grad)",

@@ -264,9 +264,9 @@ typedef enum {
 /* *value = the quantity selected by key. */
 int helm_info(const helm_ctx* c, int key, long long* value);
 
-/* Right-hand-side blocking of helm_solve / helm_adjoint_grad (the batched cycle of the
- * survey's configuration 4; the paper solves one source at a time).  The context holds
- * FGMRES state for at most max_rhs right-hand sides per block (helm_opts.max_rhs).
+/* Right-hand-side blocking of helm_solve / helm_adjoint_grad (many sources through one
+ * cycle; the paper solves one source at a time).  The context holds FGMRES state for at
+ * most max_rhs right-hand sides per block (helm_opts.max_rhs).
  *
  * helm_set_block: solve in blocks of `block` (1 <= block <= max_rhs).
  *
