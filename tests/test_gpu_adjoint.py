@@ -60,7 +60,7 @@ def test_adjoint_gradient_matches_oracle(n, order, ig):
 
 
 def test_autograd_gradient_matches_central_differences():
-    """Config-5-like check at reduced size: 2D layered medium, 4 surface sources,
+    """The differentiation workload at reduced size: 2D layered medium, 4 surface sources,
     receivers on the top interior row; dL/dkappa2 at 10 seeded interior nodes."""
     from paper_2604_19501_gb300 import helmholtz_solve
 

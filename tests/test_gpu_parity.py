@@ -184,7 +184,8 @@ def _point_source(c):
 
 @pytest.mark.parametrize("n,cyc", [((128, 128), "V"), ((64, 96), "W"), ((16, 16, 24), "V")])
 def test_solve_fp64_matches_oracle(n, cyc):
-    """Config-1-like solves: identical iteration counts and solutions within 1e-10."""
+    """Small constant-medium solves (128^2 cells incl. the layer, 12 ppw): identical iteration
+    counts and solutions within 1e-10."""
     import workloads
 
     kappa2 = workloads.constant_medium(n) if len(n) == 2 and n[0] == 128 else None
