@@ -184,8 +184,9 @@ def _point_source(c):
 
 @pytest.mark.parametrize("n,cyc", [((128, 128), "V"), ((64, 96), "W"), ((16, 16, 24), "V")])
 def test_solve_fp64_matches_oracle(n, cyc):
-    """Small constant-medium solves (128^2 cells incl. the layer, 12 ppw): identical iteration
-    counts and solutions within 1e-10."""
+    """Small FP64 solves at 12 ppw (a constant medium on 128^2 cells incl. a 16-cell layer, a
+    seeded 64x96 medium with the W cycle, a 3D grid): identical iteration counts and solutions
+    within 1e-10."""
     import workloads
 
     kappa2 = workloads.constant_medium(n) if len(n) == 2 and n[0] == 128 else None
