@@ -418,12 +418,13 @@ def kernel_model(info, its, restart, n1, n3, dim=2, elem=8):
 def cycle_bytes(info, n1, n3):
     """Algorithmic HBM bytes of one fused 2D cycle (levels 1-2 and the level-3 transfers):
     fine down reads v (16 B) and kappa (4 B) per fine node and writes r2 (8 B per level-2
-    node); level-2 residual and level-2 up each read the stencil (8 B per coefficient),
-    1/diag and r2 and write 8 B per level-2 node, s2 is read once more by the restriction;
-    the restriction writes and the up pass reads 16 B per level-3 node; fine up reads v,
-    kappa and y2 and writes z (8 B per fine node)."""
+    node); level-2 residual and level-2 up each read the upper half of the complex-symmetric
+    stencil (8 B per coefficient, (ncoef + 1) / 2 coefficients: the lower half is the
+    mirrored upper half of the neighbours), 1/diag and r2 and write 8 B per level-2 node,
+    s2 is read once more by the restriction; the restriction writes and the up pass reads
+    16 B per level-3 node; fine up reads v, kappa and y2 and writes z (8 B per fine node)."""
     n2 = info["nodes2"]
-    ncoef = (2 * info["radius2"] + 1) ** 2
+    ncoef = ((2 * info["radius2"] + 1) ** 2 + 1) // 2
     level2 = 8 + 2 * (8 * ncoef + 8 + 8 + 8) + 8 + 8
     return n1 * (20 + 20 + 8) + n2 * level2 + n3 * 32
 

@@ -80,6 +80,19 @@ __device__ __forceinline__ float2 fine_apply_win(const float2 (&wx)[3][3], const
   return acc;
 }
 
+// Entry (dx, dy) of the level-2 stencil at node idx.  The Galerkin operator R H P with
+// P = 4 R^T of a complex-symmetric H is complex-symmetric, so an entry of the lower half
+// of the stencil (dy < 0, or dy = 0 and dx < 0) is the mirrored entry stored at the
+// neighbour; reading those from the neighbour keeps DRAM reads to the upper half of the
+// planes (the shifted reads hit L1/L2).
+template <int R>
+__device__ __forceinline__ float2 coef2_sym(const Cycle2D& c, long long idx, int dx, int dy) {
+  constexpr int W = 2 * R + 1;
+  const long long n = c.g2.size;
+  if (dy > 0 || (dy == 0 && dx >= 0)) return c.coef2[((dx + R) + W * (dy + R)) * n + idx];
+  return c.coef2[((-dx + R) + W * (-dy + R)) * n + idx + dx + (long long)c.g2.N[0] * dy];
+}
+
 // (H x) at tile position li (row stride S) from tiles of x and c
 template <int ORDER>
 __device__ __forceinline__ float2 fine_apply_tile(const float2* __restrict__ sx, const float2* __restrict__ sc, int li,
@@ -221,7 +234,7 @@ __global__ void __launch_bounds__(kThreads) fine_down_kernel(const Cycle2D c, co
 template <int R>
 __global__ void __launch_bounds__(kThreads) l2_resid_kernel(const Cycle2D c, const float2* __restrict__ r2,
                                                             float2* __restrict__ s2) {
-  constexpr int NX = kTX + 2 * R, NY = kTY + 2 * R, W = 2 * R + 1;
+  constexpr int NX = kTX + 2 * R, NY = kTY + 2 * R;
   __shared__ float2 sx[NX * NY];
   const GridDims& g = c.g2;
   const int N0 = g.N[0], N1 = g.N[1];
@@ -248,8 +261,7 @@ __global__ void __launch_bounds__(kThreads) l2_resid_kernel(const Cycle2D c, con
 #pragma unroll
     for (int dx = -R; dx <= R; ++dx) {
       if (gx + dx < 0 || gx + dx >= N0) continue;
-      const int o = (dx + R) + W * (dy + R);
-      ax = cmac(ax, c.coef2[o * g.size + idx], sx[(tx + R + dx) + NX * (ty + R + dy)]);
+      ax = cmac(ax, coef2_sym<R>(c, idx, dx, dy), sx[(tx + R + dx) + NX * (ty + R + dy)]);
     }
   }
   s2[rhs * g.size + idx] = rb[idx] - ax;
@@ -326,7 +338,7 @@ __device__ __forceinline__ void prolong_tile(const float2* __restrict__ ce, int 
 template <int R, int PW>
 __global__ void __launch_bounds__(kThreads) l2_up_kernel(const Cycle2D c, const float2* __restrict__ r2,
                                                          const double2* __restrict__ e3, float2* __restrict__ y2) {
-  constexpr int NX = kTX + 2 * R, NY = kTY + 2 * R, W = 2 * R + 1;
+  constexpr int NX = kTX + 2 * R, NY = kTY + 2 * R;
   constexpr int MX = NX / 2 + PW + 2, MY = NY / 2 + PW + 2;   // coarse cover of the widened tile
   __shared__ float2 sx[NX * NY];
   __shared__ float2 sp[NX * NY];
@@ -373,8 +385,7 @@ __global__ void __launch_bounds__(kThreads) l2_up_kernel(const Cycle2D c, const 
 #pragma unroll
     for (int dx = -R; dx <= R; ++dx) {
       if (gx + dx < 0 || gx + dx >= N0) continue;
-      const int o = (dx + R) + W * (dy + R);
-      ax = cmac(ax, c.coef2[o * g.size + idx], sx[(tx + R + dx) + NX * (ty + R + dy)]);
+      ax = cmac(ax, coef2_sym<R>(c, idx, dx, dy), sx[(tx + R + dx) + NX * (ty + R + dy)]);
     }
   }
   const float2 xc = sx[(tx + R) + NX * (ty + R)];
