@@ -689,8 +689,8 @@ int k_arnoldi_df(const KrylovState& st, const FineOp& op, const float4* cdf, con
     // the templated update kernels above do the small step in their last block
     KernelTimer kt(HELM_K_KRYLOV_OTHER, s);
     arnoldi_small_kernel<<<1, 32, 0, s>>>(st, j, st.m);
+    HELM_LAUNCH_CHECK();
   }
-  HELM_LAUNCH_CHECK();
   return 0;
 }
 
