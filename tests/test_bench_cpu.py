@@ -68,3 +68,19 @@ def test_uneven_sizes_and_3d_workload():
     assert wl["widths6"] == [4, 4, 4, 4, 0, 4] and wl["owidths"] == [(4, 4), (4, 4), (0, 4)]
     assert wl["q"][0, 8, 12] != 0 and np.count_nonzero(wl["q"]) == 1   # centre of the top face
     assert bench.n_nodes(wl) == 13 * 17 * 25
+
+
+def test_cpu_baseline_repeats_solves_to_its_budget(monkeypatch):
+    """The GPU arm's cpu_baseline repeats the sample solve until --cpu-seconds of solve
+    time are spent and reports nodes x solves / total time."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    monkeypatch.setattr(bench, "oracle_solve", lambda smp, args: (0.3, 8))
+    args = type("A", (), {"cpu_seconds": 10.0})()
+    smp = dict(solver="fgmres", cells="576x576", nodes=332929, n=512)
+    c = bench.cpu_baseline(smp, args)
+    assert c["value"] == pytest.approx(332929 * 34 / 1e6 / (0.3 * 34))
+    assert c["sample"].count("34 full FGMRES solves") == 1 and c["kind"] == "oracle"
+    args.cpu_seconds = 0.0
+    assert "full FGMRES solve to" in bench.cpu_baseline(smp, args)["sample"]
