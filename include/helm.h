@@ -53,8 +53,9 @@ typedef enum { HELM_SMOOTHER_JACOBI = 0, HELM_SMOOTHER_REDBLACK = 1 } helm_smoot
  * (smoothing, residuals, transfers) in complex FP32; the coarsest solve, the FGMRES
  * basis and the Arnoldi kernels (outer matvec, orthogonalisation) in double-float
  * arithmetic (an unevaluated sum of two FP32 values, about 48 significant bits, on the
- * FP32 pipes); the Givens rotations, the solution and the true residual in complex
- * FP64.  The coarsest factorisation itself is computed in FP64 in both modes. */
+ * FP32 pipes), and so is the true residual q - H p (from a double-float copy of p; error
+ * about 2^-46 |H| |p|); the Givens rotations and the solution in complex FP64.  The
+ * coarsest factorisation itself is computed in FP64 in both modes. */
 typedef enum { HELM_FP64 = 0, HELM_MIXED = 1 } helm_precision;
 typedef enum { HELM_C128 = 0, HELM_C64 = 1 } helm_dtype;
 /* HELM_SOLVER_FGMRES: FGMRES(restart) preconditioned by the cycle (Sec. 5).

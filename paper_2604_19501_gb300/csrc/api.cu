@@ -87,6 +87,7 @@ struct helm_ctx {
   int* d_bad = nullptr;
   LaunchTimer timer;
   float4* cdf = nullptr;                       // mixed precision: fine coefficients as double-float
+  float4* xd = nullptr;                        // mixed precision: the solution as double-float [B][n]
 };
 
 namespace {
@@ -505,10 +506,17 @@ int fgmres_block(helm_ctx* c, const double2* q, double2* p, int B, double tol, i
     }
     for (int r = 0; r < B; ++r) {
       if (!part[r]) continue;
-      if (int st = k_update_solution(c->ks[r], n, p + (size_t)r * n, Zp(0, r), zp, vstride, k[r], c->s)) return st;
-      if (int st = k_true_residual(c->ks[r], c->fine, c->kap64, q + (size_t)r * n, p + (size_t)r * n,
-                                   c->r + (size_t)r * n, c->s))
+      float4* xd = df ? c->xd + (size_t)r * n : nullptr;
+      if (int st = k_update_solution(c->ks[r], n, p + (size_t)r * n, Zp(0, r), zp, vstride, k[r], xd, c->s))
         return st;
+      // mixed precision: the true residual in double-float from the copy of x just written
+      if (df) {
+        if (int st = k_true_residual_df(c->ks[r], c->fine, c->cdf, q + (size_t)r * n, xd, c->r + (size_t)r * n, c->s))
+          return st;
+      } else if (int st = k_true_residual(c->ks[r], c->fine, c->kap64, q + (size_t)r * n, p + (size_t)r * n,
+                                          c->r + (size_t)r * n, c->s)) {
+        return st;
+      }
     }
     if (int st = sync_scal(c, B)) return st;
     for (int r = 0; r < B; ++r) {
@@ -583,9 +591,15 @@ int stationary_block(helm_ctx* c, const double2* q, double2* p, int B, double to
       for (int r = 0; r < B; ++r) {
         if (!act[r]) continue;
         double2* xr = x + (size_t)r * n;
-        if (int st = k_add_correction(n, xr, (const char*)c->Z + (size_t)r * n * zes, zp, c->s)) return st;
-        if (int st = k_true_residual(c->ks[r], c->fine, c->kap64, qc + (size_t)r * n, xr, c->r + (size_t)r * n, c->s))
+        float4* xd = df ? c->xd + (size_t)r * n : nullptr;
+        if (int st = k_add_correction(n, xr, (const char*)c->Z + (size_t)r * n * zes, zp, xd, c->s)) return st;
+        if (df) {
+          if (int st = k_true_residual_df(c->ks[r], c->fine, c->cdf, qc + (size_t)r * n, xd, c->r + (size_t)r * n, c->s))
+            return st;
+        } else if (int st = k_true_residual(c->ks[r], c->fine, c->kap64, qc + (size_t)r * n, xr, c->r + (size_t)r * n,
+                                            c->s)) {
           return st;
+        }
       }
       HELM_CUDA_TRY(cudaMemcpyAsync(c->h_scal, c->d_scal, sizeof(double) * KS_COUNT * B, cudaMemcpyDeviceToHost, c->s));
       return 0;
@@ -850,7 +864,8 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
     if ((st = krylov_alloc(c->ks[r], m, c->d_scal + (size_t)r * KS_COUNT, c->d_kpart, c->d_kcounter)))
       return bail(st);
   if (o->precision == HELM_MIXED) {
-    if ((st = dmalloc(&c->cdf, n1 * sizeof(float4)))) return bail(st);
+    if ((st = dmalloc(&c->cdf, n1 * sizeof(float4))) || (st = dmalloc(&c->xd, (size_t)B * n1 * sizeof(float4))))
+      return bail(st);
     if ((st = k_coef_df(c->fine, c->kap64, c->cdf, c->s))) return bail(HELM_ECUDA);
   }
   if (cudaMallocHost(&c->h_scal, sizeof(double) * KS_COUNT * B) != cudaSuccess) return bail(fail(HELM_ENOMEM, "pinned alloc"));
@@ -871,7 +886,7 @@ int helm_destroy(helm_ctx* c) {
   for (void* p : {(void*)c->d_gam, (void*)c->d_gam32, (void*)c->d_gam_cyc, (void*)c->d_gam32_cyc, (void*)c->kap64, (void*)c->kap32, (void*)c->A2_64, (void*)c->A2_dinv64,
                   (void*)c->A2_32, (void*)c->A2_dinv32, (void*)c->Mk2, (void*)c->A3_64, (void*)c->A3_dinv64,
                   (void*)c->V, (void*)c->w, (void*)c->r, c->Z, (void*)c->stage, (void*)c->d_bad,
-                  (void*)c->cdf, (void*)c->d_scal, (void*)c->d_kpart, (void*)c->d_kcounter})
+                  (void*)c->cdf, (void*)c->xd, (void*)c->d_scal, (void*)c->d_kpart, (void*)c->d_kcounter})
     cudaFree(p);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   delete[] c->h_gam;

@@ -107,6 +107,46 @@ __device__ __forceinline__ dd dd_make(double v) {
   const float hi = __double2float_rn(v);
   return dd{hi, __double2float_rn(v - (double)hi)};
 }
+
+// ---- FP64 <-> double-float without FP64 instructions.  GB300 retires FP64 arithmetic and
+// the FP64 <-> FP32 conversions at about the FP64 rate (1/64 of FP32), so streaming
+// kernels convert with integer operations on the IEEE 754 bit patterns (binary64: sign,
+// 11 exponent bits with bias 1023, 52 fraction bits; binary32: sign, 8 with bias 127, 23).
+
+// (double)f exactly: exponent rebiased by 1023 - 127 = 896, fraction moved to the top of
+// the 52-bit field.  Subnormals, infinities and NaNs take the conversion instruction.
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e == 0u || e == 0xFFu) {
+    if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)sgn);   // signed zero
+    return (double)f;
+  }
+  return __longlong_as_double(
+      (long long)(sgn | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
+// x = hi + lo + d, |d| < 2^-46 |x|: hi holds the leading 24 significand bits of x
+// (truncated), lo the next 23 (truncated); 0 <= lo / hi < ulp(hi) / hi, so the pair is
+// not normalised in the round-to-nearest sense, which the operations below allow.
+// Zeros are exact; |x| outside [2^-103, 2^128) takes the conversion instructions.
+__device__ __forceinline__ dd split_d(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned sgn = (unsigned)(u >> 32) & 0x80000000u;
+  const int fe = (int)((u >> 52) & 0x7FFu) - 896;   // biased binary32 exponent of x
+  if (fe < 24 || fe > 254) {
+    if ((u << 1) == 0ull) return dd{__uint_as_float(sgn), 0.f};
+    return dd_make(x);
+  }
+  const float hi = __uint_as_float(sgn | ((unsigned)fe << 23) | ((unsigned)(u >> 29) & 0x7FFFFFu));
+  // fraction bits 28..6 below hi as r * 2^-23 in [0, 1) (exact), then scaled by their
+  // weight 2^(fe - 150), a normal float for fe >= 24; the product is exact
+  const float f = __uint_as_float(0x3F800000u | ((unsigned)(u >> 6) & 0x7FFFFFu)) - 1.0f;
+  const float lo = f * __uint_as_float((unsigned)(fe - 23) << 23);
+  return dd{hi, __uint_as_float(__float_as_uint(lo) | sgn)};
+}
+
 __device__ __forceinline__ dd dd_add(dd a, dd b) {
   float s, t;
   two_sum(a.hi, b.hi, s, t);

@@ -92,23 +92,39 @@ __device__ __forceinline__ c2<T> fine_apply_at(const FineOp& op, c2<T> diag, con
 //     Mz  = mc z_c + sum_f z_f,  Mcz = mc c_c z_c + sum_f c_f z_f   (mc = 8 in 2D, 6 in 3D)
 // (f: face neighbours, e: the other non-zero offsets, i.e. 2D corners and 3D edges).
 // Sums are running accumulators (racc, df64.cuh), normalised once where they leave the sum.
-__device__ __forceinline__ cdd fine_apply_df(const FineOp& op, const float4* __restrict__ cdf,
-                                             const float2* __restrict__ z, long long p, int i, int j, int k,
-                                             dd ih2, dd ih2_6, dd inv24) {
+//
+// With z in double-float (TZ = float4: hi, lo per component), H z = H z_hi + H z_lo: the
+// high parts go through the exact-weight form above, the low parts (below 2^-23 |z_hi|)
+// through the same stencil in FP32, whose rounding is then of order 2^-47 |H| |z|.
+__device__ __forceinline__ float2 df_hi(float2 v) { return v; }
+__device__ __forceinline__ float2 df_hi(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 df_lo(float4 v) { return make_float2(v.z, v.w); }
+
+template <typename TZ>
+__device__ __forceinline__ cdd fine_apply_df_t(const FineOp& op, const float4* __restrict__ cdf,
+                                               const TZ* __restrict__ z, long long p, int i, int j, int k,
+                                               dd ih2, dd ih2_6, dd inv24) {
+  constexpr bool LO = sizeof(TZ) == sizeof(float4);
   const long long sy = op.g.N[0];
   const long long sz = (long long)op.g.N[0] * op.g.N[1];
   const cdd cc = cdd_load(cdf[p]);
-  const float2 zc = z[p];
+  const TZ zc4 = z[p];
+  const float2 zc = df_hi(zc4);
   const bool is3 = op.g.dim == 3;
+  // low parts: Laplacian-type sum, mass sums (FP32)
+  float2 l_lo = make_float2(0.f, 0.f), z_lo = make_float2(0.f, 0.f), m_lo = make_float2(0.f, 0.f);
   if (op.order == 0) {
     const float wc = 2.0f * op.g.dim;
     racc Lr{0.f, 0.f}, Li{0.f, 0.f};
     racc_add_prod(Lr, wc, zc.x);
     racc_add_prod(Li, wc, zc.y);
+    if constexpr (LO) l_lo = cscale(df_lo(zc4), wc);
     auto face = [&](long long q) {
-      const float2 zq = z[q];
+      const TZ zq4 = z[q];
+      const float2 zq = df_hi(zq4);
       racc_add(Lr, -zq.x);
       racc_add(Li, -zq.y);
+      if constexpr (LO) l_lo = l_lo - df_lo(zq4);
     };
     if (i > 0) face(p - 1);
     if (i < op.g.N[0] - 1) face(p + 1);
@@ -121,6 +137,12 @@ __device__ __forceinline__ cdd fine_apply_df(const FineOp& op, const float4* __r
     const dd lr = dd_mul(racc_dd(Lr), ih2), li = dd_mul(racc_dd(Li), ih2);
     racc Wr{lr.hi, lr.lo}, Wi{li.hi, li.lo};
     cacc_add_cz(Wr, Wi, cc, zc, -1.f);
+    if constexpr (LO) {
+      // ih2 L_lo - c_c z_c,lo
+      const float2 h = cscale(l_lo, ih2.hi) - cmul(make_float2(cc.re.hi, cc.im.hi), df_lo(zc4));
+      racc_add(Wr, h.x);
+      racc_add(Wi, h.y);
+    }
     return cdd{racc_dd(Wr), racc_dd(Wi)};
   }
   const float wc = is3 ? 24.f : 20.f, wf = is3 ? 2.f : 4.f, mc = is3 ? 6.f : 8.f;
@@ -136,6 +158,12 @@ __device__ __forceinline__ cdd fine_apply_df(const FineOp& op, const float4* __r
     cacc_add_cz(Mr, Mi, cc, make_float2(pr, pi), 1.f);
     cacc_add_cz(Mr, Mi, cc, ez, 1.f);
   }
+  if constexpr (LO) {
+    const float2 zl = df_lo(zc4);
+    l_lo = cscale(zl, wc);
+    z_lo = cscale(zl, mc);
+    m_lo = cmul(make_float2(cc.re.hi, cc.im.hi), z_lo);
+  }
   const int zlo = is3 ? -1 : 0, zhi = is3 ? 1 : 0;
   for (int dz = zlo; dz <= zhi; ++dz) {
     const int kk = k + dz;
@@ -149,16 +177,25 @@ __device__ __forceinline__ cdd fine_apply_df(const FineOp& op, const float4* __r
         const int nz = (dx != 0) + (dy != 0) + (dz != 0);
         if (nz == 0 || nz == 3) continue;
         const long long q = p + dx + dy * sy + dz * sz;
-        const float2 zq = z[q];
+        const TZ zq4 = z[q];
+        const float2 zq = df_hi(zq4);
         if (nz == 1) {
           racc_add(Lr, -wf * zq.x);   // wf a power of two: exact
           racc_add(Li, -wf * zq.y);
           racc_add(Zr, zq.x);
           racc_add(Zi, zq.y);
-          cacc_add_cz(Mr, Mi, cdd_load(cdf[q]), zq, 1.f);
+          const cdd cq = cdd_load(cdf[q]);
+          cacc_add_cz(Mr, Mi, cq, zq, 1.f);
+          if constexpr (LO) {
+            const float2 zl = df_lo(zq4);
+            l_lo = l_lo - cscale(zl, wf);
+            z_lo = z_lo + zl;
+            m_lo = m_lo + cmul(make_float2(cq.re.hi, cq.im.hi), zl);
+          }
         } else {
           racc_add(Lr, -zq.x);
           racc_add(Li, -zq.y);
+          if constexpr (LO) l_lo = l_lo - df_lo(zq4);
         }
       }
     }
@@ -170,7 +207,20 @@ __device__ __forceinline__ cdd fine_apply_df(const FineOp& op, const float4* __r
   racc_add_dd(Mi, cc.im, dd_of(Zr));
   const cdd L{racc_dd(Lr), racc_dd(Li)};
   const cdd mass{racc_dd(Mr), racc_dd(Mi)};
-  return cdd_sub(cdd_scale(L, ih2_6), cdd_scale(mass, inv24));
+  cdd h = cdd_sub(cdd_scale(L, ih2_6), cdd_scale(mass, inv24));
+  if constexpr (LO) {
+    // (ih2 / 6) L_lo - (1/24) (c_c Mz_lo + Mcz_lo)
+    const float2 hl = cscale(l_lo, ih2_6.hi) - cscale(cmul(make_float2(cc.re.hi, cc.im.hi), z_lo) + m_lo, inv24.hi);
+    h.re = dd_add(h.re, dd{hl.x, 0.f});
+    h.im = dd_add(h.im, dd{hl.y, 0.f});
+  }
+  return h;
+}
+
+__device__ __forceinline__ cdd fine_apply_df(const FineOp& op, const float4* __restrict__ cdf,
+                                             const float2* __restrict__ z, long long p, int i, int j, int k,
+                                             dd ih2, dd ih2_6, dd inv24) {
+  return fine_apply_df_t<float2>(op, cdf, z, p, i, j, k, ih2, ih2_6, inv24);
 }
 
 }  // namespace helm

@@ -207,14 +207,24 @@ __global__ void lsq_kernel(KrylovState st, int k, int m) {
 // cycle iteration, one right-hand side per call.
 template <typename TZ>
 __global__ void __launch_bounds__(kThreads) add_correction_kernel(long long n, double2* __restrict__ x,
-                                                                  const c2<TZ>* __restrict__ z) {
+                                                                  const c2<TZ>* __restrict__ z,
+                                                                  float4* __restrict__ xd) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
-    const c2<double> d = cvt<double>(z[p]);
     double2 v = x[p];
-    v.x += d.x;
-    v.y += d.y;
-    x[p] = v;
+    if constexpr (sizeof(TZ) == sizeof(float)) {
+      // (double) z by bit operations (the same values), and x's double-float copy
+      const float2 zf = z[p];
+      v.x += f2d(zf.x);
+      v.y += f2d(zf.y);
+      x[p] = v;
+      if (xd) xd[p] = cdd_store(cdd{split_d(v.x), split_d(v.y)});
+    } else {
+      const c2<double> d = cvt<double>(z[p]);
+      v.x += d.x;
+      v.y += d.y;
+      x[p] = v;
+    }
   }
 }
 
@@ -236,11 +246,13 @@ __global__ void __launch_bounds__(kThreads) solution_update_kernel(long long n, 
 }
 
 // x += Z y for a c64 basis Z: the correction sum_q y_q z_q is formed in double-float (z_q
-// are exact floats, y_q rounded to about 48 bits) and added to x in FP64.
+// are exact floats, y_q rounded to about 48 bits) and added to x in FP64; xd receives the
+// double-float copy of the new x that the double-float true residual reads.
 __global__ void __launch_bounds__(kThreads) solution_update_df_kernel(long long n, double2* __restrict__ x,
                                                                       const float2* __restrict__ Z,
                                                                       long long zstride, int k,
-                                                                      const double2* __restrict__ y) {
+                                                                      const double2* __restrict__ y,
+                                                                      float4* __restrict__ xd) {
   __shared__ float4 sy[64];
   for (int i = threadIdx.x; i < k; i += blockDim.x) sy[i] = cdd_store(cdd_make(y[i]));
   __syncthreads();
@@ -249,9 +261,10 @@ __global__ void __launch_bounds__(kThreads) solution_update_df_kernel(long long 
     cdd acc = cdd_zero();
     for (int q = 0; q < k; ++q) acc = cdd_add(acc, cdd_mulf(cdd_load(sy[q]), Z[q * zstride + p]));
     double2 xv = x[p];
-    xv.x += (double)acc.re.hi + (double)acc.re.lo;
-    xv.y += (double)acc.im.hi + (double)acc.im.lo;
+    xv.x += f2d(acc.re.hi) + f2d(acc.re.lo);
+    xv.y += f2d(acc.im.hi) + f2d(acc.im.lo);
     x[p] = xv;
+    xd[p] = cdd_store(cdd{split_d(xv.x), split_d(xv.y)});
   }
 }
 
@@ -333,6 +346,7 @@ __global__ void coef_df_kernel(FineOp op, const double* __restrict__ kap, float4
   }
 }
 
+
 // Reduction of per-thread double-float accumulators sdf[i * blockDim + tid] (nval sums):
 // warps reduce in double-float, the block partials go to part (as float4), and the last
 // block adds the partials in block order and converts each sum to FP64 once.
@@ -365,6 +379,43 @@ __device__ bool reduce_finish_df(float4* sdf, int nval, double2* __restrict__ pa
   if (tid == 0) *counter = 0u;
   __syncthreads();
   return true;
+}
+
+// r = b - H x and ||r||^2 (out[0].x) in double-float arithmetic on the FP32 pipes, from the
+// double-float copy xd of x: H x by the exact-weight operator on x_hi plus the FP32
+// stencil of x_lo (fine_apply_df_t), b split into double-float by bit operations, r
+// returned as c128 (relative error about 2^-46 against FP64 arithmetic).
+__global__ void __launch_bounds__(kThreads) true_residual_df_kernel(FineOp op, DfConsts K,
+                                                                    const float4* __restrict__ cdf,
+                                                                    const double2* __restrict__ b,
+                                                                    const float4* __restrict__ xd,
+                                                                    double2* __restrict__ r,
+                                                                    double2* __restrict__ part,
+                                                                    unsigned* __restrict__ counter,
+                                                                    double2* __restrict__ out) {
+  extern __shared__ double2 sacc[];
+  float4* sdf = reinterpret_cast<float4*>(sacc);
+  const int tid = threadIdx.x;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (long long p = blockIdx.x * (long long)blockDim.x + tid; p < op.g.size;
+       p += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    node_coords(op.g, p, i, j, k);
+    const cdd hx = fine_apply_df_t<float4>(op, cdf, xd, p, i, j, k, K.ih2, K.ih2_6, K.inv24);
+    const double2 bv = b[p];
+    const dd br = split_d(bv.x), bi = split_d(bv.y);
+    racc rr{br.hi, br.lo}, ri{bi.hi, bi.lo};
+    racc_add(rr, -hx.re.hi);
+    racc_add(rr, -hx.re.lo);
+    racc_add(ri, -hx.im.hi);
+    racc_add(ri, -hx.im.lo);
+    const cdd rv{racc_dd(rr), racc_dd(ri)};
+    r[p] = make_double2(f2d(rv.re.hi) + f2d(rv.re.lo), f2d(rv.im.hi) + f2d(rv.im.lo));
+    const float4 r4 = cdd_store(rv);
+    df_cmacc(acc, r4, r4);
+  }
+  sdf[tid] = acc;
+  reduce_finish_df(sdf, 1, part, counter, out);
 }
 
 __global__ void __launch_bounds__(kThreads) arnoldi_matvec_df_kernel(
@@ -528,13 +579,14 @@ int arnoldi_df_launch(int bl, size_t sm, const FineOp& op, const DfConsts& K, co
 __global__ void __launch_bounds__(kThreads) start_cycle_df_kernel(long long n, const double2* __restrict__ r,
                                                                   float4* __restrict__ v, KrylovState st, int m) {
   const double beta = st.scal[KS_BETA];
-  const double s = 1.0 / beta;
+  // 1 / beta as double-float; r split by bit operations (no FP64 instruction per node)
+  const dd s = dd_make(1.0 / beta);
   if (blockIdx.x == 0)
     for (int i = threadIdx.x; i <= m; i += blockDim.x) st.g[i] = make_double2(i == 0 ? beta : 0.0, 0.0);
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
     const double2 a = r[p];
-    v[p] = cdd_store(cdd_make(make_double2(a.x * s, a.y * s)));
+    v[p] = cdd_store(cdd_scale(cdd{split_d(a.x), split_d(a.y)}, s));
   }
 }
 
@@ -713,24 +765,24 @@ int k_normalize(const KrylovState& st, long long n, const double2* w, const doub
 }
 
 int k_update_solution(const KrylovState& st, long long n, double2* x, const void* Z, Prec zp,
-                      long long zstride, int k, cudaStream_t s) {
+                      long long zstride, int k, float4* xd, cudaStream_t s) {
   KernelTimer kt(HELM_K_KRYLOV_OTHER, s);
   lsq_kernel<<<1, 32, 0, s>>>(st, k, st.m);
   HELM_LAUNCH_CHECK();
   if (zp == P64)
     solution_update_kernel<double><<<grid_blocks(n), kThreads, 0, s>>>(n, x, (const double2*)Z, zstride, k, st.y);
   else
-    solution_update_df_kernel<<<grid_blocks(n), kThreads, 0, s>>>(n, x, (const float2*)Z, zstride, k, st.y);
+    solution_update_df_kernel<<<grid_blocks(n), kThreads, 0, s>>>(n, x, (const float2*)Z, zstride, k, st.y, xd);
   HELM_LAUNCH_CHECK();
   return 0;
 }
 
-int k_add_correction(long long n, double2* x, const void* z, Prec zp, cudaStream_t s) {
+int k_add_correction(long long n, double2* x, const void* z, Prec zp, float4* xd, cudaStream_t s) {
   KernelTimer kt(HELM_K_KRYLOV_OTHER, s);
   if (zp == P64)
-    add_correction_kernel<double><<<grid_blocks(n), kThreads, 0, s>>>(n, x, (const double2*)z);
+    add_correction_kernel<double><<<grid_blocks(n), kThreads, 0, s>>>(n, x, (const double2*)z, nullptr);
   else
-    add_correction_kernel<float><<<grid_blocks(n), kThreads, 0, s>>>(n, x, (const float2*)z);
+    add_correction_kernel<float><<<grid_blocks(n), kThreads, 0, s>>>(n, x, (const float2*)z, xd);
   HELM_LAUNCH_CHECK();
   return 0;
 }
@@ -741,6 +793,18 @@ int k_true_residual(const KrylovState& st, const FineOp& op, const double* kap64
   KernelTimer kt(HELM_K_KRYLOV_OTHER, s);
   true_residual_kernel<<<bl, kThreads, kThreads * sizeof(double2), s>>>(op, kap64, b, x, r, st.part,
                                                                        st.counter, st.red);
+  HELM_LAUNCH_CHECK();
+  set_scalar_kernel<<<1, 32, 0, s>>>(st.scal + KS_BETA, st.red, 1);
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
+int k_true_residual_df(const KrylovState& st, const FineOp& op, const float4* cdf, const double2* b,
+                       const float4* xd, double2* r, cudaStream_t s) {
+  const int bl = grid_blocks(op.g.size);
+  KernelTimer kt(HELM_K_KRYLOV_OTHER, s);
+  true_residual_df_kernel<<<bl, kThreads, kThreads * sizeof(float4), s>>>(op, df_consts(op), cdf, b, xd, r, st.part,
+                                                                          st.counter, st.red);
   HELM_LAUNCH_CHECK();
   set_scalar_kernel<<<1, 32, 0, s>>>(st.scal + KS_BETA, st.red, 1);
   HELM_LAUNCH_CHECK();

@@ -48,13 +48,18 @@ int k_arnoldi_df(const KrylovState& st, const FineOp& op, const float4* cdf, con
                  const float4* V, long long vstride, int j, cudaStream_t s);
 int k_normalize_df(const KrylovState& st, long long n, const float4* w, const float4* V, long long vstride, int j,
                    float4* vout, cudaStream_t s);
-// y = R^-1 g (k x k) and x += Z y.
+// y = R^-1 g (k x k) and x += Z y; for a c64 basis (zp = P32) also xd = x as double-float.
 int k_update_solution(const KrylovState& st, long long n, double2* x, const void* Z, Prec zp,
-                      long long zstride, int k, cudaStream_t s);
-// x += z (z c128 or c64), summed in FP64.
-int k_add_correction(long long n, double2* x, const void* z, Prec zp, cudaStream_t s);
+                      long long zstride, int k, float4* xd, cudaStream_t s);
+// x += z (z c128 or c64), summed in FP64; for c64 z and a non-null xd also xd = x as
+// double-float.
+int k_add_correction(long long n, double2* x, const void* z, Prec zp, float4* xd, cudaStream_t s);
 // r = b - H x in FP64, scal[KS_BETA] = ||r||.
 int k_true_residual(const KrylovState& st, const FineOp& op, const double* kap64, const double2* b,
                     const double2* x, double2* r, cudaStream_t s);
+// The same in double-float arithmetic from xd (x as double-float) and the double-float
+// coefficients cdf; r is c128.
+int k_true_residual_df(const KrylovState& st, const FineOp& op, const float4* cdf, const double2* b,
+                       const float4* xd, double2* r, cudaStream_t s);
 
 }  // namespace helm
