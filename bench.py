@@ -42,7 +42,7 @@ UNIT = "Mdof*solves/s"
 FP64_PEAK_TFLOPS = 1.26   # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
 # DRAM read + write bytes of one coarsest-solve launch (sweep_kernel) on the default
 # workload, from one ncu capture of the current kernel (profiles/sweep_kernel_2112_traffic.md)
-SWEEP_TRAFFIC_DEFAULT = 2.9925e9 + 53.1e6
+SWEEP_TRAFFIC_DEFAULT = 2.9926e9 + 53.4e6
 
 
 def parse():

@@ -103,10 +103,24 @@ __device__ __forceinline__ void addto(double2& a, double2 b) {
 __device__ __forceinline__ void addto(float4& a, float4 b) { df_acc_add(a, b); }
 __device__ __forceinline__ void zero(double2& a) { a = make_double2(0.0, 0.0); }
 __device__ __forceinline__ void zero(float4& a) { a = make_float4(0.f, 0.f, 0.f, 0.f); }
+// Double-float values and accumulators share the float4 layout (re_hi, im_hi, re_lo,
+// im_lo); the solve's scratch vectors (update vectors, w) hold double-float values in the
+// 16-byte slots of the FP64 layout.  Conversions from and to c128 use bit operations
+// (f2d, split_d): GB300 runs FP64 conversions and additions at the FP64 rate.
 __device__ __forceinline__ void from_c128(double2& a, double2 v) { a = v; }
-__device__ __forceinline__ void from_c128(float4& a, double2 v) { a = to_df(v); }
+__device__ __forceinline__ void from_c128(float4& a, double2 v) {
+  const dd re = split_d(v.x), im = split_d(v.y);
+  a = make_float4(re.hi, im.hi, re.lo, im.lo);
+}
 __device__ __forceinline__ double2 to_c128(double2 a) { return a; }
-__device__ __forceinline__ double2 to_c128(float4 a) { return from_df(a); }
+__device__ __forceinline__ double2 to_c128(float4 a) { return make_double2(f2d(a.x) + f2d(a.z), f2d(a.y) + f2d(a.w)); }
+__device__ __forceinline__ double2 norm(double2 a) { return a; }
+__device__ __forceinline__ float4 norm(float4 a) {
+  const dd re = dd_norm(a.x, a.z), im = dd_norm(a.y, a.w);
+  return make_float4(re.hi, im.hi, re.lo, im.lo);
+}
+__device__ __forceinline__ double2 neg(double2 a) { return make_double2(-a.x, -a.y); }
+__device__ __forceinline__ float4 neg(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
 __device__ __forceinline__ double2 ldcg(const double2* p) { return __ldcg(p); }
 __device__ __forceinline__ float4 ldcg(const float4* p) { return __ldcg(p); }
 
@@ -259,7 +273,9 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
   unsigned char* const local = smem + NST * kStageBytes;
   E* const vs = reinterpret_cast<E*>(local);   // row values [kJobRows][RG]
   E* const red = vs;                           // row-part sums [threads][RG], after the stages
-  double2* const rbs = reinterpret_cast<double2*>(vs + (kJobRows > kSweepThreads ? kJobRows : kSweepThreads) * RG);   // forward r_B [kTile][RG]
+  E* const rbs = vs + (kJobRows > kSweepThreads ? kJobRows : kSweepThreads) * RG;   // forward r_B [kTile][RG]
+  E* const uvE = reinterpret_cast<E*>(a.uv);   // update vectors and w in the arithmetic's form
+  E* const wE = reinterpret_cast<E*>(a.w);
   SweepMeta* const metas = reinterpret_cast<SweepMeta*>(local + kLocalBytes);   // [2]: current and next job
   uint64_t* const full = reinterpret_cast<uint64_t*>(metas + 2);
   uint64_t* const empty = full + NST;
@@ -309,6 +325,13 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
   // ---- consumers
   long long ci = 0;   // position in the fill sequence
   bool ok = true;     // uniform over the consumers: false once a dependency failed anywhere
+  // backward output: x = w - (G x_B) at node gi, as c128 and (double-float) its copy xd
+  auto write_x = [&](long long gi, E w, E o) {
+    addto(w, neg(o));
+    w = norm(w);
+    a.x[gi] = to_c128(w);
+    if constexpr (DF) a.xd[gi] = w;
+  };
   auto consume = [&](auto&& body) {
     const int q = (int)(ci % NST);
     const uint32_t par = (uint32_t)((ci / NST) & 1);
@@ -424,7 +447,7 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
     const int nsplit = min(kSplitMax, kSweepThreads / cols);
     const int c = tid % cols, part = tid / cols;
     const bool act = part < nsplit;
-    double2 wv[RG];   // backward: w at this thread's output column
+    E wv[RG];   // backward: w at this thread's output column
     for (int p = 0; p < npass; ++p) {
       const int r0 = p * RG, nr = min(RG, a.nrhs - r0);
       if (p > 0) {
@@ -441,10 +464,11 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
               const int r = r0 + q % nr;
               E* dst = vs + (q / nr) * RG + q % nr;
               if (fwd) {
-                double2 v = pv[i];
-                if (pc2[i].x >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + pc2[i].x));
-                if (pc2[i].y >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + pc2[i].y));
-                from_c128(*dst, v);
+                E v;
+                from_c128(v, pv[i]);
+                if (pc2[i].x >= 0) addto(v, ldcg(uvE + r * a.uv_total + pc2[i].x));
+                if (pc2[i].y >= 0) addto(v, ldcg(uvE + r * a.uv_total + pc2[i].y));
+                *dst = norm(v);
               } else {
                 const long long gi = r * a.nodes + pI[i];
                 if (DF) *reinterpret_cast<float4*>(dst) = __ldcg(a.xd + gi);
@@ -457,11 +481,12 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
             const int t = r0j + q / nr, r = r0 + q % nr;
             E* dst = vs + (q / nr) * RG + q % nr;
             if (fwd) {
-              double2 v = a.b[r * a.nodes + a.S[m.S_off + t]];
+              E v;
+              from_c128(v, a.b[r * a.nodes + a.S[m.S_off + t]]);
               const int2 cc = a.ctb[m.ctb_off + t];
-              if (cc.x >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + cc.x));
-              if (cc.y >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + cc.y));
-              from_c128(*dst, v);
+              if (cc.x >= 0) addto(v, ldcg(uvE + r * a.uv_total + cc.x));
+              if (cc.y >= 0) addto(v, ldcg(uvE + r * a.uv_total + cc.y));
+              *dst = norm(v);
             } else {
               const long long gi = r * a.nodes + a.B[m.B_off + t];
               if (DF) *reinterpret_cast<float4*>(dst) = __ldcg(a.xd + gi);
@@ -475,16 +500,17 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
             const int q = tid + i * kSweepThreads;
             if (q < cols * nr) {
               const int r = r0 + q % nr;
-              double2 v = make_double2(0.0, 0.0);
-              if (qc2[i].x >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + qc2[i].x));
-              if (qc2[i].y >= 0) addto(v, __ldcg(a.uv + r * a.uv_total + qc2[i].y));
+              E v;
+              zero(v);
+              if (qc2[i].x >= 0) addto(v, ldcg(uvE + r * a.uv_total + qc2[i].x));
+              if (qc2[i].y >= 0) addto(v, ldcg(uvE + r * a.uv_total + qc2[i].y));
               rbs[(q / nr) * RG + q % nr] = v;
             }
           }
         } else if (nchunks == 1 && tid < cols) {
 #pragma unroll
           for (int rr = 0; rr < RG; ++rr)
-            if (rr < nr) wv[rr] = __ldcg(a.w + (r0 + rr) * a.nodes + sI[0]);
+            if (rr < nr) wv[rr] = ldcg(wE + (r0 + rr) * a.nodes + sI[0]);
         }
       }
       consumer_sync();
@@ -521,18 +547,16 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
           for (int pp = 1; pp < nsplit; ++pp) addto(v, red[(pp * cols + tid) * RG + rr]);
           const int r = r0 + rr;
           if (nchunks == 1) {
-            const double2 o = to_c128(v);
+            const E o = norm(v);
             const int t = c0j + tid;
             if (fwd && t >= nS) {
-              const double2 rb = rbs[tid * RG + rr];
-              a.uv[r * a.uv_total + m.uv_off + t - nS] = make_double2(rb.x + m.bsign * o.x, rb.y + m.bsign * o.y);
+              E u = rbs[tid * RG + rr];
+              addto(u, m.bsign > 0 ? o : neg(o));
+              uvE[r * a.uv_total + m.uv_off + t - nS] = norm(u);
             } else if (fwd) {
-              a.w[r * a.nodes + sidx[tid]] = o;
+              wE[r * a.nodes + sidx[tid]] = o;
             } else {
-              const long long gi = r * a.nodes + sidx[tid];
-              const double2 xv = make_double2(wv[rr].x - o.x, wv[rr].y - o.y);
-              a.x[gi] = xv;
-              if (DF) a.xd[gi] = to_df(xv);
+              write_x(r * a.nodes + sidx[tid], wv[rr], o);
             }
           } else {
             reinterpret_cast<E*>(a.part)[((long long)(m.pbase + m.chunk) * a.nrhs + r) * kPartBlock + tid] = v;
@@ -567,25 +591,21 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
             for (int u = 0; u < 8; ++u) addto(v, t8[u]);
           }
           for (; ch < nchunks; ++ch) addto(v, ldcg(src + ch * step));
-          const double2 o = to_c128(v);
+          const E o = norm(v);
           const int t = c0j + i;
           if (fwd && t >= nS) {
             // r_F at t: the children's update-vector entries mapped to t (t is a boundary position)
-            double2 rb = make_double2(0.0, 0.0);
+            E rb;
+            zero(rb);
             const int2 cc = a.ctb[m.ctb_off + t];
-            if (cc.x >= 0) addto(rb, __ldcg(a.uv + r * a.uv_total + cc.x));
-            if (cc.y >= 0) addto(rb, __ldcg(a.uv + r * a.uv_total + cc.y));
-            a.uv[r * a.uv_total + m.uv_off + t - nS] = make_double2(rb.x + m.bsign * o.x, rb.y + m.bsign * o.y);
+            if (cc.x >= 0) addto(rb, ldcg(uvE + r * a.uv_total + cc.x));
+            if (cc.y >= 0) addto(rb, ldcg(uvE + r * a.uv_total + cc.y));
+            addto(rb, m.bsign > 0 ? o : neg(o));
+            uvE[r * a.uv_total + m.uv_off + t - nS] = norm(rb);
           } else {
             const long long gi = r * a.nodes + sidx[i];
-            if (fwd) {
-              a.w[gi] = o;
-            } else {
-              const double2 wv1 = __ldcg(a.w + gi);
-              const double2 xv = make_double2(wv1.x - o.x, wv1.y - o.y);
-              a.x[gi] = xv;
-              if (DF) a.xd[gi] = to_df(xv);
-            }
+            if (fwd) wE[gi] = o;
+            else write_x(gi, ldcg(wE + gi), o);
           }
         }
       }
