@@ -258,11 +258,12 @@ __global__ void __launch_bounds__(kThreads) solution_update_df_kernel(long long 
   __syncthreads();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
-    cdd acc = cdd_zero();
-    for (int q = 0; q < k; ++q) acc = cdd_add(acc, cdd_mulf(cdd_load(sy[q]), Z[q * zstride + p]));
+    racc re{0.f, 0.f}, im{0.f, 0.f};
+    for (int q = 0; q < k; ++q) cacc_add_cz(re, im, cdd_load(sy[q]), Z[q * zstride + p], 1.f);
+    const dd ar = racc_dd(re), ai = racc_dd(im);
     double2 xv = x[p];
-    xv.x += f2d(acc.re.hi) + f2d(acc.re.lo);
-    xv.y += f2d(acc.im.hi) + f2d(acc.im.lo);
+    xv.x += f2d(ar.hi) + f2d(ar.lo);
+    xv.y += f2d(ai.hi) + f2d(ai.lo);
     x[p] = xv;
     xd[p] = cdd_store(cdd{split_d(xv.x), split_d(xv.y)});
   }
