@@ -518,12 +518,21 @@ __global__ void __launch_bounds__(kThreads, 4) arnoldi_matvec_df_t(FineOp op, Df
   reduce_finish_df(sdf, NV, part, counter, out);
 }
 
+// A load the compiler keeps in place (not merged with an earlier load of the same entry):
+// the dot pass re-reads V from L1 instead of holding the subtraction's values in registers.
+__device__ __forceinline__ float4 ld_reread(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+  return v;
+}
+
 // Second CGS pass: w' = w - V h1 and h2 = V^H w', |w'|^2 (double-float), accumulators in
 // registers (the dot pass re-reads V right after the subtraction read it: L1 hits).
 // The block that finishes the reduction also forms the Hessenberg column, its Givens
 // rotation and the residual estimate (the small step, no separate launch).
+// Three blocks per SM (80 registers) up to seven basis vectors, two above: no spills.
 template <int NV>
-__global__ void __launch_bounds__(kThreads, 2) arnoldi_update_df_t(long long n, float4* __restrict__ w,
+__global__ void __launch_bounds__(kThreads, NV <= 7 ? 3 : 2) arnoldi_update_df_t(long long n, float4* __restrict__ w,
                                                                    const float4* __restrict__ V, long long vstride,
                                                                    const double2* __restrict__ h1,
                                                                    double2* __restrict__ part,
@@ -546,7 +555,7 @@ __global__ void __launch_bounds__(kThreads, 2) arnoldi_update_df_t(long long n, 
     const float4 w4 = cdd_store(cdd{racc_dd(re), racc_dd(im)});
     w[p] = w4;
 #pragma unroll
-    for (int q = 0; q < NV; ++q) df_cmacc(acc[q], V[q * vstride + p], w4);
+    for (int q = 0; q < NV; ++q) df_cmacc(acc[q], ld_reread(V + q * vstride + p), w4);
     df_cmacc(acc[NV], w4, w4);
   }
 #pragma unroll
@@ -569,8 +578,10 @@ int arnoldi_df_launch(int bl, size_t sm, const FineOp& op, const DfConsts& K, co
     HELM_LAUNCH_CHECK();
   }
   {
+    // one wave of resident blocks: three per SM up to seven basis vectors, two above
+    const int blu = NV <= 7 ? std::min(bl, 152 * 3) : bl;
     KernelTimer kt(HELM_K_ARNOLDI_UPDATE, s);
-    arnoldi_update_df_t<NV><<<bl, kThreads, sm, s>>>(op.g.size, w, V, vstride, st.h1, st.part, st.counter, st.h2, st);
+    arnoldi_update_df_t<NV><<<blu, kThreads, sm, s>>>(op.g.size, w, V, vstride, st.h1, st.part, st.counter, st.h2, st);
     HELM_LAUNCH_CHECK();
   }
   return 0;
