@@ -261,3 +261,30 @@ def test_zero_rhs_and_errors():
     with pytest.raises(HelmError):
         Case((18, 16)).solver()
     s.close()
+
+
+@pytest.mark.parametrize("n", [(128, 128), (16, 16, 24)])
+def test_mixed_true_residual_is_fp64_class(n):
+    """Mixed precision forms the true residual q - H p in double-float from a double-float
+    copy of p (rounding of order 2^-46 |H| |p|).  Solved to 1e-9, the reported residual
+    agrees with the FP64 residual of the returned p (oracle operator, on the CPU) within
+    2^-40 || |H| |p| + |q| ||, and both are below the tolerance up to that bound."""
+    import workloads
+
+    kappa2 = workloads.constant_medium(n) if len(n) == 2 else None
+    c = Case(n, abc=16 if len(n) == 2 else 4, alpha3=1.117, kappa2=kappa2, G_ppw=12, seed=3)
+    s = c.solver(precision="mixed")
+    q = _point_source(c)
+    tol = 1e-9
+    p, st = s.solve(_t(q), tol=tol, maxit=400)
+    s.close()
+    assert st[0]["converged"]
+    A = c.hier.A_outer
+    pn = _n(p).ravel()
+    qn = q.ravel()
+    r = qn - A @ pn
+    scale = np.linalg.norm(abs(A) @ np.abs(pn) + np.abs(qn))
+    bound = 2.0 ** -40 * scale
+    assert abs(st[0]["relres"] - np.linalg.norm(r) / np.linalg.norm(qn)) * np.linalg.norm(qn) <= bound
+    assert st[0]["relres"] < tol
+    assert np.linalg.norm(r) <= tol * np.linalg.norm(qn) + bound
