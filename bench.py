@@ -54,8 +54,9 @@ def parse():
     ap.add_argument("--n", type=int, default=2048, help="interior cells per axis")
     ap.add_argument("--pad", type=int, default=32, help="absorbing-layer cells per side")
     ap.add_argument("--ppw", type=int, default=12)
-    ap.add_argument("--method", default="paper", choices=["paper", "baseline"],
-                    help="paper: 4th-order 9-point + cubic transfers (Sec. 3); baseline: 5-point + FW/bilinear")
+    ap.add_argument("--method", default="paper", choices=["paper", "five-point"],
+                    help="paper: 4th-order 9-point + cubic transfers (Sec. 3); five-point: 2nd-order 5-point + "
+                         "full weighting / bilinear")
     ap.add_argument("--cycle", default="V")
     ap.add_argument("--jacobi", type=float, default=None)
     ap.add_argument("--restart", type=int, default=10)
