@@ -84,3 +84,21 @@ def test_plan_rejects_bad_arguments():
         coarse_plan((33, 33), 0)
     with pytest.raises(HelmError):
         coarse_plan((33, 33), 1, grid=0)
+
+
+def test_plan_valid_on_seeded_random_grids():
+    """Seeded random 2D and 3D coarsest grids (ragged sizes, radii 1-3, both storage
+    forms, small and large resident grids): every plan passes the library's checks and
+    stores the nested-dissection entry count re-derived above."""
+    import numpy as np
+
+    rng = np.random.default_rng(2604)
+    for _ in range(24):
+        dim = int(rng.integers(2, 4))
+        n = tuple(int(v) for v in (rng.integers(5, 90, 2) if dim == 2 else rng.integers(5, 22, 3)))
+        r = int(rng.integers(1, 4))
+        sym = bool(rng.integers(0, 2))
+        grid = int(rng.choice([1, 7, 152, 608]))
+        st = coarse_plan(n, r, symmetric=sym, grid=grid)
+        assert st["factor_entries"] == _nd_entries(n, r, 64) + st["bwd_entries"], (n, r)
+        assert st["jobs"] >= 2 * st["fronts"]
