@@ -40,12 +40,13 @@ sys.path.insert(0, ROOT)
 METRIC = "Mdof*solves/s to 1e-6 rel-res"
 UNIT = "Mdof*solves/s"
 FP64_PEAK_TFLOPS = 1.26   # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
-# DRAM read + write bytes of one coarsest-solve launch (sweep_kernel) on the default
-# workload, from one ncu capture of the current kernel (profiles/sweep_kernel_2112_traffic.md)
-SWEEP_TRAFFIC_DEFAULT = 2.9926e9 + 53.4e6
+# The numerical n_crit of Table 1 (cubic transfers, 2D): the largest grid, in points per
+# direction, on which the multigrid convergence stayed stable at G points per wavelength
+TABLE1_NCRIT_CUBIC = {10: 248, 11: 536, 12: 1396}
+MIXED_DTYPE = "f32 cycle + double-float (2x f32) Krylov basis/true residual/coarsest solve + f64 Givens/solution"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=25)
@@ -102,7 +103,12 @@ def parse():
     ap.add_argument("--solver", default="fgmres", choices=["fgmres", "cycle"],
                     help="fgmres: FGMRES preconditioned by the cycle; cycle: RS-CGC as a solver "
                          "(stationary cycle iteration, Sec. 5)")
-    return ap.parse_args()
+    ap.add_argument("--no-autotune-cycle", action="store_true",
+                    help="keep the default kernels of the fused cycle's fine passes instead of timing every kind")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the side measurements of the 2D run (FP64 path, points-per-wavelength and "
+                         "grid-size sweeps), which run after the timed region")
+    return ap.parse_args(argv)
 
 
 # ------------------------------------------------------------------ workload
@@ -170,12 +176,6 @@ def n_nodes(wl):
     for v in wl["n"]:
         out *= v + 1
     return out
-
-
-def default_workload(args):
-    """The configuration the sweep traffic figure was captured on."""
-    return (args.dim, args.n, args.pad, args.ppw, args.method, args.precision, args.cycle, args.sources, args.cslp,
-            args.solver, args.medium) == (2, 2048, 32, 12, "paper", "mixed", "V", 1, 0.0, "fgmres", "layered")
 
 
 def medium_name(args):
@@ -328,7 +328,7 @@ def oracle_sample(args, log):
     shape = "x".join(str(v) for v in wl["n"])
     log(f"oracle set-up {time.perf_counter() - t0:.1f} s ({shape} cells)")
     return dict(h=h, cy=cy, A=h.A_outer, q=wl["q"].ravel(), nodes=n_nodes(wl), cells=shape,
-                n=args.cpu_cells3 if args.dim == 3 else args.cpu_n, solver=args.solver)
+                n=args.cpu_cells3 if args.dim == 3 else args.cpu_n, solver=args.solver, args=sargs, wl=wl)
 
 
 def oracle_solve(smp, args):
@@ -384,7 +384,6 @@ def reference_arm(args):
     if rank != 0:
         return 0
     log = lambda m: print(m, file=sys.stderr, flush=True)
-    wl = workload(args)
     smp = oracle_sample(args, log)
     for _ in range(args.warmup):
         oracle_solve(smp, args)
@@ -396,7 +395,9 @@ def reference_arm(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": describe(args, wl),
+        "config": dict(describe(smp["args"], smp["wl"]),
+                       precision="the CPU oracle: complex FP64 throughout (NumPy/SciPy, SuperLU coarsest solve)",
+                       sample_of=describe(args, workload(args))["workload"]),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": ORACLE_THREADS, "kind": "oracle",
                          "sample": cpu_sample_note(smp, its, t_step)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -447,6 +448,120 @@ def cycle_bytes(info, n1, n3):
     return n1 * (20 + 20 + 8) + n2 * level2 + n3 * 32
 
 
+def make_solver(wl, args, dev, precision=None, cslp=None, coarse_refine=0):
+    import torch
+
+    from paper_2604_19501_gb300 import Solver
+
+    return Solver(torch.from_numpy(wl["kappa2"]).to(dev), wl["n"], wl["omega"], abc_width=wl["widths6"],
+                  alpha3=wl["alpha3"], stencil=wl["order"], intergrid=wl["intergrid"], cycle=args.cycle,
+                  jacobi_w=wl["jw"], precision=precision or args.precision, restart=args.restart,
+                  stream=torch.cuda.current_stream(dev).cuda_stream, cslp_beta=args.cslp if cslp is None else cslp,
+                  solver=args.solver, coarse_refine=coarse_refine)
+
+
+def timed_solves(s, q, args, reps, warm=1):
+    """Solves of q after `warm` untimed ones: (ms per solve by CUDA events on the current
+    stream, stats of the last solve, its field)."""
+    import torch
+
+    p, st = None, None
+    for _ in range(warm):
+        p, st = s.solve(q, p, tol=args.tol, maxit=args.maxit)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        p, st = s.solve(q, p, tol=args.tol, maxit=args.maxit)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, st[0], p
+
+
+def side_measurements(args, wl, p_main, main_ms, main_its, dev, log):
+    """Measurements beside the timed region of the 2D run, each on its own context:
+    the plain FP64 GPU path on the same workload (its time, and the difference of the two
+    fields), iterations and throughput at 10, 11 and 12 points per wavelength with and
+    without the complex shift of RS-CGC + CSLP, and iterations against grid size at the
+    run's points per wavelength."""
+    import argparse
+
+    import torch
+
+    out = {}
+    nodes = n_nodes(wl)
+    q = torch.from_numpy(wl["q"]).to(dev)
+    if args.precision == "mixed":
+        s64 = make_solver(wl, args, dev, precision="fp64")
+        ms, st, p64 = timed_solves(s64, q, args, reps=3)
+        s64.close()
+        diff = (p_main - p64).abs()
+        out["fp64_path"] = {
+            "ms_per_solve": ms, "value": nodes / 1e3 / ms, "unit": UNIT, "iterations": st["iterations"],
+            "converged": st["converged"], "relres": st["relres"], "mixed_speedup": ms / main_ms,
+            "note": "same workload, method and tolerance with every step in complex FP64 (one kernel per step, "
+                    "FP64 coarsest factors and Krylov basis), 3 timed solves after one untimed"}
+        out["error_vs_fp64"] = {
+            "max_rel": float(diff.max() / p64.abs().max()),
+            "l2_rel": float(torch.linalg.vector_norm(diff) / torch.linalg.vector_norm(p64)),
+            "note": "mixed-precision field of the timed run against the FP64 GPU field of the same workload; "
+                    "the FP64 path matches the oracle to 1e-10 on this workload at 576^2 cells (tests)"}
+        log(f"fp64 path: {ms:.2f} ms, {st}; error vs fp64 {out['error_vs_fp64']}")
+        sr = make_solver(wl, args, dev, coarse_refine=1)
+        ms_r, st_r, p_r = timed_solves(sr, q, args, reps=3)
+        sr.close()
+        out["coarse_refine_1"] = {
+            "ms_per_solve": ms_r, "value": nodes / 1e3 / ms_r, "unit": UNIT, "iterations": st_r["iterations"],
+            "relres": st_r["relres"],
+            "max_rel_diff_vs_fp64": float((p_r - p64).abs().max() / p64.abs().max()),
+            "note": "the timed configuration with one step of iterative refinement after every coarsest direct "
+                    "solve (helm_opts.coarse_refine = 1): an exact coarsest solve to the arithmetic's level"}
+        log(f"coarse_refine=1: {ms_r:.2f} ms, {st_r}")
+        del p64, diff, p_r
+    if args.dim == 2 and args.method == "paper" and args.solver == "fgmres" and args.cslp == 0.0:
+        rows = []
+        for G in (12, 11, 10):
+            sargs = argparse.Namespace(**vars(args))
+            sargs.ppw = G
+            wlg = workload(sargs)
+            qg = torch.from_numpy(wlg["q"]).to(dev)
+            for beta in ((0.0,) if G == 12 else (0.0, 0.03)):
+                if G == args.ppw and beta == 0.0:
+                    ms, its, conv = main_ms, main_its, True
+                else:
+                    sg = make_solver(wlg, sargs, dev, cslp=beta)
+                    ms, st, _ = timed_solves(sg, qg, sargs, reps=2)
+                    sg.close()
+                    its, conv = st["iterations"], st["converged"]
+                rows.append({"ppw": G, "cslp_beta": beta, "alpha3": wlg["alpha3"], "iterations": its,
+                             "converged": conv, "ms_per_solve": ms, "value": nodes / 1e3 / ms})
+                log(f"ppw {G} cslp {beta}: {its} its, {ms:.2f} ms")
+        out["ppw"] = {"rows": rows, "points_per_direction": wl["n"][0] + 1,
+                      "table1_numerical_n_crit_cubic": TABLE1_NCRIT_CUBIC,
+                      "note": "RS-CGC, and RS-CGC + CSLP (complex shift 0.03 k^2 in the cycle, Sec. 5), on the "
+                              "run's workload at G points per wavelength at the slowest velocity; maxit "
+                              f"{args.maxit}. Table 1 gives the grid size (points per direction) up to which "
+                              "the paper saw G-independent convergence"}
+        sizes = []
+        for n_int in (512, 1024):
+            if n_int >= args.n:
+                continue
+            sargs = argparse.Namespace(**vars(args))
+            sargs.n = n_int
+            wln = workload(sargs)
+            sn = make_solver(wln, sargs, dev)
+            ms, st, _ = timed_solves(sn, torch.from_numpy(wln["q"]).to(dev), sargs, reps=3)
+            sn.close()
+            sizes.append({"cells": wln["n"][0], "points_per_direction": wln["n"][0] + 1, "iterations": st["iterations"],
+                          "ms_per_solve": ms, "value": n_nodes(wln) / 1e3 / ms})
+            log(f"size {wln['n'][0]}: {st['iterations']} its, {ms:.2f} ms")
+        sizes.append({"cells": wl["n"][0], "points_per_direction": wl["n"][0] + 1, "iterations": main_its,
+                      "ms_per_solve": main_ms, "value": nodes / 1e3 / main_ms})
+        out["size_sweep"] = {"rows": sizes, "ppw": args.ppw,
+                             "note": "the run's method and medium recipe at growing interior size (+ the same layer)"}
+    return out
+
+
 def our_arm(args):
     import numpy as np
     import torch
@@ -483,6 +598,10 @@ def our_arm(args):
     if args.autotune:
         tuned = s.autotune_block(q)
         log(f"autotuned block: {tuned[0]} (ms per rhs and iteration: {tuned[1]})")
+    tuned_cycle = None
+    if args.dim == 2 and args.precision == "mixed" and args.cycle == "V" and not args.no_autotune_cycle:
+        tuned_cycle = s.autotune_cycle(max(1, args.block or args.sources))
+        log(f"autotuned fine-pass kernels: {tuned_cycle[0]} (ms per down + up pair: {tuned_cycle[1]})")
     for _ in range(args.warmup):
         p, stats = s.solve(q, p, tol=args.tol, maxit=args.maxit)
     its = stats[0]["iterations"] if stats else None
@@ -554,8 +673,6 @@ def our_arm(args):
                     "algorithmic_bytes_per_launch": model[dom]["bytes"], "launches_timed": cnt,
                     "peak_note": "FP64 ALU peak: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz"}
 
-    if roof is not None and dom == "coarse" and default_workload(args):
-        roof["traffic"] = SWEEP_TRAFFIC_DEFAULT
     # cycle kernels (fine, level-2, transfers) against the HBM roofline, per cycle
     cyc = None
     if args.dim == 2 and info.get("double_float") and all(prof.get(k, (0, 0))[1] for k in ("fine", "stencil", "transfer")):
@@ -565,6 +682,11 @@ def our_arm(args):
         peak = hbm_peak_gbs()
         cyc = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                "algorithmic_bytes_per_cycle": model["cycle"]["bytes"], "ms_per_cycle": t_cyc * 1e3}
+
+    # ---- side measurements (after the timed region, own contexts)
+    extras = {}
+    if world == 1 and args.dim == 2 and nsrc == 1 and not args.no_extras:
+        extras = side_measurements(args, wl, p, t_max / args.steps * 1e3, its, dev, log)
 
     # ---- CPU oracle on a bounded sample
     cpu = None
@@ -576,7 +698,7 @@ def our_arm(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "dtype": MIXED_DTYPE if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": describe(args, wl),
         "iterations": its if nsrc == 1 else [x["iterations"] for x in all_stats[-nsrc:]],
         "converged": converged, "relres": max(x["relres"] for x in all_stats),
@@ -588,9 +710,12 @@ def our_arm(args):
         "cycle_roofline": cyc,
         "graphs": s.info()["graphs"] if args.graphs else None,
         "autotuned_block": tuned[0] if tuned else None,
+        "cycle_kernels": ({"chosen": tuned_cycle[0], "ms_per_fine_pass_pair": tuned_cycle[1]} if tuned_cycle
+                          else None),
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
+    line.update(extras)
     if rank == 0:
         print(json.dumps(line), flush=True)
     s.close()
@@ -710,7 +835,7 @@ def uneven_arm(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_conc / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": MIXED_DTYPE, "data": "synthetic",
         "config": {"workload": (f"uneven batch of {len(sizes)} 2D layered/faulted media (seeded), interior "
                                 f"cells {sizes} + {args.pad}-cell layer, {sum(nodes)} nodes in all, "
                                 f"{args.ppw} points per wavelength, centre point source each"),
@@ -852,7 +977,7 @@ def adjoint_arm(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "dtype": MIXED_DTYPE if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": (f"differentiation: {describe(args, wl)['workload']}; {nsrc} seeded surface sources as one "
                                 f"block, receivers on the top interior row, data from a 2%-perturbed medium"),
                    "method": describe(args, wl)["method"] + "; adjoint solves on the conjugated receiver residuals "

@@ -113,6 +113,17 @@ typedef struct {
                              time); a smaller count leaves the rest of the GPU to contexts
                              solving at the same time on other streams.  Results do not
                              depend on it. */
+  int coarse_refine;      /* steps of iterative refinement after every coarsest direct solve
+                             (helm_coarse_solve and the cycle): e <- e + A3^-1 (b - A3 e), the
+                             residual formed in FP64 with the assembled level-3 stencil.  The
+                             direct solve eliminates the nested-dissection fronts with row
+                             pivoting inside each front only; separator blocks of the
+                             indefinite real-shifted operator that are close to singular
+                             amplify rounding, so its backward error grows with the grid (on
+                             529^2 coarsest nodes about 3e-9 with FP64 factors and 1e-7 with
+                             double-float factors) although the operator itself is well
+                             conditioned.  One step brings the residual to the level of the
+                             arithmetic.  Each step costs a second solve.  Default 0. */
 } helm_opts;
 
 /* Per-solve statistics, one entry per right-hand side. */
@@ -128,7 +139,7 @@ typedef struct helm_ctx helm_ctx;
 /* Fills *o with defaults: 2D, h = 1, gamma_max = 1, alpha2 = alpha3 = 1,
  * 2nd-order stencil, FW transfers, V(1,1), Jacobi w = (0.8, 0.8), rb_w = 1,
  * FP64, restart 10, max_rhs 1, default stream, fuse_cycle 1, graphs 0,
- * cslp_beta 0, solver FGMRES, coarse_blocks 0.  The caller sets dim, n,
+ * cslp_beta 0, solver FGMRES, coarse_blocks 0, coarse_refine 0.  The caller sets dim, n,
  * omega, abc_width and the shifts. */
 int helm_default_opts(helm_opts* o);
 
@@ -203,10 +214,12 @@ int helm_prolong_add(helm_ctx* c, int level, int dtype, const void* ec, void* xf
  * *radius.  out may be NULL to query r only.  Synchronises the stream. */
 int helm_get_stencil(helm_ctx* c, int level, double* out, int* radius);
 
-/* e = (H_4h^alpha)^-1 b on level 3 by the direct factorisation (c128). */
+/* e = (H_4h^alpha)^-1 b on level 3 by the direct factorisation (c128), followed by
+ * helm_opts.coarse_refine steps of iterative refinement. */
 int helm_coarse_solve(helm_ctx* c, const void* b, void* e, int n_rhs);
 
-/* e = (H_4h^alpha)^-1 b like helm_coarse_solve, but the call allocates nothing.
+/* e = (H_4h^alpha)^-1 b like helm_coarse_solve (without the refinement steps of
+ * helm_opts.coarse_refine), but the call allocates nothing.
  * The paper has no counterpart: this entry point exists for callers that cannot
  * call cudaMalloc, such as a host framework that reserves all device memory
  * up front and forbids further allocations, or a latency-sensitive loop that
@@ -218,12 +231,30 @@ int helm_coarse_solve(helm_ctx* c, const void* b, void* e, int n_rhs);
  * vectors of all nested-dissection fronts, two vectors over the coarsest nodes
  * and the solve's partial sums, plus completion counters (two per front, one per
  * output split across jobs); larger requests return HELM_EINVAL and do nothing.  The first call on a device looks up the array's
- * device address with that device current; later calls reuse it.  All calls
+ * device address with that device current; later calls reuse it.  The device the
+ * context was set up on must be current: a call made with another device current
+ * returns HELM_EINVAL and does nothing.  All calls
  * share the array: calls that may overlap on the GPU (two streams, two
  * contexts, two threads) race and corrupt each other's results, so serialise
  * them.  Nothing in the array needs to start at zero: every entry a call reads
  * is written earlier in the same call.  b, e: c128 device pointers. */
 int helm_coarse_solve_noalloc(helm_ctx* c, const void* b, void* e, int n_rhs);
+
+/* Failure detection of the coarsest solve (test support; the paper has no counterpart).
+ * Every wait of the coarsest-solve kernel is bounded: a job that waits longer than a
+ * limit (SM clock cycles, default 4e9, about 2 s at the maximum clock) for a front it
+ * depends on records an error, the kernel's blocks skip their remaining arithmetic and
+ * return, and the call reports HELM_ECUDA with "did not complete in time" in
+ * helm_last_error.  The error stays recorded in the context: every later call that runs
+ * the coarsest solve reports it again (set up a new context to continue).  The GPU and
+ * the CUDA context stay usable.
+ * helm_coarse_wait_check exercises that path without a fault: it sets the context's
+ * dependency-wait limit to wait_cycles (>= 1) and makes job `job` of the solve's job list
+ * (-1: the last job that has a dependency) wait for a completion count no solve reaches,
+ * so that the context's next coarsest solve runs out of time after wait_cycles.  The
+ * context is only fit for that check afterwards.  HELM_EINVAL for a bad limit or job.
+ * Synchronises the stream. */
+int helm_coarse_wait_check(helm_ctx* c, long long wait_cycles, int job);
 
 /* Plan of the coarsest-level direct solve, computed on the host only (no GPU and no
  * context needed), as helm_setup builds it for a level-3 grid of n_nodes[0..dim-1]
@@ -259,7 +290,8 @@ typedef enum {
   HELM_INFO_COARSE_LEVELS = 7,       /* levels of the nested-dissection tree */
   HELM_INFO_COARSE_BWD_ENTRIES = 8,  /* complex entries the backward sweep reads per solve */
   HELM_INFO_DOUBLE_FLOAT = 9,        /* 1 if the coarsest factors and Krylov basis are double-float */
-  HELM_INFO_GRAPHS = 10              /* CUDA graphs instantiated (helm_opts.graphs); -1 after a failed capture */
+  HELM_INFO_GRAPHS = 10,             /* CUDA graphs instantiated (helm_opts.graphs); -1 after a failed capture */
+  HELM_INFO_CYCLE_KERNELS = 11       /* kernels of the fused cycle's fine passes (helm_set_cycle_kernels) */
 } helm_info_key;
 
 /* *value = the quantity selected by key. */
@@ -280,6 +312,21 @@ int helm_info(const helm_ctx* c, int key, long long* value);
 int helm_set_block(helm_ctx* c, int block);
 int helm_autotune_block(helm_ctx* c, const void* q, int n_rhs, int probe_iters, int* best,
                         double* ms_per_rhs_iter);
+
+/* Kernels of the two fine passes of the fused 2D cycle (helm_opts.fuse_cycle; the mixed-
+ * precision V(1,1) Jacobi cycle): 0 = shared-memory tiles (16 x 16 level-2 nodes down,
+ * 32 x 16 fine nodes up); 1, 2, 3 = one warp per vertical strip of 58-60 fine columns
+ * walking segments of 8, 16 or 32 coarse rows with a register window of three fine rows
+ * (default 2).  Every kind computes the same operators and sums in the same order.
+ *
+ * helm_set_cycle_kernels: use kernel kind `kind`.
+ *
+ * helm_autotune_cycle: time the two fine passes of every kind on n_rhs right-hand sides
+ * (the context's workspaces, zero inputs), keep the fastest, return it in *best and the
+ * times (ms per down + up pair, optional caller-owned host array of 4 entries) in ms.
+ * HELM_EINVAL if the context's cycle has no fused passes.  Synchronises the stream. */
+int helm_set_cycle_kernels(helm_ctx* c, int kind);
+int helm_autotune_cycle(helm_ctx* c, int n_rhs, int* best, double* ms);
 
 /* ---- Launch timer (tracing) ---- */
 

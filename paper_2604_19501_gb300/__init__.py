@@ -43,7 +43,7 @@ class Solver:
                  alpha3=1.0, stencil="2nd", intergrid="fw", cycle="V", nu=(1, 1),
                  smoother="jacobi", jacobi_w=(0.8, 0.8), rb_w=1.0, precision="fp64", restart=10,
                  max_rhs=1, stream=None, fuse_cycle=True, graphs=False, cslp_beta=0.0,
-                 solver="fgmres", coarse_blocks=0):
+                 solver="fgmres", coarse_blocks=0, coarse_refine=0):
         self.n = tuple(int(v) for v in n)
         self.dim = len(self.n)
         o = HelmOpts()
@@ -73,6 +73,7 @@ class Solver:
         o.cslp_beta = float(cslp_beta)
         o.solver = _ffi.SOLVER[solver]
         o.coarse_blocks = int(coarse_blocks)
+        o.coarse_refine = int(coarse_refine)
         if stream is None:
             import torch
 
@@ -227,6 +228,18 @@ class Solver:
             b *= 2
         cands.append(cap)
         return best.value, {c: costs[i] for i, c in enumerate(cands[:7])}
+
+    def set_cycle_kernels(self, kind):
+        """Kernels of the fused cycle's fine passes: "tiles", "rows8", "rows16" or "rows32"."""
+        check(_lib.helm_set_cycle_kernels(self._ctx, _ffi.CYCLE_KERNELS.index(kind)), "helm_set_cycle_kernels")
+
+    def autotune_cycle(self, n_rhs=1):
+        """Time the fused cycle's fine passes with every kernel kind and keep the fastest.
+        Returns (kind, {kind: ms per down + up pair})."""
+        best = ctypes.c_int(0)
+        ms = (ctypes.c_double * 4)()
+        check(_lib.helm_autotune_cycle(self._ctx, int(n_rhs), ctypes.byref(best), ms), "helm_autotune_cycle")
+        return _ffi.CYCLE_KERNELS[best.value], {k: ms[i] for i, k in enumerate(_ffi.CYCLE_KERNELS)}
 
     def coarse_solve(self, b, e=None):
         e = _empty_like(b) if e is None else e

@@ -14,7 +14,8 @@ PRECISION = {"fp64": 0, "mixed": 1}
 DTYPE = {"c128": 0, "c64": 1}
 SOLVER = {"fgmres": 0, "cycle": 1}
 INFO_KEYS = ["nodes1", "nodes2", "nodes3", "radius2", "radius3", "coarse_entries", "coarse_fronts",
-             "coarse_levels", "coarse_bwd_entries", "double_float", "graphs"]
+             "coarse_levels", "coarse_bwd_entries", "double_float", "graphs", "cycle_kernels"]
+CYCLE_KERNELS = ["tiles", "rows8", "rows16", "rows32"]
 KERNEL_CLASSES = ["fine", "stencil", "transfer", "coarse", "arnoldi_matvec", "arnoldi_update",
                   "arnoldi_norm", "krylov_other", "setup"]
 
@@ -46,6 +47,7 @@ class HelmOpts(ctypes.Structure):
         ("cslp_beta", ctypes.c_double),
         ("solver", ctypes.c_int),
         ("coarse_blocks", ctypes.c_int),
+        ("coarse_refine", ctypes.c_int),
     ]
 
 
@@ -77,9 +79,12 @@ SIGNATURES = {
     "helm_get_stencil": (_I, [_P, _I, _P, ctypes.POINTER(_I)]),
     "helm_coarse_solve": (_I, [_P, _P, _P, _I]),
     "helm_coarse_solve_noalloc": (_I, [_P, _P, _P, _I]),
+    "helm_coarse_wait_check": (_I, [_P, ctypes.c_longlong, _I]),
     "helm_cycle": (_I, [_P, _P, _P, _I]),
     "helm_set_block": (_I, [_P, _I]),
     "helm_autotune_block": (_I, [_P, _P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "helm_set_cycle_kernels": (_I, [_P, _I]),
+    "helm_autotune_cycle": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "helm_coarse_plan": (_I, [_I, ctypes.POINTER(_I), _I, _I, _I, _I, ctypes.POINTER(ctypes.c_longlong)]),
     "helm_launch_count": (ctypes.c_longlong, [_P]),
     "helm_info": (_I, [_P, _I, ctypes.POINTER(ctypes.c_longlong)]),

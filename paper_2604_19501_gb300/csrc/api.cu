@@ -59,6 +59,7 @@ struct helm_ctx {
   void *l1a = nullptr, *l1b = nullptr, *l1r = nullptr;
   void *l2b = nullptr, *l2a = nullptr, *l2c = nullptr, *l2r = nullptr;
   double2 *l3b = nullptr, *l3e = nullptr;
+  double2 *l3r = nullptr, *l3d = nullptr;      // coarsest-solve refinement: residual and correction
   // Krylov workspaces (one right-hand side at a time)
   double2 *V = nullptr, *w = nullptr, *r = nullptr;
   void* Z = nullptr;
@@ -86,6 +87,7 @@ struct helm_ctx {
   long long launches = 0;
   int* d_bad = nullptr;
   LaunchTimer timer;
+  int fine_kind = HELM_FINE_ROWS16;            // kernels of the fused fine passes (FineKind)
   float4* cdf = nullptr;                       // mixed precision: fine coefficients as double-float
   float4* xd = nullptr;                        // mixed precision: the solution as double-float [B][n]
 };
@@ -157,8 +159,10 @@ void free_workspaces(helm_ctx* c) {
   for (void* p : {c->l1a, c->l1b, c->l1r, c->l2b, c->l2a, c->l2c, c->l2r}) cudaFree(p);
   cudaFree(c->l3b);
   cudaFree(c->l3e);
+  cudaFree(c->l3r);
+  cudaFree(c->l3d);
   c->l1a = c->l1b = c->l1r = c->l2b = c->l2a = c->l2c = c->l2r = nullptr;
-  c->l3b = c->l3e = nullptr;
+  c->l3b = c->l3e = c->l3r = c->l3d = nullptr;
   c->rhs_cap = 0;
 }
 
@@ -176,6 +180,10 @@ int ensure_workspaces(helm_ctx* c, int nrhs) {
   if (int st = dmalloc(&c->l2r, n2 * e)) return st;
   if (int st = dmalloc(&c->l3b, n3 * e)) return st;
   if (int st = dmalloc(&c->l3e, n3 * e)) return st;
+  if (c->o.coarse_refine > 0) {
+    if (int st = dmalloc(&c->l3r, n3 * e)) return st;
+    if (int st = dmalloc(&c->l3d, n3 * e)) return st;
+  }
   c->rhs_cap = nrhs;
   return 0;
 }
@@ -221,6 +229,20 @@ int smooth(helm_ctx* c, int level, Prec P, const void* b, Prec bs, void** x, voi
   return 0;
 }
 
+// The coarsest solve of the cycle and of helm_coarse_solve: the direct factorisation, then
+// o.coarse_refine steps of iterative refinement e <- e + A3^-1 (b - A3 e) with the
+// residual formed in FP64 from the assembled level-3 stencil.  The workspaces must hold
+// nrhs right-hand sides (ensure_workspaces) and must not be b or e.
+int coarse_apply(helm_ctx* c, const double2* b, double2* e, int nrhs) {
+  if (int st = coarse_solve(c->cs, b, e, nrhs, c->s)) return st;
+  for (int k = 0; k < c->o.coarse_refine; ++k) {
+    if (int st = row_op(c, 2, P64, MODE_RESID, P64, P64, P64, e, b, c->l3r, nrhs, 0.0, 0)) return st;
+    if (int st = coarse_solve(c->cs, c->l3r, c->l3d, nrhs, c->s)) return st;
+    if (int st = launch_add_c128(c->l3d, e, c->g[2].size * nrhs, c->s)) return st;
+  }
+  return 0;
+}
+
 // One visit of level 2 (index 1): smoothing, residual, restriction, exact coarsest solve,
 // prolongation and correction, smoothing.  x2 in/out through *x.
 int visit_level2(helm_ctx* c, Prec P, void** x, void** t, bool first, int nrhs) {
@@ -229,14 +251,14 @@ int visit_level2(helm_ctx* c, Prec P, void** x, void** t, bool first, int nrhs) 
   const long long n3 = c->g[2].size * nrhs;
   if (P == P64) {
     if (int st = launch_restrict(c->g[1], c->g[2], c->tR2, P64, c->l2r, c->l3b, nrhs, c->s)) return st;
-    if (int st = coarse_solve(c->cs, c->l3b, c->l3e, nrhs, c->s)) return st;
+    if (int st = coarse_apply(c, c->l3b, c->l3e, nrhs)) return st;
     if (int st = launch_prolong_add(c->g[1], c->g[2], c->tP2, P64, c->l3e, *x, nrhs, c->s)) return st;
   } else {
     // restrict in c64 into the upper half of l3e, widen to c128, solve, narrow back
     float2* b32 = (float2*)c->l3e;
     if (int st = launch_restrict(c->g[1], c->g[2], c->tR2, P32, c->l2r, b32, nrhs, c->s)) return st;
     if (int st = launch_convert(P32, P64, b32, c->l3b, n3, c->s)) return st;
-    if (int st = coarse_solve(c->cs, c->l3b, c->l3e, nrhs, c->s)) return st;
+    if (int st = coarse_apply(c, c->l3b, c->l3e, nrhs)) return st;
     float2* e32 = (float2*)c->l3b;
     if (int st = launch_convert(P64, P32, c->l3e, e32, n3, c->s)) return st;
     if (int st = launch_prolong_add(c->g[1], c->g[2], c->tP2, P32, e32, *x, nrhs, c->s)) return st;
@@ -253,7 +275,7 @@ bool fused_cycle(const helm_ctx* c, Prec vs, Prec zs) {
          (c->r2 == 1 || c->r2 == 2);
 }
 
-int run_cycle_fused(helm_ctx* c, const void* v, void* z, int nrhs) {
+Cycle2D make_cycle2d(const helm_ctx* c) {
   Cycle2D cy;
   cy.fine = c->fine_cyc;
   cy.kap = c->kap32;
@@ -267,6 +289,12 @@ int run_cycle_fused(helm_ctx* c, const void* v, void* z, int nrhs) {
   cy.pw2 = c->tP2.radius;
   cy.w1 = (float)c->o.jacobi_w[0];
   cy.w2 = (float)c->o.jacobi_w[1];
+  cy.fine_kind = c->fine_kind;
+  return cy;
+}
+
+int run_cycle_fused(helm_ctx* c, const void* v, void* z, int nrhs) {
+  const Cycle2D cy = make_cycle2d(c);
   const float4* vd = static_cast<const float4*>(v);
   float2* r2 = static_cast<float2*>(c->l2b);
   float2* s2 = static_cast<float2*>(c->l2r);
@@ -274,7 +302,7 @@ int run_cycle_fused(helm_ctx* c, const void* v, void* z, int nrhs) {
   if (int st = cycle2d_fine_down(cy, vd, r2, nrhs, c->s)) return st;
   if (int st = cycle2d_l2_resid(cy, r2, s2, nrhs, c->s)) return st;
   if (int st = cycle2d_l2_restrict(cy, s2, c->l3b, nrhs, c->s)) return st;
-  if (int st = coarse_solve(c->cs, c->l3b, c->l3e, nrhs, c->s)) return st;
+  if (int st = coarse_apply(c, c->l3b, c->l3e, nrhs)) return st;
   if (int st = cycle2d_l2_up(cy, r2, c->l3e, y2, nrhs, c->s)) return st;
   return cycle2d_fine_up(cy, vd, y2, static_cast<float2*>(z), nrhs, c->s);
 }
@@ -675,6 +703,7 @@ int helm_default_opts(helm_opts* o) {
   o->cslp_beta = 0.0;
   o->solver = HELM_SOLVER_FGMRES;
   o->coarse_blocks = 0;
+  o->coarse_refine = 0;
   return HELM_OK;
 }
 
@@ -693,6 +722,7 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
     return fail(HELM_EINVAL, "non-finite shift or layer amplitude");
   if (o->solver != HELM_SOLVER_FGMRES && o->solver != HELM_SOLVER_CYCLE) return fail(HELM_EINVAL, "bad solver");
   if (o->coarse_blocks < 0) return fail(HELM_EINVAL, "coarse_blocks must be >= 0");
+  if (o->coarse_refine < 0 || o->coarse_refine > 8) return fail(HELM_EINVAL, "coarse_refine must be in [0, 8]");
   if (o->stencil != HELM_STENCIL_2ND && o->stencil != HELM_STENCIL_4TH) return fail(HELM_EINVAL, "bad stencil");
   if (o->intergrid < HELM_INTERGRID_FW || o->intergrid > HELM_INTERGRID_LEVDEP)
     return fail(HELM_EINVAL, "bad intergrid transfer");
@@ -1040,7 +1070,9 @@ int helm_get_stencil(helm_ctx* c, int level, double* out, int* radius) {
 int helm_coarse_solve(helm_ctx* c, const void* b, void* e, int n_rhs) {
   if (!c || !b || !e || n_rhs < 1) return fail(HELM_EINVAL, "bad argument");
   LaunchScope scope(c);
-  if (int st = coarse_solve(c->cs, (const double2*)b, (double2*)e, n_rhs, c->s)) return st;
+  if (c->o.coarse_refine > 0)
+    if (int st = ensure_workspaces(c, n_rhs)) return st;
+  if (int st = coarse_apply(c, (const double2*)b, (double2*)e, n_rhs)) return st;
   if (int st = coarse_status(c->cs, c->s)) return st;
   return HELM_OK;
 }
@@ -1051,6 +1083,11 @@ int helm_coarse_solve_noalloc(helm_ctx* c, const void* b, void* e, int n_rhs) {
   if (int st = coarse_solve_noalloc(c->cs, (const double2*)b, (double2*)e, n_rhs, c->s)) return st;
   if (int st = coarse_status(c->cs, c->s)) return st;
   return HELM_OK;
+}
+
+int helm_coarse_wait_check(helm_ctx* c, long long wait_cycles, int job) {
+  if (!c) return fail(HELM_EINVAL, "null context");
+  return coarse_plant_unreachable_wait(c->cs, wait_cycles, job, c->s);
 }
 
 int helm_cycle(helm_ctx* c, const void* v, void* z, int n_rhs) {
@@ -1159,6 +1196,62 @@ int helm_autotune_block(helm_ctx* c, const void* q, int n_rhs, int probe_iters, 
   return HELM_OK;
 }
 
+int helm_set_cycle_kernels(helm_ctx* c, int kind) {
+  if (!c) return fail(HELM_EINVAL, "null context");
+  if (kind < HELM_FINE_TILES || kind > HELM_FINE_ROWS32) return fail(HELM_EINVAL, "unknown fine-pass kernel kind");
+  c->fine_kind = kind;
+  return HELM_OK;
+}
+
+int helm_autotune_cycle(helm_ctx* c, int n_rhs, int* best, double* ms) {
+  if (!c || !best) return fail(HELM_EINVAL, "null argument");
+  if (n_rhs < 1) return fail(HELM_EINVAL, "n_rhs must be >= 1");
+  if (!fused_cycle(c, P_DF, P32)) return fail(HELM_EINVAL, "the context's cycle has no fused fine passes");
+  LaunchScope scope(c);
+  if (int st = ensure_workspaces(c, n_rhs)) return st;
+  const long long n1 = c->g[0].size * n_rhs, n2 = c->g[1].size * n_rhs;
+  // inputs: v = 0 (double-float) and y2 = 0; the passes' cost does not depend on the values
+  HELM_CUDA_TRY(cudaMemsetAsync(c->l1r, 0, n1 * sizeof(float4), c->s));
+  HELM_CUDA_TRY(cudaMemsetAsync(c->l2a, 0, n2 * sizeof(float2), c->s));
+  Cycle2D cy = make_cycle2d(c);
+  cudaEvent_t e0, e1;
+  HELM_CUDA_TRY(cudaEventCreate(&e0));
+  HELM_CUDA_TRY(cudaEventCreate(&e1));
+  const float4* v = static_cast<const float4*>(c->l1r);
+  int status = HELM_OK;
+  double best_ms = 0.0;
+  int best_k = c->fine_kind;
+  for (int k = HELM_FINE_TILES; k <= HELM_FINE_ROWS32 && status == HELM_OK; ++k) {
+    cy.fine_kind = k;
+    constexpr int kReps = 5;
+    for (int rep = -1; rep < kReps && status == HELM_OK; ++rep) {   // one untimed pass first
+      if (rep == 0) cudaEventRecord(e0, c->s);
+      status = cycle2d_fine_down(cy, v, static_cast<float2*>(c->l2b), n_rhs, c->s);
+      if (status == HELM_OK)
+        status = cycle2d_fine_up(cy, v, static_cast<const float2*>(c->l2a), static_cast<float2*>(c->l1a), n_rhs, c->s);
+    }
+    if (status != HELM_OK) break;
+    cudaEventRecord(e1, c->s);
+    float t = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+      status = fail(HELM_ECUDA, "autotune timing failed");
+      break;
+    }
+    const double per = t / kReps;
+    if (ms) ms[k] = per;
+    if (k == HELM_FINE_TILES || per < best_ms) {
+      best_ms = per;
+      best_k = k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status != HELM_OK) return status;
+  c->fine_kind = best_k;
+  *best = best_k;
+  return HELM_OK;
+}
+
 int helm_info(const helm_ctx* c, int key, long long* value) {
   if (!c || !value) return fail(HELM_EINVAL, "null argument");
   switch (key) {
@@ -1173,6 +1266,7 @@ int helm_info(const helm_ctx* c, int key, long long* value) {
     case HELM_INFO_COARSE_BWD_ENTRIES: *value = c->cs.bwd_entries; break;
     case HELM_INFO_DOUBLE_FLOAT: *value = c->cs.df ? 1 : 0; break;
     case HELM_INFO_GRAPHS: *value = c->graphs_broken ? -1 : (long long)c->graphs.size(); break;
+    case HELM_INFO_CYCLE_KERNELS: *value = c->fine_kind; break;
     default: return fail(HELM_EINVAL, "unknown info key");
   }
   return HELM_OK;

@@ -715,6 +715,7 @@ int coarse_plan_stats(const GridDims& g, int r, int leaf_max, bool symmetric, in
 
 int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef, int leaf_max,
                  bool symmetric, bool df, cudaStream_t s, int blocks) {
+  HELM_CUDA_TRY(cudaGetDevice(&cs.device));
   int grid = 0, grid_group = 0;
   if (int st = sweep_grid_size(&grid, &grid_group)) return st;
   CoarsePlan P;
@@ -826,6 +827,32 @@ int coarse_solve(CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaS
   return sweep_launch(cs, b, e, nrhs, cs.d_uv, cs.d_w, cs.d_part, cs.d_counters, cs.d_xd, s);
 }
 
+int coarse_plant_unreachable_wait(CoarseSolver& cs, long long wait_cycles, int job, cudaStream_t s) {
+  if (wait_cycles < 1) {
+    set_error("wait limit must be at least one cycle");
+    return HELM_EINVAL;
+  }
+  if (job < -1 || job >= cs.njobs) {
+    set_error("job index out of range");
+    return HELM_EINVAL;
+  }
+  HELM_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<SweepMeta> meta(cs.njobs);
+  HELM_CUDA_TRY(cudaMemcpy(meta.data(), cs.d_meta, cs.njobs * sizeof(SweepMeta), cudaMemcpyDeviceToHost));
+  if (job == -1)
+    for (int j = cs.njobs - 1; j >= 0 && job < 0; --j)
+      if (meta[j].nwait > 0) job = j;
+  if (job < 0 || meta[job].nwait < 1) {
+    set_error("the chosen job has no dependency to wait for");
+    return HELM_EINVAL;
+  }
+  // a completion count no solve reaches: each counter counts output units of one front
+  meta[job].target[0] = 0x40000000;
+  HELM_CUDA_TRY(cudaMemcpy(cs.d_meta + job, &meta[job], sizeof(SweepMeta), cudaMemcpyHostToDevice));
+  cs.wait_cycles = wait_cycles;
+  return 0;
+}
+
 int coarse_status(const CoarseSolver& cs, cudaStream_t s) {
   if (!cs.d_err) return 0;
   HELM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -859,8 +886,15 @@ int coarse_solve_noalloc(const CoarseSolver& cs, const double2* b, double2* e, i
               " complex scratch entries; the static array holds " + std::to_string(kNoAllocScratchEntries));
     return HELM_EINVAL;
   }
+  // the array's address is per device: look it up on the context's device, and refuse a
+  // call made with another device current (its stream and buffers live on the context's)
   int dev = 0;
   HELM_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != cs.device) {
+    set_error("allocation-free coarsest solve: device " + std::to_string(dev) + " is current, the context was set up on " +
+              std::to_string(cs.device));
+    return HELM_EINVAL;
+  }
   if (dev < 0 || dev >= kMaxDevices) {
     set_error("device ordinal out of range for the allocation-free scratch table");
     return HELM_EINVAL;

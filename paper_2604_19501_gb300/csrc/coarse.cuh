@@ -19,6 +19,9 @@ constexpr int kTile = 128;           // output columns of one job (one thread ea
 constexpr int kPartBlock = 128;      // partial-sum entries per chunk and right-hand side
 constexpr int kRhsGroup = 4;         // right-hand sides sharing each staged factor entry
 
+// Default limit on a wait of the solve kernel, in SM clock cycles (about 2 s at 2 GHz).
+constexpr long long kDefaultWaitCycles = 4000000000LL;
+
 // Error codes the solve kernel leaves in CoarseSolver::d_err.
 constexpr int kErrPivot = 1;       // factorisation: zero or non-finite pivot
 constexpr int kErrSweepWait = 2;   // solve: a dependency did not complete in time
@@ -107,6 +110,8 @@ struct CoarseSolver {
   int max_nB = 0;                     // largest boundary of a front
   int* d_err = nullptr;
   long long* launches = nullptr;
+  int device = -1;                    // device current at set-up (the device of every buffer above)
+  long long wait_cycles = kDefaultWaitCycles;   // limit on a dependency wait of the solve kernel
 };
 
 // Symbolic analysis and numeric factorisation of the coarsest operator given by its
@@ -127,6 +132,11 @@ int coarse_solve_noalloc(const CoarseSolver& cs, const double2* b, double2* e, i
 // Host only: the plan coarse_setup builds (tree, fronts, solve jobs for `grid` resident
 // blocks), checked; stats as documented for helm_coarse_plan.
 int coarse_plan_stats(const GridDims& g, int r, int leaf_max, bool symmetric, int grid, long long stats[8]);
+
+// Failure-detection check: sets the dependency-wait limit and, for job >= 0 (-1: the last
+// job with a dependency), raises that job's first completion target beyond anything the
+// solve can reach, so that the next solve's wait runs out and reports kErrSweepWait.
+int coarse_plant_unreachable_wait(CoarseSolver& cs, long long wait_cycles, int job, cudaStream_t s);
 
 // Waits for the stream and reports an error a solve kernel left in d_err.
 int coarse_status(const CoarseSolver& cs, cudaStream_t s);

@@ -37,9 +37,11 @@ namespace helm {
 namespace {
 
 constexpr int kSplitMax = 16;                              // forward row parts per column
-// Limit on any wait, in cycles of the waiting multiprocessor's clock (clock64 is
-// monotonic per multiprocessor): about 2 s at the maximum SM clock, longer below it.
-constexpr long long kWaitCycles = 4000000000LL;
+// Limit on a wait for a factor copy, in cycles of the waiting multiprocessor's clock
+// (clock64 is monotonic per multiprocessor): about 2 s at the maximum SM clock, longer
+// below it.  Dependency waits take their limit from the launch (CoarseSolver::wait_cycles,
+// the same by default).
+constexpr long long kWaitCycles = kDefaultWaitCycles;
 constexpr int kStageBytes = kStageEntries * 16;
 // Resident blocks per multiprocessor the kernel is shaped for: enough jobs in flight that
 // one job's fixed latencies (dependency wait, gathers, write-back) overlap the others'
@@ -91,6 +93,7 @@ struct SweepArgs {
   int nrhs;
   long long nodes;
   long long uv_total;
+  long long wait_cycles;   // limit on a dependency wait (SM clock cycles)
 };
 
 // ---- element operations on 16-byte complex values: double2 (FP64) or float4 (double-float)
@@ -125,7 +128,7 @@ __device__ __forceinline__ double2 ldcg(const double2* p) { return __ldcg(p); }
 __device__ __forceinline__ float4 ldcg(const float4* p) { return __ldcg(p); }
 
 // ---- synchronisation primitives
-__device__ __forceinline__ bool expired(long long t0) { return clock64() - t0 > kWaitCycles; }
+__device__ __forceinline__ bool expired(long long t0, long long limit = kWaitCycles) { return clock64() - t0 > limit; }
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -149,16 +152,16 @@ __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p) {
   return old;
 }
 
-// *p >= target within the time limit; false on a timeout (recorded) or when another
+// *p >= target within `limit` cycles; false on a timeout (recorded) or when another
 // block has already recorded an error.
-__device__ bool wait_count(const unsigned* p, unsigned target, int* err) {
+__device__ bool wait_count(const unsigned* p, unsigned target, int* err, long long limit) {
   if (ld_acquire(p) >= target) return true;
   const long long t0 = clock64();
   while (true) {
     __nanosleep(64);
     if (ld_acquire(p) >= target) return true;
     if (ld_relaxed(err)) return false;
-    if (expired(t0)) {
+    if (expired(t0, limit)) {
       atomicCAS(err, 0, kErrSweepWait);
       return false;
     }
@@ -434,7 +437,7 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
       if (good && m.nwait > 0) {
         good = !ld_relaxed(a.err);
         for (int q = 0; q < m.nwait && good; ++q)
-          good = wait_count(a.counters + m.wait[q], (unsigned)m.target[q], a.err);
+          good = wait_count(a.counters + m.wait[q], (unsigned)m.target[q], a.err, a.wait_cycles);
       }
       *flag = good;
     }
@@ -687,6 +690,7 @@ int sweep_launch(const CoarseSolver& cs, const double2* b, double2* e, int nrhs,
   a.nrhs = nrhs;
   a.nodes = cs.g.size;
   a.uv_total = cs.uv_total;
+  a.wait_cycles = cs.wait_cycles;
   cudaError_t le;
   if (nrhs == 1) le = cs.df ? launch_one<true, 1>(a, cs.grid, s) : launch_one<false, 1>(a, cs.grid, s);
   else le = cs.df ? launch_one<true, kRhsGroup>(a, cs.grid_group, s) : launch_one<false, kRhsGroup>(a, cs.grid_group, s);

@@ -10,6 +10,8 @@
 //    fine nodes outside the grid are left out.
 // Values outside the grid are held as zero in the tiles, which reproduces the Dirichlet
 // ghost of the operators and the transfers' omission of outside nodes.
+#include <type_traits>
+
 #include "cycle2d.cuh"
 #include "timer.cuh"
 
@@ -451,14 +453,508 @@ __global__ void __launch_bounds__(kThreads) fine_up_kernel(const Cycle2D c, cons
   }
 }
 
+// ---------------------------------------------------------------- row-streaming fine passes
+// The same two fine passes without shared memory: one warp per (strip, segment) of the
+// fine grid.  Lane l holds coarse column I = I0 + l and the fine columns 2I and 2I + 1;
+// the warp walks down the fine rows with a window of three rows of x1 and c in registers,
+// takes the column neighbours of its two columns from the adjacent lanes (shuffles), and
+// forms the restriction along x by shuffles and along y in a ring of three coarse-row
+// accumulators.  The row loop is unrolled by six so that every ring slot is a compile-time
+// register.  Lanes at the strip edges only supply halo values; neighbouring warps cover
+// the next strip.  Values outside the grid are zero, as in the tile kernels, and the sums
+// are taken in the tile kernels' order (restriction: x first, then y, weights in order).
+constexpr int kRsWarps = 4;   // warps per block
+
+__host__ __device__ constexpr int fdiv(int a, int b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
+__host__ __device__ constexpr int mod3(int a) { return ((a % 3) + 3) % 3; }
+
+__device__ __forceinline__ float2 shup(float2 v) {
+  return make_float2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
+}
+__device__ __forceinline__ float2 shdn(float2 v) {
+  return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
+}
+
+// one fine row of a warp's two columns: x1, c (and the halo columns' from the neighbours)
+struct RsRow {
+  float2 xl, xe, xo, xr;   // x1 at columns 2I - 1, 2I, 2I + 1, 2I + 2
+  float2 cl, ce, co, cr;   // c at the same columns (4th order only)
+  float2 ve, vo;           // v at 2I, 2I + 1
+  float2 de, dn;           // 1 / diagonal at 2I, 2I + 1 (fine up pass)
+};
+// loaded values of one fine row
+struct RsLoad {
+  float4 ve, vo;
+  float ke, ko, gy;
+};
+
+// Staging of the rows a warp streams: every lane copies its own entries (v at its two
+// columns, 2 x 16 B; kappa, 2 x 4 B; the row's gamma_y, 4 B; in the up pass y2 at its
+// coarse column, 8 B) with
+// cp.async into a ring of kRing rows in shared memory, kAhead rows ahead of the row in
+// use, so that each warp keeps about kAhead rows of loads in flight without holding them
+// in registers.  A lane reads back only what it copied itself: its cp.async.wait_group
+// makes the data visible to it.  Entries outside the grid are zero-filled (source size 0,
+// the source address then being the array's base, which is valid).
+constexpr int kRing = 8;                          // fine rows per warp ring
+constexpr int kAhead = 6;                         // rows in flight ahead of the current one
+constexpr int kVRowBytes = 32 * 2 * 16;           // v: two float4 per lane
+constexpr int kKRowBytes = 32 * 4 * 4;            // kappa at the two columns and gamma_y: four floats per lane
+constexpr int kCRing = 8;                         // coarse rows per warp ring (fine up pass)
+constexpr int kCRowBytes = 32 * 8;                // y2: one float2 per lane
+constexpr int kRsDownWarpBytes = kRing * (kVRowBytes + kKRowBytes);
+constexpr int kRsUpWarpBytes = kRsDownWarpBytes + kCRing * kCRowBytes;
+static_assert(kRing >= kAhead + 2, "a ring slot is refilled two steps after its row was read");
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool ok) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+template <int ORDER>
+__device__ __forceinline__ float2 diag_c(float2 cc, float ih2) {
+  if (ORDER == 0) return make_float2(4.f * ih2 - cc.x, -cc.y);
+  return make_float2(float(20.0 / 6.0) * ih2 - float(8.0 / 12.0) * cc.x, -float(8.0 / 12.0) * cc.y);
+}
+
+// (H x1) at the column of `mid` whose left / right neighbours are xl / xr in the three rows
+template <int ORDER>
+__device__ __forceinline__ float2 rs_apply(float2 cm, float2 xm, float2 xlm, float2 xrm, float2 clm, float2 crm,
+                                           float2 xu, float2 cu, float2 xd, float2 cd, float2 xul, float2 xur,
+                                           float2 xdl, float2 xdr, float ih2) {
+  const float2 diag = diag_c<ORDER>(cm, ih2);
+  if (ORDER == 0) {
+    float2 sum = xlm + xrm;
+    sum = sum + xu;
+    sum = sum + xd;
+    return cmul(diag, xm) - cscale(sum, ih2);
+  }
+  const float wface = float(-4.0 / 6.0) * ih2, wedge = float(-1.0 / 6.0) * ih2;
+  auto face = [&](float2 xf, float2 cf) {
+    return make_float2(wface - float(1.0 / 24.0) * (cm.x + cf.x), -float(1.0 / 24.0) * (cm.y + cf.y));
+  };
+  // the tile kernels' order: rows -1, 0, +1, columns -1, 0, +1
+  float2 acc = cmul(diag, xm);
+  acc = acc + cscale(xul, wedge);
+  acc = cmac(acc, face(xu, cu), xu);
+  acc = acc + cscale(xur, wedge);
+  acc = cmac(acc, face(xlm, clm), xlm);
+  acc = cmac(acc, face(xrm, crm), xrm);
+  acc = acc + cscale(xdl, wedge);
+  acc = cmac(acc, face(xd, cd), xd);
+  acc = acc + cscale(xdr, wedge);
+  return acc;
+}
+
+template <int ORDER, int RW, int SEG>
+struct RsDown {
+  static constexpr int LO = RW;            // lanes [LO, 30] own their coarse column
+  static constexpr int CS = 31 - LO;       // coarse columns per strip
+  static constexpr int T = 2 * SEG + RW + 4;   // fine rows a warp visits: 2 J0 - 4 ...
+};
+
+template <int ORDER, int RW, int SEG>
+__global__ void __launch_bounds__(32 * kRsWarps) fine_down_rs_kernel(const Cycle2D c, const float4* __restrict__ v,
+                                                                     float2* __restrict__ r2) {
+  using P = RsDown<ORDER, RW, SEG>;
+  const GridDims& g = c.fine.g;
+  const GridDims& g2 = c.g2;
+  const int N0 = g.N[0], N1 = g.N[1];
+  const int lane = threadIdx.x & 31;
+  const int nstrip = (g2.N[0] + P::CS - 1) / P::CS;
+  const int nseg = (g2.N[1] + SEG - 1) / SEG;
+  const int wid = blockIdx.x * kRsWarps + (threadIdx.x >> 5);
+  if (wid >= nstrip * nseg) return;   // a whole warp
+  const int strip = wid % nstrip, seg = wid / nstrip;
+  const int Ic = strip * P::CS - P::LO + lane;
+  const int J0 = seg * SEG;
+  const int xe = 2 * Ic, xo = xe + 1;
+  const bool ine = xe >= 0 && xe < N0, ino = xo >= 0 && xo < N0;
+  const bool own = lane >= P::LO && lane <= 30 && Ic < g2.N[0];
+  const int Ybase = 2 * J0 - 4;
+  const float4* vb = v + (long long)blockIdx.y * g.size;
+  float2* rb = r2 + (long long)blockIdx.y * g2.size;
+  const float omega2 = (float)c.fine.omega2, ih2 = (float)c.fine.inv_h2, w1 = c.w1;
+  const float gxe = ine ? c.fine.gam32[0][xe] : 0.f, gxo = ino ? c.fine.gam32[0][xo] : 0.f;
+  const float* __restrict__ gyt = c.fine.gam32[1];
+  const float* __restrict__ kap = c.kap;
+  const float* w = c_w[RW - 1];
+
+  extern __shared__ __align__(16) unsigned char rs_smem[];
+  unsigned char* const ring = rs_smem + (threadIdx.x >> 5) * kRsDownWarpBytes;
+  const uint32_t vring = smem_addr(ring) + lane * 32, kring = smem_addr(ring + kRing * kVRowBytes) + lane * 16;
+  RsRow W[3];
+  float2 acc[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) acc[q] = z2();
+
+  // fine row t into ring slot t % kRing (zeros outside the grid)
+  auto issue = [&](int t) {
+    const int y = Ybase + t;
+    const bool iny = y >= 0 && y < N1;
+    const long long row = (long long)(iny ? y : 0) * N0;
+    const int sl = t % kRing;
+    cp_async16(vring + sl * kVRowBytes, iny && ine ? vb + row + xe : vb, iny && ine);
+    cp_async16(vring + sl * kVRowBytes + 16, iny && ino ? vb + row + xo : vb, iny && ino);
+    cp_async4(kring + sl * kKRowBytes, iny && ine ? kap + row + xe : kap, iny && ine);
+    cp_async4(kring + sl * kKRowBytes + 4, iny && ino ? kap + row + xo : kap, iny && ino);
+    cp_async4(kring + sl * kKRowBytes + 8, iny ? gyt + y : gyt, iny);
+  };
+  auto load = [&](int t, RsLoad& ld) {
+    const int sl = t % kRing;
+    const float4* vs = reinterpret_cast<const float4*>(ring + sl * kVRowBytes) + 2 * lane;
+    const float* ks = reinterpret_cast<const float*>(ring + kRing * kVRowBytes + sl * kKRowBytes) + 4 * lane;
+    ld.ve = vs[0];
+    ld.vo = vs[1];
+    ld.ke = ks[0];
+    ld.ko = ks[1];
+    ld.gy = ks[2];
+  };
+  auto node = [&](float4 vv, float kk, float gx, float gy, float2& x, float2& cc, float2& vo) {
+    const float cre = omega2 * kk;
+    cc = make_float2(cre, -cre * (gx + gy));
+    vo = make_float2(vv.x, vv.y);
+    x = cscale(cmul(rcp_c(diag_c<ORDER>(cc, ih2)), vo), w1);
+  };
+  // row t into window slot: own columns, then the neighbours' (zero outside the grid:
+  // v = kappa = 0 there, and x1 = 0 with them; a zero kappa gives a finite diagonal)
+  auto fill = [&](const RsLoad& ld, RsRow& R) {
+    node(ld.ve, ld.ke, gxe, ld.gy, R.xe, R.ce, R.ve);
+    node(ld.vo, ld.ko, gxo, ld.gy, R.xo, R.co, R.vo);
+    R.xl = shup(R.xo);
+    R.xr = shdn(R.xe);
+    if (ORDER == 1) {
+      R.cl = shup(R.co);
+      R.cr = shdn(R.ce);
+    }
+  };
+
+  // fine row t = t0 + S of the warp's visit; S is a compile-time step of the six-fold unroll
+  auto step = [&](int t0, auto Sc) {
+    constexpr int S = decltype(Sc)::value;
+    const int t = t0 + S;
+    if (t >= P::T) return;
+    if (t + kAhead < P::T) issue(t + kAhead);
+    cp_commit();
+    cp_wait<kAhead>();   // row t has landed
+    RsLoad ld;
+    load(t, ld);
+    RsRow& cur = W[S % 3];
+    fill(ld, cur);
+    if (t < 2) return;
+    const RsRow& up = W[(S + 1) % 3];   // row t - 2
+    const RsRow& md = W[(S + 2) % 3];   // row t - 1 (the residual row)
+    const int y = Ybase + t - 1;
+    const bool iny = y >= 0 && y < N1;
+    float2 re = z2(), ro = z2();
+    if (iny && ine)
+      re = md.ve - rs_apply<ORDER>(md.ce, md.xe, md.xl, md.xo, md.cl, md.co, up.xe, up.ce, cur.xe, cur.ce, up.xl,
+                                   up.xo, cur.xl, cur.xo, ih2);
+    if (iny && ino)
+      ro = md.vo - rs_apply<ORDER>(md.co, md.xo, md.xe, md.xr, md.ce, md.cr, up.xo, up.co, cur.xo, cur.co, up.xe,
+                                   up.xr, cur.xe, cur.xr, ih2);
+    // restriction along x, in weight order
+    float2 rx = z2();
+    if constexpr (RW == 2) {
+      const float2 rel = shup(re), rol = shup(ro), rer = shdn(re);
+      rx.x = fmaf(w[0], rel.x, rx.x); rx.y = fmaf(w[0], rel.y, rx.y);
+      rx.x = fmaf(w[1], rol.x, rx.x); rx.y = fmaf(w[1], rol.y, rx.y);
+      rx.x = fmaf(w[2], re.x, rx.x);  rx.y = fmaf(w[2], re.y, rx.y);
+      rx.x = fmaf(w[3], ro.x, rx.x);  rx.y = fmaf(w[3], ro.y, rx.y);
+      rx.x = fmaf(w[4], rer.x, rx.x); rx.y = fmaf(w[4], rer.y, rx.y);
+    } else {
+      const float2 rol = shup(ro);
+      rx.x = fmaf(w[0], rol.x, rx.x); rx.y = fmaf(w[0], rol.y, rx.y);
+      rx.x = fmaf(w[1], re.x, rx.x);  rx.y = fmaf(w[1], re.y, rx.y);
+      rx.x = fmaf(w[2], ro.x, rx.x);  rx.y = fmaf(w[2], ro.y, rx.y);
+    }
+    // along y: residual row tm = t - 1 = 6k + u adds w[tm - 2 jr + RW] rx to the coarse
+    // rows jr = 3k + q with |tm - 2 jr| <= RW (coarse row J = J0 - 2 + jr)
+    constexpr int u = S - 1;
+    constexpr int qlo = fdiv(u - RW + 1, 2), qhi = fdiv(u + RW, 2);
+#pragma unroll
+    for (int q = qlo; q <= qhi; ++q) {
+      const float wq = w[u - 2 * q + RW];
+      acc[mod3(q)].x = fmaf(wq, rx.x, acc[mod3(q)].x);
+      acc[mod3(q)].y = fmaf(wq, rx.y, acc[mod3(q)].y);
+    }
+    // coarse row jr is complete once tm = 2 jr + RW
+    if constexpr (((u - RW) & 1) == 0) {
+      constexpr int qd = fdiv(u - RW, 2);
+      const int J = J0 - 2 + t0 / 2 + qd;   // t0 = 6k: 3k = t0 / 2
+      if (own && J >= J0 && J < J0 + SEG && J < g2.N[1]) rb[Ic + (long long)g2.N[0] * J] = acc[mod3(qd)];
+      acc[mod3(qd)] = z2();
+    }
+  };
+
+  for (int t = 0; t < kAhead; ++t) {
+    if (t < P::T) issue(t);
+    cp_commit();
+  }
+  for (int t0 = 0; t0 < P::T; t0 += 6) {
+    step(t0, std::integral_constant<int, 0>{});
+    step(t0, std::integral_constant<int, 1>{});
+    step(t0, std::integral_constant<int, 2>{});
+    step(t0, std::integral_constant<int, 3>{});
+    step(t0, std::integral_constant<int, 4>{});
+    step(t0, std::integral_constant<int, 5>{});
+  }
+  cp_wait<0>();
+}
+
+template <int ORDER, int PW, int SEG>
+struct RsUp {
+  static constexpr int CU = 29;            // lanes [1, 29] own both their fine columns
+  static constexpr int RS = 2 * SEG;       // fine rows written per warp
+  static constexpr int T = RS + 3;         // fine rows visited: Y0 - 2 ... Y0 + RS
+};
+
+template <int ORDER, int PW, int SEG>
+__global__ void __launch_bounds__(32 * kRsWarps) fine_up_rs_kernel(const Cycle2D c, const float4* __restrict__ v,
+                                                                   const float2* __restrict__ y2,
+                                                                   float2* __restrict__ z) {
+  using P = RsUp<ORDER, PW, SEG>;
+  const GridDims& g = c.fine.g;
+  const GridDims& g2 = c.g2;
+  const int N0 = g.N[0], N1 = g.N[1];
+  const int lane = threadIdx.x & 31;
+  const int nstrip = (N0 + 2 * P::CU - 1) / (2 * P::CU);
+  const int nseg = (N1 + P::RS - 1) / P::RS;
+  const int wid = blockIdx.x * kRsWarps + (threadIdx.x >> 5);
+  if (wid >= nstrip * nseg) return;   // a whole warp
+  const int strip = wid % nstrip, seg = wid / nstrip;
+  const int Ic = strip * P::CU - 1 + lane;
+  const int Y0 = seg * P::RS, Ybase = Y0 - 2;
+  const int cb = Ybase / 2 - 1;   // coarse row of ring index jc = 0 (Ybase is even)
+  const int xe = 2 * Ic, xo = xe + 1;
+  const bool ine = xe >= 0 && xe < N0, ino = xo >= 0 && xo < N0;
+  const bool own = lane >= 1 && lane <= P::CU;
+  const bool inc = Ic >= 0 && Ic < g2.N[0];
+  const float4* vb = v + (long long)blockIdx.y * g.size;
+  const float2* yb = y2 + (long long)blockIdx.y * g2.size;
+  float2* zb = z + (long long)blockIdx.y * g.size;
+  const float omega2 = (float)c.fine.omega2, ih2 = (float)c.fine.inv_h2, w1 = c.w1;
+  const float gxe = ine ? c.fine.gam32[0][xe] : 0.f, gxo = ino ? c.fine.gam32[0][xo] : 0.f;
+  const float* __restrict__ gyt = c.fine.gam32[1];
+  const float* __restrict__ kap = c.kap;
+
+  extern __shared__ __align__(16) unsigned char rs_smem[];
+  unsigned char* const ring = rs_smem + (threadIdx.x >> 5) * kRsUpWarpBytes;
+  const uint32_t vring = smem_addr(ring) + lane * 32, kring = smem_addr(ring + kRing * kVRowBytes) + lane * 16;
+  const uint32_t cring = smem_addr(ring + kRsDownWarpBytes) + lane * 8;
+  RsRow W[3];
+  float2 pe[3], po[3];   // coarse rows prolongated along x to the columns 2I, 2I + 1
+
+  // fine row t into ring slot t % kRing, and with it (t even) coarse row t / 2 + 2 of y2
+  // into coarse slot (t / 2 + 2) % kCRing; zeros outside the grids
+  auto issue_coarse = [&](int jc) {
+    const int J = cb + jc;
+    const bool ok = inc && J >= 0 && J < g2.N[1];
+    cp_async8(cring + (jc % kCRing) * kCRowBytes, ok ? yb + Ic + (long long)g2.N[0] * J : yb, ok);
+  };
+  auto issue = [&](int t) {
+    const int y = Ybase + t;
+    const bool iny = y >= 0 && y < N1;
+    const long long row = (long long)(iny ? y : 0) * N0;
+    const int sl = t % kRing;
+    cp_async16(vring + sl * kVRowBytes, iny && ine ? vb + row + xe : vb, iny && ine);
+    cp_async16(vring + sl * kVRowBytes + 16, iny && ino ? vb + row + xo : vb, iny && ino);
+    cp_async4(kring + sl * kKRowBytes, iny && ine ? kap + row + xe : kap, iny && ine);
+    cp_async4(kring + sl * kKRowBytes + 4, iny && ino ? kap + row + xo : kap, iny && ino);
+    cp_async4(kring + sl * kKRowBytes + 8, iny ? gyt + y : gyt, iny);
+    if ((t & 1) == 0) issue_coarse(t / 2 + 2);
+  };
+  auto load = [&](int t, RsLoad& ld) {
+    const int sl = t % kRing;
+    const float4* vs = reinterpret_cast<const float4*>(ring + sl * kVRowBytes) + 2 * lane;
+    const float* ks = reinterpret_cast<const float*>(ring + kRing * kVRowBytes + sl * kKRowBytes) + 4 * lane;
+    ld.ve = vs[0];
+    ld.vo = vs[1];
+    ld.ke = ks[0];
+    ld.ko = ks[1];
+    ld.gy = ks[2];
+  };
+  // coarse row jc of y2 (staged) prolongated along x (the tile kernels' prolong_1d)
+  auto coarse = [&](int jc, float2& e, float2& o) {
+    const float2 yv = *(reinterpret_cast<const float2*>(ring + kRsDownWarpBytes + (jc % kCRing) * kCRowBytes) + lane);
+    const float2 yl = shup(yv), yr = shdn(yv);
+    o = cscale(yv + yr, 0.5f);
+    if (PW == 1) {
+      e = yv;
+    } else {
+      e = cscale(yv, 0.75f);
+      e.x = fmaf(0.125f, yl.x + yr.x, e.x);
+      e.y = fmaf(0.125f, yl.y + yr.y, e.y);
+    }
+  };
+  auto node = [&](float4 vv, float kk, float gx, float gy, float2 py, float2& x, float2& cc, float2& vo, float2& di) {
+    const float cre = omega2 * kk;
+    cc = make_float2(cre, -cre * (gx + gy));
+    vo = make_float2(vv.x, vv.y);
+    di = rcp_c(diag_c<ORDER>(cc, ih2));
+    x = cscale(cmul(di, vo), w1) + py;
+  };
+
+  auto step = [&](int t0, auto Sc) {
+    constexpr int S = decltype(Sc)::value;
+    const int t = t0 + S;
+    if (t >= P::T) return;
+    if (t + kAhead < P::T) issue(t + kAhead);
+    cp_commit();
+    cp_wait<kAhead>();   // fine row t (and for t even coarse row t / 2 + 2) has landed
+    // prolongation along y to fine row t: coarse ring index jc = floor(t / 2) + 1 (t0 / 2 = 3k)
+    float2 pye, pyo;
+    if constexpr ((S & 1) == 0) {
+      constexpr int jm = mod3(S / 2), j0 = mod3(S / 2 + 1), jp = mod3(S / 2 + 2);
+      coarse(t / 2 + 2, pe[jp], po[jp]);
+      if constexpr (PW == 1) {
+        pye = pe[j0];
+        pyo = po[j0];
+      } else {
+        pye = cscale(pe[j0], 0.75f);
+        pye.x = fmaf(0.125f, pe[jm].x + pe[jp].x, pye.x);
+        pye.y = fmaf(0.125f, pe[jm].y + pe[jp].y, pye.y);
+        pyo = cscale(po[j0], 0.75f);
+        pyo.x = fmaf(0.125f, po[jm].x + po[jp].x, pyo.x);
+        pyo.y = fmaf(0.125f, po[jm].y + po[jp].y, pyo.y);
+      }
+    } else {
+      constexpr int j0 = mod3((S - 1) / 2 + 1), j1 = mod3((S - 1) / 2 + 2);
+      pye = cscale(pe[j0] + pe[j1], 0.5f);
+      pyo = cscale(po[j0] + po[j1], 0.5f);
+    }
+    const int y = Ybase + t;
+    const bool iny = y >= 0 && y < N1;
+    RsRow& cur = W[S % 3];
+    RsLoad ld;
+    load(t, ld);
+    cur.xe = cur.xo = cur.ce = cur.co = cur.ve = cur.vo = cur.de = cur.dn = z2();
+    if (iny && ine) node(ld.ve, ld.ke, gxe, ld.gy, pye, cur.xe, cur.ce, cur.ve, cur.de);
+    if (iny && ino) node(ld.vo, ld.ko, gxo, ld.gy, pyo, cur.xo, cur.co, cur.vo, cur.dn);
+    cur.xl = shup(cur.xo);
+    cur.xr = shdn(cur.xe);
+    if constexpr (ORDER == 1) {
+      cur.cl = shup(cur.co);
+      cur.cr = shdn(cur.ce);
+    }
+    if (t < 3) return;
+    // z at fine row t - 1 (rows Y0 ... Y0 + RS - 1)
+    const RsRow& up = W[(S + 1) % 3];
+    const RsRow& md = W[(S + 2) % 3];
+    const int ym = y - 1;
+    if (!own || ym >= N1) return;
+    const long long row = (long long)ym * N0;
+    if (ine) {
+      const float2 res = md.ve - rs_apply<ORDER>(md.ce, md.xe, md.xl, md.xo, md.cl, md.co, up.xe, up.ce, cur.xe, cur.ce,
+                                                 up.xl, up.xo, cur.xl, cur.xo, ih2);
+      zb[row + xe] = md.xe + cscale(cmul(md.de, res), w1);
+    }
+    if (ino) {
+      const float2 res = md.vo - rs_apply<ORDER>(md.co, md.xo, md.xe, md.xr, md.ce, md.cr, up.xo, up.co, cur.xo, cur.co,
+                                                 up.xe, up.xr, cur.xe, cur.xr, ih2);
+      zb[row + xo] = md.xo + cscale(cmul(md.dn, res), w1);
+    }
+  };
+
+  // coarse rows 0 and 1 travel with fine row 0
+  issue_coarse(0);
+  issue_coarse(1);
+  for (int t = 0; t < kAhead; ++t) {
+    if (t < P::T) issue(t);
+    cp_commit();
+  }
+  cp_wait<kAhead - 1>();
+  coarse(0, pe[0], po[0]);
+  coarse(1, pe[1], po[1]);
+  for (int t0 = 0; t0 < P::T; t0 += 6) {
+    step(t0, std::integral_constant<int, 0>{});
+    step(t0, std::integral_constant<int, 1>{});
+    step(t0, std::integral_constant<int, 2>{});
+    step(t0, std::integral_constant<int, 3>{});
+    step(t0, std::integral_constant<int, 4>{});
+    step(t0, std::integral_constant<int, 5>{});
+  }
+  cp_wait<0>();
+}
+
 inline dim3 tiles(const GridDims& g, int tx, int ty, int nrhs) {
   return dim3((g.N[0] + tx - 1) / tx, (g.N[1] + ty - 1) / ty, nrhs);
+}
+
+template <int ORDER, int RW, int SEG>
+int launch_down_rs(const Cycle2D& c, const float4* v, float2* r2, int nrhs, cudaStream_t s) {
+  using P = RsDown<ORDER, RW, SEG>;
+  const long long warps = (long long)((c.g2.N[0] + P::CS - 1) / P::CS) * ((c.g2.N[1] + SEG - 1) / SEG);
+  const dim3 grid((unsigned)((warps + kRsWarps - 1) / kRsWarps), (unsigned)nrhs);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(fine_down_rs_kernel<ORDER, RW, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kRsWarps * kRsDownWarpBytes);
+    attr = true;
+  }
+  fine_down_rs_kernel<ORDER, RW, SEG><<<grid, 32 * kRsWarps, kRsWarps * kRsDownWarpBytes, s>>>(c, v, r2);
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
+template <int ORDER, int PW, int SEG>
+int launch_up_rs(const Cycle2D& c, const float4* v, const float2* y2, float2* z, int nrhs, cudaStream_t s) {
+  using P = RsUp<ORDER, PW, SEG>;
+  const long long warps =
+      (long long)((c.fine.g.N[0] + 2 * P::CU - 1) / (2 * P::CU)) * ((c.fine.g.N[1] + P::RS - 1) / P::RS);
+  const dim3 grid((unsigned)((warps + kRsWarps - 1) / kRsWarps), (unsigned)nrhs);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(fine_up_rs_kernel<ORDER, PW, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kRsWarps * kRsUpWarpBytes);
+    attr = true;
+  }
+  fine_up_rs_kernel<ORDER, PW, SEG><<<grid, 32 * kRsWarps, kRsWarps * kRsUpWarpBytes, s>>>(c, v, y2, z);
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
+template <int SEG>
+int down_rs(const Cycle2D& c, const float4* v, float2* r2, int nrhs, cudaStream_t s) {
+  if (c.fine.order == 0 && c.rw1 == 1) return launch_down_rs<0, 1, SEG>(c, v, r2, nrhs, s);
+  if (c.fine.order == 0 && c.rw1 == 2) return launch_down_rs<0, 2, SEG>(c, v, r2, nrhs, s);
+  if (c.fine.order == 1 && c.rw1 == 1) return launch_down_rs<1, 1, SEG>(c, v, r2, nrhs, s);
+  if (c.fine.order == 1 && c.rw1 == 2) return launch_down_rs<1, 2, SEG>(c, v, r2, nrhs, s);
+  set_error("fused fine pass: unsupported order or transfer");
+  return HELM_EINVAL;
+}
+
+template <int SEG>
+int up_rs(const Cycle2D& c, const float4* v, const float2* y2, float2* z, int nrhs, cudaStream_t s) {
+  if (c.fine.order == 0 && c.rw1 == 1) return launch_up_rs<0, 1, SEG>(c, v, y2, z, nrhs, s);
+  if (c.fine.order == 0 && c.rw1 == 2) return launch_up_rs<0, 2, SEG>(c, v, y2, z, nrhs, s);
+  if (c.fine.order == 1 && c.rw1 == 1) return launch_up_rs<1, 1, SEG>(c, v, y2, z, nrhs, s);
+  if (c.fine.order == 1 && c.rw1 == 2) return launch_up_rs<1, 2, SEG>(c, v, y2, z, nrhs, s);
+  set_error("fused fine pass: unsupported order or transfer");
+  return HELM_EINVAL;
 }
 
 }  // namespace
 
 int cycle2d_fine_down(const Cycle2D& c, const float4* v, float2* r2, int nrhs, cudaStream_t s) {
   KernelTimer kt(HELM_K_FINE, s);
+  switch (c.fine_kind) {
+    case HELM_FINE_ROWS8: return down_rs<8>(c, v, r2, nrhs, s);
+    case HELM_FINE_ROWS16: return down_rs<16>(c, v, r2, nrhs, s);
+    case HELM_FINE_ROWS32: return down_rs<32>(c, v, r2, nrhs, s);
+    default: break;
+  }
   const dim3 grid = tiles(c.g2, kFD, kFD, nrhs);
   auto smem = [](int rw) {
     const int nx = 2 * kFD + 2 * rw + 1, nf = nx - 2;
@@ -524,6 +1020,12 @@ int cycle2d_l2_up(const Cycle2D& c, const float2* r2, const double2* e3, float2*
 
 int cycle2d_fine_up(const Cycle2D& c, const float4* v, const float2* y2, float2* z, int nrhs, cudaStream_t s) {
   KernelTimer kt(HELM_K_FINE, s);
+  switch (c.fine_kind) {
+    case HELM_FINE_ROWS8: return up_rs<8>(c, v, y2, z, nrhs, s);
+    case HELM_FINE_ROWS16: return up_rs<16>(c, v, y2, z, nrhs, s);
+    case HELM_FINE_ROWS32: return up_rs<32>(c, v, y2, z, nrhs, s);
+    default: break;
+  }
   const dim3 grid = tiles(c.fine.g, kFX, kFY, nrhs);
 #define HELM_FU(O, PW)                                                                  \
   if (c.fine.order == O && c.rw1 == PW) {                                               \

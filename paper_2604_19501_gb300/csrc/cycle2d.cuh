@@ -14,6 +14,10 @@
 
 namespace helm {
 
+// Kernels of the two fine passes: shared-memory tiles, or one warp per strip walking
+// segments of 8, 16 or 32 coarse rows (16, 32, 64 fine rows) with a register window.
+enum FineKind { HELM_FINE_TILES = 0, HELM_FINE_ROWS8 = 1, HELM_FINE_ROWS16 = 2, HELM_FINE_ROWS32 = 3 };
+
 struct Cycle2D {
   FineOp fine;              // level-1 operator (FP32 tables in gam32)
   const float* kap;         // FP32 slowness squared, level-1 nodes
@@ -23,6 +27,7 @@ struct Cycle2D {
   const float2* dinv2;      // level-2 1 / diagonal
   int rw1, rw2, pw2;        // transfer radii: R1 = P1 (level 1-2), R2, P2 (level 2-3)
   float w1, w2;             // Jacobi weights
+  int fine_kind;            // FineKind of the fine passes
 };
 
 // The passes above for nrhs right-hand sides stored back to back.

@@ -250,6 +250,25 @@ __global__ void to_df_kernel(const double2* __restrict__ x, float4* __restrict__
   }
 }
 
+__global__ void add_c128_kernel(const double2* __restrict__ x, double2* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double2 a = x[i];
+    double2 b = y[i];
+    b.x += a.x;
+    b.y += a.y;
+    y[i] = b;
+  }
+}
+
+int launch_add_c128(const double2* x, double2* y, long long n, cudaStream_t s) {
+  const int th = 256;
+  const int bl = (int)std::min<long long>(blocks_for(n, th), 152LL * 16);
+  KernelTimer kt(HELM_K_TRANSFER, s);
+  add_c128_kernel<<<bl, th, 0, s>>>(x, y, n);
+  HELM_LAUNCH_CHECK();
+  return 0;
+}
+
 int launch_convert(Prec from, Prec to, const void* x, void* y, long long n, cudaStream_t s) {
   const int th = 256;
   const int bl = (int)std::min<long long>(blocks_for(n, th), 152LL * 16);

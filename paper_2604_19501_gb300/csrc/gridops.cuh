@@ -38,4 +38,7 @@ int launch_prolong_add(const GridDims& gf, const GridDims& gc, const Transfer& t
 // y = convert(x) between c128 and c64 storage, n complex entries.
 int launch_convert(Prec from, Prec to, const void* x, void* y, long long n, cudaStream_t s);
 
+// y += x for n complex FP64 entries.
+int launch_add_c128(const double2* x, double2* y, long long n, cudaStream_t s);
+
 }  // namespace helm

@@ -41,6 +41,31 @@ def test_fused_cycle_matches_oracle_and_unfused(n, order, ig):
     assert rel(z, zu) < 1e-5
 
 
+@pytest.mark.parametrize("n,order,ig", CONFIGS)
+def test_fine_pass_kernels_agree(n, order, ig):
+    """Every kernel kind of the fine passes (shared-memory tiles; one warp per strip with
+    segments of 8, 16 and 32 coarse rows) against the oracle cycle and against each other
+    (the same operators and sums in the same order: FP32 rounding only), and the autotuner
+    picks one of them."""
+    from paper_2604_19501_gb300 import _ffi
+
+    c = Case(n, order=order, intergrid=ig, alpha3=1.05, seed=14, abc=2 if min(n) <= 8 else 4)
+    v = np.stack([rand_complex(c.grid.shape, 15 + k) for k in range(2)])
+    ref = np.stack([OC.Cycle(c.hier)(vk.ravel()).reshape(vk.shape) for vk in v])
+    s = c.solver(precision="mixed")
+    out = {}
+    for kind in _ffi.CYCLE_KERNELS:
+        s.set_cycle_kernels(kind)
+        out[kind] = _n(s.cycle(_t(v)))
+        assert rel(out[kind], ref) < 1e-5, kind
+        assert rel(out[kind], out["tiles"]) < 1e-6, kind
+    best, ms = s.autotune_cycle(2)
+    assert best in _ffi.CYCLE_KERNELS and set(ms) == set(_ffi.CYCLE_KERNELS) and all(t > 0 for t in ms.values())
+    assert s.info()["cycle_kernels"] == _ffi.CYCLE_KERNELS.index(best)
+    assert rel(_n(s.cycle(_t(v))), ref) < 1e-5
+    s.close()
+
+
 def test_fused_cycle_batch_is_per_rhs():
     c = Case((48, 40), order="4th", intergrid="cubic", alpha3=1.05, seed=6)
     s = c.solver(precision="mixed")
