@@ -74,6 +74,7 @@ static_assert((smem_bytes<1>() + 1024) * blocks_per_sm_target<1>() <= 233472 &&
               "the targeted blocks per multiprocessor fit in shared memory");
 static_assert(kTile <= kPartBlock, "partial block");
 static_assert(kTile <= kSweepThreads, "one thread per output column at least");
+static_assert(kSweepThreads >= 64, "thread 32 (warp 1) publishes completions");
 
 struct SweepArgs {
   const SweepMeta* meta;
@@ -411,6 +412,11 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
 
   bool pre_done = false;   // the current job's first-pass indices and b are already in registers
   int cur = 0;
+  // job records travel two jobs ahead: word (lane l) of the next job's record is in a
+  // register of the record warp when the current job starts, the one after it is loaded then
+  int next_word = 0;
+  if (warp == kMetaWarp && (int)(blockIdx.x + gridDim.x) < a.njobs)
+    next_word = reinterpret_cast<const int*>(a.meta + blockIdx.x + gridDim.x)[lane];
   for (int j = blockIdx.x; j < a.njobs; j += gridDim.x, cur ^= 1) {
     const SweepMeta& m = metas[cur];
     int* const sidx = sidx2 + cur * kTile;
@@ -420,9 +426,9 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
     const int nst = job_stages(rows, m.srows);
     const int nchunks = m.nchunks;
     const int jn = j + gridDim.x;
-    // the next job's record, read now and stored after this job's stages
-    int next_word = 0;
-    if (warp == kMetaWarp && jn < a.njobs) next_word = reinterpret_cast<const int*>(a.meta + jn)[lane];
+    const int jnn = jn + gridDim.x;
+    int next2_word = 0;
+    if (warp == kMetaWarp && jnn < a.njobs) next2_word = reinterpret_cast<const int*>(a.meta + jnn)[lane];
 
     if (!pre_done) {
       gather_idx(m, 0, min(RG, a.nrhs));
@@ -450,6 +456,9 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
     const int nsplit = min(kSplitMax, kSweepThreads / cols);
     const int c = tid % cols, part = tid / cols;
     const bool act = part < nsplit;
+    // one row part per column: every active thread ends with its column's whole sum, and the
+    // reduction through shared memory (and its two barriers) is skipped
+    const bool direct = nsplit == 1;
     E wv[RG];   // backward: w at this thread's output column
     for (int p = 0; p < npass; ++p) {
       const int r0 = p * RG, nr = min(RG, a.nrhs - r0);
@@ -516,7 +525,13 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
             if (rr < nr) wv[rr] = ldcg(wE + (r0 + rr) * a.nodes + sI[0]);
         }
       }
-      consumer_sync();
+      const bool last = p == npass - 1;
+      if (last && warp == kMetaWarp && jn < a.njobs) reinterpret_cast<int*>(metas + (cur ^ 1))[lane] = next_word;
+      consumer_sync();   // row values in place; the next job's record too
+      // the next job's indices, read while this one streams its factor rows (its b once
+      // they have arrived); this job's index registers are no longer needed
+      pre_done = last && jn < a.njobs;
+      if (pre_done) gather_idx(metas[cur ^ 1], 0, min(RG, a.nrhs));
       E acc[RG];
 #pragma unroll
       for (int rr = 0; rr < RG; ++rr) zero(acc[rr]);
@@ -534,20 +549,25 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
           }
         });
       }
-      const bool last = p == npass - 1;
-      if (last && warp == kMetaWarp && jn < a.njobs) reinterpret_cast<int*>(metas + (cur ^ 1))[lane] = next_word;
-      consumer_sync();   // every thread is done with the row values red overwrites; the next record is in place
-      if (ok && act)
+      // the next job's right-hand-side values at the row nodes just gathered (this job's
+      // value registers were consumed before its stage loop)
+      if (pre_done) gather_b(metas[cur ^ 1], 0, min(RG, a.nrhs));
+      if (!direct) {
+        consumer_sync();   // every thread is done with the row values red overwrites
+        if (ok && act)
 #pragma unroll
-        for (int rr = 0; rr < RG; ++rr) red[tid * RG + rr] = acc[rr];
-      // the next job's indices, read while this one finishes (its b once they have arrived)
-      pre_done = last && jn < a.njobs;
-      if (pre_done) gather_idx(metas[cur ^ 1], 0, min(RG, a.nrhs));
-      consumer_sync();
+          for (int rr = 0; rr < RG; ++rr) red[tid * RG + rr] = acc[rr];
+        consumer_sync();
+      }
       if (ok && tid < cols) {
-        for (int rr = 0; rr < nr; ++rr) {
-          E v = red[tid * RG + rr];
-          for (int pp = 1; pp < nsplit; ++pp) addto(v, red[(pp * cols + tid) * RG + rr]);
+#pragma unroll
+        for (int rr = 0; rr < RG; ++rr) {
+          if (rr >= nr) break;
+          E v = acc[rr];
+          if (!direct) {
+            v = red[tid * RG + rr];
+            for (int pp = 1; pp < nsplit; ++pp) addto(v, red[(pp * cols + tid) * RG + rr]);
+          }
           const int r = r0 + rr;
           if (nchunks == 1) {
             const E o = norm(v);
@@ -612,10 +632,12 @@ __global__ void __launch_bounds__(kBlockThreads, blocks_per_sm_target<RG>()) swe
           }
         }
       }
+      consumer_sync();   // the finalisation's outputs are written (a single job's were, at the pass's end)
     }
-    consumer_sync();
-    if (finalized && ok && tid == 0) red_release(a.counters + m.done);
-    if (pre_done) gather_b(metas[cur ^ 1], 0, min(RG, a.nrhs));
+    // published by a thread of warp 1: its release waits for the outputs to be visible while
+    // thread 0 already polls the next job's dependencies
+    if (finalized && ok && tid == 32) red_release(a.counters + m.done);
+    next_word = next2_word;
   }
 }
 

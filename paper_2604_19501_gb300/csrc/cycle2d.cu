@@ -269,38 +269,52 @@ __global__ void __launch_bounds__(kThreads) l2_resid_kernel(const Cycle2D c, con
   s2[rhs * g.size + idx] = rb[idx] - ax;
 }
 
-// b3 = R2 s2 in c128 (one thread per level-3 node)
+// b3 = R2 s2 in c128 by tiles: a kRX x kRY tile of level-3 nodes per block, its level-2
+// cover (widened by RW) staged in shared memory, then the restriction along x and along y
+// with the weights in the per-node kernel's order (x first, then y).
+constexpr int kRX = 32, kRY = 8;
 template <int RW>
-__global__ void __launch_bounds__(kThreads) l2_restrict_kernel(const Cycle2D c, const float2* __restrict__ s2,
-                                                               double2* __restrict__ b3, int nrhs) {
+__global__ void __launch_bounds__(kThreads) l2_restrict_tile_kernel(const Cycle2D c, const float2* __restrict__ s2,
+                                                                    double2* __restrict__ b3) {
+  constexpr int NX = 2 * (kRX - 1) + 2 * RW + 1, NY = 2 * (kRY - 1) + 2 * RW + 1;
+  __shared__ float2 sf[NY * NX];
+  __shared__ float2 sx[NY * kRX];
   const GridDims& gf = c.g2;
   const GridDims& gc = c.g3;
-  const long long I = blockIdx.x * (long long)kThreads + threadIdx.x;
-  if (I >= gc.size) return;
-  int ci, cj, ck;
-  node_coords(gc, I, ci, cj, ck);
-  const float* w = c_w[RW - 1];
-  for (int r = 0; r < nrhs; ++r) {
-    float2 acc = z2();
-    const float2* sb = s2 + r * gf.size;
-#pragma unroll
-    for (int ay = -RW; ay <= RW; ++ay) {
-      const int fy = 2 * cj + ay;
-      if (fy < 0 || fy >= gf.N[1]) continue;
-      const float wy = w[ay + RW];
-#pragma unroll
-      for (int ax = -RW; ax <= RW; ++ax) {
-        const int fx = 2 * ci + ax;
-        if (fx < 0 || fx >= gf.N[0]) continue;
-        const float2 t = sb[fx + (long long)gf.N[0] * fy];
-        const float wgt = wy * w[ax + RW];
-        acc.x = fmaf(wgt, t.x, acc.x);
-        acc.y = fmaf(wgt, t.y, acc.y);
-      }
-    }
-    b3[r * gc.size + I] = make_double2(acc.x, acc.y);
+  const int I0 = blockIdx.x * kRX, J0 = blockIdx.y * kRY, rhs = blockIdx.z;
+  const int X0 = 2 * I0 - RW, Y0 = 2 * J0 - RW;
+  const float2* sb = s2 + (long long)rhs * gf.size;
+  for (int q = threadIdx.x; q < NX * NY; q += kThreads) {
+    const int fx = X0 + q % NX, fy = Y0 + q / NX;
+    sf[q] = (fx >= 0 && fx < gf.N[0] && fy >= 0 && fy < gf.N[1]) ? sb[fx + (long long)gf.N[0] * fy] : z2();
   }
+  __syncthreads();
+  const float* w = c_w[RW - 1];
+  for (int q = threadIdx.x; q < NY * kRX; q += kThreads) {
+    const int ly = q / kRX, i = q % kRX;
+    float2 acc = z2();
+#pragma unroll
+    for (int a = 0; a <= 2 * RW; ++a) {
+      const float2 t = sf[ly * NX + 2 * i + a];
+      acc.x = fmaf(w[a], t.x, acc.x);
+      acc.y = fmaf(w[a], t.y, acc.y);
+    }
+    sx[q] = acc;
+  }
+  __syncthreads();
+  const int i = threadIdx.x % kRX, j = threadIdx.x / kRX;
+  const int I = I0 + i, J = J0 + j;
+  if (I >= gc.N[0] || J >= gc.N[1]) return;
+  float2 acc = z2();
+#pragma unroll
+  for (int b = 0; b <= 2 * RW; ++b) {
+    const float2 t = sx[(2 * j + b) * kRX + i];
+    acc.x = fmaf(w[b], t.x, acc.x);
+    acc.y = fmaf(w[b], t.y, acc.y);
+  }
+  b3[(long long)rhs * gc.size + I + (long long)gc.N[0] * J] = make_double2(acc.x, acc.y);
 }
+static_assert(kRX * kRY == kThreads, "one thread per level-3 node of the tile");
 
 // Prolongation of a coarse field (held in a tile) to the fine tile positions
 // [X0, X0 + NX) x [Y0, Y0 + NY): separable, P = 4 R^T, i.e. weights 2 w per axis.  Along
@@ -480,7 +494,6 @@ struct RsRow {
   float2 xl, xe, xo, xr;   // x1 at columns 2I - 1, 2I, 2I + 1, 2I + 2
   float2 cl, ce, co, cr;   // c at the same columns (4th order only)
   float2 ve, vo;           // v at 2I, 2I + 1
-  float2 de, dn;           // 1 / diagonal at 2I, 2I + 1 (fine up pass)
 };
 // loaded values of one fine row
 struct RsLoad {
@@ -496,15 +509,17 @@ struct RsLoad {
 // in registers.  A lane reads back only what it copied itself: its cp.async.wait_group
 // makes the data visible to it.  Entries outside the grid are zero-filled (source size 0,
 // the source address then being the array's base, which is valid).
-constexpr int kRing = 8;                          // fine rows per warp ring
-constexpr int kAhead = 6;                         // rows in flight ahead of the current one
+constexpr int kRing = 6;                          // fine rows per warp ring (the unroll: slot = step)
+constexpr int kAhead = 4;                         // rows in flight ahead of the current one
 constexpr int kVRowBytes = 32 * 2 * 16;           // v: two float4 per lane
 constexpr int kKRowBytes = 32 * 4 * 4;            // kappa at the two columns and gamma_y: four floats per lane
-constexpr int kCRing = 8;                         // coarse rows per warp ring (fine up pass)
+constexpr int kCRing = 4;                         // coarse rows per warp ring (fine up pass)
 constexpr int kCRowBytes = 32 * 8;                // y2: one float2 per lane
 constexpr int kRsDownWarpBytes = kRing * (kVRowBytes + kKRowBytes);
 constexpr int kRsUpWarpBytes = kRsDownWarpBytes + kCRing * kCRowBytes;
 static_assert(kRing >= kAhead + 2, "a ring slot is refilled two steps after its row was read");
+static_assert(kRing == 6, "ring slots are the steps of the six-fold unroll");
+constexpr int kRsMinBlocks = 5;                   // resident blocks per SM the kernels are shaped for
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool ok) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
@@ -565,7 +580,7 @@ struct RsDown {
 };
 
 template <int ORDER, int RW, int SEG>
-__global__ void __launch_bounds__(32 * kRsWarps) fine_down_rs_kernel(const Cycle2D c, const float4* __restrict__ v,
+__global__ void __launch_bounds__(32 * kRsWarps, kRsMinBlocks) fine_down_rs_kernel(const Cycle2D c, const float4* __restrict__ v,
                                                                      float2* __restrict__ r2) {
   using P = RsDown<ORDER, RW, SEG>;
   const GridDims& g = c.fine.g;
@@ -597,12 +612,18 @@ __global__ void __launch_bounds__(32 * kRsWarps) fine_down_rs_kernel(const Cycle
   RsRow W[3];
   float2 acc[3];
 #pragma unroll
-  for (int q = 0; q < 3; ++q) acc[q] = z2();
+  for (int q = 0; q < 3; ++q) {
+    acc[q] = z2();
+    // zero rows before the first: the residual rows formed from them only feed coarse
+    // rows above the segment, whose accumulators are cleared before they are reused
+    W[q].xl = W[q].xe = W[q].xo = W[q].xr = W[q].cl = W[q].ce = W[q].co = W[q].cr = W[q].ve = W[q].vo = z2();
+  }
 
-  // fine row t into ring slot t % kRing (zeros outside the grid)
-  auto issue = [&](int t) {
+  // fine row t into ring slot t % kRing (zeros outside the grid, and for rows past the
+  // warp's visit, `want` false)
+  auto issue = [&](int t, bool want) {
     const int y = Ybase + t;
-    const bool iny = y >= 0 && y < N1;
+    const bool iny = want && y >= 0 && y < N1;
     const long long row = (long long)(iny ? y : 0) * N0;
     const int sl = t % kRing;
     cp_async16(vring + sl * kVRowBytes, iny && ine ? vb + row + xe : vb, iny && ine);
@@ -640,19 +661,22 @@ __global__ void __launch_bounds__(32 * kRsWarps) fine_down_rs_kernel(const Cycle
     }
   };
 
-  // fine row t = t0 + S of the warp's visit; S is a compile-time step of the six-fold unroll
-  auto step = [&](int t0, auto Sc) {
+  // fine row t = t0 + S of the warp's visit; S is a compile-time step of the six-fold
+  // unroll.  Full groups of six steps run without branches (so that the scheduler can
+  // overlap adjacent rows); only the last, partial group checks t < T.
+  auto step = [&](int t0, auto Sc, auto Checked) {
     constexpr int S = decltype(Sc)::value;
     const int t = t0 + S;
-    if (t >= P::T) return;
-    if (t + kAhead < P::T) issue(t + kAhead);
+    if constexpr (decltype(Checked)::value) {
+      if (t >= P::T) return;
+    }
+    issue(t + kAhead, t + kAhead < P::T);
     cp_commit();
     cp_wait<kAhead>();   // row t has landed
     RsLoad ld;
     load(t, ld);
     RsRow& cur = W[S % 3];
     fill(ld, cur);
-    if (t < 2) return;
     const RsRow& up = W[(S + 1) % 3];   // row t - 2
     const RsRow& md = W[(S + 2) % 3];   // row t - 1 (the residual row)
     const int y = Ybase + t - 1;
@@ -699,16 +723,27 @@ __global__ void __launch_bounds__(32 * kRsWarps) fine_down_rs_kernel(const Cycle
   };
 
   for (int t = 0; t < kAhead; ++t) {
-    if (t < P::T) issue(t);
+    issue(t, t < P::T);
     cp_commit();
   }
-  for (int t0 = 0; t0 < P::T; t0 += 6) {
-    step(t0, std::integral_constant<int, 0>{});
-    step(t0, std::integral_constant<int, 1>{});
-    step(t0, std::integral_constant<int, 2>{});
-    step(t0, std::integral_constant<int, 3>{});
-    step(t0, std::integral_constant<int, 4>{});
-    step(t0, std::integral_constant<int, 5>{});
+  using Ct = std::true_type;
+  using Cf = std::false_type;
+  int t0 = 0;
+  for (; t0 + 6 <= P::T; t0 += 6) {
+    step(t0, std::integral_constant<int, 0>{}, Cf{});
+    step(t0, std::integral_constant<int, 1>{}, Cf{});
+    step(t0, std::integral_constant<int, 2>{}, Cf{});
+    step(t0, std::integral_constant<int, 3>{}, Cf{});
+    step(t0, std::integral_constant<int, 4>{}, Cf{});
+    step(t0, std::integral_constant<int, 5>{}, Cf{});
+  }
+  if (t0 < P::T) {
+    step(t0, std::integral_constant<int, 0>{}, Ct{});
+    step(t0, std::integral_constant<int, 1>{}, Ct{});
+    step(t0, std::integral_constant<int, 2>{}, Ct{});
+    step(t0, std::integral_constant<int, 3>{}, Ct{});
+    step(t0, std::integral_constant<int, 4>{}, Ct{});
+    step(t0, std::integral_constant<int, 5>{}, Ct{});
   }
   cp_wait<0>();
 }
@@ -721,7 +756,7 @@ struct RsUp {
 };
 
 template <int ORDER, int PW, int SEG>
-__global__ void __launch_bounds__(32 * kRsWarps) fine_up_rs_kernel(const Cycle2D c, const float4* __restrict__ v,
+__global__ void __launch_bounds__(32 * kRsWarps, kRsMinBlocks) fine_up_rs_kernel(const Cycle2D c, const float4* __restrict__ v,
                                                                    const float2* __restrict__ y2,
                                                                    float2* __restrict__ z) {
   using P = RsUp<ORDER, PW, SEG>;
@@ -755,6 +790,9 @@ __global__ void __launch_bounds__(32 * kRsWarps) fine_up_rs_kernel(const Cycle2D
   const uint32_t cring = smem_addr(ring + kRsDownWarpBytes) + lane * 8;
   RsRow W[3];
   float2 pe[3], po[3];   // coarse rows prolongated along x to the columns 2I, 2I + 1
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    W[q].xl = W[q].xe = W[q].xo = W[q].xr = W[q].cl = W[q].ce = W[q].co = W[q].cr = W[q].ve = W[q].vo = z2();
 
   // fine row t into ring slot t % kRing, and with it (t even) coarse row t / 2 + 2 of y2
   // into coarse slot (t / 2 + 2) % kCRing; zeros outside the grids
@@ -763,9 +801,9 @@ __global__ void __launch_bounds__(32 * kRsWarps) fine_up_rs_kernel(const Cycle2D
     const bool ok = inc && J >= 0 && J < g2.N[1];
     cp_async8(cring + (jc % kCRing) * kCRowBytes, ok ? yb + Ic + (long long)g2.N[0] * J : yb, ok);
   };
-  auto issue = [&](int t) {
+  auto issue = [&](int t, bool want) {
     const int y = Ybase + t;
-    const bool iny = y >= 0 && y < N1;
+    const bool iny = want && y >= 0 && y < N1;
     const long long row = (long long)(iny ? y : 0) * N0;
     const int sl = t % kRing;
     cp_async16(vring + sl * kVRowBytes, iny && ine ? vb + row + xe : vb, iny && ine);
@@ -773,7 +811,7 @@ __global__ void __launch_bounds__(32 * kRsWarps) fine_up_rs_kernel(const Cycle2D
     cp_async4(kring + sl * kKRowBytes, iny && ine ? kap + row + xe : kap, iny && ine);
     cp_async4(kring + sl * kKRowBytes + 4, iny && ino ? kap + row + xo : kap, iny && ino);
     cp_async4(kring + sl * kKRowBytes + 8, iny ? gyt + y : gyt, iny);
-    if ((t & 1) == 0) issue_coarse(t / 2 + 2);
+    if ((t & 1) == 0 && want) issue_coarse(t / 2 + 2);
   };
   auto load = [&](int t, RsLoad& ld) {
     const int sl = t % kRing;
@@ -798,19 +836,20 @@ __global__ void __launch_bounds__(32 * kRsWarps) fine_up_rs_kernel(const Cycle2D
       e.y = fmaf(0.125f, yl.y + yr.y, e.y);
     }
   };
-  auto node = [&](float4 vv, float kk, float gx, float gy, float2 py, float2& x, float2& cc, float2& vo, float2& di) {
+  auto node = [&](float4 vv, float kk, float gx, float gy, float2 py, float2& x, float2& cc, float2& vo) {
     const float cre = omega2 * kk;
     cc = make_float2(cre, -cre * (gx + gy));
     vo = make_float2(vv.x, vv.y);
-    di = rcp_c(diag_c<ORDER>(cc, ih2));
-    x = cscale(cmul(di, vo), w1) + py;
+    x = cscale(cmul(rcp_c(diag_c<ORDER>(cc, ih2)), vo), w1) + py;
   };
 
-  auto step = [&](int t0, auto Sc) {
+  auto step = [&](int t0, auto Sc, auto Checked) {
     constexpr int S = decltype(Sc)::value;
     const int t = t0 + S;
-    if (t >= P::T) return;
-    if (t + kAhead < P::T) issue(t + kAhead);
+    if constexpr (decltype(Checked)::value) {
+      if (t >= P::T) return;
+    }
+    issue(t + kAhead, t + kAhead < P::T);
     cp_commit();
     cp_wait<kAhead>();   // fine row t (and for t even coarse row t / 2 + 2) has landed
     // prolongation along y to fine row t: coarse ring index jc = floor(t / 2) + 1 (t0 / 2 = 3k)
@@ -839,31 +878,30 @@ __global__ void __launch_bounds__(32 * kRsWarps) fine_up_rs_kernel(const Cycle2D
     RsRow& cur = W[S % 3];
     RsLoad ld;
     load(t, ld);
-    cur.xe = cur.xo = cur.ce = cur.co = cur.ve = cur.vo = cur.de = cur.dn = z2();
-    if (iny && ine) node(ld.ve, ld.ke, gxe, ld.gy, pye, cur.xe, cur.ce, cur.ve, cur.de);
-    if (iny && ino) node(ld.vo, ld.ko, gxo, ld.gy, pyo, cur.xo, cur.co, cur.vo, cur.dn);
+    cur.xe = cur.xo = cur.ce = cur.co = cur.ve = cur.vo = z2();
+    if (iny && ine) node(ld.ve, ld.ke, gxe, ld.gy, pye, cur.xe, cur.ce, cur.ve);
+    if (iny && ino) node(ld.vo, ld.ko, gxo, ld.gy, pyo, cur.xo, cur.co, cur.vo);
     cur.xl = shup(cur.xo);
     cur.xr = shdn(cur.xe);
     if constexpr (ORDER == 1) {
       cur.cl = shup(cur.co);
       cur.cr = shdn(cur.ce);
     }
-    if (t < 3) return;
-    // z at fine row t - 1 (rows Y0 ... Y0 + RS - 1)
+    // z at fine row t - 1 (rows Y0 ... Y0 + RS - 1, i.e. 3 <= t <= RS + 2)
     const RsRow& up = W[(S + 1) % 3];
     const RsRow& md = W[(S + 2) % 3];
     const int ym = y - 1;
-    if (!own || ym >= N1) return;
+    const bool out = own && ym >= Y0 && ym < Y0 + P::RS && ym < N1;
     const long long row = (long long)ym * N0;
-    if (ine) {
+    if (out && ine) {
       const float2 res = md.ve - rs_apply<ORDER>(md.ce, md.xe, md.xl, md.xo, md.cl, md.co, up.xe, up.ce, cur.xe, cur.ce,
                                                  up.xl, up.xo, cur.xl, cur.xo, ih2);
-      zb[row + xe] = md.xe + cscale(cmul(md.de, res), w1);
+      zb[row + xe] = md.xe + cscale(cmul(rcp_c(diag_c<ORDER>(md.ce, ih2)), res), w1);
     }
-    if (ino) {
+    if (out && ino) {
       const float2 res = md.vo - rs_apply<ORDER>(md.co, md.xo, md.xe, md.xr, md.ce, md.cr, up.xo, up.co, cur.xo, cur.co,
                                                  up.xe, up.xr, cur.xe, cur.xr, ih2);
-      zb[row + xo] = md.xo + cscale(cmul(md.dn, res), w1);
+      zb[row + xo] = md.xo + cscale(cmul(rcp_c(diag_c<ORDER>(md.co, ih2)), res), w1);
     }
   };
 
@@ -871,19 +909,30 @@ __global__ void __launch_bounds__(32 * kRsWarps) fine_up_rs_kernel(const Cycle2D
   issue_coarse(0);
   issue_coarse(1);
   for (int t = 0; t < kAhead; ++t) {
-    if (t < P::T) issue(t);
+    issue(t, t < P::T);
     cp_commit();
   }
   cp_wait<kAhead - 1>();
   coarse(0, pe[0], po[0]);
   coarse(1, pe[1], po[1]);
-  for (int t0 = 0; t0 < P::T; t0 += 6) {
-    step(t0, std::integral_constant<int, 0>{});
-    step(t0, std::integral_constant<int, 1>{});
-    step(t0, std::integral_constant<int, 2>{});
-    step(t0, std::integral_constant<int, 3>{});
-    step(t0, std::integral_constant<int, 4>{});
-    step(t0, std::integral_constant<int, 5>{});
+  using Ct = std::true_type;
+  using Cf = std::false_type;
+  int t0 = 0;
+  for (; t0 + 6 <= P::T; t0 += 6) {
+    step(t0, std::integral_constant<int, 0>{}, Cf{});
+    step(t0, std::integral_constant<int, 1>{}, Cf{});
+    step(t0, std::integral_constant<int, 2>{}, Cf{});
+    step(t0, std::integral_constant<int, 3>{}, Cf{});
+    step(t0, std::integral_constant<int, 4>{}, Cf{});
+    step(t0, std::integral_constant<int, 5>{}, Cf{});
+  }
+  if (t0 < P::T) {
+    step(t0, std::integral_constant<int, 0>{}, Ct{});
+    step(t0, std::integral_constant<int, 1>{}, Ct{});
+    step(t0, std::integral_constant<int, 2>{}, Ct{});
+    step(t0, std::integral_constant<int, 3>{}, Ct{});
+    step(t0, std::integral_constant<int, 4>{}, Ct{});
+    step(t0, std::integral_constant<int, 5>{}, Ct{});
   }
   cp_wait<0>();
 }
@@ -992,9 +1041,9 @@ int cycle2d_l2_resid(const Cycle2D& c, const float2* r2, float2* s2, int nrhs, c
 
 int cycle2d_l2_restrict(const Cycle2D& c, const float2* s2, double2* b3, int nrhs, cudaStream_t s) {
   KernelTimer kt(HELM_K_TRANSFER, s);
-  const int bl = blocks_for(c.g3.size, kThreads);
-  if (c.rw2 == 1) l2_restrict_kernel<1><<<bl, kThreads, 0, s>>>(c, s2, b3, nrhs);
-  else if (c.rw2 == 2) l2_restrict_kernel<2><<<bl, kThreads, 0, s>>>(c, s2, b3, nrhs);
+  const dim3 grid = tiles(c.g3, kRX, kRY, nrhs);
+  if (c.rw2 == 1) l2_restrict_tile_kernel<1><<<grid, kThreads, 0, s>>>(c, s2, b3);
+  else if (c.rw2 == 2) l2_restrict_tile_kernel<2><<<grid, kThreads, 0, s>>>(c, s2, b3);
   else { set_error("fused restriction: unsupported radius"); return HELM_EINVAL; }
   HELM_LAUNCH_CHECK();
   return 0;

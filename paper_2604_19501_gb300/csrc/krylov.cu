@@ -3,9 +3,9 @@
 //
 // One Arnoldi step j, after z_j = M^-1 v_j:
 //   arnoldi_matvec   w = H z_j and the first classical Gram-Schmidt pass h1 = V^H w
-//   arnoldi_update   w <- w - V h1 and the second pass h2 = V^H w, ||w||^2
-//   arnoldi_small    H(:, j) = h1 + h2, ||w - V h2||, Givens rotations, residual estimate
-//   arnoldi_normalize v_{j+1} = (w - V h2) / ||w - V h2||
+//   arnoldi_update   w' = w - V h1 (not stored) and the second pass h2 = V^H w', ||w'||^2
+//   arnoldi_small    H(:, j) = h1 + h2, ||w' - V h2||, Givens rotations, residual estimate
+//   arnoldi_normalize v_{j+1} = (w - V (h1 + h2)) / ||w' - V h2||
 // (classical Gram-Schmidt with one re-orthogonalisation, CGS2).  Every reduction keeps
 // per-thread partial sums in shared memory over a fixed grid, reduces each block once and
 // lets the last block sum the block partials in block order, so the result does not
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kThreads) arnoldi_matvec_kernel(
   reduce_finish(sacc, nv + 1, part, counter, out);
 }
 
-// w <- w - sum_i h1_i v_i; h2_i = v_i^H w; ||w||^2.
+// w' = w - sum_i h1_i v_i (kept in registers); h2_i = v_i^H w'; ||w'||^2.
 __global__ void __launch_bounds__(kThreads) arnoldi_update_kernel(
     long long n, double2* __restrict__ w, const double2* __restrict__ V, long long vstride, int nv,
     const double2* __restrict__ h1, double2* __restrict__ part, unsigned* __restrict__ counter,
@@ -108,7 +108,6 @@ __global__ void __launch_bounds__(kThreads) arnoldi_update_kernel(
       wv.x -= h.x * v.x - h.y * v.y;
       wv.y -= h.x * v.y + h.y * v.x;
     }
-    w[p] = wv;
     for (int q = 0; q < nv; ++q) {
       double2& a = sacc[q * blockDim.x + tid];
       a = cmacc(a, V[q * vstride + p], wv);
@@ -118,7 +117,7 @@ __global__ void __launch_bounds__(kThreads) arnoldi_update_kernel(
   reduce_finish(sacc, nv + 1, part, counter, out);
 }
 
-// v_out = (w - sum_i h2_i v_i) * st->inv_hn
+// v_out = (w - sum_i h_i v_i) * st->inv_hn with h = h1 + h2 (stored in h2 by the small step)
 __global__ void __launch_bounds__(kThreads) arnoldi_normalize_kernel(
     long long n, const double2* __restrict__ w, const double2* __restrict__ V, long long vstride, int nv,
     const double2* __restrict__ h2, const double* __restrict__ inv_hn, double2* __restrict__ vout) {
@@ -145,7 +144,9 @@ __device__ void arnoldi_small_body(const KrylovState& st, int j, int m) {
   double hs2 = 0.0;
   for (int i = 0; i <= j; ++i) {
     const double2 a = st.h1[i], b = st.h2[i];
-    H[i * m + j] = make_double2(a.x + b.x, a.y + b.y);
+    const double2 hsum = make_double2(a.x + b.x, a.y + b.y);
+    H[i * m + j] = hsum;
+    st.h2[i] = hsum;   // the normalisation forms w - V (h1 + h2) from the unmodified w
     hs2 += b.x * b.x + b.y * b.y;
   }
   const double hn = sqrt(fmax(st.h2[j + 1].x - hs2, 0.0));
@@ -454,7 +455,6 @@ __global__ void __launch_bounds__(kThreads) arnoldi_update_df_kernel(
     racc re{w0.x, w0.z}, im{w0.y, w0.w};
     for (int q = 0; q < nv; ++q) cacc_sub_cdd(re, im, cdd_load(sh[q]), cdd_load(V[q * vstride + p]));
     const float4 w4 = cdd_store(cdd{racc_dd(re), racc_dd(im)});
-    w[p] = w4;
     for (int q = 0; q < nv; ++q) df_cmacc(sdf[q * blockDim.x + tid], V[q * vstride + p], w4);
     df_cmacc(sdf[nv * blockDim.x + tid], w4, w4);
   }
@@ -526,8 +526,9 @@ __device__ __forceinline__ float4 ld_reread(const float4* p) {
   return v;
 }
 
-// Second CGS pass: w' = w - V h1 and h2 = V^H w', |w'|^2 (double-float), accumulators in
-// registers (the dot pass re-reads V right after the subtraction read it: L1 hits).
+// Second CGS pass: w' = w - V h1 (not stored) and h2 = V^H w', |w'|^2 (double-float),
+// accumulators in registers (the dot pass re-reads V right after the subtraction read it:
+// L1 hits).
 // The block that finishes the reduction also forms the Hessenberg column, its Givens
 // rotation and the residual estimate (the small step, no separate launch).
 // Three blocks per SM (80 registers) up to seven basis vectors, two above: no spills.
@@ -553,7 +554,6 @@ __global__ void __launch_bounds__(kThreads, NV <= 7 ? 3 : 2) arnoldi_update_df_t
 #pragma unroll
     for (int q = 0; q < NV; ++q) cacc_sub_cdd(re, im, cdd_load(sh[q]), cdd_load(V[q * vstride + p]));
     const float4 w4 = cdd_store(cdd{racc_dd(re), racc_dd(im)});
-    w[p] = w4;
 #pragma unroll
     for (int q = 0; q < NV; ++q) df_cmacc(acc[q], ld_reread(V + q * vstride + p), w4);
     df_cmacc(acc[NV], w4, w4);

@@ -16,7 +16,7 @@ struct KrylovState {
   double* cs = nullptr;      // m Givens cosines
   double2* y = nullptr;      // m least-squares solution
   double2* h1 = nullptr;     // first Gram-Schmidt pass (+ ||w||^2)
-  double2* h2 = nullptr;     // second pass (+ ||w||^2)
+  double2* h2 = nullptr;     // second pass (+ ||w'||^2); h1 + h2 after the small step
   double2* red = nullptr;    // reduction outputs
   double* scal = nullptr;    // KS_* scalars
   double2* part = nullptr;   // per-block partial sums (shared by the states of a context)
@@ -38,7 +38,7 @@ int k_start_cycle(const KrylovState& st, long long n, const double2* r, double2*
 // Arnoldi step j from z_j (c128 or c64): w, H(:, j), rotations, estimate scal[KS_EST].
 int k_arnoldi(const KrylovState& st, const FineOp& op, const double* kap64, const void* z, Prec zp,
               double2* w, const double2* V, long long vstride, int j, cudaStream_t s);
-// v_{j+1} = (w - V h2) / hn.
+// v_{j+1} = (w - V h) / hn, h = h1 + h2 (stored in h2 by the Arnoldi step's small step).
 int k_normalize(const KrylovState& st, long long n, const double2* w, const double2* V, long long vstride,
                 int j, double2* vout, cudaStream_t s);
 // Double-float variants (mixed precision): V and w stored as float4 (hi, lo) pairs.
