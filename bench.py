@@ -109,6 +109,9 @@ def parse(argv=None):
                          "then comes from a short pass after the timed region); all = every class")
     ap.add_argument("--no-autotune-cycle", action="store_true",
                     help="keep the default kernels of the fused cycle's fine passes instead of timing every kind")
+    ap.add_argument("--coarse-block-min", type=int, default=0,
+                    help="coarsest fronts with at least this many eliminated nodes take the blocked "
+                         "elimination at set-up (helm_opts.coarse_block_min; 0 = the library's default)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the side measurements of the 2D run (FP64 path, points-per-wavelength and "
                          "grid-size sweeps), which run after the timed region")
@@ -461,7 +464,7 @@ def make_solver(wl, args, dev, precision=None, cslp=None, coarse_refine=0):
                   alpha3=wl["alpha3"], stencil=wl["order"], intergrid=wl["intergrid"], cycle=args.cycle,
                   jacobi_w=wl["jw"], precision=precision or args.precision, restart=args.restart,
                   stream=torch.cuda.current_stream(dev).cuda_stream, cslp_beta=args.cslp if cslp is None else cslp,
-                  solver=args.solver, coarse_refine=coarse_refine)
+                  solver=args.solver, coarse_refine=coarse_refine, coarse_block_min=args.coarse_block_min)
 
 
 def timed_solves(s, q, args, reps, warm=1):

@@ -124,6 +124,11 @@ typedef struct {
                              double-float factors) although the operator itself is well
                              conditioned.  One step brings the residual to the level of the
                              arithmetic.  Each step costs a second solve.  Default 0. */
+  int coarse_block_min;   /* coarsest fronts with at least this many eliminated nodes are
+                             eliminated in panels of 64 columns (pivot rows by partial
+                             pivoting, the rest of the front updated by complex FP64 matrix
+                             products), smaller ones one pivot per pass; 0 (default) = 512.
+                             The two orders give the same factors up to rounding. */
 } helm_opts;
 
 /* Per-solve statistics, one entry per right-hand side. */
@@ -139,7 +144,7 @@ typedef struct helm_ctx helm_ctx;
 /* Fills *o with defaults: 2D, h = 1, gamma_max = 1, alpha2 = alpha3 = 1,
  * 2nd-order stencil, FW transfers, V(1,1), Jacobi w = (0.8, 0.8), rb_w = 1,
  * FP64, restart 10, max_rhs 1, default stream, fuse_cycle 1, graphs 0,
- * cslp_beta 0, solver FGMRES, coarse_blocks 0, coarse_refine 0.  The caller sets dim, n,
+ * cslp_beta 0, solver FGMRES, coarse_blocks 0, coarse_refine 0, coarse_block_min 0.  The caller sets dim, n,
  * omega, abc_width and the shifts. */
 int helm_default_opts(helm_opts* o);
 

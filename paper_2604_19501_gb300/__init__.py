@@ -43,7 +43,8 @@ class Solver:
                  alpha3=1.0, stencil="2nd", intergrid="fw", cycle="V", nu=(1, 1),
                  smoother="jacobi", jacobi_w=(0.8, 0.8), rb_w=1.0, precision="fp64", restart=10,
                  max_rhs=1, stream=None, fuse_cycle=True, graphs=False, cslp_beta=0.0,
-                 solver="fgmres", coarse_blocks=0, coarse_refine=0):
+                 solver="fgmres", coarse_blocks=0, coarse_refine=0,
+                 coarse_block_min=0):
         self.n = tuple(int(v) for v in n)
         self.dim = len(self.n)
         o = HelmOpts()
@@ -74,6 +75,7 @@ class Solver:
         o.solver = _ffi.SOLVER[solver]
         o.coarse_blocks = int(coarse_blocks)
         o.coarse_refine = int(coarse_refine)
+        o.coarse_block_min = int(coarse_block_min)
         if stream is None:
             import torch
 

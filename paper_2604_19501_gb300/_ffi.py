@@ -48,6 +48,7 @@ class HelmOpts(ctypes.Structure):
         ("solver", ctypes.c_int),
         ("coarse_blocks", ctypes.c_int),
         ("coarse_refine", ctypes.c_int),
+        ("coarse_block_min", ctypes.c_int),
     ]
 
 

@@ -704,6 +704,7 @@ int helm_default_opts(helm_opts* o) {
   o->solver = HELM_SOLVER_FGMRES;
   o->coarse_blocks = 0;
   o->coarse_refine = 0;
+  o->coarse_block_min = 0;
   return HELM_OK;
 }
 
@@ -723,6 +724,7 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
   if (o->solver != HELM_SOLVER_FGMRES && o->solver != HELM_SOLVER_CYCLE) return fail(HELM_EINVAL, "bad solver");
   if (o->coarse_blocks < 0) return fail(HELM_EINVAL, "coarse_blocks must be >= 0");
   if (o->coarse_refine < 0 || o->coarse_refine > 8) return fail(HELM_EINVAL, "coarse_refine must be in [0, 8]");
+  if (o->coarse_block_min < 0) return fail(HELM_EINVAL, "coarse_block_min must be >= 0");
   if (o->stencil != HELM_STENCIL_2ND && o->stencil != HELM_STENCIL_4TH) return fail(HELM_EINVAL, "bad stencil");
   if (o->intergrid < HELM_INTERGRID_FW || o->intergrid > HELM_INTERGRID_LEVDEP)
     return fail(HELM_EINVAL, "bad intergrid transfer");
@@ -873,7 +875,8 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
   // mixed precision: the coarsest factors in double-float arithmetic (FP32 pipes);
   // FP64 mode: native FP64
   const bool df = o->precision == HELM_MIXED;
-  if ((st = coarse_setup(c->cs, c->g[2], c->r3, c->A3_64, 64, symmetric, df, c->s, o->coarse_blocks))) return bail(st);
+  if ((st = coarse_setup(c->cs, c->g[2], c->r3, c->A3_64, 64, symmetric, df, c->s, o->coarse_blocks,
+                         o->coarse_block_min > 0 ? o->coarse_block_min : kHugeFront))) return bail(st);
 
   // workspaces
   const int m = o->restart;

@@ -714,7 +714,7 @@ int coarse_plan_stats(const GridDims& g, int r, int leaf_max, bool symmetric, in
 }
 
 int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef, int leaf_max,
-                 bool symmetric, bool df, cudaStream_t s, int blocks) {
+                 bool symmetric, bool df, cudaStream_t s, int blocks, int huge_min) {
   HELM_CUDA_TRY(cudaGetDevice(&cs.device));
   int grid = 0, grid_group = 0;
   if (int st = sweep_grid_size(&grid, &grid_group)) return st;
@@ -758,43 +758,94 @@ int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef
   HELM_CUDA_TRY(cudaMalloc(&d_upool, std::max<long long>(1, uoff) * sizeof(double2)));
   HELM_CUDA_TRY(cudaMalloc(&d_piv, maxbig * sizeof(int)));
   HELM_CUDA_TRY(cudaMalloc(&d_akk, maxbig * sizeof(double2)));
+  // fronts with at least huge_min eliminated nodes: blocked elimination (coarse_blocked.cu)
+  int max_huge_S = 0;
+  long long max_huge_ld = 0;
+  std::vector<std::vector<int>> normal(cs.nlevels), big_normal(cs.nlevels), huge(cs.nlevels);
+  for (int h = 0; h < cs.nlevels; ++h) {
+    for (int f : cs.level_fronts[h]) (desc[f].nS >= huge_min ? huge[h] : normal[h]).push_back(f);
+    for (int f : bigs[h])
+      if (desc[f].nS < huge_min) big_normal[h].push_back(f);
+    for (int f : huge[h]) {
+      max_huge_S = std::max(max_huge_S, desc[f].nS);
+      max_huge_ld = std::max<long long>(max_huge_ld, 2LL * desc[f].nS + desc[f].nB);
+    }
+  }
+  float2* d_w32 = nullptr;
+  double2 *d_dinv = nullptr, *d_xbuf = nullptr;
+  int* d_hpiv = nullptr;
+  if (max_huge_S > 0) {
+    HELM_CUDA_TRY(cudaMalloc(&d_w32, (size_t)max_huge_S * 64 * sizeof(float2)));
+    HELM_CUDA_TRY(cudaMalloc(&d_dinv, (size_t)64 * 64 * sizeof(double2)));
+    HELM_CUDA_TRY(cudaMalloc(&d_xbuf, (size_t)64 * max_huge_ld * sizeof(double2)));
+    HELM_CUDA_TRY(cudaMalloc(&d_hpiv, 64 * sizeof(int)));
+  }
+  auto free_setup = [&]() {
+    cudaFree(d_aug);
+    cudaFree(d_upool);
+    cudaFree(d_ents);
+    cudaFree(d_piv);
+    cudaFree(d_akk);
+    cudaFree(d_w32);
+    cudaFree(d_dinv);
+    cudaFree(d_xbuf);
+    cudaFree(d_hpiv);
+  };
   {
     KernelTimer kt(HELM_K_SETUP, s);
     for (int h = 0; h < cs.nlevels; ++h) {
-      const int nf = (int)cs.level_fronts[h].size();
-      fact_assemble_kernel<<<nf, 256, 0, s>>>(cs.d_desc, cs.d_level_list[h], d_aug, d_ents, coef, d_upool,
-                                              cs.d_kids, cs.d_cmap);
-      HELM_LAUNCH_CHECK();
+      int* d_normal = nullptr;
+      int* d_bign = nullptr;
+      if (upload(&d_normal, normal[h]) || upload(&d_bign, big_normal[h])) { free_setup(); return HELM_ECUDA; }
+      auto fail_level = [&](int st) { cudaFree(d_normal); cudaFree(d_bign); free_setup(); return st; };
+      if (!normal[h].empty()) {
+        fact_assemble_kernel<<<(int)normal[h].size(), 256, 0, s>>>(cs.d_desc, d_normal, d_aug, d_ents, coef, d_upool,
+                                                                   cs.d_kids, cs.d_cmap);
+        if (cudaGetLastError() != cudaSuccess) return fail_level(HELM_ECUDA);
+        count_launch();
+      }
+      for (int f : huge[h])
+        if (int st = big_front_assemble(desc[f], desc, P.kids, d_aug, d_ents, coef, d_upool, cs.d_cmap, s))
+          return fail_level(st);
       if (!smalls[h].empty()) {
         fact_gj_kernel<<<(int)smalls[h].size(), 512, 0, s>>>(cs.d_desc, cs.small_list[h], d_aug, cs.d_err);
-        HELM_LAUNCH_CHECK();
+        if (cudaGetLastError() != cudaSuccess) return fail_level(HELM_ECUDA);
+        count_launch();
       }
-      if (!bigs[h].empty()) {
+      if (!big_normal[h].empty()) {
         int maxS = 0, maxF = 0, maxLd = 0;
-        for (int f : bigs[h]) {
+        for (int f : big_normal[h]) {
           maxS = std::max(maxS, desc[f].nS);
           maxF = std::max(maxF, desc[f].nS + desc[f].nB);
           maxLd = std::max(maxLd, 2 * desc[f].nS + desc[f].nB);
         }
-        const dim3 gp((maxLd + 2047) / 2048, (unsigned)bigs[h].size());
-        const dim3 ge((maxF + 7) / 8, (unsigned)bigs[h].size());
+        const dim3 gp((maxLd + 2047) / 2048, (unsigned)big_normal[h].size());
+        const dim3 ge((maxF + 7) / 8, (unsigned)big_normal[h].size());
         for (int k = 0; k < maxS; ++k) {
-          gj_pivot_kernel<<<gp, 256, 0, s>>>(cs.d_desc, cs.big_list[h], d_aug, k, d_piv, d_akk, cs.d_err);
-          HELM_LAUNCH_CHECK();
-          gj_elim_kernel<<<ge, 256, 0, s>>>(cs.d_desc, cs.big_list[h], d_aug, k, d_piv, d_akk);
-          HELM_LAUNCH_CHECK();
+          gj_pivot_kernel<<<gp, 256, 0, s>>>(cs.d_desc, d_bign, d_aug, k, d_piv, d_akk, cs.d_err);
+          gj_elim_kernel<<<ge, 256, 0, s>>>(cs.d_desc, d_bign, d_aug, k, d_piv, d_akk);
+          if (cudaGetLastError() != cudaSuccess) return fail_level(HELM_ECUDA);
+          count_launch();
+          count_launch();
         }
       }
-      fact_extract_kernel<<<nf, 256, 0, s>>>(cs.d_desc, cs.d_level_list[h], d_aug, cs.d_factors, d_upool, df);
-      HELM_LAUNCH_CHECK();
+      for (int f : huge[h])
+        if (int st = big_front_eliminate(desc[f], d_aug, d_w32, d_hpiv, d_dinv, d_xbuf, cs.d_err, s)) return fail_level(st);
+      if (!normal[h].empty()) {
+        fact_extract_kernel<<<(int)normal[h].size(), 256, 0, s>>>(cs.d_desc, d_normal, d_aug, cs.d_factors, d_upool, df);
+        if (cudaGetLastError() != cudaSuccess) return fail_level(HELM_ECUDA);
+        count_launch();
+      }
+      for (int f : huge[h])
+        if (int st = big_front_extract(desc[f], d_aug, cs.d_factors, d_upool, df, s)) return fail_level(st);
+      // the level's device lists are read by kernels still queued: free them after the stream
+      if (cudaStreamSynchronize(s) != cudaSuccess) return fail_level(HELM_ECUDA);
+      cudaFree(d_normal);
+      cudaFree(d_bign);
     }
   }
   HELM_CUDA_TRY(cudaStreamSynchronize(s));
-  cudaFree(d_aug);
-  cudaFree(d_upool);
-  cudaFree(d_ents);
-  cudaFree(d_piv);
-  cudaFree(d_akk);
+  free_setup();
   int herr = 0;
   HELM_CUDA_TRY(cudaMemcpy(&herr, cs.d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (herr) { set_error("coarsest factorisation: zero or non-finite pivot"); return HELM_ENUMERIC; }

@@ -119,8 +119,9 @@ struct CoarseSolver {
 // symmetric: the operator is complex-symmetric (A = A^T), which halves the stored coupling.
 // df: store the factors as double-float and apply them on the FP32 pipes.
 // blocks: resident blocks of the solve kernel (0: all that fit on the device).
+// huge_min: fronts with at least this many eliminated nodes take the blocked elimination.
 int coarse_setup(CoarseSolver& cs, const GridDims& g, int r, const double2* coef, int leaf_max,
-                 bool symmetric, bool df, cudaStream_t s, int blocks = 0);
+                 bool symmetric, bool df, cudaStream_t s, int blocks = 0, int huge_min = 512);
 
 // e = A^-1 b for nrhs vectors (c128, [nrhs][nodes]).
 int coarse_solve(CoarseSolver& cs, const double2* b, double2* e, int nrhs, cudaStream_t s);
@@ -137,6 +138,22 @@ int coarse_plan_stats(const GridDims& g, int r, int leaf_max, bool symmetric, in
 // job with a dependency), raises that job's first completion target beyond anything the
 // solve can reach, so that the next solve's wait runs out and reports kErrSweepWait.
 int coarse_plant_unreachable_wait(CoarseSolver& cs, long long wait_cycles, int job, cudaStream_t s);
+
+// Large fronts (by default at least kHugeFront eliminated nodes; coarse_blocked.cu; in 3D their
+// boundaries reach thousands of nodes, where an elimination pass per pivot would stream
+// the whole front once per pivot): grid-wide
+// assembly of the augmented front [F | I_S], blocked Gauss-Jordan elimination of its first
+// nS columns (panels of 64 columns: pivot rows chosen by partial pivoting, the rest updated
+// by complex FP64 matrix products), and grid-wide extraction of M, G^T and the update
+// matrix.  Workspaces: w32 (nS x 64 complex FP32), piv (64 ints), dinv (64 x 64 complex),
+// xbuf (64 x ld complex).
+constexpr int kHugeFront = 512;
+int big_front_assemble(const FrontDesc& d, const std::vector<FrontDesc>& desc, const std::vector<int>& kids,
+                       double2* aug, const int2* d_ents, const double2* coef, const double2* upool, const int* d_cmap,
+                       cudaStream_t s);
+int big_front_eliminate(const FrontDesc& d, double2* aug, float2* w32, int* piv, double2* dinv, double2* xbuf, int* err,
+                        cudaStream_t s);
+int big_front_extract(const FrontDesc& d, const double2* aug, double2* factors, double2* upool, bool df, cudaStream_t s);
 
 // Waits for the stream and reports an error a solve kernel left in d_err.
 int coarse_status(const CoarseSolver& cs, cudaStream_t s);
