@@ -24,7 +24,8 @@ __constant__ float c_w[2][5] = {{0.25f, 0.5f, 0.25f, 0.f, 0.f},
 
 constexpr int kThreads = 256;
 constexpr int kFD = 16;              // fine down pass: coarse tile side
-constexpr int kTX = 32, kTY = 8;     // level-2 passes: tile of level-2 nodes
+constexpr int kL2Threads = 512;      // level-2 passes: threads per block, one per node
+constexpr int kTX = 32, kTY = 16;    // level-2 passes: tile of level-2 nodes
 constexpr int kFX = 32, kFY = 16;    // fine up pass: tile of fine nodes
 
 __device__ __forceinline__ float2 z2() { return make_float2(0.f, 0.f); }
@@ -93,6 +94,34 @@ __device__ __forceinline__ float2 coef2_sym(const Cycle2D& c, long long idx, int
   const long long n = c.g2.size;
   if (dy > 0 || (dy == 0 && dx >= 0)) return c.coef2[((dx + R) + W * (dy + R)) * n + idx];
   return c.coef2[((-dx + R) + W * (-dy + R)) * n + idx + dx + (long long)c.g2.N[0] * dy];
+}
+
+// The whole stencil of node idx, loaded into registers (the level-2 passes issue these
+// loads when they start, so that they are in flight while the block stages its tile).
+// No bounds checks: an own entry is read at idx, and a mirrored entry at idx + dx + N0 dy,
+// which for the lower-half offsets lies less than 2 N0 + 3 entries before idx and so inside
+// the upper-half planes of lower index (all planes are allocated and hold finite values);
+// a coefficient that belongs to no neighbour meets a zero x of the tile.
+template <int R>
+__device__ __forceinline__ void l2_coefs(const Cycle2D& c, long long idx, float2 (&cf)[(2 * R + 1) * (2 * R + 1)]) {
+  constexpr int W = 2 * R + 1;
+#pragma unroll
+  for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+    for (int dx = -R; dx <= R; ++dx) cf[(dx + R) + W * (dy + R)] = coef2_sym<R>(c, idx, dx, dy);
+}
+// sum_{dx,dy} A2(idx; dx, dy) x(idx + (dx, dy)) with x from a tile (row stride NX, zero
+// outside the grid) whose entry li is node idx, in the order of the rows and columns
+template <int R, int NX>
+__device__ __forceinline__ float2 l2_sum(const float2 (&cf)[(2 * R + 1) * (2 * R + 1)], const float2* __restrict__ sx,
+                                         int li) {
+  constexpr int W = 2 * R + 1;
+  float2 ax = z2();
+#pragma unroll
+  for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+    for (int dx = -R; dx <= R; ++dx) ax = cmac(ax, cf[(dx + R) + W * (dy + R)], sx[li + dx + NX * dy]);
+  return ax;
 }
 
 // (H x) at tile position li (row stride S) from tiles of x and c
@@ -234,40 +263,35 @@ __global__ void __launch_bounds__(kThreads) fine_down_kernel(const Cycle2D c, co
 // ---------------------------------------------------------------- level 2
 // A kTX x kTY tile of level-2 nodes; x2 = w2 D2^-1 r2 on the tile widened by R.
 template <int R>
-__global__ void __launch_bounds__(kThreads) l2_resid_kernel(const Cycle2D c, const float2* __restrict__ r2,
-                                                            float2* __restrict__ s2) {
+__global__ void __launch_bounds__(kL2Threads, 2) l2_resid_kernel(const Cycle2D c, const float2* __restrict__ r2,
+                                                                  float2* __restrict__ s2) {
   constexpr int NX = kTX + 2 * R, NY = kTY + 2 * R;
   __shared__ float2 sx[NX * NY];
   const GridDims& g = c.g2;
   const int N0 = g.N[0], N1 = g.N[1];
   const int T0x = blockIdx.x * kTX, T0y = blockIdx.y * kTY, rhs = blockIdx.z;
   const float2* rb = r2 + rhs * g.size;
-  for (int q = threadIdx.x; q < NX * NY; q += kThreads) {
-    const int gx = T0x - R + q % NX, gy = T0y - R + q / NX;
+  const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
+  const int gx = T0x + tx, gy = T0y + ty;
+  const bool in = gx < N0 && gy < N1;
+  const long long idx = in ? gx + (long long)N0 * gy : 0;
+  float2 cf[(2 * R + 1) * (2 * R + 1)];
+  l2_coefs<R>(c, idx, cf);
+  for (int q = threadIdx.x; q < NX * NY; q += kL2Threads) {
+    const int sxg = T0x - R + q % NX, syg = T0y - R + q / NX;
     float2 xx = z2();
-    if (gx >= 0 && gx < N0 && gy >= 0 && gy < N1) {
-      const long long idx = gx + (long long)N0 * gy;
-      xx = cscale(cmul(c.dinv2[idx], rb[idx]), c.w2);
+    if (sxg >= 0 && sxg < N0 && syg >= 0 && syg < N1) {
+      const long long j = sxg + (long long)N0 * syg;
+      xx = cscale(cmul(c.dinv2[j], rb[j]), c.w2);
     }
     sx[q] = xx;
   }
   __syncthreads();
-  const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
-  const int gx = T0x + tx, gy = T0y + ty;
-  if (gx >= N0 || gy >= N1) return;
-  const long long idx = gx + (long long)N0 * gy;
-  float2 ax = z2();
-#pragma unroll
-  for (int dy = -R; dy <= R; ++dy) {
-    if (gy + dy < 0 || gy + dy >= N1) continue;
-#pragma unroll
-    for (int dx = -R; dx <= R; ++dx) {
-      if (gx + dx < 0 || gx + dx >= N0) continue;
-      ax = cmac(ax, coef2_sym<R>(c, idx, dx, dy), sx[(tx + R + dx) + NX * (ty + R + dy)]);
-    }
-  }
+  if (!in) return;
+  const float2 ax = l2_sum<R, NX>(cf, sx, (tx + R) + NX * (ty + R));
   s2[rhs * g.size + idx] = rb[idx] - ax;
 }
+static_assert(kTX * kTY == kL2Threads, "one thread per level-2 node of the tile");
 
 // b3 = R2 s2 in c128 by tiles: a kRX x kRY tile of level-3 nodes per block, its level-2
 // cover (widened by RW) staged in shared memory, then the restriction along x and along y
@@ -334,16 +358,16 @@ __device__ __forceinline__ float2 prolong_1d(const float2* __restrict__ e, int f
   acc.y = fmaf(0.125f, p[-stride].y + p[stride].y, acc.y);
   return acc;
 }
-template <int PW>
+template <int PW, int NT>
 __device__ __forceinline__ void prolong_tile(const float2* __restrict__ ce, int J0x, int J0y, int MX, int MY,
                                              float2* __restrict__ u, float2* __restrict__ out, int X0, int Y0,
                                              int NX, int NY) {
-  for (int q = threadIdx.x; q < MY * NX; q += kThreads) {
+  for (int q = threadIdx.x; q < MY * NX; q += NT) {
     const int jy = q / NX, lx = q % NX;
     u[q] = prolong_1d<PW>(ce + jy * MX, X0 + lx, J0x, 1);
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < NY * NX; q += kThreads) {
+  for (int q = threadIdx.x; q < NY * NX; q += NT) {
     const int ly = q / NX, lx = q % NX;
     out[q] = prolong_1d<PW>(u + lx, Y0 + ly, J0y, NX);
   }
@@ -352,7 +376,7 @@ __device__ __forceinline__ void prolong_tile(const float2* __restrict__ ce, int 
 // level-2 post pass on a kTX x kTY tile: x2 = w2 D2^-1 r2 + P2 e3 on the tile widened by
 // R, then one Jacobi step at the tile nodes
 template <int R, int PW>
-__global__ void __launch_bounds__(kThreads) l2_up_kernel(const Cycle2D c, const float2* __restrict__ r2,
+__global__ void __launch_bounds__(kL2Threads, 2) l2_up_kernel(const Cycle2D c, const float2* __restrict__ r2,
                                                          const double2* __restrict__ e3, float2* __restrict__ y2) {
   constexpr int NX = kTX + 2 * R, NY = kTY + 2 * R;
   constexpr int MX = NX / 2 + PW + 2, MY = NY / 2 + PW + 2;   // coarse cover of the widened tile
@@ -368,7 +392,13 @@ __global__ void __launch_bounds__(kThreads) l2_up_kernel(const Cycle2D c, const 
   const int J0x = (X0 - PW + 1) >> 1, J0y = (Y0 - PW + 1) >> 1;
   const float2* rb = r2 + rhs * g.size;
   const double2* eb = e3 + rhs * g3.size;
-  for (int q = threadIdx.x; q < MX * MY; q += kThreads) {
+  const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
+  const int gx = T0x + tx, gy = T0y + ty;
+  const bool in = gx < N0 && gy < N1;
+  const long long idx = in ? gx + (long long)N0 * gy : 0;
+  float2 cf[(2 * R + 1) * (2 * R + 1)];
+  l2_coefs<R>(c, idx, cf);
+  for (int q = threadIdx.x; q < MX * MY; q += kL2Threads) {
     const int Jx = J0x + q % MX, Jy = J0y + q / MX;
     float2 e = z2();
     if (Jx >= 0 && Jx < g3.N[0] && Jy >= 0 && Jy < g3.N[1]) {
@@ -378,32 +408,20 @@ __global__ void __launch_bounds__(kThreads) l2_up_kernel(const Cycle2D c, const 
     se[q] = e;
   }
   __syncthreads();
-  prolong_tile<PW>(se, J0x, J0y, MX, MY, su, sp, X0, Y0, NX, NY);
+  prolong_tile<PW, kL2Threads>(se, J0x, J0y, MX, MY, su, sp, X0, Y0, NX, NY);
   __syncthreads();
-  for (int q = threadIdx.x; q < NX * NY; q += kThreads) {
-    const int gx = X0 + q % NX, gy = Y0 + q / NX;
+  for (int q = threadIdx.x; q < NX * NY; q += kL2Threads) {
+    const int sxg = X0 + q % NX, syg = Y0 + q / NX;
     float2 xx = z2();
-    if (gx >= 0 && gx < N0 && gy >= 0 && gy < N1) {
-      const long long idx = gx + (long long)N0 * gy;
-      xx = cscale(cmul(c.dinv2[idx], rb[idx]), c.w2) + sp[q];
+    if (sxg >= 0 && sxg < N0 && syg >= 0 && syg < N1) {
+      const long long j = sxg + (long long)N0 * syg;
+      xx = cscale(cmul(c.dinv2[j], rb[j]), c.w2) + sp[q];
     }
     sx[q] = xx;
   }
   __syncthreads();
-  const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
-  const int gx = T0x + tx, gy = T0y + ty;
-  if (gx >= N0 || gy >= N1) return;
-  const long long idx = gx + (long long)N0 * gy;
-  float2 ax = z2();
-#pragma unroll
-  for (int dy = -R; dy <= R; ++dy) {
-    if (gy + dy < 0 || gy + dy >= N1) continue;
-#pragma unroll
-    for (int dx = -R; dx <= R; ++dx) {
-      if (gx + dx < 0 || gx + dx >= N0) continue;
-      ax = cmac(ax, coef2_sym<R>(c, idx, dx, dy), sx[(tx + R + dx) + NX * (ty + R + dy)]);
-    }
-  }
+  if (!in) return;
+  const float2 ax = l2_sum<R, NX>(cf, sx, (tx + R) + NX * (ty + R));
   const float2 xc = sx[(tx + R) + NX * (ty + R)];
   y2[rhs * g.size + idx] = xc + cscale(cmul(c.dinv2[idx], rb[idx] - ax), c.w2);
 }
@@ -436,7 +454,7 @@ __global__ void __launch_bounds__(kThreads) fine_up_kernel(const Cycle2D c, cons
     se[q] = (Jx >= 0 && Jx < g2.N[0] && Jy >= 0 && Jy < g2.N[1]) ? yb[Jx + (long long)g2.N[0] * Jy] : z2();
   }
   __syncthreads();
-  prolong_tile<PW>(se, J0x, J0y, MX, MY, su, sp, X0, Y0, NX, NY);
+  prolong_tile<PW, kThreads>(se, J0x, J0y, MX, MY, su, sp, X0, Y0, NX, NY);
   __syncthreads();
   for (int q = threadIdx.x; q < NX * NY; q += kThreads) {
     const int gx = X0 + q % NX, gy = Y0 + q / NX;
@@ -491,8 +509,10 @@ __device__ __forceinline__ float2 shdn(float2 v) {
 
 // one fine row of a warp's two columns: x1, c (and the halo columns' from the neighbours)
 struct RsRow {
-  float2 xl, xe, xo, xr;   // x1 at columns 2I - 1, 2I, 2I + 1, 2I + 2
-  float2 cl, ce, co, cr;   // c at the same columns (4th order only)
+  float2 xe, xo;           // x1 at columns 2I, 2I + 1
+  float2 ue, uo;           // c x1 at 2I, 2I + 1 (4th order only)
+  float2 ce, co;           // c at 2I, 2I + 1
+  float2 de, dob;          // w1 / diagonal at 2I, 2I + 1 (fine up pass)
   float2 ve, vo;           // v at 2I, 2I + 1
 };
 // loaded values of one fine row
@@ -543,33 +563,55 @@ __device__ __forceinline__ float2 diag_c(float2 cc, float ih2) {
   return make_float2(float(20.0 / 6.0) * ih2 - float(8.0 / 12.0) * cc.x, -float(8.0 / 12.0) * cc.y);
 }
 
-// (H x1) at the column of `mid` whose left / right neighbours are xl / xr in the three rows
+// (H x1) at a node from sums over its neighbours: sf, se the sums of x1 over the face and
+// the corner neighbours, tf the sum of c x1 over the face neighbours.  Grouping the face
+// weights wf - (c_m + c_f) / 24 of the 4th-order stencil (Eq. disc4thCompact) by term:
+//   H x = d x_m + wf sf + we se - (c_m sf + tf) / 24,     d = 20 / (6 h^2) - (8 / 12) c_m;
+// 2nd order (5 points): H x = (4 / h^2 - c_m) x_m - sf / h^2.  Each node's c x1 is formed
+// once, when its row is formed, and used by the three rows around it.
 template <int ORDER>
-__device__ __forceinline__ float2 rs_apply(float2 cm, float2 xm, float2 xlm, float2 xrm, float2 clm, float2 crm,
-                                           float2 xu, float2 cu, float2 xd, float2 cd, float2 xul, float2 xur,
-                                           float2 xdl, float2 xdr, float ih2) {
+__device__ __forceinline__ float2 rs_apply(float2 cm, float2 xm, float2 sf, float2 se, float2 tf, float ih2) {
   const float2 diag = diag_c<ORDER>(cm, ih2);
-  if (ORDER == 0) {
-    float2 sum = xlm + xrm;
-    sum = sum + xu;
-    sum = sum + xd;
-    return cmul(diag, xm) - cscale(sum, ih2);
-  }
+  if (ORDER == 0) return cmul(diag, xm) - cscale(sf, ih2);
   const float wface = float(-4.0 / 6.0) * ih2, wedge = float(-1.0 / 6.0) * ih2;
-  auto face = [&](float2 xf, float2 cf) {
-    return make_float2(wface - float(1.0 / 24.0) * (cm.x + cf.x), -float(1.0 / 24.0) * (cm.y + cf.y));
-  };
-  // the tile kernels' order: rows -1, 0, +1, columns -1, 0, +1
   float2 acc = cmul(diag, xm);
-  acc = acc + cscale(xul, wedge);
-  acc = cmac(acc, face(xu, cu), xu);
-  acc = acc + cscale(xur, wedge);
-  acc = cmac(acc, face(xlm, clm), xlm);
-  acc = cmac(acc, face(xrm, crm), xrm);
-  acc = acc + cscale(xdl, wedge);
-  acc = cmac(acc, face(xd, cd), xd);
-  acc = acc + cscale(xdr, wedge);
+  acc.x = fmaf(wface, sf.x, acc.x);
+  acc.y = fmaf(wface, sf.y, acc.y);
+  acc.x = fmaf(wedge, se.x, acc.x);
+  acc.y = fmaf(wedge, se.y, acc.y);
+  const float2 q = cmac(tf, cm, sf);
+  acc.x = fmaf(float(-1.0 / 24.0), q.x, acc.x);
+  acc.y = fmaf(float(-1.0 / 24.0), q.y, acc.y);
   return acc;
+}
+
+// c x1 of a freshly formed row (4th order)
+template <int ORDER>
+__device__ __forceinline__ void rs_row_prod(RsRow& R) {
+  if (ORDER == 1) {
+    R.ue = cmul(R.ce, R.xe);
+    R.uo = cmul(R.co, R.xo);
+  }
+}
+
+// H x1 at the two columns 2I, 2I + 1 of the middle row md, with rows up / dn above and
+// below.  The column left of 2I is lane - 1's 2I + 1 and the one right of 2I + 1 is
+// lane + 1's 2I, so the neighbour sums take one shuffle per column pair: faces of 2I are
+// md(2I - 1), md(2I + 1), up(2I), dn(2I); its corners up / dn at 2I - 1 and 2I + 1.
+template <int ORDER>
+__device__ __forceinline__ void rs_apply_row(const RsRow& up, const RsRow& md, const RsRow& dn, float ih2, float2& he,
+                                             float2& ho) {
+  const float2 a = up.xo + dn.xo, b = up.xe + dn.xe;   // vertical pairs at 2I + 1, 2I
+  const float2 sfe = (shup(md.xo) + md.xo) + b, sfo = (md.xe + shdn(md.xe)) + a;
+  float2 see = z2(), seo = z2(), tfe = z2(), tfo = z2();
+  if (ORDER == 1) {
+    see = shup(a) + a;
+    seo = b + shdn(b);
+    tfe = (shup(md.uo) + md.uo) + (up.ue + dn.ue);
+    tfo = (md.ue + shdn(md.ue)) + (up.uo + dn.uo);
+  }
+  he = rs_apply<ORDER>(md.ce, md.xe, sfe, see, tfe, ih2);
+  ho = rs_apply<ORDER>(md.co, md.xo, sfo, seo, tfo, ih2);
 }
 
 template <int ORDER, int RW, int SEG>
@@ -616,7 +658,7 @@ __global__ void __launch_bounds__(32 * kRsWarps, kRsMinBlocks) fine_down_rs_kern
     acc[q] = z2();
     // zero rows before the first: the residual rows formed from them only feed coarse
     // rows above the segment, whose accumulators are cleared before they are reused
-    W[q].xl = W[q].xe = W[q].xo = W[q].xr = W[q].cl = W[q].ce = W[q].co = W[q].cr = W[q].ve = W[q].vo = z2();
+    W[q].xe = W[q].xo = W[q].ue = W[q].uo = W[q].ce = W[q].co = W[q].de = W[q].dob = W[q].ve = W[q].vo = z2();
   }
 
   // fine row t into ring slot t % kRing (zeros outside the grid, and for rows past the
@@ -653,12 +695,7 @@ __global__ void __launch_bounds__(32 * kRsWarps, kRsMinBlocks) fine_down_rs_kern
   auto fill = [&](const RsLoad& ld, RsRow& R) {
     node(ld.ve, ld.ke, gxe, ld.gy, R.xe, R.ce, R.ve);
     node(ld.vo, ld.ko, gxo, ld.gy, R.xo, R.co, R.vo);
-    R.xl = shup(R.xo);
-    R.xr = shdn(R.xe);
-    if (ORDER == 1) {
-      R.cl = shup(R.co);
-      R.cr = shdn(R.ce);
-    }
+    rs_row_prod<ORDER>(R);
   };
 
   // fine row t = t0 + S of the warp's visit; S is a compile-time step of the six-fold
@@ -681,13 +718,9 @@ __global__ void __launch_bounds__(32 * kRsWarps, kRsMinBlocks) fine_down_rs_kern
     const RsRow& md = W[(S + 2) % 3];   // row t - 1 (the residual row)
     const int y = Ybase + t - 1;
     const bool iny = y >= 0 && y < N1;
-    float2 re = z2(), ro = z2();
-    if (iny && ine)
-      re = md.ve - rs_apply<ORDER>(md.ce, md.xe, md.xl, md.xo, md.cl, md.co, up.xe, up.ce, cur.xe, cur.ce, up.xl,
-                                   up.xo, cur.xl, cur.xo, ih2);
-    if (iny && ino)
-      ro = md.vo - rs_apply<ORDER>(md.co, md.xo, md.xe, md.xr, md.ce, md.cr, up.xo, up.co, cur.xo, cur.co, up.xe,
-                                   up.xr, cur.xe, cur.xr, ih2);
+    float2 he, ho;
+    rs_apply_row<ORDER>(up, md, cur, ih2, he, ho);
+    const float2 re = iny && ine ? md.ve - he : z2(), ro = iny && ino ? md.vo - ho : z2();
     // restriction along x, in weight order
     float2 rx = z2();
     if constexpr (RW == 2) {
@@ -791,8 +824,9 @@ __global__ void __launch_bounds__(32 * kRsWarps, kRsMinBlocks) fine_up_rs_kernel
   RsRow W[3];
   float2 pe[3], po[3];   // coarse rows prolongated along x to the columns 2I, 2I + 1
 #pragma unroll
-  for (int q = 0; q < 3; ++q)
-    W[q].xl = W[q].xe = W[q].xo = W[q].xr = W[q].cl = W[q].ce = W[q].co = W[q].cr = W[q].ve = W[q].vo = z2();
+  for (int q = 0; q < 3; ++q) {
+    W[q].xe = W[q].xo = W[q].ue = W[q].uo = W[q].ce = W[q].co = W[q].de = W[q].dob = W[q].ve = W[q].vo = z2();
+  }
 
   // fine row t into ring slot t % kRing, and with it (t even) coarse row t / 2 + 2 of y2
   // into coarse slot (t / 2 + 2) % kCRing; zeros outside the grids
@@ -836,11 +870,12 @@ __global__ void __launch_bounds__(32 * kRsWarps, kRsMinBlocks) fine_up_rs_kernel
       e.y = fmaf(0.125f, yl.y + yr.y, e.y);
     }
   };
-  auto node = [&](float4 vv, float kk, float gx, float gy, float2 py, float2& x, float2& cc, float2& vo) {
+  auto node = [&](float4 vv, float kk, float gx, float gy, float2 py, float2& x, float2& cc, float2& di, float2& vo) {
     const float cre = omega2 * kk;
     cc = make_float2(cre, -cre * (gx + gy));
     vo = make_float2(vv.x, vv.y);
-    x = cscale(cmul(rcp_c(diag_c<ORDER>(cc, ih2)), vo), w1) + py;
+    di = cscale(rcp_c(diag_c<ORDER>(cc, ih2)), w1);
+    x = cmul(di, vo) + py;
   };
 
   auto step = [&](int t0, auto Sc, auto Checked) {
@@ -878,31 +913,20 @@ __global__ void __launch_bounds__(32 * kRsWarps, kRsMinBlocks) fine_up_rs_kernel
     RsRow& cur = W[S % 3];
     RsLoad ld;
     load(t, ld);
-    cur.xe = cur.xo = cur.ce = cur.co = cur.ve = cur.vo = z2();
-    if (iny && ine) node(ld.ve, ld.ke, gxe, ld.gy, pye, cur.xe, cur.ce, cur.ve);
-    if (iny && ino) node(ld.vo, ld.ko, gxo, ld.gy, pyo, cur.xo, cur.co, cur.vo);
-    cur.xl = shup(cur.xo);
-    cur.xr = shdn(cur.xe);
-    if constexpr (ORDER == 1) {
-      cur.cl = shup(cur.co);
-      cur.cr = shdn(cur.ce);
-    }
+    cur.xe = cur.xo = cur.ce = cur.co = cur.de = cur.dob = cur.ve = cur.vo = z2();
+    if (iny && ine) node(ld.ve, ld.ke, gxe, ld.gy, pye, cur.xe, cur.ce, cur.de, cur.ve);
+    if (iny && ino) node(ld.vo, ld.ko, gxo, ld.gy, pyo, cur.xo, cur.co, cur.dob, cur.vo);
+    rs_row_prod<ORDER>(cur);
     // z at fine row t - 1 (rows Y0 ... Y0 + RS - 1, i.e. 3 <= t <= RS + 2)
     const RsRow& up = W[(S + 1) % 3];
     const RsRow& md = W[(S + 2) % 3];
     const int ym = y - 1;
     const bool out = own && ym >= Y0 && ym < Y0 + P::RS && ym < N1;
     const long long row = (long long)ym * N0;
-    if (out && ine) {
-      const float2 res = md.ve - rs_apply<ORDER>(md.ce, md.xe, md.xl, md.xo, md.cl, md.co, up.xe, up.ce, cur.xe, cur.ce,
-                                                 up.xl, up.xo, cur.xl, cur.xo, ih2);
-      zb[row + xe] = md.xe + cscale(cmul(rcp_c(diag_c<ORDER>(md.ce, ih2)), res), w1);
-    }
-    if (out && ino) {
-      const float2 res = md.vo - rs_apply<ORDER>(md.co, md.xo, md.xe, md.xr, md.ce, md.cr, up.xo, up.co, cur.xo, cur.co,
-                                                 up.xe, up.xr, cur.xe, cur.xr, ih2);
-      zb[row + xo] = md.xo + cscale(cmul(rcp_c(diag_c<ORDER>(md.co, ih2)), res), w1);
-    }
+    float2 he, ho;
+    rs_apply_row<ORDER>(up, md, cur, ih2, he, ho);
+    if (out && ine) zb[row + xe] = md.xe + cmul(md.de, md.ve - he);
+    if (out && ino) zb[row + xo] = md.xo + cmul(md.dob, md.vo - ho);
   };
 
   // coarse rows 0 and 1 travel with fine row 0
@@ -1032,8 +1056,8 @@ int cycle2d_fine_down(const Cycle2D& c, const float4* v, float2* r2, int nrhs, c
 int cycle2d_l2_resid(const Cycle2D& c, const float2* r2, float2* s2, int nrhs, cudaStream_t s) {
   KernelTimer kt(HELM_K_STENCIL, s);
   const dim3 grid = tiles(c.g2, kTX, kTY, nrhs);
-  if (c.r2 == 1) l2_resid_kernel<1><<<grid, kThreads, 0, s>>>(c, r2, s2);
-  else if (c.r2 == 2) l2_resid_kernel<2><<<grid, kThreads, 0, s>>>(c, r2, s2);
+  if (c.r2 == 1) l2_resid_kernel<1><<<grid, kL2Threads, 0, s>>>(c, r2, s2);
+  else if (c.r2 == 2) l2_resid_kernel<2><<<grid, kL2Threads, 0, s>>>(c, r2, s2);
   else { set_error("fused level-2 pass: unsupported stencil radius"); return HELM_EINVAL; }
   HELM_LAUNCH_CHECK();
   return 0;
@@ -1054,7 +1078,7 @@ int cycle2d_l2_up(const Cycle2D& c, const float2* r2, const double2* e3, float2*
   const dim3 grid = tiles(c.g2, kTX, kTY, nrhs);
 #define HELM_L2U(R, PW)                                                                 \
   if (c.r2 == R && c.pw2 == PW) {                                                       \
-    l2_up_kernel<R, PW><<<grid, kThreads, 0, s>>>(c, r2, e3, y2);                       \
+    l2_up_kernel<R, PW><<<grid, kL2Threads, 0, s>>>(c, r2, e3, y2);                     \
     HELM_LAUNCH_CHECK();                                                                \
     return 0;                                                                           \
   }
