@@ -798,6 +798,22 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
   c->fine.gam[0] = c->d_gam;
   c->fine.gam[1] = c->d_gam + c->g[0].N[0];
   c->fine.gam[2] = c->d_gam + c->g[0].N[0] + c->g[0].N[1];
+  for (int a = 0, off2 = 0; a < o->dim; off2 += c->g[0].N[a], ++a) {
+    // the real-coefficient box of the double-float operator: indices with gamma zero at
+    // themselves and their neighbours; left empty unless they form one contiguous range
+    const int na = c->g[0].N[a];
+    auto zero = [&](int i) { return i < 0 || i >= na || gam[off2 + i] == 0.0; };
+    int lo = -1, hi = -2;
+    for (int i = 0; i < na; ++i)
+      if (zero(i - 1) && zero(i) && zero(i + 1)) {
+        if (lo < 0) lo = i;
+        hi = i;
+      }
+    bool contiguous = lo >= 0;
+    for (int i = lo; contiguous && i <= hi; ++i) contiguous = zero(i - 1) && zero(i) && zero(i + 1);
+    c->fine.rc_lo[a] = contiguous ? lo : 1;
+    c->fine.rc_hi[a] = contiguous ? hi : 0;
+  }
   {
     std::vector<float> g32(gam.begin(), gam.end());
     if (int st = dmalloc(&c->d_gam32, tot * sizeof(float))) return bail(st);
@@ -811,6 +827,10 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
   // that gamma_x + gamma_y (+ gamma_z) + beta enters every coefficient
   c->fine_cyc = c->fine;
   if (o->cslp_beta != 0.0) {
+    for (int a = 0; a < 3; ++a) {   // the shifted coefficients are complex everywhere
+      c->fine_cyc.rc_lo[a] = 1;
+      c->fine_cyc.rc_hi[a] = 0;
+    }
     std::vector<double> gs(gam);
     for (int i = 0; i < c->g[0].N[0]; ++i) gs[i] += o->cslp_beta;
     std::vector<float> gs32(gs.begin(), gs.end());

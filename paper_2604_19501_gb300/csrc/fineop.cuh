@@ -100,7 +100,22 @@ __device__ __forceinline__ float2 df_hi(float2 v) { return v; }
 __device__ __forceinline__ float2 df_hi(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 df_lo(float4 v) { return make_float2(v.z, v.w); }
 
-template <typename TZ>
+//
+// RC: every coefficient c the node reads (its own and its face neighbours') is real, i.e.
+// the absorbing profile is zero there (df_real_coef); the products with the imaginary
+// parts, exact zeros, are then left out: the result has the same value (at most the sign
+// of a zero differs).
+template <bool RC>
+__device__ __forceinline__ void cacc_add_c(racc& re, racc& im, cdd x, float2 z, float s) {
+  if (RC) {
+    racc_add_ddf(re, x.re, s * z.x);
+    racc_add_ddf(im, x.re, s * z.y);
+  } else {
+    cacc_add_cz(re, im, x, z, s);
+  }
+}
+
+template <typename TZ, bool RC = false>
 __device__ __forceinline__ cdd fine_apply_df_t(const FineOp& op, const float4* __restrict__ cdf,
                                                const TZ* __restrict__ z, long long p, int i, int j, int k,
                                                dd ih2, dd ih2_6, dd inv24) {
@@ -136,7 +151,7 @@ __device__ __forceinline__ cdd fine_apply_df_t(const FineOp& op, const float4* _
     }
     const dd lr = dd_mul(racc_dd(Lr), ih2), li = dd_mul(racc_dd(Li), ih2);
     racc Wr{lr.hi, lr.lo}, Wi{li.hi, li.lo};
-    cacc_add_cz(Wr, Wi, cc, zc, -1.f);
+    cacc_add_c<RC>(Wr, Wi, cc, zc, -1.f);
     if constexpr (LO) {
       // ih2 L_lo - c_c z_c,lo
       const float2 h = cscale(l_lo, ih2.hi) - cmul(make_float2(cc.re.hi, cc.im.hi), df_lo(zc4));
@@ -155,8 +170,8 @@ __device__ __forceinline__ cdd fine_apply_df_t(const FineOp& op, const float4* _
   {
     const float pr = mc * zc.x, pi = mc * zc.y;
     const float2 ez = make_float2(fmaf(mc, zc.x, -pr), fmaf(mc, zc.y, -pi));
-    cacc_add_cz(Mr, Mi, cc, make_float2(pr, pi), 1.f);
-    cacc_add_cz(Mr, Mi, cc, ez, 1.f);
+    cacc_add_c<RC>(Mr, Mi, cc, make_float2(pr, pi), 1.f);
+    cacc_add_c<RC>(Mr, Mi, cc, ez, 1.f);
   }
   if constexpr (LO) {
     const float2 zl = df_lo(zc4);
@@ -185,7 +200,7 @@ __device__ __forceinline__ cdd fine_apply_df_t(const FineOp& op, const float4* _
           racc_add(Zr, zq.x);
           racc_add(Zi, zq.y);
           const cdd cq = cdd_load(cdf[q]);
-          cacc_add_cz(Mr, Mi, cq, zq, 1.f);
+          cacc_add_c<RC>(Mr, Mi, cq, zq, 1.f);
           if constexpr (LO) {
             const float2 zl = df_lo(zq4);
             l_lo = l_lo - cscale(zl, wf);
@@ -202,9 +217,9 @@ __device__ __forceinline__ cdd fine_apply_df_t(const FineOp& op, const float4* _
   }
   // mass = c_c Mz + Mcz
   racc_add_dd(Mr, cc.re, dd_of(Zr));
-  racc_add_dd(Mr, dd_neg(cc.im), dd_of(Zi));
+  if (!RC) racc_add_dd(Mr, dd_neg(cc.im), dd_of(Zi));
   racc_add_dd(Mi, cc.re, dd_of(Zi));
-  racc_add_dd(Mi, cc.im, dd_of(Zr));
+  if (!RC) racc_add_dd(Mi, cc.im, dd_of(Zr));
   const cdd L{racc_dd(Lr), racc_dd(Li)};
   const cdd mass{racc_dd(Mr), racc_dd(Mi)};
   cdd h = cdd_sub(cdd_scale(L, ih2_6), cdd_scale(mass, inv24));
@@ -217,10 +232,28 @@ __device__ __forceinline__ cdd fine_apply_df_t(const FineOp& op, const float4* _
   return h;
 }
 
+// True when the absorbing profile is zero at node (i, j, k) and at its face neighbours,
+// so that the coefficients c = omega^2 kappa^2 (1 - i gamma) the operator reads there are
+// real: the node lies in the box FineOp::rc_lo / rc_hi, set up from the gamma tables.
+__device__ __forceinline__ bool df_real_coef(const FineOp& op, int i, int j, int k) {
+  return i >= op.rc_lo[0] && i <= op.rc_hi[0] && j >= op.rc_lo[1] && j <= op.rc_hi[1] &&
+         (op.g.dim == 2 || (k >= op.rc_lo[2] && k <= op.rc_hi[2]));
+}
+
+// H z for a node, with the real-coefficient form where it applies (divergent only in
+// warps that straddle the inner edge of the absorbing layer)
+template <typename TZ>
+__device__ __forceinline__ cdd fine_apply_df_any(const FineOp& op, const float4* __restrict__ cdf,
+                                                 const TZ* __restrict__ z, long long p, int i, int j, int k,
+                                                 dd ih2, dd ih2_6, dd inv24) {
+  if (df_real_coef(op, i, j, k)) return fine_apply_df_t<TZ, true>(op, cdf, z, p, i, j, k, ih2, ih2_6, inv24);
+  return fine_apply_df_t<TZ, false>(op, cdf, z, p, i, j, k, ih2, ih2_6, inv24);
+}
+
 __device__ __forceinline__ cdd fine_apply_df(const FineOp& op, const float4* __restrict__ cdf,
                                              const float2* __restrict__ z, long long p, int i, int j, int k,
                                              dd ih2, dd ih2_6, dd inv24) {
-  return fine_apply_df_t<float2>(op, cdf, z, p, i, j, k, ih2, ih2_6, inv24);
+  return fine_apply_df_any<float2>(op, cdf, z, p, i, j, k, ih2, ih2_6, inv24);
 }
 
 }  // namespace helm

@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(kThreads) true_residual_df_kernel(FineOp op, D
        p += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
     node_coords(op.g, p, i, j, k);
-    const cdd hx = fine_apply_df_t<float4>(op, cdf, xd, p, i, j, k, K.ih2, K.ih2_6, K.inv24);
+    const cdd hx = fine_apply_df_any<float4>(op, cdf, xd, p, i, j, k, K.ih2, K.ih2_6, K.inv24);
     const double2 bv = b[p];
     const dd br = split_d(bv.x), bi = split_d(bv.y);
     racc rr{br.hi, br.lo}, ri{bi.hi, bi.lo};
