@@ -29,6 +29,24 @@ constexpr int kTX = 32, kTY = 16;    // level-2 passes: tile of level-2 nodes
 constexpr int kFX = 32, kFY = 16;    // fine up pass: tile of fine nodes
 
 __device__ __forceinline__ float2 z2() { return make_float2(0.f, 0.f); }
+
+// asynchronous global -> shared copies (zero-filled when ok is false: source size 0, the
+// source address then being the array's base, which is valid)
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool ok) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 // 1 / d as conj(d) / |d|^2 with one IEEE round-to-nearest reciprocal
 __device__ __forceinline__ float2 rcp_c(float2 d) {
   const float r = __frcp_rn(fmaf(d.x, d.x, d.y * d.y));
@@ -83,32 +101,34 @@ __device__ __forceinline__ float2 fine_apply_win(const float2 (&wx)[3][3], const
   return acc;
 }
 
-// Entry (dx, dy) of the level-2 stencil at node idx.  The Galerkin operator R H P with
-// P = 4 R^T of a complex-symmetric H is complex-symmetric, so an entry of the lower half
-// of the stencil (dy < 0, or dy = 0 and dx < 0) is the mirrored entry stored at the
-// neighbour; reading those from the neighbour keeps DRAM reads to the upper half of the
-// planes (the shifted reads hit L1/L2).
+// Entry o = (dx + R) + W (dy + R) of the level-2 stencil at node idx.  The Galerkin
+// operator R H P with P = 4 R^T of a complex-symmetric H is complex-symmetric, so an entry
+// of the lower half of the stencil (dy < 0, or dy = 0 and dx < 0) is the mirrored entry
+// stored at the neighbour; reading those from the neighbour keeps DRAM reads to the upper
+// half of the planes (the shifted reads hit L1/L2).  Offsets are 32-bit (the launchers
+// check ncoef x nodes < 2^31).  No bounds checks: an own entry is read at idx, and a
+// mirrored entry at idx + dx + N0 dy, which for the lower-half offsets lies less than
+// 2 N0 + 3 entries before idx and so inside the upper-half planes of lower index (all
+// planes are allocated and hold finite values); a coefficient that belongs to no
+// neighbour meets a zero x of the tile.
 template <int R>
-__device__ __forceinline__ float2 coef2_sym(const Cycle2D& c, long long idx, int dx, int dy) {
+__device__ __forceinline__ float2 l2_coef(const Cycle2D& c, int idx, int o) {
   constexpr int W = 2 * R + 1;
-  const long long n = c.g2.size;
-  if (dy > 0 || (dy == 0 && dx >= 0)) return c.coef2[((dx + R) + W * (dy + R)) * n + idx];
-  return c.coef2[((-dx + R) + W * (-dy + R)) * n + idx + dx + (long long)c.g2.N[0] * dy];
+  const int dx = o % W - R, dy = o / W - R;
+  const bool up = dy > 0 || (dy == 0 && dx >= 0);
+  const int plane = up ? o : (-dx + R) + W * (-dy + R);
+  return c.coef2[plane * (int)c.g2.size + idx + (up ? 0 : dx + c.g2.N[0] * dy)];
 }
-
-// The whole stencil of node idx, loaded into registers (the level-2 passes issue these
-// loads when they start, so that they are in flight while the block stages its tile).
-// No bounds checks: an own entry is read at idx, and a mirrored entry at idx + dx + N0 dy,
-// which for the lower-half offsets lies less than 2 N0 + 3 entries before idx and so inside
-// the upper-half planes of lower index (all planes are allocated and hold finite values);
-// a coefficient that belongs to no neighbour meets a zero x of the tile.
+// The whole stencil of node idx, loaded into registers (the up pass issues these loads
+// when it starts, so that they are in flight while the block stages its tile).
 template <int R>
-__device__ __forceinline__ void l2_coefs(const Cycle2D& c, long long idx, float2 (&cf)[(2 * R + 1) * (2 * R + 1)]) {
-  constexpr int W = 2 * R + 1;
+__device__ __forceinline__ void l2_coefs(const Cycle2D& c, int idx, float2 (&cf)[(2 * R + 1) * (2 * R + 1)]) {
 #pragma unroll
-  for (int dy = -R; dy <= R; ++dy)
-#pragma unroll
-    for (int dx = -R; dx <= R; ++dx) cf[(dx + R) + W * (dy + R)] = coef2_sym<R>(c, idx, dx, dy);
+  for (int o = 0; o < (2 * R + 1) * (2 * R + 1); ++o) cf[o] = l2_coef<R>(c, idx, o);
+}
+// the launchers' check for the 32-bit offsets of l2_coef
+inline bool l2_offsets_fit(const Cycle2D& c, long long ntiles) {
+  return ntiles <= INT32_MAX && (long long)(2 * c.r2 + 1) * (2 * c.r2 + 1) * c.g2.size <= INT32_MAX;
 }
 // sum_{dx,dy} A2(idx; dx, dy) x(idx + (dx, dy)) with x from a tile (row stride NX, zero
 // outside the grid) whose entry li is node idx, in the order of the rows and columns
@@ -261,37 +281,94 @@ __global__ void __launch_bounds__(kThreads) fine_down_kernel(const Cycle2D c, co
 }
 
 // ---------------------------------------------------------------- level 2
-// A kTX x kTY tile of level-2 nodes; x2 = w2 D2^-1 r2 on the tile widened by R.
+static_assert(kTX * kTY == kL2Threads, "one thread per level-2 node of the tile");
+
+// Level-2 residual s2 = r2 - H2 x2, x2 = w2 D2^-1 r2, as a persistent kernel: block b walks
+// the tiles b, b + G, b + 2G, ... (G resident blocks).  The next tile's inputs are in flight while the current tile is
+// summed: its staged values (1 / diag and r2 on the widened tile) go by cp.async into
+// the other half of a double buffer, and each stencil coefficient register is reloaded
+// for the next tile right after its product with the current tile is formed.
+// Coefficient offsets are 32-bit (the launcher checks ncoef x nodes < 2^31).  Tiles of
+// kPX x kPY level-2 nodes, one per thread; tile t = (bx, by, rhs) in row-major order.
+constexpr int kPThreads = 256;
+constexpr int kPX = 32, kPY = 8;
+static_assert(kPX * kPY == kPThreads, "one thread per level-2 node of the tile");
 template <int R>
-__global__ void __launch_bounds__(kL2Threads, 2) l2_resid_kernel(const Cycle2D c, const float2* __restrict__ r2,
-                                                                  float2* __restrict__ s2) {
-  constexpr int NX = kTX + 2 * R, NY = kTY + 2 * R;
-  __shared__ float2 sx[NX * NY];
+__global__ void __launch_bounds__(kPThreads, 2) l2_resid_pers_kernel(const Cycle2D c, const float2* __restrict__ r2,
+                                                                      float2* __restrict__ s2, int ntx, int nty,
+                                                                      int ntiles) {
+  constexpr int W = 2 * R + 1, NC = W * W;
+  constexpr int NX = kPX + 2 * R, NY = kPY + 2 * R, NS = NX * NY;
+  constexpr int SPT = (NS + kPThreads - 1) / kPThreads;   // staged entries per thread
+  __shared__ float2 sx[NS];
+  __shared__ __align__(16) float2 sdr[2][2][NS];          // [buffer][1/diag, r2][entry]
   const GridDims& g = c.g2;
   const int N0 = g.N[0], N1 = g.N[1];
-  const int T0x = blockIdx.x * kTX, T0y = blockIdx.y * kTY, rhs = blockIdx.z;
-  const float2* rb = r2 + rhs * g.size;
-  const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
-  const int gx = T0x + tx, gy = T0y + ty;
-  const bool in = gx < N0 && gy < N1;
-  const long long idx = in ? gx + (long long)N0 * gy : 0;
-  float2 cf[(2 * R + 1) * (2 * R + 1)];
-  l2_coefs<R>(c, idx, cf);
-  for (int q = threadIdx.x; q < NX * NY; q += kL2Threads) {
-    const int sxg = T0x - R + q % NX, syg = T0y - R + q / NX;
-    float2 xx = z2();
-    if (sxg >= 0 && sxg < N0 && syg >= 0 && syg < N1) {
-      const long long j = sxg + (long long)N0 * syg;
-      xx = cscale(cmul(c.dinv2[j], rb[j]), c.w2);
+  const int tx = threadIdx.x % kPX, ty = threadIdx.x / kPX;
+  const int li = (tx + R) + NX * (ty + R);
+  // the node of tile t this thread sums: flat index within its right-hand side, and rhs
+  auto node = [&](int t, int& idx, int& rhs, bool& in) {
+    const int bx = t % ntx, by = (t / ntx) % nty;
+    rhs = t / (ntx * nty);
+    const int gx = bx * kPX + tx, gy = by * kPY + ty;
+    in = gx < N0 && gy < N1;
+    idx = in ? gx + N0 * gy : 0;
+  };
+  auto stage_copy = [&](int t, int buf) {   // cp.async of the staged inputs of tile t
+    const int bx = t % ntx, by = (t / ntx) % nty, rhs = t / (ntx * nty);
+    const float2* rb = r2 + rhs * g.size;
+#pragma unroll
+    for (int k = 0; k < SPT; ++k) {
+      const int q = threadIdx.x + k * kPThreads;
+      if (q < NS) {
+        const int sxg = bx * kPX - R + q % NX, syg = by * kPY - R + q / NX;
+        const bool ok = sxg >= 0 && sxg < N0 && syg >= 0 && syg < N1;
+        const int j = ok ? sxg + N0 * syg : 0;
+        cp_async8(smem_addr(&sdr[buf][0][q]), c.dinv2 + j, ok);
+        cp_async8(smem_addr(&sdr[buf][1][q]), rb + j, ok);
+      }
     }
-    sx[q] = xx;
+    cp_commit();
+  };
+  int t = blockIdx.x;
+  if (t >= ntiles) return;
+  float2 cf[NC];
+  int idx, rhs;
+  bool in;
+  node(t, idx, rhs, in);
+#pragma unroll
+  for (int o = 0; o < NC; ++o) cf[o] = l2_coef<R>(c, idx, o);
+  float2 ro = r2[idx + rhs * g.size];
+  stage_copy(t, 0);
+  for (int buf = 0; t < ntiles; t += gridDim.x, buf ^= 1) {
+    cp_wait<0>();   // this thread's copies of tile t have landed
+#pragma unroll
+    for (int k = 0; k < SPT; ++k) {
+      const int q = threadIdx.x + k * kPThreads;
+      if (q < NS) sx[q] = cscale(cmul(sdr[buf][0][q], sdr[buf][1][q]), c.w2);
+    }
+    const int tn = t + gridDim.x;
+    const bool more = tn < ntiles;
+    if (more) stage_copy(tn, buf ^ 1);
+    int idxn = 0, rhsn = 0;
+    bool inn = false;
+    if (more) node(tn, idxn, rhsn, inn);
+    __syncthreads();
+    float2 ax = z2();
+#pragma unroll
+    for (int o = 0; o < NC; ++o) {
+      const int dx = o % W - R, dy = o / W - R;
+      ax = cmac(ax, cf[o], sx[li + dx + NX * dy]);
+      if (more) cf[o] = l2_coef<R>(c, idxn, o);
+    }
+    if (in) s2[idx + rhs * g.size] = ro - ax;
+    if (more) ro = r2[idxn + rhsn * g.size];
+    idx = idxn;
+    rhs = rhsn;
+    in = inn;
+    __syncthreads();
   }
-  __syncthreads();
-  if (!in) return;
-  const float2 ax = l2_sum<R, NX>(cf, sx, (tx + R) + NX * (ty + R));
-  s2[rhs * g.size + idx] = rb[idx] - ax;
 }
-static_assert(kTX * kTY == kL2Threads, "one thread per level-2 node of the tile");
 
 // b3 = R2 s2 in c128 by tiles: a kRX x kRY tile of level-3 nodes per block, its level-2
 // cover (widened by RW) staged in shared memory, then the restriction along x and along y
@@ -395,7 +472,7 @@ __global__ void __launch_bounds__(kL2Threads, 2) l2_up_kernel(const Cycle2D c, c
   const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
   const int gx = T0x + tx, gy = T0y + ty;
   const bool in = gx < N0 && gy < N1;
-  const long long idx = in ? gx + (long long)N0 * gy : 0;
+  const int idx = in ? gx + N0 * gy : 0;
   float2 cf[(2 * R + 1) * (2 * R + 1)];
   l2_coefs<R>(c, idx, cf);
   for (int q = threadIdx.x; q < MX * MY; q += kL2Threads) {
@@ -541,21 +618,6 @@ static_assert(kRing >= kAhead + 2, "a ring slot is refilled two steps after its 
 static_assert(kRing == 6, "ring slots are the steps of the six-fold unroll");
 constexpr int kRsMinBlocks = 5;                   // resident blocks per SM the kernels are shaped for
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool ok) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, bool ok) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, bool ok) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 template <int ORDER>
 __device__ __forceinline__ float2 diag_c(float2 cc, float ih2) {
@@ -961,6 +1023,17 @@ __global__ void __launch_bounds__(32 * kRsWarps, kRsMinBlocks) fine_up_rs_kernel
   cp_wait<0>();
 }
 
+// SMs of the current device (the persistent level-2 passes run two blocks on each)
+inline int resident_sms() {
+  static const int sms = [] {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }();
+  return sms;
+}
+
 inline dim3 tiles(const GridDims& g, int tx, int ty, int nrhs) {
   return dim3((g.N[0] + tx - 1) / tx, (g.N[1] + ty - 1) / ty, nrhs);
 }
@@ -1055,9 +1128,15 @@ int cycle2d_fine_down(const Cycle2D& c, const float4* v, float2* r2, int nrhs, c
 
 int cycle2d_l2_resid(const Cycle2D& c, const float2* r2, float2* s2, int nrhs, cudaStream_t s) {
   KernelTimer kt(HELM_K_STENCIL, s);
-  const dim3 grid = tiles(c.g2, kTX, kTY, nrhs);
-  if (c.r2 == 1) l2_resid_kernel<1><<<grid, kL2Threads, 0, s>>>(c, r2, s2);
-  else if (c.r2 == 2) l2_resid_kernel<2><<<grid, kL2Threads, 0, s>>>(c, r2, s2);
+  const int ntx = (c.g2.N[0] + kPX - 1) / kPX, nty = (c.g2.N[1] + kPY - 1) / kPY;
+  const long long nt = (long long)ntx * nty * nrhs;
+  if (!l2_offsets_fit(c, nt)) {
+    set_error("fused level-2 pass: grid too large for 32-bit coefficient offsets");
+    return HELM_EINVAL;
+  }
+  const int grid = (int)std::min<long long>(nt, 2LL * resident_sms());
+  if (c.r2 == 1) l2_resid_pers_kernel<1><<<grid, kPThreads, 0, s>>>(c, r2, s2, ntx, nty, (int)nt);
+  else if (c.r2 == 2) l2_resid_pers_kernel<2><<<grid, kPThreads, 0, s>>>(c, r2, s2, ntx, nty, (int)nt);
   else { set_error("fused level-2 pass: unsupported stencil radius"); return HELM_EINVAL; }
   HELM_LAUNCH_CHECK();
   return 0;
@@ -1076,6 +1155,10 @@ int cycle2d_l2_restrict(const Cycle2D& c, const float2* s2, double2* b3, int nrh
 int cycle2d_l2_up(const Cycle2D& c, const float2* r2, const double2* e3, float2* y2, int nrhs, cudaStream_t s) {
   KernelTimer kt(HELM_K_STENCIL, s);
   const dim3 grid = tiles(c.g2, kTX, kTY, nrhs);
+  if (!l2_offsets_fit(c, 0)) {
+    set_error("fused level-2 pass: grid too large for 32-bit coefficient offsets");
+    return HELM_EINVAL;
+  }
 #define HELM_L2U(R, PW)                                                                 \
   if (c.r2 == R && c.pw2 == PW) {                                                       \
     l2_up_kernel<R, PW><<<grid, kL2Threads, 0, s>>>(c, r2, e3, y2);                     \
