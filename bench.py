@@ -112,6 +112,9 @@ def parse(argv=None):
     ap.add_argument("--coarse-block-min", type=int, default=0,
                     help="coarsest fronts with at least this many eliminated nodes take the blocked "
                          "elimination at set-up (helm_opts.coarse_block_min; 0 = the library's default)")
+    ap.add_argument("--arnoldi-passes", type=int, default=0,
+                    help="Gram-Schmidt passes of the mixed-precision Arnoldi step (helm_opts.arnoldi_passes; "
+                         "0 = the library's default)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the side measurements of the 2D run (FP64 path, points-per-wavelength and "
                          "grid-size sweeps), which run after the timed region")
@@ -464,7 +467,8 @@ def make_solver(wl, args, dev, precision=None, cslp=None, coarse_refine=0):
                   alpha3=wl["alpha3"], stencil=wl["order"], intergrid=wl["intergrid"], cycle=args.cycle,
                   jacobi_w=wl["jw"], precision=precision or args.precision, restart=args.restart,
                   stream=torch.cuda.current_stream(dev).cuda_stream, cslp_beta=args.cslp if cslp is None else cslp,
-                  solver=args.solver, coarse_refine=coarse_refine, coarse_block_min=args.coarse_block_min)
+                  solver=args.solver, coarse_refine=coarse_refine, coarse_block_min=args.coarse_block_min,
+                  arnoldi_passes=args.arnoldi_passes)
 
 
 def timed_solves(s, q, args, reps, warm=1):
@@ -589,7 +593,7 @@ def our_arm(args):
                intergrid=wl["intergrid"], cycle=args.cycle, jacobi_w=wl["jw"],
                precision=args.precision, restart=args.restart, stream=stream.cuda_stream,
                max_rhs=max(1, args.block or args.sources), graphs=args.graphs, cslp_beta=args.cslp,
-               solver=args.solver)
+               solver=args.solver, coarse_block_min=args.coarse_block_min, arnoldi_passes=args.arnoldi_passes)
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
     info = s.info()

@@ -44,7 +44,7 @@ class Solver:
                  smoother="jacobi", jacobi_w=(0.8, 0.8), rb_w=1.0, precision="fp64", restart=10,
                  max_rhs=1, stream=None, fuse_cycle=True, graphs=False, cslp_beta=0.0,
                  solver="fgmres", coarse_blocks=0, coarse_refine=0,
-                 coarse_block_min=0):
+                 coarse_block_min=0, arnoldi_passes=0):
         self.n = tuple(int(v) for v in n)
         self.dim = len(self.n)
         o = HelmOpts()
@@ -76,6 +76,7 @@ class Solver:
         o.coarse_blocks = int(coarse_blocks)
         o.coarse_refine = int(coarse_refine)
         o.coarse_block_min = int(coarse_block_min)
+        o.arnoldi_passes = int(arnoldi_passes)
         if stream is None:
             import torch
 

@@ -49,6 +49,7 @@ class HelmOpts(ctypes.Structure):
         ("coarse_blocks", ctypes.c_int),
         ("coarse_refine", ctypes.c_int),
         ("coarse_block_min", ctypes.c_int),
+        ("arnoldi_passes", ctypes.c_int),
     ]
 
 

@@ -436,6 +436,9 @@ int run_iteration(helm_ctx* c, const std::tuple<int, int, unsigned long long>& k
 // rotations and convergence test, and leaves the block's Arnoldi steps once it has
 // converged.  Per right-hand side the arithmetic is that of a single solve.
 // Layouts: V [m+1][B][n], Z [m][B][n], w and r [B][n].
+// Gram-Schmidt passes of the mixed-precision Arnoldi step when helm_opts.arnoldi_passes is 0
+constexpr int kDefaultArnoldiPasses = 2;
+
 int fgmres_block(helm_ctx* c, const double2* q, double2* p, int B, double tol, int maxit, helm_stats* out) {
   const long long n = c->g[0].size;
   const int m = c->o.restart;
@@ -491,7 +494,8 @@ int fgmres_block(helm_ctx* c, const double2* q, double2* p, int B, double tol, i
           if (!act[r]) continue;
           if (df) {
             if (int st = k_arnoldi_df(c->ks[r], c->fine, c->cdf, (const float2*)Zp(j, r),
-                                      reinterpret_cast<float4*>(c->w) + (size_t)r * n, Vd(0, r), vstride, j, c->s))
+                                      reinterpret_cast<float4*>(c->w) + (size_t)r * n, Vd(0, r), vstride, j,
+                                      c->o.arnoldi_passes ? c->o.arnoldi_passes : kDefaultArnoldiPasses, c->s))
               return st;
           } else if (int st = k_arnoldi(c->ks[r], c->fine, c->kap64, Zp(j, r), zp, c->w + (size_t)r * n, Vp(0, r),
                                         vstride, j, c->s)) {
@@ -705,6 +709,7 @@ int helm_default_opts(helm_opts* o) {
   o->coarse_blocks = 0;
   o->coarse_refine = 0;
   o->coarse_block_min = 0;
+  o->arnoldi_passes = 0;
   return HELM_OK;
 }
 
@@ -725,6 +730,7 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
   if (o->coarse_blocks < 0) return fail(HELM_EINVAL, "coarse_blocks must be >= 0");
   if (o->coarse_refine < 0 || o->coarse_refine > 8) return fail(HELM_EINVAL, "coarse_refine must be in [0, 8]");
   if (o->coarse_block_min < 0) return fail(HELM_EINVAL, "coarse_block_min must be >= 0");
+  if (o->arnoldi_passes < 0 || o->arnoldi_passes > 2) return fail(HELM_EINVAL, "arnoldi_passes must be 0, 1 or 2");
   if (o->stencil != HELM_STENCIL_2ND && o->stencil != HELM_STENCIL_4TH) return fail(HELM_EINVAL, "bad stencil");
   if (o->intergrid < HELM_INTERGRID_FW || o->intergrid > HELM_INTERGRID_LEVDEP)
     return fail(HELM_EINVAL, "bad intergrid transfer");

@@ -6,7 +6,9 @@
 //   arnoldi_update   w' = w - V h1 (not stored) and the second pass h2 = V^H w', ||w'||^2
 //   arnoldi_small    H(:, j) = h1 + h2, ||w' - V h2||, Givens rotations, residual estimate
 //   arnoldi_normalize v_{j+1} = (w - V (h1 + h2)) / ||w' - V h2||
-// (classical Gram-Schmidt with one re-orthogonalisation, CGS2).  Every reduction keeps
+// (classical Gram-Schmidt with one re-orthogonalisation, CGS2).  In the mixed precision
+// the step can instead take one double-float pass (arnoldi_cgs_df_t: matvec, h = V^H w and
+// ||w||^2 in one kernel; helm_opts.arnoldi_passes = 1).  Every reduction keeps
 // per-thread partial sums in shared memory over a fixed grid, reduces each block once and
 // lets the last block sum the block partials in block order, so the result does not
 // depend on scheduling.
@@ -563,9 +565,60 @@ __global__ void __launch_bounds__(kThreads, NV <= 7 ? 3 : 2) arnoldi_update_df_t
   if (reduce_finish_df(sdf, NV + 1, part, counter, out) && tid == 0) arnoldi_small_body(st, NV - 1, st.m);
 }
 
+// One-pass Arnoldi step (helm_opts.arnoldi_passes = 1): w = H z and the projections
+// h = V^H w in double-float arithmetic (classical Gram-Schmidt once, about 48-bit) with
+// ||w||^2, per-thread accumulators in registers.  The last block zeroes h1 and runs the
+// small step, which reads h from h2 and ||w||^2 from h2[j + 1]: the new column's norm is
+// sqrt(||w||^2 - ||h||^2), exact for an orthonormal V; the subtraction loses digits only
+// when w lies almost inside span(V), where the Givens estimate drops to the level of
+// convergence and the iteration ends.
+template <int NV>
+__global__ void __launch_bounds__(kThreads, 2) arnoldi_cgs_df_t(FineOp op, DfConsts K, const float4* __restrict__ cdf,
+                                                                const float2* __restrict__ z, float4* __restrict__ w,
+                                                                const float4* __restrict__ V, long long vstride,
+                                                                KrylovState st) {
+  extern __shared__ double2 sacc[];
+  float4* sdf = reinterpret_cast<float4*>(sacc);
+  const int tid = threadIdx.x;
+  float4 acc[NV + 1];
+#pragma unroll
+  for (int q = 0; q <= NV; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (long long p = blockIdx.x * (long long)blockDim.x + tid; p < op.g.size; p += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    node_coords(op.g, p, i, j, k);
+    const float4 wv = cdd_store(fine_apply_df(op, cdf, z, p, i, j, k, K.ih2, K.ih2_6, K.inv24));
+    w[p] = wv;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) df_cmacc(acc[q], V[q * vstride + p], wv);
+    df_cmacc(acc[NV], wv, wv);
+  }
+#pragma unroll
+  for (int q = 0; q <= NV; ++q) sdf[q * blockDim.x + tid] = acc[q];
+  if (reduce_finish_df(sdf, NV + 1, st.part, st.counter, st.h2) && tid == 0) {
+    for (int i = 0; i < NV; ++i) st.h1[i] = make_double2(0.0, 0.0);
+    arnoldi_small_body(st, NV - 1, st.m);
+  }
+}
+
 template <int NV>
 int arnoldi_df_launch(int bl, size_t sm, const FineOp& op, const DfConsts& K, const float4* cdf, const float2* z,
-                      float4* w, const float4* V, long long vstride, const KrylovState& st, cudaStream_t s) {
+                      float4* w, const float4* V, long long vstride, const KrylovState& st, int passes,
+                      cudaStream_t s) {
+  if (passes == 1) {
+    // one wave of the blocks that fit (two per SM at most, by the launch bounds)
+    static const int blc = [sm] {
+      cudaFuncSetAttribute(arnoldi_cgs_df_t<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      int per_sm = 0, dev = 0, sms = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, arnoldi_cgs_df_t<NV>, kThreads, sm);
+      return std::max(1, per_sm * std::max(sms, 1));
+    }();
+    KernelTimer kt(HELM_K_ARNOLDI_MATVEC, s);
+    arnoldi_cgs_df_t<NV><<<std::min(bl, blc), kThreads, sm, s>>>(op, K, cdf, z, w, V, vstride, st);
+    HELM_LAUNCH_CHECK();
+    return 0;
+  }
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(arnoldi_matvec_df_t<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -717,7 +770,7 @@ int k_start_cycle_df(const KrylovState& st, long long n, const double2* r, float
 }
 
 int k_arnoldi_df(const KrylovState& st, const FineOp& op, const float4* cdf, const float2* z, float4* w,
-                 const float4* V, long long vstride, int j, cudaStream_t s) {
+                 const float4* V, long long vstride, int j, int passes, cudaStream_t s) {
   const long long n = op.g.size;
   const int bl = grid_blocks(n);
   const int nv = j + 1;
@@ -734,7 +787,7 @@ int k_arnoldi_df(const KrylovState& st, const FineOp& op, const float4* cdf, con
     int st2 = 0;
     switch (nv) {
 #define HELM_NV(N) \
-  case N: st2 = arnoldi_df_launch<N>(bl, sm, op, K, cdf, z, w, V, vstride, st, s); break;
+  case N: st2 = arnoldi_df_launch<N>(bl, sm, op, K, cdf, z, w, V, vstride, st, passes, s); break;
       HELM_NV(1) HELM_NV(2) HELM_NV(3) HELM_NV(4) HELM_NV(5) HELM_NV(6) HELM_NV(7) HELM_NV(8) HELM_NV(9) HELM_NV(10)
 #undef HELM_NV
     }

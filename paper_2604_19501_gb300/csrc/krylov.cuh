@@ -44,8 +44,9 @@ int k_normalize(const KrylovState& st, long long n, const double2* w, const doub
 // Double-float variants (mixed precision): V and w stored as float4 (hi, lo) pairs.
 int k_coef_df(const FineOp& op, const double* kap64, float4* cdf, cudaStream_t s);
 int k_start_cycle_df(const KrylovState& st, long long n, const double2* r, float4* v0, cudaStream_t s);
+// passes: 2 = CGS2 (FP32 first pass, double-float second pass), 1 = one double-float pass.
 int k_arnoldi_df(const KrylovState& st, const FineOp& op, const float4* cdf, const float2* z, float4* w,
-                 const float4* V, long long vstride, int j, cudaStream_t s);
+                 const float4* V, long long vstride, int j, int passes, cudaStream_t s);
 int k_normalize_df(const KrylovState& st, long long n, const float4* w, const float4* V, long long vstride, int j,
                    float4* vout, cudaStream_t s);
 // y = R^-1 g (k x k) and x += Z y; for a c64 basis (zp = P32) also xd = x as double-float.

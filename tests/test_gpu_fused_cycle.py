@@ -99,3 +99,25 @@ def test_fused_solve_matches_unfused_and_oracle(order, ig, alpha3):
     assert abs(st[0]["iterations"] - stu[0]["iterations"]) <= 1
     assert rel(p.ravel(), xo) < 1e-5
     assert rel(p, pu) < 1e-5
+
+
+@pytest.mark.parametrize("passes", [1, 2])
+def test_arnoldi_passes_match_oracle(passes):
+    """The mixed-precision Arnoldi step with one double-float Gram-Schmidt pass (norm from
+    ||w||^2 - ||h||^2) and with CGS2, on the layered medium with restarts (FGMRES(5)):
+    iteration count within one of the oracle's FGMRES, solution within 1e-5."""
+    import workloads
+
+    n = (160, 160)
+    k2 = workloads.layered_faulted_2d(128, 16, seed=21)
+    c = Case(n, abc=16, order="4th", intergrid="cubic", alpha3=1.0045, G_ppw=12, kappa2=k2)
+    q = workloads.point_source(n)
+    s = c.solver(precision="mixed", jacobi_w=(0.89, 0.89), restart=5, arnoldi_passes=passes)
+    p, st = s.solve(_t(q), tol=1e-6, maxit=400)
+    p = _n(p)
+    s.close()
+    cy = OC.Cycle(c.hier, weights=(0.89, 0.89))
+    xo, info = OK.fgmres(lambda x: c.hier.A[0] @ x, q.ravel(), cy, tol=1e-6, maxit=400, restart=5)
+    assert st[0]["converged"] and info["converged"]
+    assert abs(st[0]["iterations"] - info["iterations"]) <= 1, (st[0]["iterations"], info["iterations"])
+    assert rel(p.ravel(), xo) < 1e-5
