@@ -458,7 +458,7 @@ def cycle_bytes(info, n1, n3):
     return n1 * (20 + 20 + 8) + n2 * level2 + n3 * 32
 
 
-def make_solver(wl, args, dev, precision=None, cslp=None, coarse_refine=0):
+def make_solver(wl, args, dev, precision=None, cslp=None, coarse_refine=0, max_rhs=1):
     import torch
 
     from paper_2604_19501_gb300 import Solver
@@ -468,7 +468,7 @@ def make_solver(wl, args, dev, precision=None, cslp=None, coarse_refine=0):
                   jacobi_w=wl["jw"], precision=precision or args.precision, restart=args.restart,
                   stream=torch.cuda.current_stream(dev).cuda_stream, cslp_beta=args.cslp if cslp is None else cslp,
                   solver=args.solver, coarse_refine=coarse_refine, coarse_block_min=args.coarse_block_min,
-                  arnoldi_passes=args.arnoldi_passes)
+                  arnoldi_passes=args.arnoldi_passes, max_rhs=max_rhs)
 
 
 def timed_solves(s, q, args, reps, warm=1):
@@ -570,6 +570,29 @@ def side_measurements(args, wl, p_main, main_ms, main_its, dev, log):
                       "ms_per_solve": main_ms, "value": nodes / 1e3 / main_ms})
         out["size_sweep"] = {"rows": sizes, "ppw": args.ppw,
                              "note": "the run's method and medium recipe at growing interior size (+ the same layer)"}
+    if args.dim == 2 and args.method == "paper" and args.solver == "fgmres" and args.cslp == 0.0 and args.sources <= 1:
+        # the batched multi-source workload: 64 seeded surface sources at 1024^2 + the layer,
+        # FGMRES blocks of 32 against 64 single-source solves on one context each
+        sargs = argparse.Namespace(**vars(args))
+        sargs.n, sargs.sources = 1024, 64
+        wlb = workload(sargs)
+        nb = n_nodes(wlb)
+        qb = torch.from_numpy(wlb["q"]).to(dev)
+        sb = make_solver(wlb, sargs, dev, max_rhs=32)
+        ms_b, st_b, _ = timed_solves(sb, qb, sargs, reps=1)
+        sb.close()
+        s1 = make_solver(wlb, sargs, dev)
+        ms_1, st_1, _ = timed_solves(s1, qb, sargs, reps=1)
+        s1.close()
+        out["batched"] = {
+            "sources": 64, "cells": wlb["n"][0], "block": 32, "ms_per_batch": ms_b, "ms_per_batch_single": ms_1,
+            "value": 64 * nb / 1e3 / ms_b, "value_single": 64 * nb / 1e3 / ms_1, "unit": UNIT,
+            "speedup": ms_1 / ms_b, "iterations_last": st_b["iterations"],
+            "note": "64 seeded surface sources on the run's medium recipe at 1024^2 cells + the layer: one "
+                    "helm_solve of all 64 in FGMRES blocks of 32 right-hand sides (cycle and coarsest solve once "
+                    "per block iteration) against the same 64 solved one at a time (max_rhs = 1); one timed "
+                    "call each after one untimed"}
+        log(f"batched 64 sources: blocks of 32 {ms_b:.1f} ms, single {ms_1:.1f} ms ({ms_1 / ms_b:.2f}x)")
     return out
 
 
