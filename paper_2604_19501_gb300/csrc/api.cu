@@ -39,6 +39,7 @@ struct helm_ctx {
   double* d_gam = nullptr;
   float* d_gam32 = nullptr;
   FineOp fine_cyc{};                           // the cycle's fine operator (with the CSLP shift)
+  RcBox rcbox{{1, 1, 1}, {0, 0, 0}};           // real-coefficient box of fine (empty until set up)
   double* d_gam_cyc = nullptr;                 // shifted absorbing tables (CSLP only)
   float* d_gam32_cyc = nullptr;
   double* kap64 = nullptr;
@@ -493,7 +494,7 @@ int fgmres_block(helm_ctx* c, const double2* q, double2* p, int B, double tol, i
         for (int r = 0; r < B; ++r) {
           if (!act[r]) continue;
           if (df) {
-            if (int st = k_arnoldi_df(c->ks[r], c->fine, c->cdf, (const float2*)Zp(j, r),
+            if (int st = k_arnoldi_df(c->ks[r], c->fine, c->rcbox, c->cdf, (const float2*)Zp(j, r),
                                       reinterpret_cast<float4*>(c->w) + (size_t)r * n, Vd(0, r), vstride, j,
                                       c->o.arnoldi_passes ? c->o.arnoldi_passes : kDefaultArnoldiPasses, c->s))
               return st;
@@ -543,7 +544,7 @@ int fgmres_block(helm_ctx* c, const double2* q, double2* p, int B, double tol, i
         return st;
       // mixed precision: the true residual in double-float from the copy of x just written
       if (df) {
-        if (int st = k_true_residual_df(c->ks[r], c->fine, c->cdf, q + (size_t)r * n, xd, c->r + (size_t)r * n, c->s))
+        if (int st = k_true_residual_df(c->ks[r], c->fine, c->rcbox, c->cdf, q + (size_t)r * n, xd, c->r + (size_t)r * n, c->s))
           return st;
       } else if (int st = k_true_residual(c->ks[r], c->fine, c->kap64, q + (size_t)r * n, p + (size_t)r * n,
                                           c->r + (size_t)r * n, c->s)) {
@@ -626,7 +627,7 @@ int stationary_block(helm_ctx* c, const double2* q, double2* p, int B, double to
         float4* xd = df ? c->xd + (size_t)r * n : nullptr;
         if (int st = k_add_correction(n, xr, (const char*)c->Z + (size_t)r * n * zes, zp, xd, c->s)) return st;
         if (df) {
-          if (int st = k_true_residual_df(c->ks[r], c->fine, c->cdf, qc + (size_t)r * n, xd, c->r + (size_t)r * n, c->s))
+          if (int st = k_true_residual_df(c->ks[r], c->fine, c->rcbox, c->cdf, qc + (size_t)r * n, xd, c->r + (size_t)r * n, c->s))
             return st;
         } else if (int st = k_true_residual(c->ks[r], c->fine, c->kap64, qc + (size_t)r * n, xr, c->r + (size_t)r * n,
                                             c->s)) {
@@ -817,8 +818,8 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
       }
     bool contiguous = lo >= 0;
     for (int i = lo; contiguous && i <= hi; ++i) contiguous = zero(i - 1) && zero(i) && zero(i + 1);
-    c->fine.rc_lo[a] = contiguous ? lo : 1;
-    c->fine.rc_hi[a] = contiguous ? hi : 0;
+    c->rcbox.lo[a] = contiguous ? lo : 1;
+    c->rcbox.hi[a] = contiguous ? hi : 0;
   }
   {
     std::vector<float> g32(gam.begin(), gam.end());
@@ -833,10 +834,6 @@ int helm_setup(const helm_opts* o, const double* kappa2, helm_ctx** out) {
   // that gamma_x + gamma_y (+ gamma_z) + beta enters every coefficient
   c->fine_cyc = c->fine;
   if (o->cslp_beta != 0.0) {
-    for (int a = 0; a < 3; ++a) {   // the shifted coefficients are complex everywhere
-      c->fine_cyc.rc_lo[a] = 1;
-      c->fine_cyc.rc_hi[a] = 0;
-    }
     std::vector<double> gs(gam);
     for (int i = 0; i < c->g[0].N[0]; ++i) gs[i] += o->cslp_beta;
     std::vector<float> gs32(gs.begin(), gs.end());

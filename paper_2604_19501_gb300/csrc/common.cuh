@@ -107,10 +107,14 @@ struct FineOp {
   double omega2;
   const double* gam[3];    // per-axis gamma tables (device), length N[a]
   const float* gam32[3];   // the same tables in FP32 (FP32 kernels read these)
-  // per axis, the index range [rc_lo, rc_hi] where gamma is zero at the index and at both
-  // neighbours, so that a node inside the box and its face neighbours have real
-  // coefficients c (empty by default: no node is assumed to have them)
-  int rc_lo[3] = {1, 1, 1}, rc_hi[3] = {0, 0, 0};
+};
+
+// Per axis, the index range [lo, hi] where the absorbing profile is zero at the index and
+// at both neighbours, so that a node inside the box and its face neighbours have real
+// coefficients c (lo > hi: an empty range).  Kept apart from FineOp: a larger FineOp
+// parameter changed the register allocation of the FP64 operator kernels.
+struct RcBox {
+  int lo[3], hi[3];
 };
 
 // The per-axis absorbing profile in the arithmetic type of a kernel.

@@ -234,26 +234,26 @@ __device__ __forceinline__ cdd fine_apply_df_t(const FineOp& op, const float4* _
 
 // True when the absorbing profile is zero at node (i, j, k) and at its face neighbours,
 // so that the coefficients c = omega^2 kappa^2 (1 - i gamma) the operator reads there are
-// real: the node lies in the box FineOp::rc_lo / rc_hi, set up from the gamma tables.
-__device__ __forceinline__ bool df_real_coef(const FineOp& op, int i, int j, int k) {
-  return i >= op.rc_lo[0] && i <= op.rc_hi[0] && j >= op.rc_lo[1] && j <= op.rc_hi[1] &&
-         (op.g.dim == 2 || (k >= op.rc_lo[2] && k <= op.rc_hi[2]));
+// real: the node lies in the box, set up from the gamma tables.
+__device__ __forceinline__ bool df_real_coef(const RcBox& box, int dim, int i, int j, int k) {
+  return i >= box.lo[0] && i <= box.hi[0] && j >= box.lo[1] && j <= box.hi[1] &&
+         (dim == 2 || (k >= box.lo[2] && k <= box.hi[2]));
 }
 
 // H z for a node, with the real-coefficient form where it applies (divergent only in
 // warps that straddle the inner edge of the absorbing layer)
 template <typename TZ>
-__device__ __forceinline__ cdd fine_apply_df_any(const FineOp& op, const float4* __restrict__ cdf,
+__device__ __forceinline__ cdd fine_apply_df_any(const FineOp& op, const RcBox& box, const float4* __restrict__ cdf,
                                                  const TZ* __restrict__ z, long long p, int i, int j, int k,
                                                  dd ih2, dd ih2_6, dd inv24) {
-  if (df_real_coef(op, i, j, k)) return fine_apply_df_t<TZ, true>(op, cdf, z, p, i, j, k, ih2, ih2_6, inv24);
+  if (df_real_coef(box, op.g.dim, i, j, k)) return fine_apply_df_t<TZ, true>(op, cdf, z, p, i, j, k, ih2, ih2_6, inv24);
   return fine_apply_df_t<TZ, false>(op, cdf, z, p, i, j, k, ih2, ih2_6, inv24);
 }
 
-__device__ __forceinline__ cdd fine_apply_df(const FineOp& op, const float4* __restrict__ cdf,
+__device__ __forceinline__ cdd fine_apply_df(const FineOp& op, const RcBox& box, const float4* __restrict__ cdf,
                                              const float2* __restrict__ z, long long p, int i, int j, int k,
                                              dd ih2, dd ih2_6, dd inv24) {
-  return fine_apply_df_any<float2>(op, cdf, z, p, i, j, k, ih2, ih2_6, inv24);
+  return fine_apply_df_any<float2>(op, box, cdf, z, p, i, j, k, ih2, ih2_6, inv24);
 }
 
 }  // namespace helm

@@ -338,6 +338,7 @@ __global__ void set_scalar_kernel(double* dst, const double2* src_x, int do_sqrt
 // complex entry, the size of complex FP64) and run the Arnoldi streams on the FP32 pipes.
 struct DfConsts {
   dd ih2, ih2_6, inv24;
+  RcBox box;   // real-coefficient box of the operator (fine_apply_df_any)
 };
 
 // c = omega^2 kappa^2 (1 - i gamma) per node as double-float.
@@ -405,7 +406,7 @@ __global__ void __launch_bounds__(kThreads) true_residual_df_kernel(FineOp op, D
        p += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
     node_coords(op.g, p, i, j, k);
-    const cdd hx = fine_apply_df_any<float4>(op, cdf, xd, p, i, j, k, K.ih2, K.ih2_6, K.inv24);
+    const cdd hx = fine_apply_df_any<float4>(op, K.box, cdf, xd, p, i, j, k, K.ih2, K.ih2_6, K.inv24);
     const double2 bv = b[p];
     const dd br = split_d(bv.x), bi = split_d(bv.y);
     racc rr{br.hi, br.lo}, ri{bi.hi, bi.lo};
@@ -433,7 +434,7 @@ __global__ void __launch_bounds__(kThreads) arnoldi_matvec_df_kernel(
   for (long long p = blockIdx.x * (long long)blockDim.x + tid; p < op.g.size; p += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
     node_coords(op.g, p, i, j, k);
-    const float4 wv = cdd_store(fine_apply_df(op, cdf, z, p, i, j, k, K.ih2, K.ih2_6, K.inv24));
+    const float4 wv = cdd_store(fine_apply_df(op, K.box, cdf, z, p, i, j, k, K.ih2, K.ih2_6, K.inv24));
     w[p] = wv;
     for (int q = 0; q < nv; ++q) df_cmacc(sdf[q * blockDim.x + tid], V[q * vstride + p], wv);
     df_cmacc(sdf[nv * blockDim.x + tid], wv, wv);
@@ -504,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, 4) arnoldi_matvec_df_t(FineOp op, Df
   for (long long p = blockIdx.x * (long long)blockDim.x + tid; p < op.g.size; p += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
     node_coords(op.g, p, i, j, k);
-    const float4 wv = cdd_store(fine_apply_df(op, cdf, z, p, i, j, k, K.ih2, K.ih2_6, K.inv24));
+    const float4 wv = cdd_store(fine_apply_df(op, K.box, cdf, z, p, i, j, k, K.ih2, K.ih2_6, K.inv24));
     w[p] = wv;
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
@@ -586,7 +587,7 @@ __global__ void __launch_bounds__(kThreads, 2) arnoldi_cgs_df_t(FineOp op, DfCon
   for (long long p = blockIdx.x * (long long)blockDim.x + tid; p < op.g.size; p += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
     node_coords(op.g, p, i, j, k);
-    const float4 wv = cdd_store(fine_apply_df(op, cdf, z, p, i, j, k, K.ih2, K.ih2_6, K.inv24));
+    const float4 wv = cdd_store(fine_apply_df(op, K.box, cdf, z, p, i, j, k, K.ih2, K.ih2_6, K.inv24));
     w[p] = wv;
 #pragma unroll
     for (int q = 0; q < NV; ++q) df_cmacc(acc[q], V[q * vstride + p], wv);
@@ -742,8 +743,9 @@ int k_arnoldi(const KrylovState& st, const FineOp& op, const double* kap64, cons
   return 0;
 }
 
-DfConsts df_consts(const FineOp& op) {
+DfConsts df_consts(const FineOp& op, const RcBox& box) {
   DfConsts K;
+  K.box = box;
   const double ih2 = op.inv_h2;
   auto mk_dd = [](double v) {
     const float hi = (float)v;
@@ -769,8 +771,8 @@ int k_start_cycle_df(const KrylovState& st, long long n, const double2* r, float
   return 0;
 }
 
-int k_arnoldi_df(const KrylovState& st, const FineOp& op, const float4* cdf, const float2* z, float4* w,
-                 const float4* V, long long vstride, int j, int passes, cudaStream_t s) {
+int k_arnoldi_df(const KrylovState& st, const FineOp& op, const RcBox& box, const float4* cdf, const float2* z,
+                 float4* w, const float4* V, long long vstride, int j, int passes, cudaStream_t s) {
   const long long n = op.g.size;
   const int bl = grid_blocks(n);
   const int nv = j + 1;
@@ -782,7 +784,7 @@ int k_arnoldi_df(const KrylovState& st, const FineOp& op, const float4* cdf, con
     cudaFuncSetAttribute(arnoldi_update_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     attr_set = true;
   }
-  const DfConsts K = df_consts(op);
+  const DfConsts K = df_consts(op, box);
   if (nv <= kMaxNV) {
     int st2 = 0;
     switch (nv) {
@@ -864,11 +866,11 @@ int k_true_residual(const KrylovState& st, const FineOp& op, const double* kap64
   return 0;
 }
 
-int k_true_residual_df(const KrylovState& st, const FineOp& op, const float4* cdf, const double2* b,
+int k_true_residual_df(const KrylovState& st, const FineOp& op, const RcBox& box, const float4* cdf, const double2* b,
                        const float4* xd, double2* r, cudaStream_t s) {
   const int bl = grid_blocks(op.g.size);
   KernelTimer kt(HELM_K_KRYLOV_OTHER, s);
-  true_residual_df_kernel<<<bl, kThreads, kThreads * sizeof(float4), s>>>(op, df_consts(op), cdf, b, xd, r, st.part,
+  true_residual_df_kernel<<<bl, kThreads, kThreads * sizeof(float4), s>>>(op, df_consts(op, box), cdf, b, xd, r, st.part,
                                                                           st.counter, st.red);
   HELM_LAUNCH_CHECK();
   set_scalar_kernel<<<1, 32, 0, s>>>(st.scal + KS_BETA, st.red, 1);

@@ -45,8 +45,9 @@ int k_normalize(const KrylovState& st, long long n, const double2* w, const doub
 int k_coef_df(const FineOp& op, const double* kap64, float4* cdf, cudaStream_t s);
 int k_start_cycle_df(const KrylovState& st, long long n, const double2* r, float4* v0, cudaStream_t s);
 // passes: 2 = CGS2 (FP32 first pass, double-float second pass), 1 = one double-float pass.
-int k_arnoldi_df(const KrylovState& st, const FineOp& op, const float4* cdf, const float2* z, float4* w,
-                 const float4* V, long long vstride, int j, int passes, cudaStream_t s);
+// box: the real-coefficient box of op (nodes whose coefficients and face neighbours' are real).
+int k_arnoldi_df(const KrylovState& st, const FineOp& op, const RcBox& box, const float4* cdf, const float2* z,
+                 float4* w, const float4* V, long long vstride, int j, int passes, cudaStream_t s);
 int k_normalize_df(const KrylovState& st, long long n, const float4* w, const float4* V, long long vstride, int j,
                    float4* vout, cudaStream_t s);
 // y = R^-1 g (k x k) and x += Z y; for a c64 basis (zp = P32) also xd = x as double-float.
@@ -60,7 +61,7 @@ int k_true_residual(const KrylovState& st, const FineOp& op, const double* kap64
                     const double2* x, double2* r, cudaStream_t s);
 // The same in double-float arithmetic from xd (x as double-float) and the double-float
 // coefficients cdf; r is c128.
-int k_true_residual_df(const KrylovState& st, const FineOp& op, const float4* cdf, const double2* b,
+int k_true_residual_df(const KrylovState& st, const FineOp& op, const RcBox& box, const float4* cdf, const double2* b,
                        const float4* xd, double2* r, cudaStream_t s);
 
 }  // namespace helm
