@@ -11,7 +11,8 @@ import ctypes
 from . import _ffi
 from ._ffi import HelmError, HelmOpts, HelmStats, check
 
-__all__ = ["Solver", "HelmError", "level_shape", "helmholtz_solve", "coarse_plan", "solve_concurrent"]
+__all__ = ["Solver", "HelmError", "level_shape", "helmholtz_solve", "release_reused_context", "coarse_plan",
+           "solve_concurrent"]
 
 _lib = _ffi.load()
 
@@ -321,8 +322,8 @@ def _autograd_function():
         memory, one more forward solve)."""
 
         @staticmethod
-        def forward(ctx, kappa2, q, opts, tol, maxit, recompute):
-            solver = Solver(kappa2.detach().contiguous(), **opts)
+        def forward(ctx, kappa2, q, opts, tol, maxit, recompute, reuse):
+            solver = _context_for(kappa2, opts) if reuse else Solver(kappa2.detach().contiguous(), **opts)
             qd = q.detach().contiguous()
             p, _ = solver.solve(qd, tol=tol, maxit=maxit)
             ctx.solver, ctx.tol, ctx.maxit, ctx.recompute = solver, tol, maxit, recompute
@@ -338,20 +339,53 @@ def _autograd_function():
             adj = torch.empty_like(p)
             solver.adjoint_grad(p, grad_p.contiguous(), grad_k, adj, tol=ctx.tol, maxit=ctx.maxit)
             grad_q = adj.conj() if ctx.needs_input_grad[1] else None
-            solver.close()
-            return grad_k, grad_q, None, None, None, None
+            ctx.solver = None   # a context of its own is freed here, a reused one stays in the cache
+            return grad_k, grad_q, None, None, None, None, None
 
     return HelmholtzSolve
 
 
 _HELMHOLTZ_SOLVE = None
+# the context kept for reuse: the kappa2 tensor it was set up from (weak reference), that
+# tensor's version counter at set-up, the options, and the context
+_REUSE = {"ref": None, "version": None, "key": None, "solver": None}
 
 
-def helmholtz_solve(kappa2, q, n, omega, tol=1e-6, maxit=500, recompute=False, **opts):
+def _context_for(kappa2, opts):
+    """A context for kappa2 and opts: the kept one when it was set up from this very tensor
+    object, unmodified since (same autograd version counter), with the same options;
+    otherwise a new one, which replaces it (the old one is freed once no backward pass
+    holds it)."""
+    import weakref
+
+    key = repr(sorted(opts.items()))
+    r = _REUSE
+    if (r["solver"] is not None and r["ref"] is not None and r["ref"]() is kappa2
+            and r["version"] == kappa2._version and r["key"] == key):
+        return r["solver"]
+    solver = Solver(kappa2.detach().contiguous(), **opts)
+    r.update(ref=weakref.ref(kappa2), version=kappa2._version, key=key, solver=solver)
+    return solver
+
+
+def release_reused_context():
+    """Frees the context helmholtz_solve(..., reuse_context=True) keeps (once no backward
+    pass still holds it)."""
+    _REUSE.update(ref=None, version=None, key=None, solver=None)
+
+
+def helmholtz_solve(kappa2, q, n, omega, tol=1e-6, maxit=500, recompute=False, reuse_context=False, **opts):
     """Differentiable p = H(kappa2)^-1 q (torch.autograd): the backward pass is the
-    adjoint solve of helm_adjoint_grad.  ``opts`` are Solver keywords."""
+    adjoint solve of helm_adjoint_grad.  ``opts`` are Solver keywords.
+
+    By default every call sets up a context for kappa2 (the medium usually changes from one
+    call to the next).  ``reuse_context=True`` keeps the last context and uses it again
+    while the same kappa2 tensor object, unmodified (its autograd version counter
+    unchanged), comes with the same options: several sources or data sets for one medium
+    then pay for one set-up.  Changes made through ``.data`` bypass the version counter; call
+    release_reused_context() after such a change."""
     global _HELMHOLTZ_SOLVE
     if _HELMHOLTZ_SOLVE is None:
         _HELMHOLTZ_SOLVE = _autograd_function()
     o = dict(opts, n=n, omega=omega)
-    return _HELMHOLTZ_SOLVE.apply(kappa2, q, o, tol, maxit, recompute)
+    return _HELMHOLTZ_SOLVE.apply(kappa2, q, o, tol, maxit, recompute, bool(reuse_context))

@@ -112,3 +112,42 @@ def test_recompute_and_source_gradient():
     po = _oracle_solve(c, q)
     lam = np.conj(_oracle_solve(c, np.conj(mask * po)))
     assert rel(grads[0][1], lam) < 1e-8
+
+
+def test_reused_context_gives_the_same_gradients():
+    """helmholtz_solve(..., reuse_context=True): the second call with the same unmodified
+    kappa2 tensor uses the kept context (no new set-up) and gives the same field and
+    gradient bit for bit; an in-place change of kappa2 (version counter) or other options
+    make a new context, whose gradient matches a context of its own."""
+    import paper_2604_19501_gb300 as P
+    from paper_2604_19501_gb300 import helmholtz_solve
+
+    n = (48, 48)
+    c, q, mask, d = _problem(n, "4th", "cubic", 2, seed=13)
+    opts = dict(abc_width=c.abc, alpha3=c.alpha3, stencil="4th", intergrid="cubic", precision="mixed", max_rhs=2)
+    qd = torch.from_numpy(q).cuda()
+    mk = torch.from_numpy(mask).cuda()
+    k2 = torch.from_numpy(c.kappa2.copy()).cuda().requires_grad_(True)
+
+    def grad(reuse, k):
+        p = helmholtz_solve(k, qd, n, c.omega, tol=1e-10, maxit=400, reuse_context=reuse, **opts)
+        L = 0.5 * ((p.abs() ** 2) * mk).sum()
+        (g,) = torch.autograd.grad(L, (k,))
+        return p.detach().cpu().numpy(), g.cpu().numpy()
+
+    P.release_reused_context()
+    p1, g1 = grad(True, k2)
+    kept = P._REUSE["solver"]
+    p2, g2 = grad(True, k2)
+    assert P._REUSE["solver"] is kept
+    assert np.array_equal(p1, p2) and np.array_equal(g1, g2)
+    p0, g0 = grad(False, k2)          # a context of its own
+    assert rel(g1, g0) < 1e-8 and rel(p1, p0) < 1e-9
+    with torch.no_grad():
+        k2 *= 1.001                   # bumps the version counter
+    p3, g3 = grad(True, k2)
+    assert P._REUSE["solver"] is not kept
+    p4, g4 = grad(False, k2)
+    assert rel(g3, g4) < 1e-8 and rel(p3, p4) < 1e-9
+    assert rel(g3, g1) > 1e-6         # a different medium
+    P.release_reused_context()
