@@ -102,7 +102,7 @@ __device__ __forceinline__ float2 df_lo(float4 v) { return make_float2(v.z, v.w)
 
 //
 // RC: every coefficient c the node reads (its own and its face neighbours') is real, i.e.
-// the absorbing profile is zero there (df_real_coef); the products with the imaginary
+// the absorbing profile is zero there (df_real_coef_warp); the products with the imaginary
 // parts, exact zeros, are then left out: the result has the same value (at most the sign
 // of a zero differs).
 template <bool RC>
@@ -232,21 +232,28 @@ __device__ __forceinline__ cdd fine_apply_df_t(const FineOp& op, const float4* _
   return h;
 }
 
-// True when the absorbing profile is zero at node (i, j, k) and at its face neighbours,
-// so that the coefficients c = omega^2 kappa^2 (1 - i gamma) the operator reads there are
-// real: the node lies in the box, set up from the gamma tables.
-__device__ __forceinline__ bool df_real_coef(const RcBox& box, int dim, int i, int j, int k) {
-  return i >= box.lo[0] && i <= box.hi[0] && j >= box.lo[1] && j <= box.hi[1] &&
+// True when the 32 consecutive nodes of a warp (lane l at x index i, the warp starting at
+// x = i - l) lie in one row inside the real-coefficient box: the absorbing profile is zero
+// at each of them and at its face neighbours, so that the coefficients
+// c = omega^2 kappa^2 (1 - i gamma) the operator reads there are real.  Every
+// lane computes the same value (a warp that spans two rows gets false in both), so the
+// choice of form never splits a warp.
+__device__ __forceinline__ bool df_real_coef_warp(const RcBox& box, int dim, int i, int j, int k) {
+  const int xs = i - (int)(threadIdx.x & 31);
+  return xs >= box.lo[0] && xs + 31 <= box.hi[0] && j >= box.lo[1] && j <= box.hi[1] &&
          (dim == 2 || (k >= box.lo[2] && k <= box.hi[2]));
 }
 
-// H z for a node, with the real-coefficient form where it applies (divergent only in
-// warps that straddle the inner edge of the absorbing layer)
+// H z for a node, with the real-coefficient form where it applies.  The callers are 1D
+// grid-stride kernels, so the lanes of a warp hold consecutive nodes and the form is
+// chosen per warp (df_real_coef_warp): a per-node choice made the warps at the layer's
+// inner edge run both forms, which cost more in 3D than the form saves.
 template <typename TZ>
 __device__ __forceinline__ cdd fine_apply_df_any(const FineOp& op, const RcBox& box, const float4* __restrict__ cdf,
                                                  const TZ* __restrict__ z, long long p, int i, int j, int k,
                                                  dd ih2, dd ih2_6, dd inv24) {
-  if (df_real_coef(box, op.g.dim, i, j, k)) return fine_apply_df_t<TZ, true>(op, cdf, z, p, i, j, k, ih2, ih2_6, inv24);
+  if (df_real_coef_warp(box, op.g.dim, i, j, k))
+    return fine_apply_df_t<TZ, true>(op, cdf, z, p, i, j, k, ih2, ih2_6, inv24);
   return fine_apply_df_t<TZ, false>(op, cdf, z, p, i, j, k, ih2, ih2_6, inv24);
 }
 
