@@ -593,7 +593,64 @@ def side_measurements(args, wl, p_main, main_ms, main_its, dev, log):
                     "per block iteration) against the same 64 solved one at a time (max_rhs = 1); one timed "
                     "call each after one untimed"}
         log(f"batched 64 sources: blocks of 32 {ms_b:.1f} ms, single {ms_1:.1f} ms ({ms_1 / ms_b:.2f}x)")
+        out["gradient"] = gradient_measurement(args, dev, log)
     return out
+
+
+def gradient_measurement(args, dev, log, steps=3):
+    """The differentiation workload of --adjoint in brief: 16 seeded surface sources on the
+    run's medium recipe at 512^2 cells + the layer, receivers on the top interior row, data
+    from a 2%-perturbed medium; one gradient = the forward solves of the block, the receiver
+    residual and helm_adjoint_grad (adjoint solves and the fused gradient kernel)."""
+    import argparse
+
+    import numpy as np
+    import torch
+    from scipy.ndimage import gaussian_filter
+
+    sargs = argparse.Namespace(**vars(args))
+    sargs.n, sargs.sources = 512, 16
+    wlg = workload(sargs)
+    n, pad = wlg["n"], sargs.pad
+    nodes = n_nodes(wlg)
+    q = torch.from_numpy(wlg["q"]).to(dev)
+    pert = gaussian_filter(np.random.default_rng(1).standard_normal(wlg["kappa2"].shape), 8.0)
+    kap_true = wlg["kappa2"] * (1.0 + 0.02 * pert / np.abs(pert).max())
+    mask = np.zeros(wlg["kappa2"].shape, dtype=bool)
+    mask[pad, pad:n[0] - pad + 1] = True
+    md = torch.from_numpy(mask).to(dev)
+    s_true = make_solver(dict(wlg, kappa2=kap_true), sargs, dev, max_rhs=16)
+    d = s_true.solve(q, tol=1e-8, maxit=args.maxit)[0] * md
+    s_true.close()
+    s = make_solver(wlg, sargs, dev, max_rhs=16)
+    p = torch.empty_like(q)
+    grad = torch.zeros(wlg["kappa2"].shape, dtype=torch.float64, device=dev)
+
+    def step():
+        p_, st = s.solve(q, p, tol=args.tol, maxit=args.maxit)
+        grad.zero_()
+        sa = s.adjoint_grad(p_, (p_ - d) * md, grad, tol=args.tol, maxit=args.maxit)
+        return st, sa
+
+    step()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        st, sa = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s.close()
+    ms = e0.elapsed_time(e1) / steps
+    its_f = [x["iterations"] for x in st]
+    its_a = [x["iterations"] for x in sa]
+    log(f"gradient (16 sources, {n[0]}^2): {ms:.1f} ms, forward its {max(its_f)}, adjoint its {max(its_a)}")
+    return {"sources": 16, "cells": n[0], "ms_per_gradient": ms, "gradients_per_s": 1e3 / ms,
+            "value": 2 * 16 * nodes / 1e3 / ms, "unit": UNIT,
+            "iterations": {"forward": max(its_f), "adjoint": max(its_a)},
+            "note": "the --adjoint workload (config 5, 2D) in brief: one gradient of the receiver misfit = forward "
+                    "solves of 16 sources as one block + helm_adjoint_grad; value counts forward and adjoint "
+                    f"solves; {steps} timed gradients after one untimed"}
 
 
 def our_arm(args):
