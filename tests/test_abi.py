@@ -94,3 +94,25 @@ def test_solver_option_defaults_and_validation(lib):
     assert l.helm_setup(ctypes.byref(o), ctypes.cast(k, ctypes.c_void_p), ctypes.byref(ctx)) == _ffi.HELM_EINVAL
     assert b"solver" in l.helm_last_error()
     assert not ctx.value
+
+
+@pytest.mark.parametrize("field,bad,word", [("coarse_refine", -1, b"coarse_refine"), ("coarse_refine", 9, b"coarse_refine"),
+                                            ("coarse_block_min", -5, b"coarse_block_min"),
+                                            ("arnoldi_passes", 3, b"arnoldi_passes"),
+                                            ("arnoldi_passes", -1, b"arnoldi_passes")])
+def test_new_option_defaults_and_ranges(lib, field, bad, word):
+    """Defaults of the coarsest-solve refinement, the blocked-elimination threshold and the
+    Arnoldi passes (0 = the library's choice), and their range checks before any device call."""
+    from paper_2604_19501_gb300 import _ffi
+
+    l = _ffi.load()
+    o = _ffi.HelmOpts()
+    assert l.helm_default_opts(ctypes.byref(o)) == 0
+    assert o.coarse_refine == 0 and o.coarse_block_min == 0 and o.arnoldi_passes == 0
+    ctx = ctypes.c_void_p()
+    k = (ctypes.c_double * 81)()
+    o.dim, o.n[0], o.n[1] = 2, 8, 8
+    setattr(o, field, bad)
+    assert l.helm_setup(ctypes.byref(o), ctypes.cast(k, ctypes.c_void_p), ctypes.byref(ctx)) == _ffi.HELM_EINVAL
+    assert word in l.helm_last_error()
+    assert not ctx.value
