@@ -67,7 +67,7 @@ template <> struct TileShape<2> { static constexpr int X = 32, Y = 8, Z = 1; };
 template <> struct TileShape<3> { static constexpr int X = 32, Y = 4, Z = 2; };
 
 template <typename T, typename TX, typename TB, typename TY, int MODE, int DIM, int R>
-__global__ void __launch_bounds__(256, 4) stencil_tile_kernel(GridDims g, const c2<T>* __restrict__ coef,
+__global__ void __launch_bounds__(256, (DIM == 3 && sizeof(T) == sizeof(float)) ? 2 : 4) stencil_tile_kernel(GridDims g, const c2<T>* __restrict__ coef,
                                                            const c2<T>* __restrict__ dinvp,
                                                            const c2<TX>* __restrict__ x,
                                                            const c2<TB>* __restrict__ b,
@@ -86,6 +86,68 @@ __global__ void __launch_bounds__(256, 4) stencil_tile_kernel(GridDims g, const 
   const long long sz = (long long)g.N[0] * g.N[1];
   const long long idx = inside ? i + sy * j + sz * k : 0;
   const c2<T> dinv = (inside && MODE == MODE_JACOBI) ? dinvp[idx] : mk<T>(0, 0);
+  if constexpr (DIM == 3 && sizeof(T) == sizeof(float)) {
+    // FP32 3D: latency-bound on its loads, so every load is issued as early as it can be.
+    // The staged x values are loaded into registers before any of them is stored, the
+    // first z-plane of coefficients is in flight during the staging, and each plane's
+    // successor is loaded while the plane is summed.  Coefficients are read at the node
+    // itself only (in bounds for any offset); an offset outside the grid meets a zero x in
+    // the tile, so the sum needs no bounds checks and runs in the same order as below.
+    constexpr int NS = HX * HY * HZ, SPT = (NS + 255) / 256, NP = W * W;
+    static_assert(S::X * S::Y * S::Z == 256, "the launcher runs 256 threads per tile");
+    const int c0 = (tx + R) + HX * ((ty + R) + HY * (tz + RZ));
+    auto plane = [&](int dz, c2<T>(&cp)[NP]) {
+#pragma unroll
+      for (int q = 0; q < NP; ++q)
+        cp[q] = coef[((q % W) + W * ((q / W) + W * (dz + R))) * N + idx];
+    };
+    for (int r = 0; r < nrhs; ++r) {
+      const c2<TX>* xr = x + r * N;
+      c2<T> ca[NP], cb[NP];
+      plane(-R, ca);
+      c2<T> xs[SPT];
+#pragma unroll
+      for (int e = 0; e < SPT; ++e) {
+        const int q = threadIdx.x + e * 256;
+        const int gi = i0 - R + q % HX, gj = j0 - R + (q / HX) % HY, gk = k0 - RZ + q / (HX * HY);
+        const bool ok = q < NS && gi >= 0 && gi < g.N[0] && gj >= 0 && gj < g.N[1] && gk >= 0 && gk < g.N[2];
+        xs[e] = ok ? cvt<T>(xr[gi + sy * gj + sz * gk]) : mk<T>(0, 0);
+      }
+#pragma unroll
+      for (int e = 0; e < SPT; ++e) {
+        const int q = threadIdx.x + e * 256;
+        if (q < NS) sx[q] = xs[e];
+      }
+      __syncthreads();
+      c2<T> Ax = mk<T>(0, 0);
+      // planes alternate between ca and cb (the loop is unrolled by the plane count)
+#pragma unroll
+      for (int dz = -R; dz <= R; ++dz) {
+        c2<T>(&cur)[NP] = ((dz + R) & 1) ? cb : ca;
+        c2<T>(&nxt)[NP] = ((dz + R) & 1) ? ca : cb;
+        if (dz < R) plane(dz + 1, nxt);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          const int dx = q % W - R, dy = q / W - R;
+          Ax = cmac(Ax, cur[q], sx[c0 + dx + HX * (dy + HY * dz)]);
+        }
+      }
+      if (inside) {
+        const long long p = r * N + idx;
+        c2<T> out;
+        if (MODE == MODE_APPLY) {
+          out = Ax;
+        } else {
+          const c2<T> res = cvt<T>(b[p]) - Ax;
+          if (MODE == MODE_RESID) out = res;
+          else out = sx[c0] + cscale(cmul(dinv, res), w);
+        }
+        y[p] = cvt<TY>(out);
+      }
+      __syncthreads();   // the tile is reloaded for the next right-hand side
+    }
+    return;
+  }
   for (int r = 0; r < nrhs; ++r) {
     const c2<TX>* xr = x + r * N;
     for (int q = threadIdx.x; q < HX * HY * HZ; q += blockDim.x) {
