@@ -385,9 +385,20 @@ __global__ void __launch_bounds__(kThreads) l2_restrict_tile_kernel(const Cycle2
   const int I0 = blockIdx.x * kRX, J0 = blockIdx.y * kRY, rhs = blockIdx.z;
   const int X0 = 2 * I0 - RW, Y0 = 2 * J0 - RW;
   const float2* sb = s2 + (long long)rhs * gf.size;
-  for (int q = threadIdx.x; q < NX * NY; q += kThreads) {
+  // every staged value is loaded before any is stored (one memory round trip, not one per
+  // pass of the loop)
+  constexpr int NS = NX * NY, SPT = (NS + kThreads - 1) / kThreads;
+  float2 v[SPT];
+#pragma unroll
+  for (int e = 0; e < SPT; ++e) {
+    const int q = threadIdx.x + e * kThreads;
     const int fx = X0 + q % NX, fy = Y0 + q / NX;
-    sf[q] = (fx >= 0 && fx < gf.N[0] && fy >= 0 && fy < gf.N[1]) ? sb[fx + (long long)gf.N[0] * fy] : z2();
+    v[e] = (q < NS && fx >= 0 && fx < gf.N[0] && fy >= 0 && fy < gf.N[1]) ? sb[fx + (long long)gf.N[0] * fy] : z2();
+  }
+#pragma unroll
+  for (int e = 0; e < SPT; ++e) {
+    const int q = threadIdx.x + e * kThreads;
+    if (q < NS) sf[q] = v[e];
   }
   __syncthreads();
   const float* w = c_w[RW - 1];
@@ -487,14 +498,25 @@ __global__ void __launch_bounds__(kL2Threads, 2) l2_up_kernel(const Cycle2D c, c
   __syncthreads();
   prolong_tile<PW, kL2Threads>(se, J0x, J0y, MX, MY, su, sp, X0, Y0, NX, NY);
   __syncthreads();
-  for (int q = threadIdx.x; q < NX * NY; q += kL2Threads) {
-    const int sxg = X0 + q % NX, syg = Y0 + q / NX;
-    float2 xx = z2();
-    if (sxg >= 0 && sxg < N0 && syg >= 0 && syg < N1) {
-      const long long j = sxg + (long long)N0 * syg;
-      xx = cscale(cmul(c.dinv2[j], rb[j]), c.w2) + sp[q];
+  {
+    // the staged inputs are loaded before any staged value is formed (one round trip)
+    constexpr int NS = NX * NY, SPT = (NS + kL2Threads - 1) / kL2Threads;
+    float2 dv[SPT], rv[SPT];
+    bool okv[SPT];
+#pragma unroll
+    for (int e = 0; e < SPT; ++e) {
+      const int q = threadIdx.x + e * kL2Threads;
+      const int sxg = X0 + q % NX, syg = Y0 + q / NX;
+      okv[e] = q < NS && sxg >= 0 && sxg < N0 && syg >= 0 && syg < N1;
+      const long long j = okv[e] ? sxg + (long long)N0 * syg : 0;
+      dv[e] = okv[e] ? c.dinv2[j] : z2();
+      rv[e] = okv[e] ? rb[j] : z2();
     }
-    sx[q] = xx;
+#pragma unroll
+    for (int e = 0; e < SPT; ++e) {
+      const int q = threadIdx.x + e * kL2Threads;
+      if (q < NS) sx[q] = okv[e] ? cscale(cmul(dv[e], rv[e]), c.w2) + sp[q] : z2();
+    }
   }
   __syncthreads();
   if (!in) return;
