@@ -64,6 +64,125 @@ __global__ void __launch_bounds__(256) fine_row_kernel(FineOp op, const T* __res
   }
 }
 
+// FP32, 3D: the same row operations on a 32 x 4 x 2 tile of nodes whose x and coefficients
+// c = omega^2 kappa^2 (1 - i gamma), widened by one node, are staged in shared memory (all
+// of a thread's staging loads issued before any store), so that the 7- or 19-point
+// stencil of each node reads shared memory instead of global memory behind bounds checks.
+// Staged values outside the grid are zero: every skipped term of fine_apply_at becomes an
+// exact zero added at the same place of the same sum, so the results are the same.
+constexpr int kFTX = 32, kFTY = 4, kFTZ = 2;
+template <typename TX, typename SB, typename TY, int MODE>
+__global__ void __launch_bounds__(256) fine_tile3_kernel(FineOp op, const float* __restrict__ kap,
+                                                         const c2<TX>* __restrict__ x, const SB* __restrict__ b,
+                                                         c2<TY>* __restrict__ y, int nrhs, float w) {
+  constexpr int HX = kFTX + 2, HY = kFTY + 2, HZ = kFTZ + 2, NS = HX * HY * HZ, SPT = (NS + 255) / 256;
+  static_assert(kFTX * kFTY * kFTZ == 256, "one thread per node of the tile");
+  __shared__ float2 sx[NS];
+  __shared__ float2 sc[NS];
+  const GridDims& g = op.g;
+  const int tx = threadIdx.x % kFTX, ty = (threadIdx.x / kFTX) % kFTY, tz = threadIdx.x / (kFTX * kFTY);
+  const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * kFTY, k0 = blockIdx.z * kFTZ;
+  const int i = i0 + tx, j = j0 + ty, k = k0 + tz;
+  const bool inside = i < g.N[0] && j < g.N[1] && k < g.N[2];
+  const long long N = g.size, sy = g.N[0], sz = (long long)g.N[0] * g.N[1];
+  const long long idx = inside ? i + sy * j + sz * k : 0;
+  const float ih2 = (float)op.inv_h2;
+  // staged entry e of this thread: its grid node, or -1 outside the grid (or the tile)
+  auto staged = [&](int e) -> long long {
+    const int q = threadIdx.x + e * 256;
+    const int gi = i0 - 1 + q % HX, gj = j0 - 1 + (q / HX) % HY, gk = k0 - 1 + q / (HX * HY);
+    const bool ok = q < NS && gi >= 0 && gi < g.N[0] && gj >= 0 && gj < g.N[1] && gk >= 0 && gk < g.N[2];
+    return ok ? gi + sy * gj + sz * gk : -1;
+  };
+  {
+    // c on the widened tile, as fine_coef forms it (the same for every right-hand side)
+    float2 cs[SPT];
+#pragma unroll
+    for (int e = 0; e < SPT; ++e) {
+      const long long gq = staged(e);
+      cs[e] = make_float2(0.f, 0.f);
+      if (gq >= 0) {
+        const int q = threadIdx.x + e * 256;
+        const int gi = i0 - 1 + q % HX, gj = j0 - 1 + (q / HX) % HY, gk = k0 - 1 + q / (HX * HY);
+        const float gam = op.gam32[0][gi] + op.gam32[1][gj] + op.gam32[2][gk];
+        const float cre = (float)op.omega2 * kap[gq];
+        cs[e] = make_float2(cre, -cre * gam);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < SPT; ++e) {
+      const int q = threadIdx.x + e * 256;
+      if (q < NS) sc[q] = cs[e];
+    }
+  }
+  const int c0 = (tx + 1) + HX * ((ty + 1) + HY * (tz + 1));
+  for (int r = 0; r < nrhs; ++r) {
+    const c2<TX>* xr = x + r * N;
+    float2 xs[SPT];
+#pragma unroll
+    for (int e = 0; e < SPT; ++e) {
+      const long long gq = staged(e);
+      xs[e] = gq >= 0 ? cvt<float>(xr[gq]) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int e = 0; e < SPT; ++e) {
+      const int q = threadIdx.x + e * 256;
+      if (q < NS) sx[q] = xs[e];
+    }
+    __syncthreads();
+    if (inside) {
+      const float2 ci = sc[c0], xc = sx[c0];
+      // fine_diag and fine_apply_at, from the tile
+      const float2 diag = op.order == 0 ? make_float2(6.f * ih2 - ci.x, -ci.y)
+                                        : make_float2(4.f * ih2 - 0.5f * ci.x, -0.5f * ci.y);
+      float2 Ax;
+      if (op.order == 0) {
+        float2 sm = make_float2(0.f, 0.f);
+        sm = sm + sx[c0 - 1];
+        sm = sm + sx[c0 + 1];
+        sm = sm + sx[c0 - HX];
+        sm = sm + sx[c0 + HX];
+        sm = sm + sx[c0 - HX * HY];
+        sm = sm + sx[c0 + HX * HY];
+        Ax = cmul(diag, xc) - cscale(sm, ih2);
+      } else {
+        Ax = cmul(diag, xc);
+        const float wface = float(-2.0 / 6.0) * ih2, wedge = float(-1.0 / 6.0) * ih2;
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+          for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int nz = (dx != 0) + (dy != 0) + (dz != 0);
+              if (nz == 0 || nz == 3) continue;
+              const int q = c0 + dx + HX * (dy + HY * dz);
+              const float2 xv = sx[q];
+              if (nz == 1) {
+                const float2 cj = sc[q];
+                const float2 m = make_float2(wface - float(1.0 / 24.0) * (ci.x + cj.x),
+                                             -float(1.0 / 24.0) * (ci.y + cj.y));
+                Ax = cmac(Ax, m, xv);
+              } else {
+                Ax = Ax + cscale(xv, wedge);
+              }
+            }
+      }
+      const long long p = r * N + idx;
+      float2 out;
+      if (MODE == MODE_APPLY) {
+        out = Ax;
+      } else {
+        const float2 res = cvt<float>(b[p]) - Ax;
+        if (MODE == MODE_RESID) out = res;
+        else out = xc + cscale(cmul(crecip(diag), res), w);
+      }
+      y[p] = cvt<TY>(out);
+    }
+    __syncthreads();   // the tile is reloaded for the next right-hand side
+  }
+}
+
 template <typename T, typename TX, typename SB, typename TY>
 static int fine_dispatch(const FineOp& op, int mode, const void* kap, const void* x, const void* b,
                          void* y, int nrhs, double w, int colour, cudaStream_t s) {
@@ -74,6 +193,17 @@ static int fine_dispatch(const FineOp& op, int mode, const void* kap, const void
   auto B = (const SB*)b;
   auto Y = (c2<TY>*)y;
   KernelTimer kt(HELM_K_FINE, s);
+  if constexpr (std::is_same<T, float>::value) {
+    if (op.g.dim == 3 && (mode == MODE_APPLY || mode == MODE_RESID || mode == MODE_JACOBI)) {
+      const dim3 tg((op.g.N[0] + kFTX - 1) / kFTX, (op.g.N[1] + kFTY - 1) / kFTY, (op.g.N[2] + kFTZ - 1) / kFTZ);
+      if (tg.y > 65535u || tg.z > 65535u) { set_error("fine tile grid too large"); return 1; }
+      if (mode == MODE_APPLY) fine_tile3_kernel<TX, SB, TY, MODE_APPLY><<<tg, 256, 0, s>>>(op, K, X, B, Y, nrhs, (T)w);
+      else if (mode == MODE_RESID) fine_tile3_kernel<TX, SB, TY, MODE_RESID><<<tg, 256, 0, s>>>(op, K, X, B, Y, nrhs, (T)w);
+      else fine_tile3_kernel<TX, SB, TY, MODE_JACOBI><<<tg, 256, 0, s>>>(op, K, X, B, Y, nrhs, (T)w);
+      HELM_LAUNCH_CHECK();
+      return 0;
+    }
+  }
   switch (mode) {
     case MODE_APPLY: fine_row_kernel<T, TX, SB, TY, MODE_APPLY><<<bl, th, 0, s>>>(op, K, X, B, Y, nrhs, (T)w, colour); break;
     case MODE_RESID: fine_row_kernel<T, TX, SB, TY, MODE_RESID><<<bl, th, 0, s>>>(op, K, X, B, Y, nrhs, (T)w, colour); break;
