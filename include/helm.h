@@ -27,6 +27,10 @@
  * Errors.  Every call returns an int status (helm_status).  No exception or
  *   abort crosses the ABI.  helm_last_error() describes the last failure of the
  *   calling thread.
+ * Threads.  Calls on different contexts may come from different host threads at
+ *   the same time; calls on one context must not overlap.  The process-wide state
+ *   is the once-set kernel attributes (set under atomic flags) and the array of
+ *   helm_coarse_solve_noalloc, whose own rule is stated there.
  */
 #ifndef HELM_H
 #define HELM_H

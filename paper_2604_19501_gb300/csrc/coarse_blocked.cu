@@ -356,7 +356,7 @@ int big_front_eliminate(const FrontDesc& d, double2* aug, float2* w32, int* piv,
   const int nS = d.nS, nF = nS + d.nB;
   const long long ld = nF + nS;
   double2* A = aug + d.aug_off;
-  static bool attr = false;
+  static std::atomic<bool> attr{false};
   if (!attr) {
     HELM_CUDA_TRY(cudaFuncSetAttribute(pivot_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kNb * 2 * kNb * (int)sizeof(double2)));

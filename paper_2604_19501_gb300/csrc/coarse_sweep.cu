@@ -645,7 +645,7 @@ template <bool DF, int RG>
 cudaError_t launch_one(const SweepArgs& a, int grid, cudaStream_t s) {
   // every block of the grid must be resident (cooperative launch): the schedule's waits
   // rely on it; any such grid size is correct, the job sizes were planned for cs.grid
-  static bool attr = false;
+  static std::atomic<bool> attr{false};
   if (!attr) {
     const cudaError_t e = cudaFuncSetAttribute(sweep_kernel<DF, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<RG>());
     if (e != cudaSuccess) return e;

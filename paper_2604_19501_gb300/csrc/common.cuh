@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <string>
 #include <algorithm>
+#include <atomic>
 
 #include "../../include/helm.h"
 

@@ -1065,7 +1065,7 @@ int launch_down_rs(const Cycle2D& c, const float4* v, float2* r2, int nrhs, cuda
   using P = RsDown<ORDER, RW, SEG>;
   const long long warps = (long long)((c.g2.N[0] + P::CS - 1) / P::CS) * ((c.g2.N[1] + SEG - 1) / SEG);
   const dim3 grid((unsigned)((warps + kRsWarps - 1) / kRsWarps), (unsigned)nrhs);
-  static bool attr = false;
+  static std::atomic<bool> attr{false};
   if (!attr) {
     cudaFuncSetAttribute(fine_down_rs_kernel<ORDER, RW, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kRsWarps * kRsDownWarpBytes);
@@ -1082,7 +1082,7 @@ int launch_up_rs(const Cycle2D& c, const float4* v, const float2* y2, float2* z,
   const long long warps =
       (long long)((c.fine.g.N[0] + 2 * P::CU - 1) / (2 * P::CU)) * ((c.fine.g.N[1] + P::RS - 1) / P::RS);
   const dim3 grid((unsigned)((warps + kRsWarps - 1) / kRsWarps), (unsigned)nrhs);
-  static bool attr = false;
+  static std::atomic<bool> attr{false};
   if (!attr) {
     cudaFuncSetAttribute(fine_up_rs_kernel<ORDER, PW, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kRsWarps * kRsUpWarpBytes);
@@ -1130,7 +1130,7 @@ int cycle2d_fine_down(const Cycle2D& c, const float4* v, float2* r2, int nrhs, c
   };
 #define HELM_FD(O, RW)                                                                                  \
   if (c.fine.order == O && c.rw1 == RW) {                                                               \
-    static bool attr = false;                                                                           \
+    static std::atomic<bool> attr{false};                                                               \
     if (!attr) {                                                                                        \
       cudaFuncSetAttribute(fine_down_kernel<O, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem(RW)); \
       attr = true;                                                                                      \

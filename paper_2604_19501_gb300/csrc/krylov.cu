@@ -620,7 +620,7 @@ int arnoldi_df_launch(int bl, size_t sm, const FineOp& op, const DfConsts& K, co
     HELM_LAUNCH_CHECK();
     return 0;
   }
-  static bool attr_set = false;
+  static std::atomic<bool> attr_set{false};
   if (!attr_set) {
     cudaFuncSetAttribute(arnoldi_matvec_df_t<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(arnoldi_update_df_t<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -714,7 +714,7 @@ int k_arnoldi(const KrylovState& st, const FineOp& op, const double* kap64, cons
   const int bl = grid_blocks(n);
   const int nv = j + 1;
   const size_t sm = (size_t)(nv + 1) * kThreads * sizeof(double2);
-  static bool attr_set = false;
+  static std::atomic<bool> attr_set{false};
   if (!attr_set) {
     const int lim = 200 * 1024;
     cudaFuncSetAttribute(arnoldi_matvec_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
@@ -777,7 +777,7 @@ int k_arnoldi_df(const KrylovState& st, const FineOp& op, const RcBox& box, cons
   const int bl = grid_blocks(n);
   const int nv = j + 1;
   const size_t sm = (size_t)(nv + 1) * kThreads * sizeof(double2);
-  static bool attr_set = false;
+  static std::atomic<bool> attr_set{false};
   if (!attr_set) {
     const int lim = 200 * 1024;
     cudaFuncSetAttribute(arnoldi_matvec_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
