@@ -62,6 +62,8 @@ def _nd_entries(n, r, leaf_max):
     ((41, 23), 2, False, 7),        # ragged, unsymmetric storage, tiny grid
     ((17, 19, 13), 2, False, 304),  # 3D lev-dep (unsymmetric)
     ((17, 17, 17), 1, True, 64),
+    ((49, 49, 19), 2, False, 608),  # 192 x 192 x 72 cells, lev-dep
+    ((75, 75, 75), 2, False, 608),  # 296^3 cells (256^3 + 20-cell layer): fronts of up to 11,400 boundary nodes
 ])
 def test_plan_valid(n, r, sym, grid):
     st = coarse_plan(n, r, symmetric=sym, grid=grid)
