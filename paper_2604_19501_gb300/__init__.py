@@ -383,7 +383,9 @@ def helmholtz_solve(kappa2, q, n, omega, tol=1e-6, maxit=500, recompute=False, r
     while the same kappa2 tensor object, unmodified (its autograd version counter
     unchanged), comes with the same options: several sources or data sets for one medium
     then pay for one set-up.  Changes made through ``.data`` bypass the version counter; call
-    release_reused_context() after such a change."""
+    release_reused_context() after such a change.  The kept context is one context: calls
+    that reuse it, and their backward passes, must not run at the same time from several
+    host threads."""
     global _HELMHOLTZ_SOLVE
     if _HELMHOLTZ_SOLVE is None:
         _HELMHOLTZ_SOLVE = _autograd_function()
