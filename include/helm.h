@@ -124,9 +124,9 @@ typedef struct {
                              pivoting inside each front only; separator blocks of the
                              indefinite real-shifted operator that are close to singular
                              amplify rounding, so its backward error grows with the grid (on
-                             529^2 coarsest nodes about 3e-9 with FP64 factors and 1e-7 with
-                             double-float factors) although the operator itself is well
-                             conditioned.  One step brings the residual to the level of the
+                             529^2 coarsest nodes 2e-8 to 5e-8 with FP64 factors and 4e-7 to
+                             7e-7 with double-float factors, measured) although the operator
+                             itself is well conditioned.  One step brings the residual to the level of the
                              arithmetic.  Each step costs a second solve.  Default 0. */
   int coarse_block_min;   /* coarsest fronts with at least this many eliminated nodes are
                              eliminated in panels of 64 columns (pivot rows by partial
