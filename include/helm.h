@@ -121,9 +121,11 @@ typedef struct {
                              (helm_coarse_solve and the cycle): e <- e + A3^-1 (b - A3 e), the
                              residual formed in FP64 with the assembled level-3 stencil.  The
                              direct solve eliminates the nested-dissection fronts with row
-                             pivoting inside each front only; separator blocks of the
+                             pivoting inside each front only and stores the eliminated
+                             blocks' explicit inverses; separator and leaf blocks of the
                              indefinite real-shifted operator that are close to singular
-                             amplify rounding, so its backward error grows with the grid (on
+                             (condition numbers near 4e5) amplify rounding through those
+                             inverses, so its backward error grows with the grid (on
                              529^2 coarsest nodes 2e-8 to 5e-8 with FP64 factors and 4e-7 to
                              7e-7 with double-float factors, measured) although the operator
                              itself is well conditioned.  One step brings the residual to the level of the

@@ -19,8 +19,9 @@ layer.  These tests build that workload with the benchmark's own generator
   against the oracle's sparse level-3 operator H_4h^alpha = R2 R1 H_h^alpha P1 P2
   (Eq. CoarseRealShifted).  The operator is well conditioned (||A|| ||A^-1|| about 1.3e3 at
   273^2, SuperLU's residual 3e-13), but the multifrontal elimination pivots only inside
-  each front, and separator blocks of the undamped indefinite interior that are close to
-  singular amplify rounding: measured relative residuals are 5e-11 / 2e-8 with FP64 factors
+  each front and stores explicit inverses of the eliminated blocks, and separator blocks
+  of the undamped indefinite interior that are close to singular amplify rounding
+  through those inverses: measured relative residuals are 5e-11 / 2e-8 with FP64 factors
   and 2e-9 / 8e-7 with double-float factors (273^2 / 529^2).  The test bounds them at 1e-7
   (FP64) and 4e-6 (double-float), and checks that one step of iterative refinement
   (helm_opts.coarse_refine) brings both to 1e-12, where they agree with each other;
